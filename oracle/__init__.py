@@ -1,0 +1,171 @@
+"""FP64 CPU oracle of the phase-field curvature energy (Song, arXiv 2103.04856).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the plain, single-threaded FP64
+restatement of eq. Feps (Sec. 3.2) and of its exact discrete gradient that the
+CUDA path is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import it; the product package never
+does.  It shares no code with the CUDA library and imports nothing from it.
+
+Every function takes float64 numpy arrays shaped (nz, ny, nx), C-contiguous,
+periodic in all axes, and a problem dictionary with keys
+``h, eps, xi, a (6 values: a20 a11 a02 a10 a01 a00, kappa1 >= kappa2), well``
+(``well`` 0: W(u)=u^2(1-u)^2, wells 0/1; 1: the paper's W(s)=(1-s^2)^2/4).
+
+Parity status per function (what pins it, in tests/test_oracle_pins.py):
+  energy           closed forms (tanh sphere/cylinder/slab), Willmore and
+                   Helfrich reductions, phase-swap and double-well identities
+  energy_and_grad  central finite differences (all voxels of small grids) and
+                   torch FP64 autograd of the forward formula
+  grad_sampled     equals energy_and_grad at the sampled voxels
+  step / run       mass conservation, lambda = mean(g), descent of E
+  curvatures       kappa1 + kappa2 = H^eps, kappa1 kappa2 <= K^eps, tanh sphere
+  b_to_a           the eight printed rows of the paper's two parameter tables
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pf_oracle.c")
+_LIB = os.path.join(_HERE, "libpf_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("h", ctypes.c_double), ("eps", ctypes.c_double), ("xi", ctypes.c_double),
+        ("a", ctypes.c_double * 6), ("well", ctypes.c_int),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (portable flags: it also builds on aarch64)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER(_Problem)
+            D = ctypes.POINTER(ctypes.c_double)
+            for name, args in [
+                ("pfo_energy", [P, D, D]),
+                ("pfo_energy_and_grad", [P, D, D, D]),
+                ("pfo_density", [P, D, D]),
+                ("pfo_grad_sampled", [P, D, ctypes.c_int, ctypes.POINTER(ctypes.c_long), D]),
+                ("pfo_step", [P, D, D, ctypes.c_double, D]),
+                ("pfo_run", [P, D, ctypes.c_int, ctypes.c_double, D]),
+                ("pfo_curvatures", [P, D, D, D]),
+            ]:
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = ctypes.c_int
+            lib.pfo_b_to_a.argtypes = [D, D]
+            lib.pfo_b_to_a.restype = None
+            _lib = lib
+    return _lib
+
+
+def _prob(u: np.ndarray, p: dict) -> _Problem:
+    nz, ny, nx = u.shape
+    a = p["a"]
+    return _Problem(nx, ny, nz, float(p.get("h", 1.0)), float(p["eps"]),
+                    float(p.get("xi", 1e-6)), (ctypes.c_double * 6)(*[float(v) for v in a]),
+                    int(p.get("well", 0)))
+
+
+def _f64(u):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    if u.ndim != 3:
+        raise ValueError("u must be a 3-D array shaped (nz, ny, nx)")
+    return u
+
+
+def _ptr(x):
+    return x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ok(rc, name):
+    if rc != 0:
+        raise ValueError(f"{name}: invalid arguments")
+
+
+def energy(u, p) -> float:
+    u = _f64(u)
+    E = ctypes.c_double()
+    _ok(_load().pfo_energy(ctypes.byref(_prob(u, p)), _ptr(u), ctypes.byref(E)), "energy")
+    return E.value
+
+
+def density(u, p) -> np.ndarray:
+    u = _f64(u)
+    e = np.empty_like(u)
+    _ok(_load().pfo_density(ctypes.byref(_prob(u, p)), _ptr(u), _ptr(e)), "density")
+    return e
+
+
+def energy_and_grad(u, p):
+    u = _f64(u)
+    g = np.empty_like(u)
+    E = ctypes.c_double()
+    _ok(_load().pfo_energy_and_grad(ctypes.byref(_prob(u, p)), _ptr(u), ctypes.byref(E), _ptr(g)),
+        "energy_and_grad")
+    return E.value, g
+
+
+def grad_sampled(u, p, idx) -> np.ndarray:
+    u = _f64(u)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    g = np.empty(idx.shape[0], dtype=np.float64)
+    _ok(_load().pfo_grad_sampled(ctypes.byref(_prob(u, p)), _ptr(u), int(idx.shape[0]),
+                                 idx.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _ptr(g)),
+        "grad_sampled")
+    return g
+
+
+def step(u, p, tau):
+    """Returns (u_next, scalars) with scalars = [E(u), mean(u), lambda, max|g|, mean|g|]."""
+    u = _f64(u)
+    out = np.empty_like(u)
+    sc = np.empty(5, dtype=np.float64)
+    _ok(_load().pfo_step(ctypes.byref(_prob(u, p)), _ptr(u), _ptr(out), float(tau), _ptr(sc)), "step")
+    return out, sc
+
+
+def run(u, p, nsteps, tau):
+    """Returns (u_final, trace[nsteps, 5]) with the rows of ``step``."""
+    u = _f64(u).copy()
+    tr = np.empty((max(int(nsteps), 0), 5), dtype=np.float64)
+    _ok(_load().pfo_run(ctypes.byref(_prob(u, p)), _ptr(u), int(nsteps), float(tau), _ptr(tr)), "run")
+    return u, tr
+
+
+def curvatures(u, p):
+    u = _f64(u)
+    k1 = np.empty_like(u)
+    k2 = np.empty_like(u)
+    _ok(_load().pfo_curvatures(ctypes.byref(_prob(u, p)), _ptr(u), _ptr(k1), _ptr(k2)), "curvatures")
+    return k1, k2
+
+
+def b_to_a(b) -> np.ndarray:
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    if b.shape != (7,):
+        raise ValueError("b must have 7 entries")
+    a = np.empty(6, dtype=np.float64)
+    _load().pfo_b_to_a(_ptr(b), _ptr(a))
+    return a

@@ -1,0 +1,416 @@
+/*
+ * pf_oracle.c -- FP64 single-threaded oracle of the phase-field energy F_eps
+ * (Song, arXiv 2103.04856, eq. Feps) and of its exact discrete gradient.
+ *
+ * TEST INFRASTRUCTURE ONLY: the reference the CUDA path is checked against.
+ * Deliberately plain: every voxel is evaluated by itself, in the order the
+ * paper builds the quantities (Sec. 2.3 eq. Meps -> Sec. 3.1 eqs. Beps..kepsb
+ * -> Sec. 3.2 eq. Feps), and the gradient is formed in two explicit passes
+ * (local reverse mode per voxel, then the transposed finite-difference
+ * stencils).  No tiling, no fusion, no reordering.
+ *
+ * Readings taken where the paper is silent (each one is a test pin or is
+ * listed as a reading in the design notes):
+ *  - finite differences (Sec. 4.1 says only "classical, periodic"): central
+ *    first derivatives, 3-point second derivatives, 4-point mixed derivatives;
+ *    the integral is h^3 times the sum over voxels;
+ *  - n_u (x) n_u is (grad u)(grad u)^T / (|grad u|^2 + xi^2): the xi offset of
+ *    Sec. 4.1 applied to the normal as well;
+ *  - x^+ is replaced by xi*log(1+exp(x/xi)) (Sec. 4.1), evaluated in the
+ *    overflow-free form max(x,0) + xi*log1p(exp(-|x|/xi));
+ *  - the derivative of sqrt(P) is taken as 0 where P underflows to exactly 0
+ *    (its limit there);
+ *  - the a00 term uses the plain |grad u|^2, the a10/a01 terms the regularised
+ *    norm sqrt(|grad u|^2 + xi^2).
+ */
+#include "pf_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------- helpers */
+
+typedef struct { double s, c; } nsum;   /* Neumaier compensated sum */
+
+static void nsum_add(nsum* a, double v)
+{
+    double t = a->s + v;
+    if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
+    else                       a->c += (v - t) + a->s;
+    a->s = t;
+}
+static double nsum_get(const nsum* a) { return a->s + a->c; }
+
+static int wrap(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
+
+static long vid(const pfo_problem* p, int x, int y, int z)
+{
+    x = wrap(x, p->nx); y = wrap(y, p->ny); z = wrap(z, p->nz);
+    return ((long)z * p->ny + y) * p->nx + x;
+}
+
+static int check(const pfo_problem* p)
+{
+    if (!p) return -1;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return -1;
+    if (!(p->h > 0) || !(p->eps > 0) || !(p->xi > 0)) return -1;
+    if (p->well != 0 && p->well != 1) return -1;
+    return 0;
+}
+
+/* Double well and its first two derivatives (Sec. 2.3, "Notations"):
+ * well 1 is the paper's W(s) = (1-s^2)^2/4; well 0 is W(u) = u^2 (1-u)^2,
+ * the same shape moved to the wells 0 and 1. */
+static double Wp(int well, double u)
+{
+    if (well == 1) return u * u * u - u;
+    return 2.0 * u * (1.0 - u) * (1.0 - 2.0 * u);
+}
+static double Wpp(int well, double u)
+{
+    if (well == 1) return 3.0 * u * u - 1.0;
+    return 2.0 * (1.0 - 6.0 * u + 6.0 * u * u);
+}
+
+/* smooth positive part of Sec. 4.1 and its derivative (the logistic) */
+static double softplus_xi(double x, double xi)
+{
+    double m = x > 0.0 ? x : 0.0;
+    return m + xi * log1p(exp(-fabs(x) / xi));
+}
+static double softplus_xi_prime(double x, double xi)
+{
+    if (x >= 0.0) return 1.0 / (1.0 + exp(-x / xi));
+    double t = exp(x / xi);
+    return t / (1.0 + t);
+}
+
+/* Per-voxel state of the forward evaluation. */
+typedef struct {
+    double u;        /* centre value                                   */
+    double G[3];     /* grad u                                          */
+    double Hs[3][3]; /* Hess u (symmetric, all nine entries stored)     */
+    double rho, q;   /* |grad u|^2 + xi^2 and its square root          */
+    double w;        /* W'(u)/eps                                       */
+    double M[3][3];  /* eq. Meps with the regularised normal            */
+    double T, S, D;  /* Tr M, ||M||^2, 2||M||^2 - (Tr M)^2             */
+    double P, r;     /* smooth positive part of D and its square root   */
+    double e;        /* integrand of eq. Feps                           */
+} voxel;
+
+/* coefficients of eq. Feps */
+typedef struct { double c1, c2, c3, c4, c5, c6; } coefs;
+
+static coefs make_coefs(const pfo_problem* p)
+{
+    const double* a = p->a;   /* a20 a11 a02 a10 a01 a00 */
+    coefs c;
+    c.c1 = (a[0] + a[2] - a[1]) / (2.0 * p->eps);
+    c.c2 = a[1] / (2.0 * p->eps);
+    c.c3 = (a[0] - a[2]) / (2.0 * p->eps);
+    c.c4 = (a[3] + a[4]) / 2.0;
+    c.c5 = (a[3] - a[4]) / 2.0;
+    c.c6 = a[5] * p->eps;
+    return c;
+}
+
+/* Finite differences of Sec. 4.1 (reading: second-order central stencils). */
+static void stencils(const pfo_problem* p, const double* u, int x, int y, int z, voxel* v)
+{
+    const double h = p->h;
+    const int e[3][3] = { { 1, 0, 0 }, { 0, 1, 0 }, { 0, 0, 1 } };
+    v->u = u[vid(p, x, y, z)];
+    for (int c = 0; c < 3; ++c) {
+        double up = u[vid(p, x + e[c][0], y + e[c][1], z + e[c][2])];
+        double um = u[vid(p, x - e[c][0], y - e[c][1], z - e[c][2])];
+        v->G[c] = (up - um) / (2.0 * h);
+        v->Hs[c][c] = (up - 2.0 * v->u + um) / (h * h);
+    }
+    for (int c = 0; c < 3; ++c)
+        for (int d = c + 1; d < 3; ++d) {
+            int sx = e[c][0], sy = e[c][1], sz = e[c][2];
+            int tx = e[d][0], ty = e[d][1], tz = e[d][2];
+            double upp = u[vid(p, x + sx + tx, y + sy + ty, z + sz + tz)];
+            double upm = u[vid(p, x + sx - tx, y + sy - ty, z + sz - tz)];
+            double ump = u[vid(p, x - sx + tx, y - sy + ty, z - sz + tz)];
+            double umm = u[vid(p, x - sx - tx, y - sy - ty, z - sz - tz)];
+            double hcd = (upp - upm - ump + umm) / (4.0 * h * h);
+            v->Hs[c][d] = hcd;
+            v->Hs[d][c] = hcd;
+        }
+}
+
+/* Forward evaluation of one voxel: eq. Meps, the invariants of Sec. 3.1 and
+ * the integrand of eq. Feps. */
+static void forward(const pfo_problem* p, const coefs* cf, const double* u,
+                    int x, int y, int z, voxel* v)
+{
+    stencils(p, u, x, y, z, v);
+    double g2 = v->G[0] * v->G[0] + v->G[1] * v->G[1] + v->G[2] * v->G[2];
+    v->rho = g2 + p->xi * p->xi;
+    v->q = sqrt(v->rho);
+    v->w = Wp(p->well, v->u) / p->eps;
+    /* M = -eps Hess u + (W'(u)/eps) n (x) n, with n (x) n = G G^T / rho */
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            v->M[a][b] = -p->eps * v->Hs[a][b] + v->w * v->G[a] * v->G[b] / v->rho;
+    v->T = v->M[0][0] + v->M[1][1] + v->M[2][2];
+    v->S = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) v->S += v->M[a][b] * v->M[a][b];
+    v->D = 2.0 * v->S - v->T * v->T;
+    v->P = softplus_xi(v->D, p->xi);
+    v->r = sqrt(v->P);
+    v->e = cf->c1 * v->S + cf->c2 * v->T * v->T + cf->c3 * v->T * v->r
+         + cf->c4 * v->q * v->T + cf->c5 * v->q * v->r + cf->c6 * g2;
+}
+
+/* Cotangents of one voxel's integrand with respect to its stencil outputs:
+ *   ubar = de/du (through W'), Gbar[c] = de/dG_c, Hbar[c][d] = de/dHs_cd
+ * (Hbar holds the derivative with respect to each of the nine entries; the
+ * stencil transpose below visits each unordered pair once and adds both).
+ * Chain: e(S, T, r(D(S,T)), q(G), |G|^2), M(Hs, w(u), G). */
+static void local_adjoint(const pfo_problem* p, const coefs* cf, const voxel* v,
+                          double* ubar, double Gbar[3], double Hbar[3][3])
+{
+    double rp = 0.0;     /* dr/dD, defined as 0 where r == 0 */
+    if (v->r > 0.0) rp = softplus_xi_prime(v->D, p->xi) / (2.0 * v->r);
+    double k = (cf->c3 * v->T + cf->c5 * v->q) * rp;   /* de/dD */
+    double dS = cf->c1 + 2.0 * k;
+    double dT = 2.0 * cf->c2 * v->T + cf->c3 * v->r + cf->c4 * v->q - 2.0 * v->T * k;
+    double dq = cf->c4 * v->T + cf->c5 * v->r;
+
+    double L[3][3];      /* de/dM_ab */
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) L[a][b] = 2.0 * dS * v->M[a][b] + (a == b ? dT : 0.0);
+
+    double LG[3], GLG = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        LG[a] = 0.0;
+        for (int b = 0; b < 3; ++b) LG[a] += L[a][b] * v->G[b];
+        GLG += v->G[a] * LG[a];
+    }
+    /* M depends on u through w = W'(u)/eps */
+    *ubar = Wpp(p->well, v->u) / p->eps * GLG / v->rho;
+    /* M depends on G through w G G^T / rho; q and |G|^2 depend on G too */
+    for (int a = 0; a < 3; ++a)
+        Gbar[a] = 2.0 * v->w / v->rho * (LG[a] - GLG / v->rho * v->G[a])
+                + dq * v->G[a] / v->q + 2.0 * cf->c6 * v->G[a];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Hbar[a][b] = -p->eps * L[a][b];
+}
+
+/* ------------------------------------------------------------- public API */
+
+int pfo_density(const pfo_problem* p, const double* u, double* e)
+{
+    if (check(p) || !u || !e) return -1;
+    coefs cf = make_coefs(p);
+    voxel v;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                forward(p, &cf, u, x, y, z, &v);
+                e[vid(p, x, y, z)] = v.e;
+            }
+    return 0;
+}
+
+int pfo_energy(const pfo_problem* p, const double* u, double* E)
+{
+    if (check(p) || !u || !E) return -1;
+    coefs cf = make_coefs(p);
+    nsum acc = { 0.0, 0.0 };
+    voxel v;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                forward(p, &cf, u, x, y, z, &v);
+                nsum_add(&acc, v.e);
+            }
+    *E = p->h * p->h * p->h * nsum_get(&acc);
+    return 0;
+}
+
+/* cotangent fields, one record per voxel: ubar, Gbar[3], Hbar (xx yy zz xy xz yz) */
+enum { CT_U = 0, CT_GX, CT_GY, CT_GZ, CT_HXX, CT_HYY, CT_HZZ, CT_HXY, CT_HXZ, CT_HYZ, CT_N };
+
+static void cotangent_record(const pfo_problem* p, const coefs* cf, const voxel* v, double* rec)
+{
+    double ub, Gb[3], Hb[3][3];
+    local_adjoint(p, cf, v, &ub, Gb, Hb);
+    rec[CT_U] = ub;
+    rec[CT_GX] = Gb[0]; rec[CT_GY] = Gb[1]; rec[CT_GZ] = Gb[2];
+    rec[CT_HXX] = Hb[0][0]; rec[CT_HYY] = Hb[1][1]; rec[CT_HZZ] = Hb[2][2];
+    /* a mixed stencil value feeds both M_cd and M_dc */
+    rec[CT_HXY] = Hb[0][1] + Hb[1][0];
+    rec[CT_HXZ] = Hb[0][2] + Hb[2][0];
+    rec[CT_HYZ] = Hb[1][2] + Hb[2][1];
+}
+
+/* Transposed stencils: dE/du_j = h^3 * sum over the voxels i whose stencils
+ * read u_j of (cotangent_i * stencil weight of u_j in voxel i). */
+static double gather(const pfo_problem* p, const double* ct, int x, int y, int z)
+{
+    const double h = p->h;
+    const int e[3][3] = { { 1, 0, 0 }, { 0, 1, 0 }, { 0, 0, 1 } };
+    const int gidx[3] = { CT_GX, CT_GY, CT_GZ };
+    const int hdiag[3] = { CT_HXX, CT_HYY, CT_HZZ };
+    double s = ct[vid(p, x, y, z) * CT_N + CT_U];
+    for (int c = 0; c < 3; ++c) {
+        long ip = vid(p, x + e[c][0], y + e[c][1], z + e[c][2]);
+        long im = vid(p, x - e[c][0], y - e[c][1], z - e[c][2]);
+        long i0 = vid(p, x, y, z);
+        /* G_c(i) = (u(i+e_c) - u(i-e_c)) / 2h */
+        s += (ct[im * CT_N + gidx[c]] - ct[ip * CT_N + gidx[c]]) / (2.0 * h);
+        /* Hs_cc(i) = (u(i+e_c) - 2 u(i) + u(i-e_c)) / h^2 */
+        s += (ct[im * CT_N + hdiag[c]] - 2.0 * ct[i0 * CT_N + hdiag[c]]
+              + ct[ip * CT_N + hdiag[c]]) / (h * h);
+    }
+    const int pairs[3][3] = { { 0, 1, CT_HXY }, { 0, 2, CT_HXZ }, { 1, 2, CT_HYZ } };
+    for (int k = 0; k < 3; ++k) {
+        int c = pairs[k][0], d = pairs[k][1], f = pairs[k][2];
+        int sx = e[c][0] + e[d][0], sy = e[c][1] + e[d][1], sz = e[c][2] + e[d][2];
+        int tx = e[c][0] - e[d][0], ty = e[c][1] - e[d][1], tz = e[c][2] - e[d][2];
+        /* Hs_cd(i) = (u(i+c+d) - u(i+c-d) - u(i-c+d) + u(i-c-d)) / 4h^2 */
+        double vmm = ct[vid(p, x - sx, y - sy, z - sz) * CT_N + f];  /* i = j-c-d */
+        double vmp = ct[vid(p, x - tx, y - ty, z - tz) * CT_N + f];  /* i = j-c+d */
+        double vpm = ct[vid(p, x + tx, y + ty, z + tz) * CT_N + f];  /* i = j+c-d */
+        double vpp = ct[vid(p, x + sx, y + sy, z + sz) * CT_N + f];  /* i = j+c+d */
+        s += (vmm - vmp - vpm + vpp) / (4.0 * h * h);
+    }
+    return h * h * h * s;
+}
+
+int pfo_energy_and_grad(const pfo_problem* p, const double* u, double* E, double* g)
+{
+    if (check(p) || !u || !g) return -1;
+    long N = (long)p->nx * p->ny * p->nz;
+    double* ct = (double*)malloc(sizeof(double) * CT_N * (size_t)N);
+    if (!ct) return -1;
+    coefs cf = make_coefs(p);
+    nsum acc = { 0.0, 0.0 };
+    voxel v;
+    /* pass 1: forward and local reverse mode, voxel by voxel */
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                forward(p, &cf, u, x, y, z, &v);
+                nsum_add(&acc, v.e);
+                cotangent_record(p, &cf, &v, ct + vid(p, x, y, z) * CT_N);
+            }
+    /* pass 2: transposed stencils */
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) g[vid(p, x, y, z)] = gather(p, ct, x, y, z);
+    free(ct);
+    if (E) *E = p->h * p->h * p->h * nsum_get(&acc);
+    return 0;
+}
+
+int pfo_grad_sampled(const pfo_problem* p, const double* u, int n, const long* idx, double* g)
+{
+    if (check(p) || !u || (n > 0 && (!idx || !g))) return -1;
+    long N = (long)p->nx * p->ny * p->nz;
+    coefs cf = make_coefs(p);
+    /* the gradient at j reads cotangents at offsets in {-1,0,1}^3 only;
+     * compute those 27 records into a small local block */
+    double* ct = (double*)malloc(sizeof(double) * CT_N * 27);
+    if (!ct) return -1;
+    voxel v;
+    for (int k = 0; k < n; ++k) {
+        if (idx[k] < 0 || idx[k] >= N) { free(ct); return -1; }
+        int x = (int)(idx[k] % p->nx);
+        int y = (int)((idx[k] / p->nx) % p->ny);
+        int z = (int)(idx[k] / ((long)p->nx * p->ny));
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    forward(p, &cf, u, x + dx, y + dy, z + dz, &v);
+                    int l = ((dz + 1) * 3 + (dy + 1)) * 3 + (dx + 1);
+                    cotangent_record(p, &cf, &v, ct + l * CT_N);
+                }
+        /* gather on the 3x3x3 block around its centre: every offset it
+         * visits lies inside the block, so its wrap never triggers */
+        pfo_problem lp = *p;
+        lp.nx = 3; lp.ny = 3; lp.nz = 3;
+        g[k] = gather(&lp, ct, 1, 1, 1);
+    }
+    free(ct);
+    return 0;
+}
+
+int pfo_step(const pfo_problem* p, const double* u_in, double* u_out, double tau, double* sc)
+{
+    if (check(p) || !u_in || !u_out) return -1;
+    long N = (long)p->nx * p->ny * p->nz;
+    double* g = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!g) return -1;
+    double E = 0.0;
+    if (pfo_energy_and_grad(p, u_in, &E, g)) { free(g); return -1; }
+    nsum sg = { 0, 0 }, sag = { 0, 0 }, su = { 0, 0 };
+    double gmax = 0.0;
+    for (long i = 0; i < N; ++i) {
+        nsum_add(&sg, g[i]);
+        nsum_add(&sag, fabs(g[i]));
+        nsum_add(&su, u_in[i]);
+        if (fabs(g[i]) > gmax) gmax = fabs(g[i]);
+    }
+    /* volume constraint: remove the mean of the gradient (Lagrange multiplier) */
+    double lambda = nsum_get(&sg) / (double)N;
+    for (long i = 0; i < N; ++i) u_out[i] = u_in[i] - tau * (g[i] - lambda);
+    if (sc) {
+        sc[0] = E;
+        sc[1] = nsum_get(&su) / (double)N;
+        sc[2] = lambda;
+        sc[3] = gmax;
+        sc[4] = nsum_get(&sag) / (double)N;
+    }
+    free(g);
+    return 0;
+}
+
+int pfo_run(const pfo_problem* p, double* u, int nsteps, double tau, double* trace)
+{
+    if (check(p) || !u || nsteps < 0) return -1;
+    long N = (long)p->nx * p->ny * p->nz;
+    double* tmp = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!tmp) return -1;
+    for (int s = 0; s < nsteps; ++s) {
+        if (pfo_step(p, u, tmp, tau, trace ? trace + 5 * (long)s : NULL)) { free(tmp); return -1; }
+        memcpy(u, tmp, sizeof(double) * (size_t)N);
+    }
+    free(tmp);
+    return 0;
+}
+
+int pfo_curvatures(const pfo_problem* p, const double* u, double* k1, double* k2)
+{
+    if (check(p) || !u || !k1 || !k2) return -1;
+    coefs cf = make_coefs(p);
+    voxel v;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                forward(p, &cf, u, x, y, z, &v);
+                double root = sqrt(v.D > 0.0 ? v.D : 0.0);
+                double den = 2.0 * p->eps * v.q;
+                k1[vid(p, x, y, z)] = (v.T + root) / den;
+                k2[vid(p, x, y, z)] = (v.T - root) / den;
+            }
+    return 0;
+}
+
+void pfo_b_to_a(const double b[7], double a[6])
+{
+    /* h2 (H - H0)^2 + k1 K + alpha (k1 - k1_0)^2 + beta (k2 - k2_0)^2,
+     * with H = kappa1 + kappa2 and K = kappa1 kappa2, expanded in monomials */
+    double h2 = b[0], H0 = b[1], kK = b[2], al = b[3], k10 = b[4], be = b[5], k20 = b[6];
+    a[0] = h2 + al;                                  /* kappa1^2        */
+    a[1] = 2.0 * h2 + kK;                            /* kappa1 kappa2   */
+    a[2] = h2 + be;                                  /* kappa2^2        */
+    a[3] = -2.0 * h2 * H0 - 2.0 * al * k10;          /* kappa1          */
+    a[4] = -2.0 * h2 * H0 - 2.0 * be * k20;          /* kappa2          */
+    a[5] = h2 * H0 * H0 + al * k10 * k10 + be * k20 * k20;
+}

@@ -1,0 +1,66 @@
+/*
+ * pf_oracle.h -- plain, slow, single-threaded FP64 CPU oracle of the phase-field
+ * curvature energy F_eps of Song, "Generation of tubular and membranous shape
+ * textures with curvature functionals" (arXiv 2103.04856).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the checker the CUDA path is compared
+ * against.  Only the test-suite, the smoke check and the CPU-baseline leg of the
+ * benchmark may load it.  It shares no code, header, table or constant with the
+ * CUDA library in paper_2103_04856_gb300/csrc, and includes nothing from it.
+ *
+ * Field layout: u[(z*ny + y)*nx + x], periodic in all three axes, spacing h.
+ * Coefficients a = (a20, a11, a02, a10, a01, a00) in the paper's order with the
+ * paper's convention kappa1 >= kappa2 (Sec. 2.1, eq. F; Sec. 3.2, eq. Feps).
+ */
+#ifndef PF_ORACLE_H
+#define PF_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int nx, ny, nz;
+    double h;      /* grid spacing (Sec. 4.1, implementation details)            */
+    double eps;    /* phase-transition width (eq. Meps)                          */
+    double xi;     /* regularisation offset of |grad u| and of x^+ (Sec. 4.1)    */
+    double a[6];   /* a20, a11, a02, a10, a01, a00 (eq. F)                       */
+    int well;      /* 0: W(u)=u^2(1-u)^2, wells 0 and 1; 1: W(s)=(1-s^2)^2/4 (Sec. 2.3) */
+} pfo_problem;
+
+/* All functions return 0 on success, -1 on invalid arguments. */
+
+/* E = h^3 * sum_i e_i, eq. Feps evaluated with the finite differences of Sec. 4.1. */
+int pfo_energy(const pfo_problem* p, const double* u, double* E);
+
+/* Same energy plus the exact gradient g_i = dE/du_i of the discrete sum. */
+int pfo_energy_and_grad(const pfo_problem* p, const double* u, double* E, double* g);
+
+/* Per-voxel energy density e_i (so that E = h^3 * sum e_i). */
+int pfo_density(const pfo_problem* p, const double* u, double* e);
+
+/* Gradient at n selected voxels only (flat indices idx[k]); no full-grid pass.
+ * Used to check very large grids one sample at a time. */
+int pfo_grad_sampled(const pfo_problem* p, const double* u, int n, const long* idx, double* g);
+
+/* One mass-projected gradient-descent step: lambda = mean(g),
+ * u_out = u_in - tau*(g - lambda).  sc (may be NULL) receives
+ * {E(u_in), mean(u_in), lambda, max|g|, mean|g|}. */
+int pfo_step(const pfo_problem* p, const double* u_in, double* u_out, double tau, double* sc);
+
+/* nsteps steps in place; trace (may be NULL) receives nsteps rows of the five
+ * scalars of pfo_step. */
+int pfo_run(const pfo_problem* p, double* u, int nsteps, double tau, double* trace);
+
+/* Diffuse principal curvatures kappa1 >= kappa2 (eqs. kepsa, kepsb), with the
+ * exact positive part and the xi-regularised |grad u|. */
+int pfo_curvatures(const pfo_problem* p, const double* u, double* k1, double* k2);
+
+/* Redundant parameters b = (h2, H0, k1, alpha, kappa1_0, beta, kappa2_0) of
+ * eq. redundant expanded to the reduced coefficients a. */
+void pfo_b_to_a(const double b[7], double a[6]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
