@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""Benchmark of the phase-field curvature-energy hot path on GB300.
+
+Workload (one "step"): one exact mass-projected gradient-descent step (energy,
+exact discrete gradient, update u <- u - tau (g - mean g)) of each of the four
+128^3 validation problems -- tanh-profile sphere R = 32 and z-periodic
+cylinder r = 20, eps = 2, h = 1, p = k1^2 + k2^2 and p = k1 k2 -- run FP32 on
+the fused path as ONE batched launch (plus one launch applying the
+projection).  Metric: voxel energy+gradient evaluations per second
+(voxel-steps/s), compared with the FP64 plain (unfused) GPU path on the same
+workload, at the relative energy error FP32 vs FP64 reported beside it.
+
+The L2 (129 MB) is flushed by writing a 256 MB buffer before every timed step;
+step and kernel durations come from CUDA events recorded by the library on
+the launching stream around each step and around its fused sweep kernel.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pfc|reference]
+
+Under torchrun (N > 1) every rank runs the same workload on its own GPU (weak
+scaling, no collective on the data path); rank 0 prints the line with the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel energy+grad evals/sec, FP32 fused vs FP64 plain, at <=1e-4 rel energy; % HBM peak"
+UNIT = "voxel-steps/s"
+N_EDGE = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="pfc", choices=["pfc", "reference"])
+    ap.add_argument("--flush-mb", type=int, default=256)
+    ap.add_argument("--fp64-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ reference arm
+
+def run_reference(args, ws, rank):
+    """The FP64 CPU oracle on the same workload, a bounded sample per step."""
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2103_04856_gb300 import inputs as I
+    insts = I.validation_set_128()
+    fields = [inst.field().astype(np.float32).astype(np.float64) for inst in insts]
+    # size the sample so the whole run stays within ~3 minutes
+    nsteps = args.steps + args.warmup
+    t = time.perf_counter()
+    oracle.step(fields[0][:32, :32, :32].copy(), insts[0].problem(), 1e-3)
+    rate = 32 ** 3 / max(time.perf_counter() - t, 1e-6)     # voxel-steps/s, rough
+    budget = 150.0 / max(nsteps, 1)
+    edge = int(min(N_EDGE, max(16, (budget * rate) ** (1 / 3))))
+    edge -= edge % 8
+    samples = [f[:edge, :edge, :edge].copy() for f in fields]
+    total, vox = 0.0, 0
+    for k in range(nsteps):
+        i = k % len(insts)
+        t0 = time.perf_counter()
+        oracle.step(samples[i], insts[i].problem(), insts[i].tau)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            total += dt
+            vox += edge ** 3
+    value = vox / total if total > 0 else None
+    sample = (f"one FP64 oracle step per timed step on a {edge}^3 crop of the 128^3 validation fields "
+              f"(cycling sphere/cylinder x two p), single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "validation_128 (4 x 128^3 tanh sphere/cylinder)",
+                                            "sample_edge": edge},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------ helpers
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    for f in ("pfc_fused.cu", "pfc_device.cuh", "pfc_internal.h"):
+        with open(os.path.join(ROOT, "paper_2103_04856_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic():
+    """DRAM bytes per launch of the fused sweep from the committed ncu summary,
+    or None if it was taken on another version of the kernel sources."""
+    path = os.path.join(ROOT, "profiles", "fused_sweep_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("kernel_sources_sha") != kernel_sources_sha():
+            return None, "stale"
+        return float(d["traffic_bytes_per_launch"]), d.get("note", "")
+    except Exception:
+        return None, "absent"
+
+
+def cpu_baseline_oracle():
+    import oracle
+    from paper_2103_04856_gb300 import inputs as I
+    inst = I.validation_128("sphere", "k1^2+k2^2")
+    u = inst.field().astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.step(u, inst.problem(), inst.tau)
+        reps += 1
+        if time.perf_counter() - t0 > 10.0 or reps >= 5:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": reps * u.size / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} FP64 oracle step(s) of the 128^3 tanh sphere (2,097,152 voxels each), single thread"}
+
+
+# flops of one voxel-step of the fused sweep, counted from the arithmetic of
+# voxel_eval (forward + local reverse mode), the transposed-stencil gather and
+# the update, FMA = 2; see the design notes for the count.
+FLOPS_PER_VOXEL_STEP = 244
+
+
+# ------------------------------------------------------------ our arm
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2103_04856_gb300 import inputs as I
+    from paper_2103_04856_gb300 import pfc
+
+    insts = I.validation_set_128()
+    probs = [pfc.Problem.from_shape(i.shape, eps=i.eps, a=i.a, prec="fp32") for i in insts]
+    host = [i.field().astype(np.float32) for i in insts]
+    taus = [i.tau for i in insts]
+    A = [torch.tensor(h, device="cuda") for h in host]
+    B = [torch.empty_like(a) for a in A]
+    vox = sum(h.size for h in host)
+    batch = pfc.Batch(probs)
+    batch.timing(True)
+    flush = torch.empty(args.flush_mb * (1 << 20), dtype=torch.uint8, device="cuda")
+
+    # accuracy on the initial state: FP32 fused vs FP64 fused (the FP64 path
+    # equals the oracle to 1e-10 in the tests)
+    rel_err = 0.0
+    for p, h, inst in zip(probs, host, insts):
+        e32 = pfc.Context(p).energy(torch.tensor(h, device="cuda"))
+        p64 = pfc.Problem.from_shape(inst.shape, eps=inst.eps, a=inst.a, prec="fp64")
+        e64 = pfc.Context(p64).energy(torch.tensor(h.astype(np.float64), device="cuda"))
+        rel_err = max(rel_err, abs(e32 - e64) / abs(e64))
+
+    cur, nxt = A, B
+    for _ in range(args.warmup):
+        flush.zero_()
+        batch.step(cur, nxt, taus)
+        cur, nxt = nxt, cur
+    torch.cuda.synchronize()
+
+    gpu_uuid = None
+    try:
+        gpu_uuid = str(torch.cuda.get_device_properties(local).uuid)
+        if not gpu_uuid.startswith("GPU-"):
+            gpu_uuid = "GPU-" + gpu_uuid
+    except Exception:
+        gpu_uuid = None
+    clocks = ClockSampler(gpu_uuid)
+    clocks.start()
+    time.sleep(0.3)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    step_ms, sweep_ms = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        batch.step(cur, nxt, taus)
+        a, b = batch.last_timing()
+        step_ms.append(a)
+        sweep_ms.append(b)
+        cur, nxt = nxt, cur
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - t0
+    clocks.stop()
+
+    ms_step = float(np.mean(step_ms))
+    ms_sweep = float(np.mean(sweep_ms))
+    if ws > 1:
+        t = torch.tensor([ms_step, ms_sweep], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step, ms_sweep = float(t[0]), float(t[1])
+    value = ws * vox / (ms_step * 1e-3)
+
+    # mass is kept exactly by every step
+    mass_err = max(abs(c.double().mean().item() - h.astype(np.float64).mean()) for c, h in zip(cur, host))
+
+    # FP64 plain (unfused) GPU path on the same workload
+    fp64 = None
+    if args.fp64_steps > 0:
+        ctxs = [pfc.Context(pfc.Problem.from_shape(i.shape, eps=i.eps, a=i.a, prec="fp64", impl="plain"))
+                for i in insts]
+        ua = [torch.tensor(h.astype(np.float64), device="cuda") for h in host]
+        ub = [torch.empty_like(x) for x in ua]
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for k in range(args.fp64_steps + 2):
+            flush.zero_()
+            ev0.record()
+            for c, x, y, tau in zip(ctxs, ua, ub, taus):
+                c.step(x, y, tau)
+            ev1.record()
+            ev1.synchronize()
+            if k >= 2:
+                tot += ev0.elapsed_time(ev1)
+            ua, ub = ub, ua
+        ms64 = tot / args.fp64_steps
+        fp64 = {"value": vox / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64, "dtype": "f64",
+                "impl": "plain: 5 unfused passes storing grad u, Hess u and cotangents in HBM"}
+        del ctxs, ua, ub
+
+    # end to end through the public API with host buffers: pinned host -> device,
+    # one batched step, device -> pinned host, every step
+    pin_in = [torch.from_numpy(h).pin_memory() for h in host]
+    pin_out = [torch.empty_like(p).pin_memory() for p in pin_in]
+    torch.cuda.synchronize()
+    e2e_t = 0.0
+    for k in range(args.e2e_steps + 2):
+        t1 = time.perf_counter()
+        for d, p in zip(A, pin_in):
+            d.copy_(p, non_blocking=True)
+        batch.step(A, B, taus)
+        for p, d in zip(pin_out, B):
+            p.copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+        if k >= 2:
+            e2e_t += time.perf_counter() - t1
+    e2e_bytes = sum(h.nbytes for h in host)
+    e2e = {"value": ws * vox * args.e2e_steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": e2e_bytes,
+           "d2h_bytes_per_step": e2e_bytes}
+
+    peaks, peak_kind = load_peaks()
+    bytes_launch = 8.0 * vox                      # read u, write u' (FP32)
+    achieved = bytes_launch / (ms_sweep * 1e-3) / 1e9
+    traffic, traffic_note = committed_traffic()
+    sm_max = 2070.0
+    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x max clock, TFLOP/s
+    alu_achieved = FLOPS_PER_VOXEL_STEP * vox / (ms_sweep * 1e-3) / 1e12
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "peak_kind": peak_kind, "kernel": "k_fused<float,16,STEP,batch>",
+                "kernel_ms": ms_sweep, "algorithmic_bytes_per_launch": bytes_launch,
+                "alu": {"achieved_tflops": alu_achieved, "peak_tflops": alu_peak,
+                        "frac": alu_achieved / alu_peak, "flops_per_voxel_step": FLOPS_PER_VOXEL_STEP,
+                        "peak_kind": "152 SM x 128 FP32 lanes x 2 x 2070 MHz"}}
+    if traffic is None:
+        roofline["traffic_note"] = traffic_note
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_oracle()
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "validation_128: 4 x 128^3 (tanh sphere R=32, z-cylinder r=20; eps=2, h=1; "
+                                   "p=k1^2+k2^2 and p=k1k2), one batched fused step each",
+                       "voxels_per_step": vox, "l2": f"flushed ({args.flush_mb} MB write) before every timed step",
+                       "parallelism": f"replicas x{ws}"},
+            "wall_ms_per_step_incl_flush": 1e3 * wall / args.steps,
+            "rel_energy_err_fp32_vs_fp64": rel_err, "mass_drift": mass_err,
+            "fp64_plain": fp64,
+            "speedup_vs_fp64_plain": (value / ws) / fp64["value"] if fp64 else None,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 2 * args.steps, "clocks": clocks.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

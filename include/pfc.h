@@ -1,0 +1,149 @@
+/*
+ * pfc.h -- C ABI of the GB300 phase-field curvature-energy library.
+ *
+ * What it computes (Song, "Generation of tubular and membranous shape textures
+ * with curvature functionals", arXiv 2103.04856):
+ *
+ *   F_eps(u) = h^3 * sum over voxels of
+ *       c1 ||M||^2 + c2 (Tr M)^2 + c3 Tr M sqrt(D+) + c4 |grad u| Tr M
+ *     + c5 |grad u| sqrt(D+) + c6 |grad u|^2                          (Sec. 3.2, eq. Feps)
+ *   with M = -eps Hess u + (W'(u)/eps) n (x) n                        (Sec. 2.3, eq. Meps)
+ *        D = 2 ||M||^2 - (Tr M)^2, sqrt(D+) its smoothed square root   (Sec. 3.1, eqs. kepsa/kepsb)
+ *        c1 = (a20+a02-a11)/(2 eps), c2 = a11/(2 eps), c3 = (a20-a02)/(2 eps),
+ *        c4 = (a10+a01)/2, c5 = (a10-a01)/2, c6 = a00 eps.
+ *   Derivatives are periodic central finite differences on a grid of spacing h;
+ *   |grad u| is regularised as sqrt(|grad u|^2 + xi^2) and x+ as
+ *   xi log(1 + exp(x/xi)) (Sec. 4.1, implementation details).  The gradient is
+ *   the exact derivative dE/du_i of that discrete sum.  Descent steps remove the
+ *   mean of the gradient, which keeps the mass (mean of u) fixed (Sec. 4.1,
+ *   mass-preserving flow).
+ *
+ * Conventions for every entry point:
+ *  - Fields are caller-owned device arrays u[(z*ny + y)*nx + x] (torch shape
+ *    (nz, ny, nx), contiguous), of float (PFC_FP32) or double (PFC_FP64) as the
+ *    problem says, on the current CUDA device.  The library never frees them.
+ *    A base address that is not 16-byte aligned, or nx not a multiple of
+ *    16/sizeof(element), selects a slower element-wise load path (not an error).
+ *  - The stream is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    enqueued on it in order; entry points with a host output wait for it.
+ *  - Errors are returned as pfc_status; pfc_last_error() gives a message for
+ *    the calling thread.  On PFC_ECUDA the CUDA error has been consumed.
+ *  - A context is not thread-safe: one thread (or external locking) per context.
+ */
+#ifndef PFC_H
+#define PFC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* pfc_stream;   /* same type as cudaStream_t */
+
+typedef enum {
+    PFC_OK = 0,
+    PFC_EINVAL = -1,        /* bad argument: null pointer, size, parameter, host pointer */
+    PFC_ENOMEM = -2,        /* device or host allocation failed                          */
+    PFC_ECUDA = -3,         /* a CUDA call failed                                        */
+    PFC_ENONFINITE = -4,    /* energy, mass or multiplier became NaN or infinite         */
+    PFC_ETIMEOUT = -5,      /* a bounded device wait gave up                             */
+    PFC_EUNSUPPORTED = -6   /* valid request this build does not implement              */
+} pfc_status;
+
+enum { PFC_WELL_01 = 0,     /* W(u) = u^2 (1-u)^2, wells 0 and 1                         */
+       PFC_WELL_PM1 = 1 };  /* W(s) = (1-s^2)^2 / 4, wells -1 and 1 (Sec. 2.3)           */
+enum { PFC_FP32 = 0, PFC_FP64 = 1 };
+enum { PFC_IMPL_FUSED = 0,  /* one fused forward+adjoint stencil sweep                   */
+       PFC_IMPL_PLAIN = 1 };/* unfused passes that store grad u, Hess u and cotangents   */
+
+typedef struct {
+    int32_t nx, ny, nz;     /* grid size, each >= 1                                      */
+    int32_t well;           /* PFC_WELL_*                                                */
+    int32_t prec;           /* PFC_FP32 or PFC_FP64: element type of every field         */
+    int32_t impl;           /* PFC_IMPL_*                                                */
+    double h;               /* grid spacing > 0                                          */
+    double eps;             /* interface width > 0 (eq. Meps)                            */
+    double xi;              /* regularisation > 0 (Sec. 4.1; 1e-6 in the paper)          */
+    double a[6];            /* a20 a11 a02 a10 a01 a00 of eq. F, kappa1 >= kappa2         */
+    int32_t tile_y;         /* 0 = automatic; else 8 or 16 rows per CTA tile             */
+    int32_t tile_z;         /* 0 = automatic; else planes per CTA z-chunk (>= 1)         */
+} pfc_problem;
+
+typedef struct pfc_ctx pfc_ctx;
+
+/* Validates the problem and allocates the context's device scratch
+ * (ping-pong field, FP64 block partials, scalars; the plain path adds 21
+ * fields).  The current CUDA device at this call is the context's device. */
+pfc_status pfc_create(const pfc_problem* prob, pfc_ctx** out);
+void pfc_destroy(pfc_ctx* ctx);
+
+/* E = F_eps(u) (eq. Feps).  E_host receives it; the stream is synchronised. */
+pfc_status pfc_energy(pfc_ctx* ctx, const void* u, double* E_host, pfc_stream stream);
+
+/* E and g = dE/du (same layout and type as u).  g must not alias u.
+ * E_host may be NULL (then nothing is synchronised). */
+pfc_status pfc_energy_and_grad(pfc_ctx* ctx, const void* u, void* g, double* E_host,
+                               pfc_stream stream);
+
+/* One mass-projected descent step: lambda = mean(g),
+ * u_out = u_in - tau (g - lambda).  u_out must not alias u_in.
+ * scalars_dev (device, may be NULL) receives 5 doubles:
+ *   E(u_in), mean(u_in), lambda, max|g|, mean|g|.
+ * Nothing is synchronised: the call only enqueues work. */
+pfc_status pfc_step(pfc_ctx* ctx, const void* u_in, void* u_out, double tau,
+                    double* scalars_dev, pfc_stream stream);
+
+/* nsteps descent steps in place on u, keeping mean(u) at its entry value.
+ * The step loop is captured once into a CUDA graph and replayed.  trace_host
+ * (may be NULL) receives nsteps rows of the 5 scalars of pfc_step, row n
+ * describing the field the n-th step evaluated.  Synchronises the stream.
+ * Returns PFC_ENONFINITE if any step produced a non-finite scalar. */
+pfc_status pfc_run(pfc_ctx* ctx, void* u, int32_t nsteps, double tau, double* trace_host,
+                   pfc_stream stream);
+
+/* Diffuse principal curvatures kappa1 >= kappa2 at every voxel (Sec. 3.1,
+ * eqs. kepsa/kepsb, exact positive part, regularised |grad u|).  k1 and k2
+ * have the type and layout of u. */
+pfc_status pfc_curvatures(pfc_ctx* ctx, const void* u, void* k1, void* k2, pfc_stream stream);
+
+/* Many independent problems (any sizes, each with its own coefficients and
+ * step size), advanced together: every step is ONE kernel launch over the
+ * tiles of all instances, and the step loop is captured in a CUDA graph.
+ * FP32 and the fused path only. */
+typedef struct pfc_batch pfc_batch;
+pfc_status pfc_batch_create(const pfc_problem* probs, int32_t n_inst, pfc_batch** out);
+void pfc_batch_destroy(pfc_batch* batch);
+/* u[k]: device field of instance k, advanced in place by nsteps steps of
+ * size tau[k] (host array).  trace_host (may be NULL): n_inst x nsteps x 5
+ * doubles, instance-major.  Synchronises.  PFC_ENONFINITE if any instance
+ * produced a non-finite scalar (the others are still advanced). */
+pfc_status pfc_batch_run(pfc_batch* batch, void* const* u, int32_t nsteps, const double* tau,
+                         double* trace_host, pfc_stream stream);
+
+/* One exact mass-projected step of every instance (u_out[k] = u_in[k] -
+ * tau[k] (g_k - mean g_k)): one fused launch over all instances plus one
+ * launch applying the projection.  Only enqueues work (no synchronisation).
+ * u_out[k] must not alias u_in[k].  scalars_dev (device, may be NULL)
+ * receives n_inst rows of the 5 scalars of pfc_step. */
+pfc_status pfc_batch_step(pfc_batch* batch, const void* const* u_in, void* const* u_out, const double* tau,
+                          double* scalars_dev, pfc_stream stream);
+/* Optional device timing of pfc_batch_step: when enabled, the library records
+ * CUDA events on the stream around the whole step and around its fused
+ * sweep kernel; pfc_batch_last_timing waits for them and returns the two
+ * durations of the most recent step in milliseconds. */
+pfc_status pfc_batch_timing(pfc_batch* batch, int enable);
+pfc_status pfc_batch_last_timing(pfc_batch* batch, float* step_ms, float* sweep_ms);
+
+/* eq. redundant: b = (h2, H0, k1, alpha, kappa1_0, beta, kappa2_0) expanded
+ * into a = (a20, a11, a02, a10, a01, a00).  Host only. */
+pfc_status pfc_b_to_a(const double b[7], double a_out[6]);
+
+const char* pfc_status_string(pfc_status s);
+const char* pfc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

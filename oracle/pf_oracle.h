@@ -6,7 +6,7 @@
  * TEST INFRASTRUCTURE ONLY.  This is the checker the CUDA path is compared
  * against.  Only the test-suite, the smoke check and the CPU-baseline leg of the
  * benchmark may load it.  It shares no code, header, table or constant with the
- * CUDA library in paper_2103_04856_gb300/csrc, and includes nothing from it.
+ * CUDA library, and includes nothing from it.
  *
  * Field layout: u[(z*ny + y)*nx + x], periodic in all three axes, spacing h.
  * Coefficients a = (a20, a11, a02, a10, a01, a00) in the paper's order with the

@@ -1,0 +1,783 @@
+// pfc_api.cu -- the C ABI declared in include/pfc.h: argument checks, device
+// scratch, launch geometry, the CUDA-graph step loop and the batch runner.
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/pfc.h"
+#include "pfc_internal.h"
+
+using namespace pfc;
+
+static thread_local char g_err[512] = "";
+
+static pfc_status fail(pfc_status s, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define PFC_CU(call)                                                                                 \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) {                                                                     \
+            (void)cudaGetLastError();                                                                \
+            return fail(PFC_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                                   \
+        }                                                                                            \
+    } while (0)
+
+// ------------------------------------------------------------ context
+
+struct pfc_ctx {
+    pfc_problem P;
+    int device = 0;
+    int esz = 4;
+    long N = 0;
+    int tile_y = 16, zc = 0, tiles_x = 0, tiles_y = 0, chunks_z = 0, nblocks = 0;
+    int plain_nblocks = 0;
+    void* ping = nullptr;            // second field of the step loop
+    double* partials = nullptr;
+    unsigned* ints = nullptr;
+    double* scal = nullptr;
+    double* trace = nullptr;
+    int trace_cap = 0;
+    void* plain_mem = nullptr;       // 21 fields for the plain path
+    // cached step-loop graph
+    cudaGraphExec_t gexec = nullptr;
+    const void* g_u = nullptr;
+    double g_tau = 0.0;
+    int g_len = 0;
+    double* g_trace = nullptr;
+    cudaStream_t cap = nullptr;
+};
+
+static int sm_count(int dev)
+{
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    return n;
+}
+
+static pfc_status check_problem(const pfc_problem* p)
+{
+    if (!p) return fail(PFC_EINVAL, "problem is NULL");
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(PFC_EINVAL, "grid %dx%dx%d: every size must be >= 1", p->nx, p->ny, p->nz);
+    if ((double)p->nx * p->ny * p->nz > 2.0e9) return fail(PFC_EINVAL, "grid too large (more than 2e9 voxels)");
+    if (!(p->h > 0) || !isfinite(p->h)) return fail(PFC_EINVAL, "h must be finite and > 0");
+    if (!(p->eps > 0) || !isfinite(p->eps)) return fail(PFC_EINVAL, "eps must be finite and > 0");
+    if (!(p->xi > 0) || !isfinite(p->xi)) return fail(PFC_EINVAL, "xi must be finite and > 0");
+    for (int i = 0; i < 6; ++i)
+        if (!isfinite(p->a[i])) return fail(PFC_EINVAL, "coefficient a[%d] is not finite", i);
+    if (p->well != PFC_WELL_01 && p->well != PFC_WELL_PM1) return fail(PFC_EINVAL, "unknown double well %d", p->well);
+    if (p->prec != PFC_FP32 && p->prec != PFC_FP64) return fail(PFC_EINVAL, "unknown precision %d", p->prec);
+    if (p->impl != PFC_IMPL_FUSED && p->impl != PFC_IMPL_PLAIN) return fail(PFC_EINVAL, "unknown implementation %d", p->impl);
+    if (p->tile_y != 0 && p->tile_y != 8 && p->tile_y != 16) return fail(PFC_EINVAL, "tile_y must be 0, 8 or 16");
+    if (p->tile_z < 0) return fail(PFC_EINVAL, "tile_z must be >= 0");
+    return PFC_OK;
+}
+
+// Launch geometry of one problem: 32 x tile_y columns per CTA, z chunks chosen
+// so that the grid fills the GPU about twice unless the user fixed tile_z.
+static void geometry(const pfc_problem* p, int sms, int* tile_y, int* zc, int* tx, int* ty, int* cz)
+{
+    int tyv = p->tile_y ? p->tile_y : (p->prec == PFC_FP64 ? 8 : 16);
+    *tile_y = tyv;
+    *tx = (p->nx + 31) / 32;
+    *ty = (p->ny + tyv - 1) / tyv;
+    int z = p->tile_z ? p->tile_z : p->nz;
+    if (!p->tile_z) {
+        const long cols = (long)(*tx) * (*ty);
+        while (z > 16 && cols * ((p->nz + z - 1) / z) < 2L * sms) z = (z + 1) / 2;
+    }
+    if (z > p->nz) z = p->nz;
+    *zc = z;
+    *cz = (p->nz + z - 1) / z;
+}
+
+static pfc_status check_dev_ptr(const pfc_ctx* c, const void* ptr, const char* name)
+{
+    if (!ptr) return fail(PFC_EINVAL, "%s is NULL", name);
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(PFC_EINVAL, "%s: not a CUDA pointer (%s)", name, cudaGetErrorString(e));
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(PFC_EINVAL, "%s is not device memory", name);
+    if (at.device != c->device) return fail(PFC_EINVAL, "%s is on device %d, context on %d", name, at.device, c->device);
+    return PFC_OK;
+}
+
+static void free_ctx_mem(pfc_ctx* c)
+{
+    cudaFree(c->ping);
+    cudaFree(c->partials);
+    cudaFree(c->ints);
+    cudaFree(c->scal);
+    cudaFree(c->trace);
+    cudaFree(c->plain_mem);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->cap) cudaStreamDestroy(c->cap);
+}
+
+extern "C" pfc_status pfc_create(const pfc_problem* prob, pfc_ctx** out)
+{
+    if (!out) return fail(PFC_EINVAL, "out is NULL");
+    *out = nullptr;
+    pfc_status st = check_problem(prob);
+    if (st) return st;
+    pfc_ctx* c = new (std::nothrow) pfc_ctx();
+    if (!c) return fail(PFC_ENOMEM, "host allocation failed");
+    c->P = *prob;
+    c->esz = prob->prec == PFC_FP64 ? 8 : 4;
+    c->N = (long)prob->nx * prob->ny * prob->nz;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        (void)cudaGetLastError();
+        return fail(PFC_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    }
+    geometry(prob, sm_count(c->device), &c->tile_y, &c->zc, &c->tiles_x, &c->tiles_y, &c->chunks_z);
+    c->nblocks = c->tiles_x * c->tiles_y * c->chunks_z;
+    c->plain_nblocks = plain_blocks(c->N);
+    const int nparts = c->nblocks > c->plain_nblocks ? c->nblocks : c->plain_nblocks;
+    bool ok = cudaMalloc(&c->ping, (size_t)c->esz * c->N) == cudaSuccess &&
+              cudaMalloc((void**)&c->partials, sizeof(double) * NPART * (size_t)nparts) == cudaSuccess &&
+              cudaMalloc((void**)&c->ints, sizeof(unsigned) * NINTS) == cudaSuccess &&
+              cudaMalloc((void**)&c->scal, sizeof(double) * NSCAL) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok && prob->impl == PFC_IMPL_PLAIN)
+        ok = cudaMalloc(&c->plain_mem, (size_t)c->esz * c->N * 21) == cudaSuccess;
+    if (ok) ok = cudaMemset(c->ints, 0, sizeof(unsigned) * NINTS) == cudaSuccess &&
+                 cudaMemset(c->scal, 0, sizeof(double) * NSCAL) == cudaSuccess &&
+                 cudaDeviceSynchronize() == cudaSuccess;
+    if (!ok) {
+        cudaError_t le = cudaGetLastError();
+        free_ctx_mem(c);
+        delete c;
+        return fail(PFC_ENOMEM, "device allocation failed: %s", cudaGetErrorString(le));
+    }
+    *out = c;
+    return PFC_OK;
+}
+
+extern "C" void pfc_destroy(pfc_ctx* c)
+{
+    if (!c) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    free_ctx_mem(c);
+    cudaSetDevice(prev);
+    delete c;
+}
+
+template <typename T>
+static Inst<T> make_inst(const pfc_ctx* c, const void* u, void* out, double tau)
+{
+    Inst<T> in{};
+    const pfc_problem& P = c->P;
+    in.u = (const T*)u;
+    in.out = (T*)out;
+    in.nx = P.nx; in.ny = P.ny; in.nz = P.nz;
+    in.zc = c->zc;
+    in.tiles_x = c->tiles_x; in.tiles_y = c->tiles_y; in.chunks_z = c->chunks_z;
+    const int vecw = 16 / (int)sizeof(T);
+    in.vec = (P.nx % vecw == 0) && (((uintptr_t)u) % 16 == 0);
+    in.first_block = 0;
+    in.nblocks = c->nblocks;
+    in.C = make_coef<T>(P.a, P.h, P.eps, P.xi, P.well);
+    in.tau = (T)tau;
+    in.inv_N = 1.0 / (double)c->N;
+    in.partials = c->partials;
+    in.ints = c->ints;
+    in.scal = c->scal;
+    in.trace = c->trace;
+    in.trace_cap = c->trace_cap;
+    return in;
+}
+
+template <typename T>
+static PlainBufs<T> plain_bufs(const pfc_ctx* c)
+{
+    PlainBufs<T> b;
+    T* base = (T*)c->plain_mem;
+    for (int i = 0; i < 9; ++i) b.d[i] = base + (size_t)i * c->N;
+    for (int i = 0; i < 10; ++i) b.ct[i] = base + (size_t)(9 + i) * c->N;
+    b.e = base + (size_t)19 * c->N;
+    b.g = base + (size_t)20 * c->N;
+    return b;
+}
+
+// Enqueue one evaluation (MODE_ENERGY / MODE_GRAD) or one step (MODE_STEP;
+// fused: lazy offset, plain: explicit projection).
+static cudaError_t enqueue(pfc_ctx* c, int mode, const void* u, void* out, double tau, cudaStream_t s)
+{
+    if (c->P.impl == PFC_IMPL_PLAIN) {
+        if (c->P.prec == PFC_FP64)
+            return launch_plain<double>((const double*)u, (double*)out, plain_bufs<double>(c), c->P.nx, c->P.ny,
+                                        c->P.nz, make_coef<double>(c->P.a, c->P.h, c->P.eps, c->P.xi, c->P.well),
+                                        mode, tau, 1.0 / (double)c->N, c->partials, c->plain_nblocks, c->ints,
+                                        c->scal, c->trace, c->trace_cap, s);
+        return launch_plain<float>((const float*)u, (float*)out, plain_bufs<float>(c), c->P.nx, c->P.ny, c->P.nz,
+                                   make_coef<float>(c->P.a, c->P.h, c->P.eps, c->P.xi, c->P.well), mode,
+                                   (float)tau, 1.0 / (double)c->N, c->partials, c->plain_nblocks, c->ints, c->scal,
+                                   c->trace, c->trace_cap, s);
+    }
+    if (c->P.prec == PFC_FP64) return launch_fused<double>(make_inst<double>(c, u, out, tau), mode, c->tile_y, s);
+    return launch_fused<float>(make_inst<float>(c, u, out, tau), mode, c->tile_y, s);
+}
+
+static pfc_status read_scalar(pfc_ctx* c, int slot, double* host, cudaStream_t s)
+{
+    PFC_CU(cudaMemcpyAsync(host, c->scal + slot, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PFC_CU(cudaStreamSynchronize(s));
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_energy(pfc_ctx* c, const void* u, double* E_host, pfc_stream stream)
+{
+    if (!c) return fail(PFC_EINVAL, "context is NULL");
+    if (!E_host) return fail(PFC_EINVAL, "E_host is NULL");
+    pfc_status st = check_dev_ptr(c, u, "u");
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    PFC_CU(enqueue(c, MODE_ENERGY, u, nullptr, 0.0, s));
+    st = read_scalar(c, S_E, E_host, s);
+    if (st) return st;
+    if (!isfinite(*E_host)) return fail(PFC_ENONFINITE, "energy is not finite");
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_energy_and_grad(pfc_ctx* c, const void* u, void* g, double* E_host, pfc_stream stream)
+{
+    if (!c) return fail(PFC_EINVAL, "context is NULL");
+    pfc_status st = check_dev_ptr(c, u, "u");
+    if (st) return st;
+    if ((st = check_dev_ptr(c, g, "g"))) return st;
+    if (u == g) return fail(PFC_EINVAL, "g must not alias u");
+    cudaStream_t s = (cudaStream_t)stream;
+    PFC_CU(enqueue(c, MODE_GRAD, u, g, 0.0, s));
+    if (E_host) {
+        st = read_scalar(c, S_E, E_host, s);
+        if (st) return st;
+        if (!isfinite(*E_host)) return fail(PFC_ENONFINITE, "energy is not finite");
+    }
+    return PFC_OK;
+}
+
+// One step without the graph: u_out = u_in - tau (g - mean g).
+static pfc_status step_now(pfc_ctx* c, const void* u_in, void* u_out, double tau, cudaStream_t s)
+{
+    PFC_CU(cudaMemsetAsync(c->ints + I_COUNTER, 0, sizeof(unsigned), s));
+    PFC_CU(cudaMemsetAsync(c->scal + S_C, 0, sizeof(double), s));
+    PFC_CU(enqueue(c, MODE_STEP, u_in, u_out, tau, s));
+    if (c->P.impl == PFC_IMPL_FUSED) {
+        if (c->P.prec == PFC_FP64)
+            PFC_CU(launch_add_offset<double>((double*)u_out, (const double*)u_out, c->N, c->scal + S_C, s));
+        else
+            PFC_CU(launch_add_offset<float>((float*)u_out, (const float*)u_out, c->N, c->scal + S_C, s));
+    }
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_step(pfc_ctx* c, const void* u_in, void* u_out, double tau, double* scalars_dev,
+                               pfc_stream stream)
+{
+    if (!c) return fail(PFC_EINVAL, "context is NULL");
+    pfc_status st = check_dev_ptr(c, u_in, "u_in");
+    if (st) return st;
+    if ((st = check_dev_ptr(c, u_out, "u_out"))) return st;
+    if (u_in == u_out) return fail(PFC_EINVAL, "u_out must not alias u_in");
+    if (!isfinite(tau)) return fail(PFC_EINVAL, "tau is not finite");
+    if (scalars_dev && (st = check_dev_ptr(c, scalars_dev, "scalars_dev"))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = step_now(c, u_in, u_out, tau, s))) return st;
+    if (scalars_dev)
+        PFC_CU(cudaMemcpyAsync(scalars_dev, c->scal, 5 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return PFC_OK;
+}
+
+static pfc_status ensure_trace(pfc_ctx* c, int n)
+{
+    if (n <= c->trace_cap) return PFC_OK;
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    PFC_CU(cudaDeviceSynchronize());
+    cudaFree(c->trace);
+    c->trace = nullptr;
+    c->trace_cap = 0;
+    PFC_CU(cudaMalloc((void**)&c->trace, sizeof(double) * 5 * (size_t)n));
+    c->trace_cap = n;
+    return PFC_OK;
+}
+
+// Steps i0 .. i0+n-1 of a run: even steps read `a` and write `b`, odd steps the
+// reverse (n even keeps the parity).
+static cudaError_t enqueue_steps(pfc_ctx* c, void* a, void* b, int i0, int n, double tau, cudaStream_t s)
+{
+    for (int i = i0; i < i0 + n; ++i) {
+        const bool even = (i % 2) == 0;
+        cudaError_t e = enqueue(c, MODE_STEP, even ? a : b, even ? b : a, tau, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+extern "C" pfc_status pfc_run(pfc_ctx* c, void* u, int32_t nsteps, double tau, double* trace_host, pfc_stream stream)
+{
+    if (!c) return fail(PFC_EINVAL, "context is NULL");
+    pfc_status st = check_dev_ptr(c, u, "u");
+    if (st) return st;
+    if (nsteps < 0) return fail(PFC_EINVAL, "nsteps must be >= 0");
+    if (!isfinite(tau)) return fail(PFC_EINVAL, "tau is not finite");
+    if (nsteps == 0) return PFC_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ensure_trace(c, nsteps))) return st;
+    PFC_CU(cudaMemsetAsync(c->ints, 0, sizeof(unsigned) * NINTS, s));
+    PFC_CU(cudaMemsetAsync(c->scal, 0, sizeof(double) * NSCAL, s));
+    // a CUDA graph of G steps (G even) replayed; the remainder is launched directly
+    const int G = nsteps >= 64 ? 64 : (nsteps & ~1);
+    if (G >= 2) {
+        if (!(c->gexec && c->g_u == u && c->g_tau == tau && c->g_len == G && c->g_trace == c->trace)) {
+            if (c->gexec) {
+                cudaGraphExecDestroy(c->gexec);
+                c->gexec = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            PFC_CU(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue_steps(c, u, c->ping, 0, G, tau, c->cap);
+            cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                (void)cudaGetLastError();
+                return fail(PFC_ECUDA, "graph capture failed: %s",
+                            cudaGetErrorString(e != cudaSuccess ? e : e2));
+            }
+            e = cudaGraphInstantiate(&c->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                c->gexec = nullptr;
+                (void)cudaGetLastError();
+                return fail(PFC_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+            }
+            c->g_u = u;
+            c->g_tau = tau;
+            c->g_len = G;
+            c->g_trace = c->trace;
+        }
+        for (int k = 0; k + G <= nsteps; k += G) PFC_CU(cudaGraphLaunch(c->gexec, s));
+    }
+    const int done = G >= 2 ? (nsteps / G) * G : 0;
+    PFC_CU(enqueue_steps(c, u, c->ping, done, nsteps - done, tau, s));
+    // the result is in u (even nsteps) or in the ping buffer; apply the offset
+    const bool in_ping = (nsteps % 2) == 1;
+    if (c->P.impl == PFC_IMPL_FUSED) {
+        if (c->P.prec == PFC_FP64)
+            PFC_CU(launch_add_offset<double>((double*)u, (const double*)(in_ping ? c->ping : u), c->N, c->scal + S_C, s));
+        else
+            PFC_CU(launch_add_offset<float>((float*)u, (const float*)(in_ping ? c->ping : u), c->N, c->scal + S_C, s));
+    } else if (in_ping) {
+        PFC_CU(cudaMemcpyAsync(u, c->ping, (size_t)c->esz * c->N, cudaMemcpyDeviceToDevice, s));
+    }
+    unsigned ints[NINTS];
+    PFC_CU(cudaMemcpyAsync(ints, c->ints, sizeof ints, cudaMemcpyDeviceToHost, s));
+    if (trace_host)
+        PFC_CU(cudaMemcpyAsync(trace_host, c->trace, sizeof(double) * 5 * (size_t)nsteps, cudaMemcpyDeviceToHost, s));
+    PFC_CU(cudaStreamSynchronize(s));
+    if (ints[I_COUNTER] != (unsigned)nsteps)
+        return fail(PFC_ECUDA, "step counter %u != %d", ints[I_COUNTER], nsteps);
+    if (ints[I_NONFINITE]) return fail(PFC_ENONFINITE, "a step produced a non-finite energy, mass or multiplier");
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_curvatures(pfc_ctx* c, const void* u, void* k1, void* k2, pfc_stream stream)
+{
+    if (!c) return fail(PFC_EINVAL, "context is NULL");
+    pfc_status st = check_dev_ptr(c, u, "u");
+    if (st) return st;
+    if ((st = check_dev_ptr(c, k1, "k1")) || (st = check_dev_ptr(c, k2, "k2"))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const pfc_problem& P = c->P;
+    if (P.prec == PFC_FP64)
+        PFC_CU(launch_curvatures<double>((const double*)u, (double*)k1, (double*)k2, P.nx, P.ny, P.nz,
+                                         make_coef<double>(P.a, P.h, P.eps, P.xi, P.well), P.eps, s));
+    else
+        PFC_CU(launch_curvatures<float>((const float*)u, (float*)k1, (float*)k2, P.nx, P.ny, P.nz,
+                                        make_coef<float>(P.a, P.h, P.eps, P.xi, P.well), P.eps, s));
+    return PFC_OK;
+}
+
+// ------------------------------------------------------------ batch
+
+struct pfc_batch {
+    int n = 0;
+    int device = 0;
+    int tile_y = 16;
+    int total_blocks = 0;
+    std::vector<pfc_problem> P;
+    std::vector<Inst<float>> host;   // geometry + scratch pointers, u/out filled per run
+    std::vector<void*> ping;
+    double* partials = nullptr;
+    unsigned* ints = nullptr;
+    double* scal = nullptr;
+    double* trace = nullptr;
+    int trace_cap = 0;
+    Inst<float>* dev_even = nullptr;   // step parity 0: u -> ping
+    Inst<float>* dev_odd = nullptr;    // step parity 1: ping -> u
+    cudaGraphExec_t gexec = nullptr;
+    int g_len = 0;
+    double* g_trace = nullptr;
+    cudaStream_t cap = nullptr;
+    // pfc_batch_step: two cached descriptor sets keyed by their pointers
+    Inst<float>* dev_step[2] = { nullptr, nullptr };
+    std::vector<const void*> step_key[2];
+    std::vector<double> step_tau[2];
+    int step_lru = 0;
+    Inst<float>* pinned = nullptr;     // staging for descriptor uploads
+    cudaEvent_t ev[4] = { nullptr, nullptr, nullptr, nullptr };
+    bool timing = false;
+};
+
+static void free_batch_mem(pfc_batch* b)
+{
+    for (void* p : b->ping) cudaFree(p);
+    cudaFree(b->partials);
+    cudaFree(b->ints);
+    cudaFree(b->scal);
+    cudaFree(b->trace);
+    cudaFree(b->dev_even);
+    cudaFree(b->dev_odd);
+    cudaFree(b->dev_step[0]);
+    cudaFree(b->dev_step[1]);
+    if (b->pinned) cudaFreeHost(b->pinned);
+    for (cudaEvent_t e : b->ev)
+        if (e) cudaEventDestroy(e);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->cap) cudaStreamDestroy(b->cap);
+}
+
+extern "C" pfc_status pfc_batch_create(const pfc_problem* probs, int32_t n, pfc_batch** out)
+{
+    if (!out) return fail(PFC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!probs || n < 1) return fail(PFC_EINVAL, "need at least one problem");
+    for (int k = 0; k < n; ++k) {
+        pfc_status st = check_problem(&probs[k]);
+        if (st) return fail(st, "problem %d: %s", k, g_err);
+        if (probs[k].prec != PFC_FP32 || probs[k].impl != PFC_IMPL_FUSED)
+            return fail(PFC_EUNSUPPORTED, "problem %d: batches run FP32 on the fused path only", k);
+    }
+    pfc_batch* b = new (std::nothrow) pfc_batch();
+    if (!b) return fail(PFC_ENOMEM, "host allocation failed");
+    b->n = n;
+    b->P.assign(probs, probs + n);
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+        delete b;
+        (void)cudaGetLastError();
+        return fail(PFC_ECUDA, "cudaGetDevice failed");
+    }
+    const int sms = sm_count(b->device);
+    b->host.resize(n);
+    b->ping.assign(n, nullptr);
+    int first = 0;
+    bool ok = true;
+    b->tile_y = probs[0].tile_y ? probs[0].tile_y : 16;
+    for (int k = 0; k < n && ok; ++k) {
+        pfc_problem p = probs[k];
+        p.tile_y = b->tile_y;
+        if (!p.tile_z) p.tile_z = p.nz < 32 ? p.nz : 32;   // many instances fill the GPU; keep chunks long
+        int ty, zc, tx, tyn, cz;
+        geometry(&p, sms, &ty, &zc, &tx, &tyn, &cz);
+        Inst<float>& in = b->host[k];
+        in = Inst<float>{};
+        in.nx = p.nx; in.ny = p.ny; in.nz = p.nz;
+        in.zc = zc;
+        in.tiles_x = tx; in.tiles_y = tyn; in.chunks_z = cz;
+        in.first_block = first;
+        in.nblocks = tx * tyn * cz;
+        first += in.nblocks;
+        in.C = make_coef<float>(p.a, p.h, p.eps, p.xi, p.well);
+        in.inv_N = 1.0 / ((double)p.nx * p.ny * p.nz);
+        ok = cudaMalloc(&b->ping[k], sizeof(float) * (size_t)p.nx * p.ny * p.nz) == cudaSuccess;
+    }
+    b->total_blocks = first;
+    ok = ok && cudaMalloc((void**)&b->partials, sizeof(double) * NPART * (size_t)first) == cudaSuccess &&
+         cudaMalloc((void**)&b->ints, sizeof(unsigned) * NINTS * (size_t)n) == cudaSuccess &&
+         cudaMalloc((void**)&b->scal, sizeof(double) * NSCAL * (size_t)n) == cudaSuccess &&
+         cudaMalloc((void**)&b->dev_even, sizeof(Inst<float>) * (size_t)n) == cudaSuccess &&
+         cudaMalloc((void**)&b->dev_odd, sizeof(Inst<float>) * (size_t)n) == cudaSuccess &&
+         cudaMalloc((void**)&b->dev_step[0], sizeof(Inst<float>) * (size_t)n) == cudaSuccess &&
+         cudaMalloc((void**)&b->dev_step[1], sizeof(Inst<float>) * (size_t)n) == cudaSuccess &&
+         cudaMallocHost((void**)&b->pinned, sizeof(Inst<float>) * (size_t)n) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
+    if (!ok) {
+        cudaError_t le = cudaGetLastError();
+        free_batch_mem(b);
+        delete b;
+        return fail(PFC_ENOMEM, "device allocation failed: %s", cudaGetErrorString(le));
+    }
+    for (int k = 0; k < n; ++k) {
+        Inst<float>& in = b->host[k];
+        in.partials = b->partials + (size_t)in.first_block * NPART;
+        in.ints = b->ints + (size_t)k * NINTS;
+        in.scal = b->scal + (size_t)k * NSCAL;
+    }
+    *out = b;
+    return PFC_OK;
+}
+
+extern "C" void pfc_batch_destroy(pfc_batch* b)
+{
+    if (!b) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    free_batch_mem(b);
+    cudaSetDevice(prev);
+    delete b;
+}
+
+extern "C" pfc_status pfc_batch_run(pfc_batch* b, void* const* u, int32_t nsteps, const double* tau,
+                                    double* trace_host, pfc_stream stream)
+{
+    if (!b) return fail(PFC_EINVAL, "batch is NULL");
+    if (!u || !tau) return fail(PFC_EINVAL, "u and tau arrays are required");
+    if (nsteps < 0) return fail(PFC_EINVAL, "nsteps must be >= 0");
+    for (int k = 0; k < b->n; ++k) {
+        if (!u[k]) return fail(PFC_EINVAL, "u[%d] is NULL", k);
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, u[k]) != cudaSuccess ||
+            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            (void)cudaGetLastError();
+            return fail(PFC_EINVAL, "u[%d] is not device memory", k);
+        }
+        if (!isfinite(tau[k])) return fail(PFC_EINVAL, "tau[%d] is not finite", k);
+    }
+    if (nsteps == 0) return PFC_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nsteps > b->trace_cap) {
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+        PFC_CU(cudaDeviceSynchronize());
+        cudaFree(b->trace);
+        b->trace = nullptr;
+        b->trace_cap = 0;
+        PFC_CU(cudaMalloc((void**)&b->trace, sizeof(double) * 5 * (size_t)nsteps * b->n));
+        b->trace_cap = nsteps;
+    }
+    // per-instance descriptors for the two step parities
+    std::vector<Inst<float>> ev(b->host), od(b->host);
+    for (int k = 0; k < b->n; ++k) {
+        ev[k].u = (const float*)u[k];
+        ev[k].out = (float*)b->ping[k];
+        od[k].u = (const float*)b->ping[k];
+        od[k].out = (float*)u[k];
+        const bool aligned = ((uintptr_t)u[k]) % 16 == 0;
+        ev[k].vec = (b->P[k].nx % 4 == 0) && aligned;
+        od[k].vec = (b->P[k].nx % 4 == 0);
+        ev[k].tau = od[k].tau = (float)tau[k];
+        ev[k].trace = od[k].trace = b->trace + (size_t)k * 5 * b->trace_cap;
+        ev[k].trace_cap = od[k].trace_cap = b->trace_cap;
+    }
+    PFC_CU(cudaMemcpyAsync(b->dev_even, ev.data(), sizeof(Inst<float>) * b->n, cudaMemcpyHostToDevice, s));
+    PFC_CU(cudaMemcpyAsync(b->dev_odd, od.data(), sizeof(Inst<float>) * b->n, cudaMemcpyHostToDevice, s));
+    PFC_CU(cudaMemsetAsync(b->ints, 0, sizeof(unsigned) * NINTS * b->n, s));
+    PFC_CU(cudaMemsetAsync(b->scal, 0, sizeof(double) * NSCAL * b->n, s));
+    auto steps = [&](int i0, int cnt, cudaStream_t st) -> cudaError_t {
+        for (int i = i0; i < i0 + cnt; ++i) {
+            cudaError_t e = launch_fused_batch((i % 2) == 0 ? b->dev_even : b->dev_odd, b->n, b->total_blocks,
+                                               b->tile_y, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    const int G = nsteps >= 64 ? 64 : (nsteps & ~1);
+    if (G >= 2) {
+        // descriptors live at fixed device addresses, so the graph only depends on G
+        if (!(b->gexec && b->g_len == G && b->g_trace == b->trace)) {
+            if (b->gexec) {
+                cudaGraphExecDestroy(b->gexec);
+                b->gexec = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            PFC_CU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = steps(0, G, b->cap);
+            cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                (void)cudaGetLastError();
+                return fail(PFC_ECUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+            }
+            e = cudaGraphInstantiate(&b->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                b->gexec = nullptr;
+                (void)cudaGetLastError();
+                return fail(PFC_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+            }
+            b->g_len = G;
+            b->g_trace = b->trace;
+        }
+        for (int k = 0; k + G <= nsteps; k += G) PFC_CU(cudaGraphLaunch(b->gexec, s));
+    }
+    const int done = G >= 2 ? (nsteps / G) * G : 0;
+    PFC_CU(steps(done, nsteps - done, s));
+    const bool in_ping = (nsteps % 2) == 1;
+    for (int k = 0; k < b->n; ++k) {
+        const long N = (long)b->P[k].nx * b->P[k].ny * b->P[k].nz;
+        PFC_CU(launch_add_offset<float>((float*)u[k], (const float*)(in_ping ? b->ping[k] : u[k]), N,
+                                        b->scal + (size_t)k * NSCAL + S_C, s));
+    }
+    std::vector<unsigned> ints((size_t)NINTS * b->n);
+    PFC_CU(cudaMemcpyAsync(ints.data(), b->ints, sizeof(unsigned) * ints.size(), cudaMemcpyDeviceToHost, s));
+    if (trace_host)
+        for (int k = 0; k < b->n; ++k)
+            PFC_CU(cudaMemcpyAsync(trace_host + (size_t)k * 5 * nsteps, b->trace + (size_t)k * 5 * b->trace_cap,
+                                   sizeof(double) * 5 * (size_t)nsteps, cudaMemcpyDeviceToHost, s));
+    PFC_CU(cudaStreamSynchronize(s));
+    int bad = 0;
+    for (int k = 0; k < b->n; ++k) {
+        if (ints[(size_t)k * NINTS + I_COUNTER] != (unsigned)nsteps)
+            return fail(PFC_ECUDA, "instance %d: step counter %u != %d", k, ints[(size_t)k * NINTS + I_COUNTER], nsteps);
+        bad += ints[(size_t)k * NINTS + I_NONFINITE] != 0;
+    }
+    if (bad) return fail(PFC_ENONFINITE, "%d instance(s) produced non-finite scalars", bad);
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_batch_step(pfc_batch* b, const void* const* u_in, void* const* u_out, const double* tau,
+                                     double* scalars_dev, pfc_stream stream)
+{
+    if (!b) return fail(PFC_EINVAL, "batch is NULL");
+    if (!u_in || !u_out || !tau) return fail(PFC_EINVAL, "u_in, u_out and tau arrays are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    // descriptors for this pointer set: reuse one of the two cached sets
+    int slot = -1;
+    for (int j = 0; j < 2 && slot < 0; ++j) {
+        if ((int)b->step_key[j].size() != 2 * b->n) continue;
+        bool same = true;
+        for (int k = 0; k < b->n && same; ++k)
+            same = b->step_key[j][2 * k] == u_in[k] && b->step_key[j][2 * k + 1] == u_out[k] &&
+                   b->step_tau[j][k] == tau[k];
+        if (same) slot = j;
+    }
+    if (slot < 0) {
+        for (int k = 0; k < b->n; ++k) {
+            for (int w = 0; w < 2; ++w) {
+                const void* p = w ? (const void*)u_out[k] : u_in[k];
+                cudaPointerAttributes at;
+                if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess ||
+                    (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+                    (void)cudaGetLastError();
+                    return fail(PFC_EINVAL, "%s[%d] is not device memory", w ? "u_out" : "u_in", k);
+                }
+            }
+            if (u_in[k] == u_out[k]) return fail(PFC_EINVAL, "u_out[%d] aliases u_in[%d]", k, k);
+            if (!isfinite(tau[k])) return fail(PFC_EINVAL, "tau[%d] is not finite", k);
+        }
+        slot = b->step_lru;
+        b->step_lru ^= 1;
+        PFC_CU(cudaStreamSynchronize(s));   // the pinned staging buffer may still be in flight
+        for (int k = 0; k < b->n; ++k) {
+            Inst<float> in = b->host[k];
+            in.u = (const float*)u_in[k];
+            in.out = (float*)u_out[k];
+            in.vec = (b->P[k].nx % 4 == 0) && ((uintptr_t)u_in[k]) % 16 == 0;
+            in.tau = (float)tau[k];
+            in.trace = nullptr;
+            in.trace_cap = 0;
+            b->pinned[k] = in;
+        }
+        PFC_CU(cudaMemcpyAsync(b->dev_step[slot], b->pinned, sizeof(Inst<float>) * b->n, cudaMemcpyHostToDevice, s));
+        b->step_key[slot].resize(2 * b->n);
+        b->step_tau[slot].assign(tau, tau + b->n);
+        for (int k = 0; k < b->n; ++k) {
+            b->step_key[slot][2 * k] = u_in[k];
+            b->step_key[slot][2 * k + 1] = u_out[k];
+        }
+    }
+    if (b->timing) PFC_CU(cudaEventRecord(b->ev[0], s));
+    PFC_CU(cudaMemsetAsync(b->ints, 0, sizeof(unsigned) * NINTS * b->n, s));
+    PFC_CU(cudaMemsetAsync(b->scal, 0, sizeof(double) * NSCAL * b->n, s));
+    if (b->timing) PFC_CU(cudaEventRecord(b->ev[1], s));
+    PFC_CU(launch_fused_batch(b->dev_step[slot], b->n, b->total_blocks, b->tile_y, s));
+    if (b->timing) PFC_CU(cudaEventRecord(b->ev[2], s));
+    PFC_CU(launch_add_offset_batch(b->dev_step[slot], b->n, s));
+    if (scalars_dev)
+        PFC_CU(cudaMemcpy2DAsync(scalars_dev, 5 * sizeof(double), b->scal, NSCAL * sizeof(double), 5 * sizeof(double),
+                                 b->n, cudaMemcpyDeviceToDevice, s));
+    if (b->timing) PFC_CU(cudaEventRecord(b->ev[3], s));
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_batch_timing(pfc_batch* b, int enable)
+{
+    if (!b) return fail(PFC_EINVAL, "batch is NULL");
+    if (enable && !b->ev[0])
+        for (cudaEvent_t& e : b->ev) PFC_CU(cudaEventCreate(&e));
+    b->timing = enable != 0;
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_batch_last_timing(pfc_batch* b, float* step_ms, float* sweep_ms)
+{
+    if (!b) return fail(PFC_EINVAL, "batch is NULL");
+    if (!b->timing || !b->ev[0]) return fail(PFC_EINVAL, "timing is not enabled");
+    PFC_CU(cudaEventSynchronize(b->ev[3]));
+    float a = 0.f, c = 0.f;
+    PFC_CU(cudaEventElapsedTime(&a, b->ev[0], b->ev[3]));
+    PFC_CU(cudaEventElapsedTime(&c, b->ev[1], b->ev[2]));
+    if (step_ms) *step_ms = a;
+    if (sweep_ms) *sweep_ms = c;
+    return PFC_OK;
+}
+
+// ------------------------------------------------------------ host helpers
+
+extern "C" pfc_status pfc_b_to_a(const double b[7], double a[6])
+{
+    if (!b || !a) return fail(PFC_EINVAL, "b and a_out are required");
+    // h2 (H - H0)^2 + k1 K + alpha (kappa1 - kappa1_0)^2 + beta (kappa2 - kappa2_0)^2
+    const double h2 = b[0], H0 = b[1], kK = b[2], al = b[3], k10 = b[4], be = b[5], k20 = b[6];
+    a[0] = h2 + al;
+    a[1] = 2.0 * h2 + kK;
+    a[2] = h2 + be;
+    a[3] = -2.0 * (h2 * H0 + al * k10);
+    a[4] = -2.0 * (h2 * H0 + be * k20);
+    a[5] = h2 * H0 * H0 + al * k10 * k10 + be * k20 * k20;
+    return PFC_OK;
+}
+
+extern "C" const char* pfc_status_string(pfc_status s)
+{
+    switch (s) {
+    case PFC_OK: return "ok";
+    case PFC_EINVAL: return "invalid argument";
+    case PFC_ENOMEM: return "out of memory";
+    case PFC_ECUDA: return "CUDA error";
+    case PFC_ENONFINITE: return "non-finite result";
+    case PFC_ETIMEOUT: return "device wait timed out";
+    case PFC_EUNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+    }
+}
+
+extern "C" const char* pfc_last_error(void) { return g_err; }

@@ -1,0 +1,253 @@
+// pfc_device.cuh -- per-voxel arithmetic of the phase-field energy (Song,
+// arXiv 2103.04856, Sec. 3.2 eq. Feps) and its local reverse mode, plus the
+// block / grid reductions shared by the fused and the plain kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "pfc_internal.h"
+
+namespace pfc {
+
+// ------------------------------------------------------------ type helpers
+
+__device__ __forceinline__ float  rcp_(float x)  { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ float  rsqrt_(float x)  { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+__device__ __forceinline__ float  sqrt_(float x)  { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ float  fma_(float a, float b, float c)    { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+
+// Smooth positive part P(D) = xi log(1 + exp(D/xi)) of Sec. 4.1 and its
+// derivative P'(D) = logistic(D/xi).
+// float: outside |D| < 64 xi the correction term is below xi*1.6e-28 and is
+// dropped (P = D^+ exactly; the neglected sqrt(P) on the negative side is
+// below sqrt(xi)*1.3e-14); inside, the overflow-free form is used.
+__device__ __forceinline__ void softplus_(float D, const Coef<float>& C, float& P, float& Pp)
+{
+    float ad = fabsf(D);
+    if (ad > 64.0f * C.xi) {
+        P = D > 0.0f ? D : 0.0f;
+        Pp = D > 0.0f ? 1.0f : 0.0f;
+    } else {
+        float ex = __expf(-ad * C.inv_xi);
+        float inv = __fdividef(1.0f, 1.0f + ex);
+        P = fmaxf(D, 0.0f) + C.xi * log1pf(ex);
+        Pp = D >= 0.0f ? inv : ex * inv;
+    }
+}
+__device__ __forceinline__ void softplus_(double D, const Coef<double>& C, double& P, double& Pp)
+{
+    double ex = exp(-fabs(D) * C.inv_xi);
+    double inv = 1.0 / (1.0 + ex);
+    P = fmax(D, 0.0) + C.xi * log1p(ex);
+    Pp = D >= 0.0 ? inv : ex * inv;
+}
+
+// Cotangents of one voxel's density with respect to its ten stencil values.
+template <typename T>
+struct Cot {
+    T u;                    // through W'(u)
+    T dx, dy, dz;           // first differences u(+) - u(-)
+    T hxx, hyy, hzz;        // second differences u(+) - 2u + u(-)
+    T hxy, hxz, hyz;        // 4-point mixed differences
+};
+
+// Forward (eq. Meps, Sec. 3.1 invariants, eq. Feps) and, if GRAD, local
+// reverse mode of one voxel.  Inputs are the raw stencil values:
+//   dx = u(x+1) - u(x-1), hxx = u(x+1) - 2u + u(x-1),
+//   hxy = u(x+1,y+1) - u(x+1,y-1) - u(x-1,y+1) + u(x-1,y-1), etc.
+template <typename T, bool GRAD>
+__device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz, T hxx, T hyy,
+                                        T hzz, T hxy, T hxz, T hyz, Cot<T>& ct)
+{
+    const T Gx = dx * C.sg, Gy = dy * C.sg, Gz = dz * C.sg;
+    const T g2 = fma_(Gx, Gx, fma_(Gy, Gy, Gz * Gz));
+    const T rho = g2 + C.xi2;
+    const T irho = rcp_(rho);
+    const T iq = rsqrt_(rho);
+    const T q = rho * iq;
+    // W'(u)/eps and W''(u)/eps for the chosen double well
+    T wp, wpp;
+    if (C.well == 0) {
+        const T t = u0 - u0 * u0;                       // u (1 - u)
+        wp = T(2) * t * (T(1) - T(2) * u0);
+        wpp = T(2) - T(12) * t;                         // 2 (1 - 6u + 6u^2)
+    } else {
+        wp = u0 * u0 * u0 - u0;
+        wpp = T(3) * u0 * u0 - T(1);
+    }
+    const T w = wp * C.inv_eps;
+    const T wr = w * irho;                              // (W'/eps) / rho
+    // M = -eps Hess u + (W'/eps) G G^T / rho
+    const T wx = wr * Gx, wy = wr * Gy, wz = wr * Gz;
+    const T Mxx = fma_(C.kd, hxx, wx * Gx);
+    const T Myy = fma_(C.kd, hyy, wy * Gy);
+    const T Mzz = fma_(C.kd, hzz, wz * Gz);
+    const T Mxy = fma_(C.ko, hxy, wx * Gy);
+    const T Mxz = fma_(C.ko, hxz, wx * Gz);
+    const T Myz = fma_(C.ko, hyz, wy * Gz);
+    const T Tr = Mxx + Myy + Mzz;
+    const T off = fma_(Mxy, Mxy, fma_(Mxz, Mxz, Myz * Myz));
+    const T S = fma_(Mxx, Mxx, fma_(Myy, Myy, fma_(Mzz, Mzz, T(2) * off)));
+    // D = 2S - T^2 with the rounding error of T^2 put back (two-product)
+    const T t2 = Tr * Tr;
+    const T t2e = fma_(Tr, Tr, -t2);
+    const T D = fma_(T(2), S, -t2) - t2e;
+    T P, Pp;
+    softplus_(D, C, P, Pp);
+    const T r = sqrt_(P);
+    const T a3 = fma_(C.c3, Tr, C.c5 * q);              // c3 T + c5 q
+    const T e = fma_(C.c1, S, fma_(C.c2, t2, fma_(a3, r, fma_(C.c4 * q, Tr, C.c6 * g2))));
+    if (!GRAD) return e;
+
+    // local reverse mode: e(S, T, r(D(S,T)), q(G), |G|^2), M(Hess, w(u), G)
+    const T rp = r > T(0) ? T(0.5) * Pp * rcp_(r) : T(0);   // dr/dD, 0 where r = 0
+    const T k = a3 * rp;                                     // de/dD
+    const T dS = fma_(T(2), k, C.c1);
+    const T dT = fma_(T(2) * C.c2, Tr, fma_(C.c3, r, fma_(C.c4, q, -T(2) * Tr * k)));
+    const T dq = fma_(C.c4, Tr, C.c5 * r);
+    const T s2 = T(2) * dS;
+    // Lambda = de/dM = 2 dS M + dT I
+    const T Lxx = fma_(s2, Mxx, dT), Lyy = fma_(s2, Myy, dT), Lzz = fma_(s2, Mzz, dT);
+    const T Lxy = s2 * Mxy, Lxz = s2 * Mxz, Lyz = s2 * Myz;
+    const T LGx = fma_(Lxx, Gx, fma_(Lxy, Gy, Lxz * Gz));
+    const T LGy = fma_(Lxy, Gx, fma_(Lyy, Gy, Lyz * Gz));
+    const T LGz = fma_(Lxz, Gx, fma_(Lyz, Gy, Lzz * Gz));
+    const T GLG = fma_(Gx, LGx, fma_(Gy, LGy, Gz * LGz));
+    ct.u = wpp * C.inv_eps * GLG * irho;
+    const T al = T(2) * wr;
+    const T be = fma_(-al * GLG, irho, fma_(dq, iq, T(2) * C.c6));
+    ct.dx = C.sg * fma_(al, LGx, be * Gx);
+    ct.dy = C.sg * fma_(al, LGy, be * Gy);
+    ct.dz = C.sg * fma_(al, LGz, be * Gz);
+    ct.hxx = C.kd * Lxx;
+    ct.hyy = C.kd * Lyy;
+    ct.hzz = C.kd * Lzz;
+    const T ko2 = T(2) * C.ko;                                // Hess_cd feeds M_cd and M_dc
+    ct.hxy = ko2 * Lxy;
+    ct.hxz = ko2 * Lxz;
+    ct.hyz = ko2 * Lyz;
+    return e;
+}
+
+// ------------------------------------------------------------ accumulators
+
+// Kahan-compensated running sum in the arithmetic type (per thread, <= a
+// few hundred terms), handed to FP64 for everything beyond one thread.
+template <typename T>
+struct KSum {
+    T s = T(0), c = T(0);
+    __device__ __forceinline__ void add(T v)
+    {
+        T y = v - c;
+        T t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide reduction of NPART values (sum, except P_GMAX: max); result in
+// red[0..NPART) of shared scratch `red` (>= 32*NPART doubles) for thread 0.
+// Fixed tree: deterministic for a fixed block size.
+__device__ __forceinline__ void block_reduce_parts(double v[NPART], double* red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NPART; ++i) v[i] = (i == P_GMAX) ? warp_max(v[i]) : warp_sum(v[i]);
+    __syncthreads();  // red may still be read by a previous use
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NPART; ++i) red[wid * NPART + i] = v[i];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int i = 0; i < NPART; ++i) {
+            double x = lane < nw ? red[lane * NPART + i] : 0.0;
+            v[i] = (i == P_GMAX) ? warp_max(x) : warp_sum(x);
+        }
+    }
+}
+
+// Every CTA of a problem writes its partials; the last CTA to arrive (atomic
+// ticket, no waiting) combines all of them in a fixed order and writes the
+// problem's scalars.  `v` holds this thread's contribution.
+template <typename T>
+__device__ void grid_finish(const Inst<T>& in, int local_block, int mode, double v[NPART],
+                            double* red)
+{
+    __shared__ int am_last;
+    block_reduce_parts(v, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NPART; ++i) in.partials[(size_t)local_block * NPART + i] = v[i];
+        __threadfence();
+        unsigned t = atomicAdd(&in.ints[I_TICKET], 1u);
+        am_last = (t == (unsigned)in.nblocks - 1u);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double s[NPART];
+#pragma unroll
+    for (int i = 0; i < NPART; ++i) s[i] = 0.0;
+    for (int b = threadIdx.x; b < in.nblocks; b += blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < NPART; ++i) {
+            double x = __ldcg(&in.partials[(size_t)b * NPART + i]);
+            s[i] = (i == P_GMAX) ? fmax(s[i], x) : s[i] + x;
+        }
+    }
+    block_reduce_parts(s, red);
+    if (threadIdx.x != 0) return;
+    double* sc = in.scal;
+    const double E = s[P_E];
+    bool bad = !isfinite(E);
+    if (mode == MODE_ENERGY) {
+        sc[S_E] = E;
+    } else {
+        const double lam = s[P_G] * in.inv_N;
+        sc[S_E] = E;
+        sc[S_LAMBDA] = lam;
+        sc[S_GMAX] = s[P_GMAX];
+        sc[S_GMEAN] = s[P_AG] * in.inv_N;
+        bad = bad || !isfinite(lam);
+        if (mode == MODE_STEP) {
+            const double mass = s[P_U] * in.inv_N;
+            const unsigned cnt = in.ints[I_COUNTER];
+            if (cnt == 0) sc[S_TARGET] = mass;   // conserve the mass of the first field
+            sc[S_MASS] = mass;
+            sc[S_C] = sc[S_TARGET] - s[P_OUT] * in.inv_N;
+            bad = bad || !isfinite(mass) || !isfinite(sc[S_C]);
+            if (in.trace && (int)cnt < in.trace_cap) {
+                double* row = in.trace + (size_t)cnt * 5;
+                row[0] = E; row[1] = mass; row[2] = lam; row[3] = s[P_GMAX]; row[4] = sc[S_GMEAN];
+            }
+            in.ints[I_COUNTER] = cnt + 1;
+        }
+    }
+    if (bad) in.ints[I_NONFINITE] = 1;
+    __threadfence();
+    in.ints[I_TICKET] = 0;   // ready for the next launch on this problem
+}
+
+}  // namespace pfc

@@ -1,0 +1,397 @@
+// pfc_fused.cu -- the fused forward + adjoint stencil sweep.
+//
+// One CTA owns an output tile of 32 x TY columns (x, y) and marches through a
+// chunk of z planes.  For every plane m it
+//   1. evaluates eq. Feps and the local reverse mode (pfc_device.cuh) on the
+//      tile plus a one-column halo ring, from a ring of u planes in shared
+//      memory that cp.async keeps PD planes ahead;
+//   2. keeps the z-direction adjoint terms of its own column in registers
+//      (first/second z differences and the z parts of the xz / yz mixed
+//      differences), so that only five x/y fields per plane go through shared
+//      memory;
+//   3. one plane later, gathers the transposed stencil (the exact gradient of
+//      the discrete sum) for the tile and writes either g or the descent
+//      update u - tau g.
+// Nothing but u is read from HBM and nothing but the result is written; the
+// cotangents are recomputed per tile instead of stored.  The energy and the
+// gradient sums are reduced per CTA in FP64 and combined by the last CTA of
+// the problem (pfc_device.cuh, grid_finish).
+#include "pfc_device.cuh"
+
+namespace pfc {
+
+constexpr int TX = 32;      // output columns per tile in x
+constexpr int UXP = 40;     // u tile row in shared memory: x0-4 .. x0+35
+constexpr int NBUF = 8;     // ring of u planes
+constexpr int PD = 3;       // planes in flight ahead of the plane being consumed
+
+template <int TY>
+struct Tile {
+    static constexpr int EX = TX + 2;             // extended (halo) columns in x
+    static constexpr int EY = TY + 2;
+    static constexpr int NEXT = EX * EY;
+    static constexpr int NT = ((NEXT + 31) / 32) * 32;
+    static constexpr int UY = TY + 4;             // u rows: y0-2 .. y0+TY+1
+    static constexpr int PLANE = UY * UXP;
+};
+
+__device__ __forceinline__ int wrapi(int i, int n)
+{
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ void cp_async16(void* s, const void* g)
+{
+    unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(float* s, const float* g)
+{
+    unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double* s, const double* g)
+{
+    unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename T, int TY, int MODE, bool BATCH>
+__global__ void __launch_bounds__(Tile<TY>::NT, 1)
+k_fused(Inst<T> single, const Inst<T>* __restrict__ insts, int n_inst)
+{
+    using TL = Tile<TY>;
+    constexpr int EX = TL::EX, NEXT = TL::NEXT, NT = TL::NT, UY = TL::UY, PLANE = TL::PLANE;
+    constexpr int VEC = 16 / (int)sizeof(T);
+    constexpr int NCH = UXP / VEC;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* us = reinterpret_cast<T*>(smem_raw);   // [NBUF][UY][UXP]
+    T* fs = us + NBUF * PLANE;                 // [2][5][NEXT]
+    __shared__ double red[32 * NPART];
+
+    // ---- which problem and which tile
+    int local = blockIdx.x;
+    Inst<T> in;
+    if (BATCH) {
+        int lo = 0, hi = n_inst - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (insts[mid].first_block <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        in = insts[lo];
+        local = blockIdx.x - in.first_block;
+    } else {
+        in = single;
+    }
+    const int nx = in.nx, ny = in.ny, nz = in.nz;
+    int b = local;
+    const int tile_x = b % in.tiles_x; b /= in.tiles_x;
+    const int tile_y = b % in.tiles_y; b /= in.tiles_y;
+    const int x0 = tile_x * TX, y0 = tile_y * TY, z0 = b * in.zc;
+    const int zend = min(z0 + in.zc, nz);        // exclusive
+    const int plast = zend + 1;                   // last u plane needed
+    const size_t plane_g = (size_t)nx * ny;
+
+    const int tid = threadIdx.x;
+    const int ex = tid % EX, ey = tid / EX;       // extended column of this thread
+    const bool active = tid < NEXT;
+    const int gx = x0 + ex - 1, gy = y0 + ey - 1;
+    const bool interior = active && ex >= 1 && ex <= TX && ey >= 1 && ey <= TY && gx < nx && gy < ny;
+    const int uc = (ey + 1) * UXP + ex + 3;       // this column in a u plane
+
+    // ---- loads: every u plane of the tile, periodic in x, y and z
+    int ld_off = -1, ld_dst = 0;
+    if (in.vec && tid < UY * NCH) {
+        const int r = tid / NCH, c = tid - (tid / NCH) * NCH;
+        ld_off = wrapi(y0 - 2 + r, ny) * nx + wrapi(x0 - 4 + c * VEC, nx);
+        ld_dst = r * UXP + c * VEC;
+    }
+    auto issue = [&](int p) {
+        if (p <= plast) {
+            T* dst = us + (p & (NBUF - 1)) * PLANE;
+            const T* src = in.u + (size_t)wrapi(p, nz) * plane_g;
+            if (in.vec) {
+                if (ld_off >= 0) cp_async16(dst + ld_dst, src + ld_off);
+            } else {
+                for (int i = tid; i < PLANE; i += NT) {
+                    const int r = i / UXP, c = i - (i / UXP) * UXP;
+                    cp_async_elem(dst + i, src + wrapi(y0 - 2 + r, ny) * nx + wrapi(x0 - 4 + c, nx));
+                }
+            }
+        }
+        cp_async_commit();   // one group per plane slot, empty past the chunk
+    };
+
+    const T cin = (MODE == MODE_STEP) ? (T)in.scal[S_C] : T(0);
+
+    // ---- per-column state carried from plane to plane
+    T accC = 0, zdn = 0, hxz2 = 0, hyz2 = 0, hxz1 = 0, hyz1 = 0;
+    T fx1 = 0, fx2 = 0, fy1 = 0, fy2 = 0, fxy = 0, cpend = 0;
+    KSum<T> se, su, sg, sag, sout;
+    T gmax = 0;
+
+    auto gather = [&](int k) {
+        const T* F = fs + (k & 1) * 5 * NEXT;
+        const int c = tid;
+        const T g = cpend + F[c - 1] + F[NEXT + c + 1] + F[2 * NEXT + c - EX] + F[3 * NEXT + c + EX]
+                  + (F[4 * NEXT + c - 1 - EX] - F[4 * NEXT + c - 1 + EX])
+                  - (F[4 * NEXT + c + 1 - EX] - F[4 * NEXT + c + 1 + EX]);
+        const size_t gi = (size_t)k * plane_g + (size_t)gy * nx + gx;
+        const T ag = g < T(0) ? -g : g;
+        sg.add(g);
+        sag.add(ag);
+        gmax = ag > gmax ? ag : gmax;
+        if (MODE == MODE_GRAD) {
+            in.out[gi] = g;
+        } else {
+            const T u0 = us[(k & (NBUF - 1)) * PLANE + uc] + cin;
+            const T v = fma_(-in.tau, g, u0);
+            in.out[gi] = v;
+            su.add(u0);
+            sout.add(v);
+        }
+    };
+
+    for (int p = z0 - 2; p <= z0 + PD - 1; ++p) issue(p);
+
+    for (int m = z0 - 1; m <= zend; ++m) {
+        cp_async_wait<PD - 1>();
+        __syncthreads();
+        if (MODE != MODE_ENERGY && m - 2 >= z0 && interior) gather(m - 2);
+        issue(m + 1 + PD);
+        if (!active) continue;
+        const bool own = (m >= z0 && m < zend);
+        if (MODE == MODE_ENERGY && !(own && interior)) continue;
+        const T* pm = us + ((m - 1) & (NBUF - 1)) * PLANE + uc;
+        const T* p0 = us + (m & (NBUF - 1)) * PLANE + uc;
+        const T* pp = us + ((m + 1) & (NBUF - 1)) * PLANE + uc;
+        const T u0 = p0[0];
+        const T dx = p0[1] - p0[-1];
+        const T dy = p0[UXP] - p0[-UXP];
+        const T dz = pp[0] - pm[0];
+        const T hxx = (p0[1] + p0[-1]) - T(2) * u0;
+        const T hyy = (p0[UXP] + p0[-UXP]) - T(2) * u0;
+        const T hzz = (pp[0] + pm[0]) - T(2) * u0;
+        const T hxy = (p0[UXP + 1] - p0[UXP - 1]) - (p0[-UXP + 1] - p0[-UXP - 1]);
+        const T hxz = (pp[1] - pp[-1]) - (pm[1] - pm[-1]);
+        const T hyz = (pp[UXP] - pp[-UXP]) - (pm[UXP] - pm[-UXP]);
+        Cot<T> ct;
+        if (MODE == MODE_ENERGY) {
+            se.add(voxel_eval<T, false>(in.C, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ct));
+            continue;
+        }
+        const T e = voxel_eval<T, true>(in.C, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ct);
+        if (own && interior) se.add(e);
+        // transposed-stencil pieces of this voxel (see the gather):
+        //   x/y first+second differences read from the left/right neighbour,
+        //   z pieces from the planes below/above, the centre term stays here
+        const T X1 = ct.dx + ct.hxx, X2 = ct.hxx - ct.dx;
+        const T Y1 = ct.dy + ct.hyy, Y2 = ct.hyy - ct.dy;
+        const T zd = ct.dz + ct.hzz, zu = ct.hzz - ct.dz;
+        const T cpart = ct.u - T(2) * (ct.hxx + ct.hyy + ct.hzz);
+        if (m - 1 >= z0) {   // plane m-1 is complete: publish its x/y fields
+            cpend = accC + zu;
+            const T dxz = hxz2 - ct.hxz, dyz = hyz2 - ct.hyz;
+            T* F = fs + ((m - 1) & 1) * 5 * NEXT;
+            F[tid] = fx1 + dxz;
+            F[NEXT + tid] = fx2 - dxz;
+            F[2 * NEXT + tid] = fy1 + dyz;
+            F[3 * NEXT + tid] = fy2 - dyz;
+            F[4 * NEXT + tid] = fxy;
+        }
+        accC = cpart + zdn;
+        zdn = zd;
+        hxz2 = hxz1; hyz2 = hyz1;
+        hxz1 = ct.hxz; hyz1 = ct.hyz;
+        fx1 = X1; fx2 = X2; fy1 = Y1; fy2 = Y2; fxy = ct.hxy;
+    }
+    if (MODE != MODE_ENERGY) {
+        __syncthreads();
+        if (interior) gather(zend - 1);
+    }
+    cp_async_wait<0>();
+
+    double v[NPART];
+    v[P_E] = se.get();
+    v[P_U] = su.get();
+    v[P_G] = sg.get();
+    v[P_AG] = sag.get();
+    v[P_GMAX] = (double)gmax;
+    v[P_OUT] = sout.get();
+    grid_finish(in, local, MODE, v, red);
+}
+
+// ------------------------------------------------------------ small kernels
+
+template <typename T>
+__global__ void k_add_offset(T* __restrict__ out, const T* __restrict__ in, long n, const double* c)
+{
+    const T off = (T)(*c);
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        out[i] = in[i] + off;
+}
+
+// Batched form: blockIdx.y selects the problem; out[i] += its offset.
+__global__ void k_add_offset_batch(const Inst<float>* __restrict__ insts)
+{
+    const Inst<float>& in = insts[blockIdx.y];
+    const long n = (long)in.nx * in.ny * in.nz;
+    const float off = (float)in.scal[S_C];
+    float* out = in.out;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        out[i] += off;
+}
+
+// Diffuse principal curvatures (Sec. 3.1, eqs. kepsa/kepsb) per voxel.
+template <typename T>
+__global__ void k_curvatures(const T* __restrict__ u, T* __restrict__ k1, T* __restrict__ k2, int nx,
+                             int ny, int nz, Coef<T> C, T eps)
+{
+    const long n = (long)nx * ny * nz;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long)nx * ny));
+        auto at = [&](int dx, int dy, int dz) {
+            return u[((long)wrapi(z + dz, nz) * ny + wrapi(y + dy, ny)) * nx + wrapi(x + dx, nx)];
+        };
+        const T u0 = at(0, 0, 0);
+        const T dx = at(1, 0, 0) - at(-1, 0, 0), dy = at(0, 1, 0) - at(0, -1, 0), dz = at(0, 0, 1) - at(0, 0, -1);
+        const T hxx = at(1, 0, 0) + at(-1, 0, 0) - T(2) * u0;
+        const T hyy = at(0, 1, 0) + at(0, -1, 0) - T(2) * u0;
+        const T hzz = at(0, 0, 1) + at(0, 0, -1) - T(2) * u0;
+        const T hxy = at(1, 1, 0) - at(1, -1, 0) - at(-1, 1, 0) + at(-1, -1, 0);
+        const T hxz = at(1, 0, 1) - at(1, 0, -1) - at(-1, 0, 1) + at(-1, 0, -1);
+        const T hyz = at(0, 1, 1) - at(0, 1, -1) - at(0, -1, 1) + at(0, -1, -1);
+        const T Gx = dx * C.sg, Gy = dy * C.sg, Gz = dz * C.sg;
+        const T rho = Gx * Gx + Gy * Gy + Gz * Gz + C.xi2;
+        const T wp = C.well == 0 ? T(2) * u0 * (T(1) - u0) * (T(1) - T(2) * u0) : u0 * u0 * u0 - u0;
+        const T wr = wp * C.inv_eps / rho;
+        const T Mxx = C.kd * hxx + wr * Gx * Gx, Myy = C.kd * hyy + wr * Gy * Gy, Mzz = C.kd * hzz + wr * Gz * Gz;
+        const T Mxy = C.ko * hxy + wr * Gx * Gy, Mxz = C.ko * hxz + wr * Gx * Gz, Myz = C.ko * hyz + wr * Gy * Gz;
+        const T Tr = Mxx + Myy + Mzz;
+        const T S = Mxx * Mxx + Myy * Myy + Mzz * Mzz + T(2) * (Mxy * Mxy + Mxz * Mxz + Myz * Myz);
+        const T D = T(2) * S - Tr * Tr;
+        const T root = sqrt_(D > T(0) ? D : T(0));
+        const T den = T(2) * eps * sqrt_(rho);
+        k1[i] = (Tr + root) / den;
+        k2[i] = (Tr - root) / den;
+    }
+}
+
+// ------------------------------------------------------------ host side
+
+template <typename T>
+Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well)
+{
+    const double h3 = h * h * h;
+    Coef<T> C;
+    C.c1 = (T)((a[0] + a[2] - a[1]) / (2.0 * eps) * h3);
+    C.c2 = (T)(a[1] / (2.0 * eps) * h3);
+    C.c3 = (T)((a[0] - a[2]) / (2.0 * eps) * h3);
+    C.c4 = (T)((a[3] + a[4]) / 2.0 * h3);
+    C.c5 = (T)((a[3] - a[4]) / 2.0 * h3);
+    C.c6 = (T)(a[5] * eps * h3);
+    C.kd = (T)(-eps / (h * h));
+    C.ko = (T)(-eps / (4.0 * h * h));
+    C.sg = (T)(1.0 / (2.0 * h));
+    C.inv_eps = (T)(1.0 / eps);
+    C.xi = (T)xi;
+    C.xi2 = (T)(xi * xi);
+    C.inv_xi = (T)(1.0 / xi);
+    C.well = well;
+    return C;
+}
+template Coef<float> make_coef<float>(const double*, double, double, double, int);
+template Coef<double> make_coef<double>(const double*, double, double, double, int);
+
+int fused_threads(int tile_y) { return tile_y == 8 ? Tile<8>::NT : Tile<16>::NT; }
+
+size_t fused_smem_bytes(int elem_size, int tile_y)
+{
+    const int plane = tile_y == 8 ? Tile<8>::PLANE : Tile<16>::PLANE;
+    const int next = tile_y == 8 ? Tile<8>::NEXT : Tile<16>::NEXT;
+    return (size_t)elem_size * ((size_t)NBUF * plane + 2 * 5 * (size_t)next);
+}
+
+template <typename T, int TY, int MODE, bool BATCH>
+static cudaError_t launch_one(const Inst<T>& in, const Inst<T>* insts, int n_inst, int blocks, cudaStream_t s)
+{
+    const size_t smem = fused_smem_bytes(sizeof(T), TY);
+    static bool attr_done = false;   // per instantiation; idempotent, so a race is harmless
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_fused<T, TY, MODE, BATCH>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    k_fused<T, TY, MODE, BATCH><<<blocks, Tile<TY>::NT, smem, s>>>(in, insts, n_inst);
+    return cudaGetLastError();
+}
+
+template <typename T, int TY>
+static cudaError_t launch_mode(const Inst<T>& in, int mode, cudaStream_t s)
+{
+    switch (mode) {
+    case MODE_ENERGY: return launch_one<T, TY, MODE_ENERGY, false>(in, nullptr, 1, in.nblocks, s);
+    case MODE_GRAD: return launch_one<T, TY, MODE_GRAD, false>(in, nullptr, 1, in.nblocks, s);
+    case MODE_STEP: return launch_one<T, TY, MODE_STEP, false>(in, nullptr, 1, in.nblocks, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t launch_fused(const Inst<T>& in, int mode, int tile_y, cudaStream_t s)
+{
+    return tile_y == 8 ? launch_mode<T, 8>(in, mode, s) : launch_mode<T, 16>(in, mode, s);
+}
+template cudaError_t launch_fused<float>(const Inst<float>&, int, int, cudaStream_t);
+template cudaError_t launch_fused<double>(const Inst<double>&, int, int, cudaStream_t);
+
+cudaError_t launch_fused_batch(const Inst<float>* insts_dev, int n_inst, int total_blocks, int tile_y,
+                               cudaStream_t s)
+{
+    Inst<float> dummy{};
+    return tile_y == 8 ? launch_one<float, 8, MODE_STEP, true>(dummy, insts_dev, n_inst, total_blocks, s)
+                       : launch_one<float, 16, MODE_STEP, true>(dummy, insts_dev, n_inst, total_blocks, s);
+}
+
+template <typename T>
+cudaError_t launch_add_offset(T* out, const T* in, long n, const double* c, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    long blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_add_offset<T><<<(int)blocks, 256, 0, s>>>(out, in, n, c);
+    return cudaGetLastError();
+}
+template cudaError_t launch_add_offset<float>(float*, const float*, long, const double*, cudaStream_t);
+template cudaError_t launch_add_offset<double>(double*, const double*, long, const double*, cudaStream_t);
+
+cudaError_t launch_add_offset_batch(const Inst<float>* insts_dev, int n_inst, cudaStream_t s)
+{
+    if (n_inst <= 0) return cudaSuccess;
+    int bx = (152 * 8 + n_inst - 1) / n_inst;
+    if (bx < 8) bx = 8;
+    k_add_offset_batch<<<dim3(bx, n_inst), 256, 0, s>>>(insts_dev);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_curvatures(const T* u, T* k1, T* k2, int nx, int ny, int nz, const Coef<T>& C, double eps,
+                              cudaStream_t s)
+{
+    const long n = (long)nx * ny * nz;
+    long blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_curvatures<T><<<(int)blocks, 256, 0, s>>>(u, k1, k2, nx, ny, nz, C, (T)eps);
+    return cudaGetLastError();
+}
+template cudaError_t launch_curvatures<float>(const float*, float*, float*, int, int, int, const Coef<float>&,
+                                              double, cudaStream_t);
+template cudaError_t launch_curvatures<double>(const double*, double*, double*, int, int, int,
+                                               const Coef<double>&, double, cudaStream_t);
+
+}  // namespace pfc

@@ -1,0 +1,92 @@
+// pfc_internal.h -- types shared by the kernels and the C ABI of the
+// phase-field curvature-energy library (not part of the public interface).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pfc {
+
+enum Mode { MODE_ENERGY = 0, MODE_GRAD = 1, MODE_STEP = 2 };
+
+// Per-block FP64 partial sums written by every CTA and combined by the last.
+enum Part { P_E = 0, P_U, P_G, P_AG, P_GMAX, P_OUT, NPART };
+
+// Device scalar slots of one problem.
+//  S_E      energy of the evaluated field
+//  S_MASS   mean of the evaluated field
+//  S_LAMBDA mean of the gradient (Lagrange multiplier of the mass constraint)
+//  S_GMAX   max |g|;  S_GMEAN mean |g|
+//  S_C      offset added to the stored field on load (lazy mass projection)
+//  S_TARGET mass to keep, set from the first evaluated field of a run
+enum Scal { S_E = 0, S_MASS, S_LAMBDA, S_GMAX, S_GMEAN, S_C, S_TARGET, NSCAL = 8 };
+enum Ints { I_TICKET = 0, I_COUNTER, I_NONFINITE, NINTS = 4 };
+
+// Coefficients of eq. Feps (times h^3, so that summing the per-voxel density
+// gives E directly) and the stencil scale factors, in the arithmetic type.
+template <typename T>
+struct Coef {
+    T c1, c2, c3, c4, c5, c6;
+    T kd;       // -eps / h^2     : d M_cc / d (u+ - 2u + u-)
+    T ko;       // -eps / (4 h^2) : d M_cd / d (4-point mixed difference)
+    T sg;       // 1 / (2h)       : d G_c / d (u+ - u-)
+    T inv_eps;  // 1 / eps
+    T xi, xi2, inv_xi;
+    int well;   // 0: u^2(1-u)^2, 1: (1-s^2)^2/4
+};
+
+// One problem as seen by a fused launch.
+template <typename T>
+struct Inst {
+    const T* u;          // field read (stored field; the true field is u + scal[S_C] in MODE_STEP)
+    T* out;              // g (MODE_GRAD) or next stored field (MODE_STEP)
+    int nx, ny, nz;
+    int zc;              // planes per z-chunk
+    int tiles_x, tiles_y, chunks_z;
+    int vec;             // 1: 16-byte chunked loads are legal
+    int first_block;     // index of this problem's first CTA in the launch
+    int nblocks;
+    Coef<T> C;
+    T tau;
+    double inv_N;
+    double* partials;    // [nblocks][NPART]
+    unsigned* ints;      // [NINTS]
+    double* scal;        // [NSCAL]
+    double* trace;       // [trace_cap][5] or null
+    int trace_cap;
+};
+
+template <typename T>
+Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well);
+
+// fused kernels (pfc_fused.cu)
+template <typename T>
+cudaError_t launch_fused(const Inst<T>& in, int mode, int tile_y, cudaStream_t s);
+cudaError_t launch_fused_batch(const Inst<float>* insts_dev, int n_inst, int total_blocks,
+                               int tile_y, cudaStream_t s);
+template <typename T>
+cudaError_t launch_add_offset(T* out, const T* in, long n, const double* c, cudaStream_t s);
+// out += scal[S_C] for every problem of a batch, in place, one launch
+cudaError_t launch_add_offset_batch(const Inst<float>* insts_dev, int n_inst, cudaStream_t s);
+template <typename T>
+cudaError_t launch_curvatures(const T* u, T* k1, T* k2, int nx, int ny, int nz, const Coef<T>& C,
+                              double eps, cudaStream_t s);
+size_t fused_smem_bytes(int elem_size, int tile_y);
+int fused_threads(int tile_y);
+
+// plain unfused path (pfc_plain.cu)
+template <typename T>
+struct PlainBufs {
+    T* d[9];     // grad u (3) and Hess u (xx yy zz xy xz yz)
+    T* ct[10];   // cotangents: ubar, dx dy dz, hxx hyy hzz hxy hxz hyz
+    T* e;        // per-voxel energy density
+    T* g;        // gradient
+};
+template <typename T>
+cudaError_t launch_plain(const T* u, T* out, const PlainBufs<T>& b, int nx, int ny, int nz,
+                         const Coef<T>& C, int mode, T tau, double inv_N, double* partials,
+                         int nblocks, unsigned* ints, double* scal, double* trace, int trace_cap,
+                         cudaStream_t s);
+int plain_blocks(long n);
+
+}  // namespace pfc

@@ -1,0 +1,321 @@
+"""Thin Python binding of the C ABI in include/pfc.h (argument marshalling only).
+
+Every computation runs in libpfc.so's CUDA kernels; this module converts torch
+tensors to device pointers, passes torch's current stream, and turns status
+codes into exceptions.  If the library has not been built, the first call
+raises: there is no CPU fallback.
+
+    from paper_2103_04856_gb300 import pfc
+    ctx = pfc.Context(pfc.Problem(nx=128, ny=128, nz=128, eps=2.0, a=(1, 0, 1, 0, 0, 0)))
+    E, g = ctx.energy_and_grad(u)            # u: CUDA float32 tensor (nz, ny, nx)
+    trace = ctx.run(u, nsteps=100, tau=1e-3)  # in place, mass conserved
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpfc.so")
+
+PFC_OK, PFC_EINVAL, PFC_ENOMEM, PFC_ECUDA, PFC_ENONFINITE, PFC_ETIMEOUT, PFC_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+PFC_WELL_01, PFC_WELL_PM1 = 0, 1
+PFC_FP32, PFC_FP64 = 0, 1
+PFC_IMPL_FUSED, PFC_IMPL_PLAIN = 0, 1
+
+# every symbol include/pfc.h declares
+EXPORTED = ("pfc_create", "pfc_destroy", "pfc_energy", "pfc_energy_and_grad", "pfc_step", "pfc_run",
+            "pfc_curvatures", "pfc_batch_create", "pfc_batch_destroy", "pfc_batch_run", "pfc_batch_step",
+            "pfc_batch_timing", "pfc_batch_last_timing", "pfc_b_to_a", "pfc_status_string", "pfc_last_error")
+
+
+class PfcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"pfc status {status}: {msg}")
+        self.status = status
+
+
+class NonFiniteError(PfcError):
+    pass
+
+
+class _CProblem(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("well", ctypes.c_int32), ("prec", ctypes.c_int32), ("impl", ctypes.c_int32),
+        ("h", ctypes.c_double), ("eps", ctypes.c_double), ("xi", ctypes.c_double),
+        ("a", ctypes.c_double * 6),
+        ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32),
+    ]
+
+
+@dataclass
+class Problem:
+    """Grid and parameters of eq. Feps; ``a`` in the paper's order (a20 a11 a02 a10 a01 a00),
+    kappa1 >= kappa2.  ``prec`` is "fp32" or "fp64", ``impl`` "fused" or "plain"."""
+    nx: int
+    ny: int
+    nz: int
+    eps: float
+    a: tuple
+    h: float = 1.0
+    xi: float = 1e-6
+    well: int = PFC_WELL_01
+    prec: str = "fp32"
+    impl: str = "fused"
+    tile_y: int = 0
+    tile_z: int = 0
+
+    @classmethod
+    def from_shape(cls, shape, **kw):
+        nz, ny, nx = shape
+        return cls(nx=nx, ny=ny, nz=nz, **kw)
+
+    @property
+    def dtype(self):
+        return torch.float64 if self.prec == "fp64" else torch.float32
+
+    def _c(self) -> _CProblem:
+        if self.prec not in ("fp32", "fp64"):
+            raise ValueError("prec must be 'fp32' or 'fp64'")
+        if self.impl not in ("fused", "plain"):
+            raise ValueError("impl must be 'fused' or 'plain'")
+        if len(self.a) != 6:
+            raise ValueError("a needs 6 coefficients")
+        return _CProblem(int(self.nx), int(self.ny), int(self.nz), int(self.well),
+                         PFC_FP64 if self.prec == "fp64" else PFC_FP32,
+                         PFC_IMPL_PLAIN if self.impl == "plain" else PFC_IMPL_FUSED,
+                         float(self.h), float(self.eps), float(self.xi),
+                         (ctypes.c_double * 6)(*[float(x) for x in self.a]),
+                         int(self.tile_y), int(self.tile_z))
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library():
+    """Load libpfc.so; raises if it is missing (build it with python -m paper_2103_04856_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                               "(python -m paper_2103_04856_gb300.build)")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+        P = ctypes.POINTER(_CProblem)
+        sig = {
+            "pfc_create": ([P, ctypes.POINTER(vp)], ctypes.c_int),
+            "pfc_destroy": ([vp], None),
+            "pfc_energy": ([vp, vp, dp, vp], ctypes.c_int),
+            "pfc_energy_and_grad": ([vp, vp, vp, dp, vp], ctypes.c_int),
+            "pfc_step": ([vp, vp, vp, ctypes.c_double, vp, vp], ctypes.c_int),
+            "pfc_run": ([vp, vp, ctypes.c_int32, ctypes.c_double, dp, vp], ctypes.c_int),
+            "pfc_curvatures": ([vp, vp, vp, vp, vp], ctypes.c_int),
+            "pfc_batch_create": ([P, ctypes.c_int32, ctypes.POINTER(vp)], ctypes.c_int),
+            "pfc_batch_destroy": ([vp], None),
+            "pfc_batch_run": ([vp, ctypes.POINTER(vp), ctypes.c_int32, dp, dp, vp], ctypes.c_int),
+            "pfc_batch_step": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dp, vp, vp], ctypes.c_int),
+            "pfc_batch_timing": ([vp, ctypes.c_int], ctypes.c_int),
+            "pfc_batch_last_timing": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
+                                      ctypes.c_int),
+            "pfc_b_to_a": ([dp, dp], ctypes.c_int),
+            "pfc_status_string": ([ctypes.c_int], ctypes.c_char_p),
+            "pfc_last_error": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != PFC_OK:
+        lib = load_library()
+        msg = lib.pfc_last_error().decode(errors="replace")
+        raise (NonFiniteError if rc == PFC_ENONFINITE else PfcError)(rc, msg)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _field(t: torch.Tensor, prob: Problem, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != prob.dtype:
+        raise TypeError(f"{name} must be {prob.dtype}, got {t.dtype}")
+    if tuple(t.shape) != (prob.nz, prob.ny, prob.nx) or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous with shape {(prob.nz, prob.ny, prob.nx)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------ C-named calls
+
+def pfc_create(prob: Problem):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(lib.pfc_create(ctypes.byref(prob._c()), ctypes.byref(h)))
+    return h
+
+
+def pfc_destroy(handle):
+    if handle:
+        load_library().pfc_destroy(handle)
+
+
+def pfc_b_to_a(b) -> np.ndarray:
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    if b.shape != (7,):
+        raise ValueError("b needs 7 entries")
+    a = np.empty(6, dtype=np.float64)
+    _check(load_library().pfc_b_to_a(b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return a
+
+
+class Context:
+    """A problem bound to the current CUDA device (owns the library's scratch)."""
+
+    def __init__(self, prob: Problem):
+        self.prob = prob
+        self._h = pfc_create(prob)
+        self._lib = load_library()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            pfc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def new_field(self):
+        return torch.empty((self.prob.nz, self.prob.ny, self.prob.nx), dtype=self.prob.dtype, device="cuda")
+
+    def energy(self, u: torch.Tensor, stream=None) -> float:
+        E = ctypes.c_double()
+        _check(self._lib.pfc_energy(self._h, _field(u, self.prob, "u"), ctypes.byref(E), _stream(stream)))
+        return E.value
+
+    def energy_and_grad(self, u: torch.Tensor, g: torch.Tensor | None = None, stream=None, sync=True):
+        g = self.new_field() if g is None else g
+        E = ctypes.c_double()
+        _check(self._lib.pfc_energy_and_grad(self._h, _field(u, self.prob, "u"), _field(g, self.prob, "g"),
+                                             ctypes.byref(E) if sync else None, _stream(stream)))
+        return (E.value if sync else None), g
+
+    def step(self, u_in: torch.Tensor, u_out: torch.Tensor, tau: float, scalars: torch.Tensor | None = None,
+             stream=None):
+        sp = None
+        if scalars is not None:
+            if scalars.dtype != torch.float64 or not scalars.is_cuda or scalars.numel() < 5:
+                raise TypeError("scalars must be a CUDA float64 tensor with >= 5 entries")
+            sp = ctypes.c_void_p(scalars.data_ptr())
+        _check(self._lib.pfc_step(self._h, _field(u_in, self.prob, "u_in"), _field(u_out, self.prob, "u_out"),
+                                  float(tau), sp, _stream(stream)))
+        return u_out
+
+    def run(self, u: torch.Tensor, nsteps: int, tau: float, trace: bool = True, stream=None):
+        tr = np.empty((max(int(nsteps), 0), 5), dtype=np.float64) if trace else None
+        _check(self._lib.pfc_run(self._h, _field(u, self.prob, "u"), int(nsteps), float(tau),
+                                 tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if trace else None,
+                                 _stream(stream)))
+        return tr
+
+    def curvatures(self, u: torch.Tensor, stream=None):
+        k1, k2 = self.new_field(), self.new_field()
+        _check(self._lib.pfc_curvatures(self._h, _field(u, self.prob, "u"), _field(k1, self.prob, "k1"),
+                                        _field(k2, self.prob, "k2"), _stream(stream)))
+        return k1, k2
+
+
+class Batch:
+    """Independent FP32 problems advanced together, one launch per step (pfc_batch_*)."""
+
+    def __init__(self, probs):
+        self.probs = list(probs)
+        arr = (_CProblem * len(self.probs))(*[p._c() for p in self.probs])
+        self._lib = load_library()
+        self._h = ctypes.c_void_p()
+        _check(self._lib.pfc_batch_create(arr, len(self.probs), ctypes.byref(self._h)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pfc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, fields, nsteps: int, taus, trace: bool = True, stream=None):
+        if len(fields) != len(self.probs):
+            raise ValueError("one field per problem")
+        ptrs = (ctypes.c_void_p * len(fields))(*[_field(f, p, f"u[{k}]").value
+                                                 for k, (f, p) in enumerate(zip(fields, self.probs))])
+        taus = np.ascontiguousarray(np.broadcast_to(np.asarray(taus, dtype=np.float64), (len(fields),)))
+        tr = np.empty((len(fields), max(int(nsteps), 0), 5), dtype=np.float64) if trace else None
+        rc = self._lib.pfc_batch_run(self._h, ptrs, int(nsteps), taus.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if trace else None,
+                                     _stream(stream))
+        _check(rc)
+        return tr
+
+    def step(self, fields_in, fields_out, taus, scalars: torch.Tensor | None = None, stream=None):
+        """One exact mass-projected step of every problem (enqueue only)."""
+        n = len(self.probs)
+        if len(fields_in) != n or len(fields_out) != n:
+            raise ValueError("one input and one output field per problem")
+        pin = (ctypes.c_void_p * n)(*[_field(f, p, f"u_in[{k}]").value for k, (f, p) in enumerate(zip(fields_in, self.probs))])
+        pout = (ctypes.c_void_p * n)(*[_field(f, p, f"u_out[{k}]").value for k, (f, p) in enumerate(zip(fields_out, self.probs))])
+        taus = np.ascontiguousarray(np.broadcast_to(np.asarray(taus, dtype=np.float64), (n,)))
+        sp = None
+        if scalars is not None:
+            if scalars.dtype != torch.float64 or not scalars.is_cuda or scalars.numel() < 5 * n:
+                raise TypeError("scalars must be a CUDA float64 tensor with >= 5 * n entries")
+            sp = ctypes.c_void_p(scalars.data_ptr())
+        _check(self._lib.pfc_batch_step(self._h, pin, pout, taus.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        sp, _stream(stream)))
+
+    def timing(self, enable: bool = True):
+        _check(self._lib.pfc_batch_timing(self._h, 1 if enable else 0))
+
+    def last_timing(self):
+        """(step_ms, sweep_ms) of the most recent step; waits for it."""
+        a, b = ctypes.c_float(), ctypes.c_float()
+        _check(self._lib.pfc_batch_last_timing(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+
+class PhaseFieldEnergy(torch.autograd.Function):
+    """E = F_eps(u) with the gradient from the library's fused adjoint sweep.
+
+    ``PhaseFieldEnergy.apply(u, ctx)``: u a CUDA tensor shaped (nz, ny, nx) of
+    the context's dtype; returns a 0-d float64 tensor on u's device."""
+
+    @staticmethod
+    def forward(fctx, u, ctx: Context):
+        E, g = ctx.energy_and_grad(u.detach().contiguous())
+        fctx.save_for_backward(g)
+        return torch.tensor(E, dtype=torch.float64, device=u.device)
+
+    @staticmethod
+    def backward(fctx, grad_out):
+        (g,) = fctx.saved_tensors
+        return (grad_out.to(g.dtype) * g), None

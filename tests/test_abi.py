@@ -1,0 +1,91 @@
+"""CPU checks of the C ABI: the library loads, exports every symbol include/pfc.h
+declares, the Python struct mirrors the C struct, and the host-only helpers
+work.  No CUDA computation is launched here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pfc.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2103_04856_gb300 import build, pfc
+    if not os.path.exists(pfc.LIB_PATH):
+        build.build()
+    return pfc.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pfc_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_what_binding_exports():
+    from paper_2103_04856_gb300 import pfc
+    assert declared_functions() == sorted(pfc.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_problem_struct_layout_matches_header():
+    from paper_2103_04856_gb300 import pfc
+    # int32 x6, double x3, double[6], int32 x2  -> 24 + 24 + 48 + 8 = 104 bytes
+    assert ctypes.sizeof(pfc._CProblem) == 104
+    assert pfc._CProblem.h.offset == 24 and pfc._CProblem.a.offset == 48 and pfc._CProblem.tile_y.offset == 96
+
+
+def test_status_strings_and_b_to_a(lib):
+    from paper_2103_04856_gb300 import pfc
+    assert lib.pfc_status_string(0) == b"ok"
+    assert lib.pfc_status_string(pfc.PFC_ENONFINITE) == b"non-finite result"
+    # sponges row of the paper's Table four_shapes, host-only helper
+    np.testing.assert_allclose(pfc.pfc_b_to_a([1, 5, 0.8, 0, 0, 1, 0]), [1, 2.8, 2, -10, -10, 25])
+
+
+def test_create_rejects_bad_problems_without_touching_the_gpu(lib):
+    from paper_2103_04856_gb300 import pfc
+    h = ctypes.c_void_p()
+    bad = [dict(eps=0.0), dict(nx=0), dict(xi=-1.0), dict(tile_y=12), dict(h=float("nan"))]
+    for kw in bad:
+        base = dict(nx=8, ny=8, nz=8, eps=1.5, a=(1, 0, 1, 0, 0, 0))
+        base.update(kw)
+        p = pfc.Problem(**base)
+        rc = lib.pfc_create(ctypes.byref(p._c()), ctypes.byref(h))
+        assert rc == pfc.PFC_EINVAL, kw
+        assert lib.pfc_last_error()
+    p = pfc.Problem(nx=8, ny=8, nz=8, eps=1.5, a=(1, 0, 1, 0, 0, 0))
+    c = p._c()
+    c.well = 7
+    assert lib.pfc_create(ctypes.byref(c), ctypes.byref(h)) == pfc.PFC_EINVAL
+    assert lib.pfc_energy(None, None, None, None) == pfc.PFC_EINVAL
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2103_04856_gb300 import pfc
+    monkeypatch.setattr(pfc, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(pfc, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        pfc.load_library()
+
+
+def test_product_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2103_04856_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src, f
+                assert "pf_oracle" not in src, f
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".c", ".h")):
+            src = open(os.path.join(ROOT, "oracle", f)).read()
+            assert "paper_2103_04856_gb300" not in src and "pfc.h" not in src, f

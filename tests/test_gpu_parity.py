@@ -1,0 +1,309 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (libpfc.so).
+
+Bars (written in each test):
+  FP64 (fused and plain) vs oracle     1e-10 relative: energy, gradient (max-norm
+                                        relative to max|g|), steps and traces
+  FP32 fused vs FP64                    1e-4 relative energy, 1e-3 relative
+                                        gradient 2-norm (per evaluation, same state)
+Sizes span several tiles with ragged tails, odd sizes that take the element-wise
+load path, degenerate 1-voxel axes, and the full 128^3 / 256^3 / 512^3 grids
+(sampled against the oracle one voxel at a time).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2103_04856_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_2103_04856_gb300 import pfc
+
+
+def P(shape, a, eps=1.5, prec="fp64", impl="fused", well=0, h=1.0, xi=1e-6, **kw):
+    nz, ny, nx = shape
+    return pfc.Problem(nx=nx, ny=ny, nz=nz, eps=eps, a=tuple(a), h=h, xi=xi, well=well, prec=prec, impl=impl, **kw)
+
+
+def oprob(p):
+    return {"a": p.a, "eps": p.eps, "h": p.h, "xi": p.xi, "well": p.well}
+
+
+def dev(u, prec):
+    return torch.tensor(u, dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda").contiguous()
+
+
+def rel_max(g, gref):
+    return float(np.max(np.abs(g - gref)) / max(np.max(np.abs(gref)), 1e-300))
+
+
+SHAPES = [(7, 9, 11), (20, 24, 40), (33, 17, 64), (5, 40, 36), (2, 3, 5), (1, 4, 8), (16, 16, 16)]
+
+
+def _field_for(shape, well, seed):
+    if well == 0:
+        return I.noise(shape, 0.3, 0.1, seed)
+    return I.noise(shape, -0.1, 0.3, seed)
+
+
+@pytest.mark.parametrize("impl", ["fused", "plain"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_fp64_energy_grad_vs_oracle(shape, impl):
+    rng = np.random.default_rng(hash(shape) % 1000)
+    for well in (0, 1):
+        a = rng.uniform(-1, 1, 6)
+        p = P(shape, a, eps=1.3, h=0.9, well=well, impl=impl)
+        u = _field_for(shape, well, 3)
+        Eo, go = oracle.energy_and_grad(u, oprob(p))
+        ctx = pfc.Context(p)
+        E, g = ctx.energy_and_grad(dev(u, "fp64"))
+        assert E == pytest.approx(Eo, rel=1e-10, abs=1e-12)
+        assert rel_max(g.cpu().numpy(), go) < 1e-10
+        assert ctx.energy(dev(u, "fp64")) == pytest.approx(Eo, rel=1e-10, abs=1e-12)
+
+
+@pytest.mark.parametrize("tile", [(8, 3), (16, 5), (8, 64), (16, 1)])
+def test_fp64_tile_shapes(tile):
+    shape = (13, 20, 44)
+    a = (0.7, -0.3, 0.2, 0.5, -0.4, 0.3)
+    p = P(shape, a, tile_y=tile[0], tile_z=tile[1])
+    u = I.noise(shape, 0.3, 0.1, 4)
+    Eo, go = oracle.energy_and_grad(u, oprob(p))
+    E, g = pfc.Context(p).energy_and_grad(dev(u, "fp64"))
+    assert E == pytest.approx(Eo, rel=1e-10)
+    assert rel_max(g.cpu().numpy(), go) < 1e-10
+
+
+def test_misaligned_and_element_path():
+    shape = (6, 10, 12)
+    p = P(shape, (1, 0.5, 0.3, 0.2, 0.1, 0.4))
+    u = I.noise(shape, 0.3, 0.1, 5)
+    base = torch.zeros(u.size + 1, dtype=torch.float64, device="cuda")
+    view = base[1:].view(shape)            # 8-byte offset: not 16-byte aligned
+    view.copy_(torch.tensor(u, device="cuda"))
+    Eo, go = oracle.energy_and_grad(u, oprob(p))
+    E, g = pfc.Context(p).energy_and_grad(view)
+    assert E == pytest.approx(Eo, rel=1e-10)
+    assert rel_max(g.cpu().numpy(), go) < 1e-10
+
+
+@pytest.mark.parametrize("impl", ["fused", "plain"])
+def test_fp64_step_vs_oracle(impl):
+    shape = (12, 14, 36)
+    p = P(shape, (0.6, 0.1, 0.9, -0.3, 0.2, 0.1), impl=impl)
+    u = I.noise(shape, 0.3, 0.1, 6)
+    uo, sco = oracle.step(u, oprob(p), 1e-2)
+    ctx = pfc.Context(p)
+    ud = dev(u, "fp64")
+    out = torch.empty_like(ud)
+    sc = torch.zeros(5, dtype=torch.float64, device="cuda")
+    ctx.step(ud, out, 1e-2, sc)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(out.cpu().numpy() - uo)) < 1e-12
+    np.testing.assert_allclose(sc.cpu().numpy(), sco, rtol=1e-10, atol=1e-14)
+
+
+@pytest.mark.parametrize("impl", ["fused", "plain"])
+def test_fp64_run_32_vs_oracle(impl):
+    """The 32^3 plain FP64 descent: 100 mass-projected steps of 1e-3 from noise."""
+    inst = I.willmore_descent_32()
+    p = P(inst.shape, inst.a, eps=inst.eps, impl=impl)
+    u0 = inst.field()
+    uo, tro = oracle.run(u0, oprob(p), 100, inst.tau)
+    ud = dev(u0, "fp64")
+    tr = pfc.Context(p).run(ud, 100, inst.tau)
+    u = ud.cpu().numpy()
+    assert np.max(np.abs(u - uo)) < 1e-10 * np.max(np.abs(uo))
+    np.testing.assert_allclose(tr[:, 0], tro[:, 0], rtol=1e-10)            # energy
+    np.testing.assert_allclose(tr[:, 1], tro[:, 1], rtol=0, atol=1e-13)    # mass
+    np.testing.assert_allclose(tr[:, 2], tro[:, 2], rtol=0, atol=1e-10 * np.max(np.abs(tro[:, 3])))
+    np.testing.assert_allclose(tr[:, 3:], tro[:, 3:], rtol=1e-10)
+    assert abs(u.mean() - u0.mean()) < 1e-14
+
+
+@pytest.mark.parametrize("nsteps", [1, 3, 64, 67, 130])
+def test_run_lengths_graph_and_remainder(nsteps):
+    """Graph replays of 64 steps plus a directly launched remainder, odd and even."""
+    shape = (8, 8, 16)
+    p = P(shape, (1, 0, 1, 0, 0, 0))
+    u0 = I.noise(shape, 0.3, 0.1, 7)
+    uo, tro = oracle.run(u0, oprob(p), nsteps, 1e-3)
+    ud = dev(u0, "fp64")
+    ctx = pfc.Context(p)
+    tr = ctx.run(ud, nsteps, 1e-3)
+    assert np.max(np.abs(ud.cpu().numpy() - uo)) < 1e-11
+    np.testing.assert_allclose(tr[:, 0], tro[:, 0], rtol=1e-10)
+    # a second run on the same context (cached graph) continues from the result
+    u1, tro1 = oracle.run(uo, oprob(p), nsteps, 1e-3)
+    tr1 = ctx.run(ud, nsteps, 1e-3)
+    assert np.max(np.abs(ud.cpu().numpy() - u1)) < 1e-11
+    np.testing.assert_allclose(tr1[:, 0], tro1[:, 0], rtol=1e-10)
+
+
+def test_fp32_vs_fp64_noise():
+    for shape, a, seed in [((32, 32, 32), (1, 0, 1, 0, 0, 0), 0), ((24, 40, 48), (0.2, 0, 1, 0, -0.5, 0), 1),
+                           ((20, 30, 64), (1, 0.3, 0.2, 0, 0, 0), 2)]:
+        u = I.noise(shape, 0.3, 0.1, seed)
+        E64, g64 = pfc.Context(P(shape, a)).energy_and_grad(dev(u, "fp64"))
+        E32, g32 = pfc.Context(P(shape, a, prec="fp32")).energy_and_grad(dev(u, "fp32"))
+        Eo = oracle.energy(u.astype(np.float32).astype(np.float64), {"a": a, "eps": 1.5})
+        assert abs(E32 - E64) / abs(E64) < 1e-4
+        assert abs(E32 - Eo) / abs(Eo) < 1e-4
+        g64 = g64.cpu().numpy()
+        g32 = g32.double().cpu().numpy()
+        assert np.linalg.norm(g32 - g64) / np.linalg.norm(g64) < 1e-3
+
+
+def test_validation_128_fp32_energy_and_sampled_gradient():
+    """The four 128^3 validation problems (tanh sphere R=32 / cylinder r=20,
+    eps=2; p = k1^2+k2^2 and k1 k2), FP32 fused, in the configuration the
+    benchmark times: energy against the oracle, gradient against the oracle on
+    1024 sampled voxels."""
+    rng = np.random.default_rng(77)
+    for inst in I.validation_set_128():
+        u = inst.field()
+        u32 = u.astype(np.float32).astype(np.float64)
+        p = P(inst.shape, inst.a, eps=inst.eps, prec="fp32")
+        E, g = pfc.Context(p).energy_and_grad(dev(u, "fp32"))
+        Eo = oracle.energy(u32, oprob(p))
+        assert abs(E - Eo) / abs(Eo) < 1e-4, inst.name
+        # sample where the gradient lives (the interface) and anywhere
+        band = np.flatnonzero(np.abs(u32 - 0.5).ravel() < 0.45)
+        idx = np.concatenate([rng.choice(band, 768, replace=False), rng.integers(0, u.size, 256)])
+        go = oracle.grad_sampled(u32, oprob(p), idx)
+        gs = g.double().cpu().numpy().ravel()[idx]
+        assert np.linalg.norm(gs - go) / np.linalg.norm(go) < 1e-3, inst.name
+        # closed form the oracle is pinned to
+        sigma = math.sqrt(2) / 6
+        if inst.name == "sphere_128_k1^2+k2^2":
+            assert E / sigma / (8 * math.pi) == pytest.approx(1.1198, abs=2e-3)
+
+
+def test_fp64_plain_vs_fused_128():
+    inst = I.validation_128("sphere", "k1^2+k2^2")
+    u = dev(inst.field(), "fp64")
+    E1, g1 = pfc.Context(P(inst.shape, inst.a, eps=inst.eps, impl="plain")).energy_and_grad(u)
+    E2, g2 = pfc.Context(P(inst.shape, inst.a, eps=inst.eps)).energy_and_grad(u)
+    assert E1 == pytest.approx(E2, rel=1e-12)
+    assert rel_max(g1.cpu().numpy(), g2.cpu().numpy()) < 1e-11
+
+
+@pytest.mark.parametrize("n", [256, 512])
+def test_large_grids_sampled(n):
+    """256^3 (tube-favouring p) and 512^3 (membrane-favouring p), FP32: gradient
+    on 1024 random voxels against the oracle, energy against the FP64 GPU path
+    (itself equal to the oracle at every smaller size above)."""
+    inst = I.tube_descent_256(n) if n == 256 else I.membrane_descent_512(n)
+    u = inst.field().astype(np.float32)
+    p32 = P(inst.shape, inst.a, eps=inst.eps, prec="fp32")
+    E32, g = pfc.Context(p32).energy_and_grad(dev(u, "fp32"))
+    rng = np.random.default_rng(7)
+    idx = rng.integers(0, u.size, 1024)
+    u64 = u.astype(np.float64)
+    go = oracle.grad_sampled(u64, oprob(p32), idx)
+    gs = g.double().cpu().numpy().ravel()[idx]
+    assert np.linalg.norm(gs - go) / np.linalg.norm(go) < 1e-3
+    del g
+    ud = torch.tensor(u64, device="cuda")
+    E64 = pfc.Context(P(inst.shape, inst.a, eps=inst.eps)).energy(ud)
+    assert abs(E32 - E64) / abs(E64) < 1e-4
+
+
+def test_fp32_run_tracks_fp64():
+    inst = I.willmore_descent_32()
+    u0 = inst.field()
+    u32 = dev(u0, "fp32")
+    u64 = dev(u0.astype(np.float32), "fp64")
+    tr32 = pfc.Context(P(inst.shape, inst.a, eps=inst.eps, prec="fp32")).run(u32, 100, inst.tau)
+    tr64 = pfc.Context(P(inst.shape, inst.a, eps=inst.eps)).run(u64, 100, inst.tau)
+    np.testing.assert_allclose(tr32[:, 0], tr64[:, 0], rtol=1e-4)
+    assert np.max(np.abs(tr32[:, 1] - tr32[0, 1])) < 1e-6          # mass held in FP32
+    assert abs(u32.double().mean().item() - u0.astype(np.float32).astype(np.float64).mean()) < 1e-6
+
+
+def test_curvatures_vs_oracle():
+    shape = (24, 28, 32)
+    u = I.tanh_sphere(shape, 8, 1.5)
+    for prec, tol in (("fp64", 1e-10), ("fp32", 2e-3)):
+        p = P(shape, (1, 0, 1, 0, 0, 0), prec=prec)
+        k1, k2 = pfc.Context(p).curvatures(dev(u, prec))
+        o1, o2 = oracle.curvatures(u, oprob(p))
+        band = np.abs(u - 0.5) < 0.4
+        for k, o in ((k1, o1), (k2, o2)):
+            k = k.double().cpu().numpy()
+            assert np.max(np.abs(k - o)[band]) < tol * np.max(np.abs(o[band]))
+
+
+def test_autograd_function():
+    shape = (10, 12, 16)
+    p = P(shape, (0.5, 0.2, 1.0, 0.3, -0.2, 0.1))
+    ctx = pfc.Context(p)
+    u = dev(I.noise(shape, 0.3, 0.1, 8), "fp64").requires_grad_(True)
+    E = pfc.PhaseFieldEnergy.apply(u, ctx)
+    (3.0 * E).backward()
+    _, go = oracle.energy_and_grad(u.detach().cpu().numpy(), oprob(p))
+    assert rel_max(u.grad.cpu().numpy(), 3.0 * go) < 1e-10
+    # central differences of the GPU energy at a few voxels (smooth xi)
+    p2 = P(shape, p.a, xi=1e-2)
+    ctx2 = pfc.Context(p2)
+    base = u.detach().clone()
+    _, g2 = ctx2.energy_and_grad(base)
+    for i in (0, 77, 1500):
+        up, um = base.clone(), base.clone()
+        up.view(-1)[i] += 1e-5
+        um.view(-1)[i] -= 1e-5
+        fd = (ctx2.energy(up) - ctx2.energy(um)) / 2e-5
+        assert fd == pytest.approx(g2.view(-1)[i].item(), rel=1e-5, abs=1e-9)
+
+
+def test_batch_mixed_sizes_vs_oracle():
+    rng = np.random.default_rng(5)
+    shapes = [(16, 16, 16), (24, 24, 24), (12, 20, 32), (8, 8, 8)]
+    probs, fields, ops = [], [], []
+    for k, s in enumerate(shapes):
+        a = rng.uniform(-0.5, 0.5, 6)
+        a[0] += 1.0
+        a[2] += 1.0
+        pr = P(s, a, prec="fp32")
+        probs.append(pr)
+        fields.append(I.noise(s, 0.3, 0.1, 100 + k))
+        ops.append(oprob(pr))
+    b = pfc.Batch(probs)
+    taus = [1e-3, 2e-3, 1e-3, 5e-4]
+    devs = [dev(f, "fp32") for f in fields]
+    tr = b.run(devs, 10, taus)
+    for k in range(len(shapes)):
+        uo, tro = oracle.run(fields[k].astype(np.float32).astype(np.float64), ops[k], 10, taus[k])
+        np.testing.assert_allclose(tr[k, :, 0], tro[:, 0], rtol=1e-4)
+        assert np.max(np.abs(devs[k].double().cpu().numpy() - uo)) < 1e-5
+
+
+def test_errors_are_reported():
+    shape = (8, 8, 8)
+    p = P(shape, (1, 0, 1, 0, 0, 0))
+    ctx = pfc.Context(p)
+    u = dev(I.noise(shape, 0.3, 0.1, 9), "fp64")
+    lib = pfc.load_library()
+    import ctypes
+    E = ctypes.c_double()
+    host = np.zeros(512)
+    rc = lib.pfc_energy(ctx._h, ctypes.c_void_p(host.ctypes.data), ctypes.byref(E), None)
+    assert rc == pfc.PFC_EINVAL
+    rc = lib.pfc_energy_and_grad(ctx._h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(u.data_ptr()), None, None)
+    assert rc == pfc.PFC_EINVAL
+    bad = u.clone()
+    bad[3, 3, 3] = float("nan")
+    with pytest.raises(pfc.NonFiniteError):
+        ctx.energy(bad)
+    with pytest.raises(pfc.NonFiniteError):
+        ctx.run(bad, 3, 1e-3)
+    assert ctx.run(u, 0, 1e-3).shape == (0, 5)
+    with pytest.raises(pfc.PfcError):
+        pfc.Context(P(shape, (1, 0, 1, 0, 0, 0), eps=-1.0))
+    # the context still works after the errors
+    Eo = oracle.energy(u.cpu().numpy(), oprob(p))
+    assert ctx.energy(u) == pytest.approx(Eo, rel=1e-10)
