@@ -57,13 +57,57 @@ struct Cot {
     T hxy, hxz, hyz;        // 4-point mixed differences
 };
 
+// D = 2||M||^2 - (Tr M)^2 in FP64 from raw stencil values that are exact in
+// FP64 (differences of float inputs), for the float path's refinement.
+__device__ __forceinline__ double discriminant_fp64(const CoefD& R, int well, double u0, double dx, double dy,
+                                                    double dz, double hxx, double hyy, double hzz, double hxy,
+                                                    double hxz, double hyz)
+{
+    const double Gx = dx * R.sg, Gy = dy * R.sg, Gz = dz * R.sg;
+    const double rho = fma(Gx, Gx, fma(Gy, Gy, fma(Gz, Gz, R.xi2)));
+    const double wp = well == 0 ? 2.0 * (u0 - u0 * u0) * (1.0 - 2.0 * u0) : u0 * u0 * u0 - u0;
+    const double wr = wp * R.inv_eps / rho;
+    const double wx = wr * Gx, wy = wr * Gy, wz = wr * Gz;
+    const double Mxx = fma(R.kd, hxx, wx * Gx), Myy = fma(R.kd, hyy, wy * Gy), Mzz = fma(R.kd, hzz, wz * Gz);
+    const double Mxy = fma(R.ko, hxy, wx * Gy), Mxz = fma(R.ko, hxz, wx * Gz), Myz = fma(R.ko, hyz, wy * Gz);
+    const double Tr = Mxx + Myy + Mzz;
+    const double S = Mxx * Mxx + Myy * Myy + Mzz * Mzz + 2.0 * (Mxy * Mxy + Mxz * Mxz + Myz * Myz);
+    return 2.0 * S - Tr * Tr;
+}
+
+// Same, reading the 19 stencil inputs of a voxel from three u planes (pm, p0,
+// pp point at the voxel; `pitch` is the row pitch).  Kept out of line: it
+// runs for few voxels and must not add registers to the float hot path.
+template <typename T>
+__device__ __noinline__ double discriminant_fp64_at(const CoefD& R, int well, const T* pm, const T* p0,
+                                                    const T* pp, int pitch, double c)
+{
+    auto d = [](T v) { return (double)v; };
+    const double u0 = d(p0[0]);
+    return discriminant_fp64(
+        R, well, u0 + c, d(p0[1]) - d(p0[-1]), d(p0[pitch]) - d(p0[-pitch]), d(pp[0]) - d(pm[0]),
+        (d(p0[1]) + d(p0[-1])) - 2.0 * u0, (d(p0[pitch]) + d(p0[-pitch])) - 2.0 * u0, (d(pp[0]) + d(pm[0])) - 2.0 * u0,
+        (d(p0[pitch + 1]) - d(p0[pitch - 1])) - (d(p0[-pitch + 1]) - d(p0[-pitch - 1])),
+        (d(pp[1]) - d(pp[-1])) - (d(pm[1]) - d(pm[-1])), (d(pp[pitch]) - d(pp[-pitch])) - (d(pm[pitch]) - d(pm[-pitch])));
+}
+
+struct NoRefine {
+    __device__ __forceinline__ float operator()() const { return 0.0f; }
+};
+
 // Forward (eq. Meps, Sec. 3.1 invariants, eq. Feps) and, if GRAD, local
 // reverse mode of one voxel.  Inputs are the raw stencil values:
 //   dx = u(x+1) - u(x-1), hxx = u(x+1) - 2u + u(x-1),
 //   hxy = u(x+1,y+1) - u(x+1,y-1) - u(x-1,y+1) + u(x-1,y-1), etc.
-template <typename T, bool GRAD>
+//
+// float only: D is the difference of two O(||M||^2) numbers, so its FP32
+// error is about 2^-22 (2S + T^2).  Where that error is not small against
+// max(|D|, xi) -- near umbilics of strongly curved fields, and at the kink of
+// sqrt(D+) -- `refine()` recomputes D in FP64 from the exact float inputs
+// (rare on noise fields, never on the smooth validation shapes).
+template <typename T, bool GRAD, class Refine = NoRefine>
 __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz, T hxx, T hyy,
-                                        T hzz, T hxy, T hxz, T hyz, Cot<T>& ct)
+                                        T hzz, T hxy, T hxz, T hyz, Cot<T>& ct, const Refine& refine = Refine())
 {
     const T Gx = dx * C.sg, Gy = dy * C.sg, Gz = dz * C.sg;
     const T g2 = fma_(Gx, Gx, fma_(Gy, Gy, Gz * Gz));
@@ -97,7 +141,11 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
     // D = 2S - T^2 with the rounding error of T^2 put back (two-product)
     const T t2 = Tr * Tr;
     const T t2e = fma_(Tr, Tr, -t2);
-    const T D = fma_(T(2), S, -t2) - t2e;
+    T D = fma_(T(2), S, -t2) - t2e;
+    if (sizeof(T) == 4) {
+        const T scale = fma_(T(2), S, t2);
+        if (scale > T(4096) * fmax(fabs(D), C.xi)) D = (T)refine();
+    }
     T P, Pp;
     softplus_(D, C, P, Pp);
     const T r = sqrt_(P);

@@ -126,7 +126,8 @@ k_fused(Inst<T> single, const Inst<T>* __restrict__ insts, int n_inst)
         cp_async_commit();   // one group per plane slot, empty past the chunk
     };
 
-    const T cin = (MODE == MODE_STEP) ? (T)in.scal[S_C] : T(0);
+    const double cind = (MODE == MODE_STEP) ? in.scal[S_C] : 0.0;
+    const T cin = (T)cind;
 
     // ---- per-column state carried from plane to plane
     T accC = 0, zdn = 0, hxz2 = 0, hyz2 = 0, hxz1 = 0, hyz1 = 0;
@@ -180,11 +181,13 @@ k_fused(Inst<T> single, const Inst<T>* __restrict__ insts, int n_inst)
         const T hxz = (pp[1] - pp[-1]) - (pm[1] - pm[-1]);
         const T hyz = (pp[UXP] - pp[-UXP]) - (pm[UXP] - pm[-UXP]);
         Cot<T> ct;
+        // FP64 re-evaluation of D from the exact float inputs (float path only)
+        auto refine = [&]() -> T { return (T)discriminant_fp64_at<T>(in.C.R, in.C.well, pm, p0, pp, UXP, cind); };
         if (MODE == MODE_ENERGY) {
-            se.add(voxel_eval<T, false>(in.C, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ct));
+            se.add(voxel_eval<T, false>(in.C, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ct, refine));
             continue;
         }
-        const T e = voxel_eval<T, true>(in.C, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ct);
+        const T e = voxel_eval<T, true>(in.C, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ct, refine);
         if (own && interior) se.add(e);
         // transposed-stencil pieces of this voxel (see the gather):
         //   x/y first+second differences read from the left/right neighbour,
@@ -302,6 +305,11 @@ Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well)
     C.xi2 = (T)(xi * xi);
     C.inv_xi = (T)(1.0 / xi);
     C.well = well;
+    C.R.kd = -eps / (h * h);
+    C.R.ko = -eps / (4.0 * h * h);
+    C.R.sg = 1.0 / (2.0 * h);
+    C.R.inv_eps = 1.0 / eps;
+    C.R.xi2 = xi * xi;
     return C;
 }
 template Coef<float> make_coef<float>(const double*, double, double, double, int);

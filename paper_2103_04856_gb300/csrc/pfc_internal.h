@@ -22,6 +22,13 @@ enum Part { P_E = 0, P_U, P_G, P_AG, P_GMAX, P_OUT, NPART };
 enum Scal { S_E = 0, S_MASS, S_LAMBDA, S_GMAX, S_GMEAN, S_C, S_TARGET, NSCAL = 8 };
 enum Ints { I_TICKET = 0, I_COUNTER, I_NONFINITE, NINTS = 4 };
 
+// The same scale factors in FP64, for re-evaluating the discriminant
+// D = 2||M||^2 - (Tr M)^2 of a float voxel where FP32 cancellation would
+// matter (see voxel_eval).
+struct CoefD {
+    double kd, ko, sg, inv_eps, xi2;
+};
+
 // Coefficients of eq. Feps (times h^3, so that summing the per-voxel density
 // gives E directly) and the stencil scale factors, in the arithmetic type.
 template <typename T>
@@ -33,6 +40,7 @@ struct Coef {
     T inv_eps;  // 1 / eps
     T xi, xi2, inv_xi;
     int well;   // 0: u^2(1-u)^2, 1: (1-s^2)^2/4
+    CoefD R;
 };
 
 // One problem as seen by a fused launch.
