@@ -149,7 +149,7 @@ extern "C" pfc_status pfc_create(const pfc_problem* prob, pfc_ctx** out)
         return fail(PFC_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     }
     geometry(prob, sm_count(c->device), &c->tile_y, &c->zc, &c->tiles_x, &c->tiles_y, &c->chunks_z);
-    c->nblocks = c->tiles_x * c->tiles_y * c->chunks_z;
+    c->nblocks = (int)fused_grid((long long)c->tiles_x * c->tiles_y * prob->nz, prob->tile_z);
     c->plain_nblocks = plain_blocks(c->N);
     const int nparts = c->nblocks > c->plain_nblocks ? c->nblocks : c->plain_nblocks;
     bool ok = cudaMalloc(&c->ping, (size_t)c->esz * c->N) == cudaSuccess &&
@@ -236,8 +236,9 @@ static cudaError_t enqueue(pfc_ctx* c, int mode, const void* u, void* out, doubl
                                    (float)tau, 1.0 / (double)c->N, c->partials, c->plain_nblocks, c->ints, c->scal,
                                    c->trace, c->trace_cap, s);
     }
-    if (c->P.prec == PFC_FP64) return launch_fused<double>(make_inst<double>(c, u, out, tau), mode, c->tile_y, s);
-    return launch_fused<float>(make_inst<float>(c, u, out, tau), mode, c->tile_y, s);
+    if (c->P.prec == PFC_FP64)
+        return launch_fused<double>(make_inst<double>(c, u, out, tau), mode, c->tile_y, c->P.tile_z, s);
+    return launch_fused<float>(make_inst<float>(c, u, out, tau), mode, c->tile_y, c->P.tile_z, s);
 }
 
 static pfc_status read_scalar(pfc_ctx* c, int slot, double* host, cudaStream_t s)
@@ -428,6 +429,7 @@ struct pfc_batch {
     int n = 0;
     int device = 0;
     int tile_y = 16;
+    int max_run = 0;
     int total_blocks = 0;
     std::vector<pfc_problem> P;
     std::vector<Inst<float>> host;   // geometry + scratch pointers, u/out filled per run
@@ -437,18 +439,12 @@ struct pfc_batch {
     double* scal = nullptr;
     double* trace = nullptr;
     int trace_cap = 0;
-    Inst<float>* dev_even = nullptr;   // step parity 0: u -> ping
-    Inst<float>* dev_odd = nullptr;    // step parity 1: ping -> u
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec = nullptr;   // cached step loop, keyed by fields, steps and G
+    std::vector<void*> g_u;
+    std::vector<double> g_tau;
     int g_len = 0;
     double* g_trace = nullptr;
     cudaStream_t cap = nullptr;
-    // pfc_batch_step: two cached descriptor sets keyed by their pointers
-    Inst<float>* dev_step[2] = { nullptr, nullptr };
-    std::vector<const void*> step_key[2];
-    std::vector<double> step_tau[2];
-    int step_lru = 0;
-    Inst<float>* pinned = nullptr;     // staging for descriptor uploads
     cudaEvent_t ev[4] = { nullptr, nullptr, nullptr, nullptr };
     bool timing = false;
 };
@@ -460,11 +456,6 @@ static void free_batch_mem(pfc_batch* b)
     cudaFree(b->ints);
     cudaFree(b->scal);
     cudaFree(b->trace);
-    cudaFree(b->dev_even);
-    cudaFree(b->dev_odd);
-    cudaFree(b->dev_step[0]);
-    cudaFree(b->dev_step[1]);
-    if (b->pinned) cudaFreeHost(b->pinned);
     for (cudaEvent_t e : b->ev)
         if (e) cudaEventDestroy(e);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
@@ -494,13 +485,13 @@ extern "C" pfc_status pfc_batch_create(const pfc_problem* probs, int32_t n, pfc_
     const int sms = sm_count(b->device);
     b->host.resize(n);
     b->ping.assign(n, nullptr);
-    int first = 0;
     bool ok = true;
     b->tile_y = probs[0].tile_y ? probs[0].tile_y : 16;
+    b->max_run = probs[0].tile_z;
+    long long units = 0;
     for (int k = 0; k < n && ok; ++k) {
         pfc_problem p = probs[k];
         p.tile_y = b->tile_y;
-        if (!p.tile_z) p.tile_z = p.nz < 32 ? p.nz : 32;   // many instances fill the GPU; keep chunks long
         int ty, zc, tx, tyn, cz;
         geometry(&p, sms, &ty, &zc, &tx, &tyn, &cz);
         Inst<float>& in = b->host[k];
@@ -508,22 +499,17 @@ extern "C" pfc_status pfc_batch_create(const pfc_problem* probs, int32_t n, pfc_
         in.nx = p.nx; in.ny = p.ny; in.nz = p.nz;
         in.zc = zc;
         in.tiles_x = tx; in.tiles_y = tyn; in.chunks_z = cz;
-        in.first_block = first;
-        in.nblocks = tx * tyn * cz;
-        first += in.nblocks;
+        units += (long long)tx * tyn * p.nz;
         in.C = make_coef<float>(p.a, p.h, p.eps, p.xi, p.well);
         in.inv_N = 1.0 / ((double)p.nx * p.ny * p.nz);
         ok = cudaMalloc(&b->ping[k], sizeof(float) * (size_t)p.nx * p.ny * p.nz) == cudaSuccess;
     }
-    b->total_blocks = first;
-    ok = ok && cudaMalloc((void**)&b->partials, sizeof(double) * NPART * (size_t)first) == cudaSuccess &&
+    // every problem may get a partial from every CTA of its launch
+    const long long slots = fused_grid(units, b->max_run);
+    b->total_blocks = (int)slots;
+    ok = ok && cudaMalloc((void**)&b->partials, sizeof(double) * NPART * (size_t)slots * n) == cudaSuccess &&
          cudaMalloc((void**)&b->ints, sizeof(unsigned) * NINTS * (size_t)n) == cudaSuccess &&
          cudaMalloc((void**)&b->scal, sizeof(double) * NSCAL * (size_t)n) == cudaSuccess &&
-         cudaMalloc((void**)&b->dev_even, sizeof(Inst<float>) * (size_t)n) == cudaSuccess &&
-         cudaMalloc((void**)&b->dev_odd, sizeof(Inst<float>) * (size_t)n) == cudaSuccess &&
-         cudaMalloc((void**)&b->dev_step[0], sizeof(Inst<float>) * (size_t)n) == cudaSuccess &&
-         cudaMalloc((void**)&b->dev_step[1], sizeof(Inst<float>) * (size_t)n) == cudaSuccess &&
-         cudaMallocHost((void**)&b->pinned, sizeof(Inst<float>) * (size_t)n) == cudaSuccess &&
          cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
     if (!ok) {
         cudaError_t le = cudaGetLastError();
@@ -533,7 +519,7 @@ extern "C" pfc_status pfc_batch_create(const pfc_problem* probs, int32_t n, pfc_
     }
     for (int k = 0; k < n; ++k) {
         Inst<float>& in = b->host[k];
-        in.partials = b->partials + (size_t)in.first_block * NPART;
+        in.partials = b->partials + (size_t)k * slots * NPART;
         in.ints = b->ints + (size_t)k * NINTS;
         in.scal = b->scal + (size_t)k * NSCAL;
     }
@@ -597,22 +583,21 @@ extern "C" pfc_status pfc_batch_run(pfc_batch* b, void* const* u, int32_t nsteps
         ev[k].trace = od[k].trace = b->trace + (size_t)k * 5 * b->trace_cap;
         ev[k].trace_cap = od[k].trace_cap = b->trace_cap;
     }
-    PFC_CU(cudaMemcpyAsync(b->dev_even, ev.data(), sizeof(Inst<float>) * b->n, cudaMemcpyHostToDevice, s));
-    PFC_CU(cudaMemcpyAsync(b->dev_odd, od.data(), sizeof(Inst<float>) * b->n, cudaMemcpyHostToDevice, s));
     PFC_CU(cudaMemsetAsync(b->ints, 0, sizeof(unsigned) * NINTS * b->n, s));
     PFC_CU(cudaMemsetAsync(b->scal, 0, sizeof(double) * NSCAL * b->n, s));
     auto steps = [&](int i0, int cnt, cudaStream_t st) -> cudaError_t {
         for (int i = i0; i < i0 + cnt; ++i) {
-            cudaError_t e = launch_fused_batch((i % 2) == 0 ? b->dev_even : b->dev_odd, b->n, b->total_blocks,
-                                               b->tile_y, st);
+            cudaError_t e = launch_fused_batch((i % 2) == 0 ? ev.data() : od.data(), b->n, b->tile_y, b->max_run, st);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
     };
     const int G = nsteps >= 64 ? 64 : (nsteps & ~1);
     if (G >= 2) {
-        // descriptors live at fixed device addresses, so the graph only depends on G
-        if (!(b->gexec && b->g_len == G && b->g_trace == b->trace)) {
+        // the descriptors are kernel parameters: the graph depends on the fields and steps
+        std::vector<void*> key(u, u + b->n);
+        std::vector<double> tkey(tau, tau + b->n);
+        if (!(b->gexec && b->g_len == G && b->g_trace == b->trace && b->g_u == key && b->g_tau == tkey)) {
             if (b->gexec) {
                 cudaGraphExecDestroy(b->gexec);
                 b->gexec = nullptr;
@@ -635,6 +620,8 @@ extern "C" pfc_status pfc_batch_run(pfc_batch* b, void* const* u, int32_t nsteps
             }
             b->g_len = G;
             b->g_trace = b->trace;
+            b->g_u = key;
+            b->g_tau = tkey;
         }
         for (int k = 0; k + G <= nsteps; k += G) PFC_CU(cudaGraphLaunch(b->gexec, s));
     }
@@ -669,58 +656,33 @@ extern "C" pfc_status pfc_batch_step(pfc_batch* b, const void* const* u_in, void
     if (!b) return fail(PFC_EINVAL, "batch is NULL");
     if (!u_in || !u_out || !tau) return fail(PFC_EINVAL, "u_in, u_out and tau arrays are required");
     cudaStream_t s = (cudaStream_t)stream;
-    // descriptors for this pointer set: reuse one of the two cached sets
-    int slot = -1;
-    for (int j = 0; j < 2 && slot < 0; ++j) {
-        if ((int)b->step_key[j].size() != 2 * b->n) continue;
-        bool same = true;
-        for (int k = 0; k < b->n && same; ++k)
-            same = b->step_key[j][2 * k] == u_in[k] && b->step_key[j][2 * k + 1] == u_out[k] &&
-                   b->step_tau[j][k] == tau[k];
-        if (same) slot = j;
-    }
-    if (slot < 0) {
-        for (int k = 0; k < b->n; ++k) {
-            for (int w = 0; w < 2; ++w) {
-                const void* p = w ? (const void*)u_out[k] : u_in[k];
-                cudaPointerAttributes at;
-                if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess ||
-                    (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
-                    (void)cudaGetLastError();
-                    return fail(PFC_EINVAL, "%s[%d] is not device memory", w ? "u_out" : "u_in", k);
-                }
+    std::vector<Inst<float>> d(b->host);
+    for (int k = 0; k < b->n; ++k) {
+        for (int w = 0; w < 2; ++w) {
+            const void* p = w ? (const void*)u_out[k] : u_in[k];
+            cudaPointerAttributes at;
+            if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess ||
+                (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+                (void)cudaGetLastError();
+                return fail(PFC_EINVAL, "%s[%d] is not device memory", w ? "u_out" : "u_in", k);
             }
-            if (u_in[k] == u_out[k]) return fail(PFC_EINVAL, "u_out[%d] aliases u_in[%d]", k, k);
-            if (!isfinite(tau[k])) return fail(PFC_EINVAL, "tau[%d] is not finite", k);
         }
-        slot = b->step_lru;
-        b->step_lru ^= 1;
-        PFC_CU(cudaStreamSynchronize(s));   // the pinned staging buffer may still be in flight
-        for (int k = 0; k < b->n; ++k) {
-            Inst<float> in = b->host[k];
-            in.u = (const float*)u_in[k];
-            in.out = (float*)u_out[k];
-            in.vec = (b->P[k].nx % 4 == 0) && ((uintptr_t)u_in[k]) % 16 == 0;
-            in.tau = (float)tau[k];
-            in.trace = nullptr;
-            in.trace_cap = 0;
-            b->pinned[k] = in;
-        }
-        PFC_CU(cudaMemcpyAsync(b->dev_step[slot], b->pinned, sizeof(Inst<float>) * b->n, cudaMemcpyHostToDevice, s));
-        b->step_key[slot].resize(2 * b->n);
-        b->step_tau[slot].assign(tau, tau + b->n);
-        for (int k = 0; k < b->n; ++k) {
-            b->step_key[slot][2 * k] = u_in[k];
-            b->step_key[slot][2 * k + 1] = u_out[k];
-        }
+        if (u_in[k] == u_out[k]) return fail(PFC_EINVAL, "u_out[%d] aliases u_in[%d]", k, k);
+        if (!isfinite(tau[k])) return fail(PFC_EINVAL, "tau[%d] is not finite", k);
+        d[k].u = (const float*)u_in[k];
+        d[k].out = (float*)u_out[k];
+        d[k].vec = (b->P[k].nx % 4 == 0) && ((uintptr_t)u_in[k]) % 16 == 0;
+        d[k].tau = (float)tau[k];
+        d[k].trace = nullptr;
+        d[k].trace_cap = 0;
     }
     if (b->timing) PFC_CU(cudaEventRecord(b->ev[0], s));
     PFC_CU(cudaMemsetAsync(b->ints, 0, sizeof(unsigned) * NINTS * b->n, s));
     PFC_CU(cudaMemsetAsync(b->scal, 0, sizeof(double) * NSCAL * b->n, s));
     if (b->timing) PFC_CU(cudaEventRecord(b->ev[1], s));
-    PFC_CU(launch_fused_batch(b->dev_step[slot], b->n, b->total_blocks, b->tile_y, s));
+    PFC_CU(launch_fused_batch(d.data(), b->n, b->tile_y, b->max_run, s));
     if (b->timing) PFC_CU(cudaEventRecord(b->ev[2], s));
-    PFC_CU(launch_add_offset_batch(b->dev_step[slot], b->n, s));
+    PFC_CU(launch_add_offset_batch(d.data(), b->n, s));
     if (scalars_dev)
         PFC_CU(cudaMemcpy2DAsync(scalars_dev, 5 * sizeof(double), b->scal, NSCAL * sizeof(double), 5 * sizeof(double),
                                  b->n, cudaMemcpyDeviceToDevice, s));

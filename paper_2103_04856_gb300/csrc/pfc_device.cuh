@@ -112,9 +112,9 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
     const T Gx = dx * C.sg, Gy = dy * C.sg, Gz = dz * C.sg;
     const T g2 = fma_(Gx, Gx, fma_(Gy, Gy, Gz * Gz));
     const T rho = g2 + C.xi2;
-    const T irho = rcp_(rho);
     const T iq = rsqrt_(rho);
     const T q = rho * iq;
+    const T irho = sizeof(T) == 4 ? iq * iq : rcp_(rho);
     // W'(u)/eps and W''(u)/eps for the chosen double well
     T wp, wpp;
     if (C.well == 0) {
@@ -148,13 +148,16 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
     }
     T P, Pp;
     softplus_(D, C, P, Pp);
-    const T r = sqrt_(P);
+    // float: one reciprocal square root gives both sqrt(P) and 1/(2 sqrt(P))
+    const T rs = (sizeof(T) == 4 && P > T(0)) ? rsqrt_(P) : T(0);
+    const T r = sizeof(T) == 4 ? P * rs : sqrt_(P);
     const T a3 = fma_(C.c3, Tr, C.c5 * q);              // c3 T + c5 q
     const T e = fma_(C.c1, S, fma_(C.c2, t2, fma_(a3, r, fma_(C.c4 * q, Tr, C.c6 * g2))));
     if (!GRAD) return e;
 
     // local reverse mode: e(S, T, r(D(S,T)), q(G), |G|^2), M(Hess, w(u), G)
-    const T rp = r > T(0) ? T(0.5) * Pp * rcp_(r) : T(0);   // dr/dD, 0 where r = 0
+    // dr/dD, 0 where r = 0
+    const T rp = sizeof(T) == 4 ? T(0.5) * Pp * rs : (r > T(0) ? T(0.5) * Pp / r : T(0));
     const T k = a3 * rp;                                     // de/dD
     const T dS = fma_(T(2), k, C.c1);
     const T dT = fma_(T(2) * C.c2, Tr, fma_(C.c3, r, fma_(C.c4, q, -T(2) * Tr * k)));
@@ -236,37 +239,37 @@ __device__ __forceinline__ void block_reduce_parts(double v[NPART], double* red)
     }
 }
 
-// Every CTA of a problem writes its partials; the last CTA to arrive (atomic
-// ticket, no waiting) combines all of them in a fixed order and writes the
-// problem's scalars.  `v` holds this thread's contribution.
+// Publish one CTA's totals `tot` (shared, NPART doubles) as partial `slot`
+// of a problem; the last CTA to arrive (atomic ticket, no waiting) combines
+// all partials of the problem in a fixed order and writes its scalars.
 template <typename T>
-__device__ void grid_finish(const Inst<T>& in, int local_block, int mode, double v[NPART],
-                            double* red)
+__device__ void finish_problem(const Inst<T>& in, int slot, int mode, const double* tot)
 {
     __shared__ int am_last;
-    block_reduce_parts(v, red);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int i = 0; i < NPART; ++i) in.partials[(size_t)local_block * NPART + i] = v[i];
+        for (int i = 0; i < NPART; ++i) in.partials[(size_t)slot * NPART + i] = tot[i];
         __threadfence();
-        unsigned t = atomicAdd(&in.ints[I_TICKET], 1u);
+        const unsigned t = atomicAdd(&in.ints[I_TICKET], 1u);
         am_last = (t == (unsigned)in.nblocks - 1u);
     }
     __syncthreads();
-    if (!am_last) return;
+    if (!am_last || threadIdx.x >= 32) return;
     __threadfence();
+    const int lane = threadIdx.x;
     double s[NPART];
 #pragma unroll
     for (int i = 0; i < NPART; ++i) s[i] = 0.0;
-    for (int b = threadIdx.x; b < in.nblocks; b += blockDim.x) {
+    for (int b = lane; b < in.nblocks; b += 32) {
 #pragma unroll
         for (int i = 0; i < NPART; ++i) {
-            double x = __ldcg(&in.partials[(size_t)b * NPART + i]);
+            const double x = __ldcg(&in.partials[(size_t)b * NPART + i]);
             s[i] = (i == P_GMAX) ? fmax(s[i], x) : s[i] + x;
         }
     }
-    block_reduce_parts(s, red);
-    if (threadIdx.x != 0) return;
+#pragma unroll
+    for (int i = 0; i < NPART; ++i) s[i] = (i == P_GMAX) ? warp_max(s[i]) : warp_sum(s[i]);
+    if (lane != 0) return;
     double* sc = in.scal;
     const double E = s[P_E];
     bool bad = !isfinite(E);
@@ -296,6 +299,64 @@ __device__ void grid_finish(const Inst<T>& in, int local_block, int mode, double
     if (bad) in.ints[I_NONFINITE] = 1;
     __threadfence();
     in.ints[I_TICKET] = 0;   // ready for the next launch on this problem
+}
+
+// Grid-stride kernels (plain path): reduce each thread's FP64 values over the
+// block, then publish them as partial blockIdx.x.
+template <typename T>
+__device__ void grid_finish(const Inst<T>& in, int slot, int mode, double v[NPART], double* red)
+{
+    __shared__ double tot[NPART];
+    block_reduce_parts(v, red);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int i = 0; i < NPART; ++i) tot[i] = v[i];
+    __syncthreads();
+    finish_problem(in, slot, mode, tot);
+}
+
+// Block totals of per-thread FP32 sums for the fused sweep: every thread
+// stores its NPART values, then warp i adds column i (compensated, 20 terms
+// per lane) and finishes in FP64 across lanes.  Few FP64 operations: the
+// FP64 pipe is slow on this GPU.  `scr` holds NPART * NT floats.
+template <int NT>
+__device__ __forceinline__ void block_sums(const float v[NPART], float* scr, double* tot)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NPART; ++i) scr[i * NT + tid] = v[i];
+    __syncthreads();
+    if (warp < NPART) {
+        const float* col = scr + warp * NT;
+        double r;
+        if (warp == P_GMAX) {
+            float m = 0.0f;
+            for (int j = lane; j < NT; j += 32) m = fmaxf(m, col[j]);
+            r = warp_max((double)m);
+        } else {
+            KSum<float> k;
+            for (int j = lane; j < NT; j += 32) k.add(col[j]);
+            r = warp_sum(k.get());
+        }
+        if (lane == 0) tot[warp] = r;
+    }
+    __syncthreads();
+}
+
+// FP64 sweep: per-thread FP64 sums, plain FP64 block reduction.
+template <int NT>
+__device__ __forceinline__ void block_sums(const double v[NPART], float*, double* tot)
+{
+    __shared__ double red[32 * NPART];
+    double w[NPART];
+#pragma unroll
+    for (int i = 0; i < NPART; ++i) w[i] = v[i];
+    block_reduce_parts(w, red);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int i = 0; i < NPART; ++i) tot[i] = w[i];
+    __syncthreads();
 }
 
 }  // namespace pfc

@@ -25,12 +25,18 @@ constexpr int UXP = 40;     // u tile row in shared memory: x0-4 .. x0+35
 constexpr int NBUF = 8;     // ring of u planes
 constexpr int PD = 3;       // planes in flight ahead of the plane being consumed
 
+// Thread layout of a tile (TY rows of 32 output columns, plus a one-column
+// halo ring whose cotangents the gather needs):
+//   warps 0 .. TY-1 : interior rows, lane = x          (these also gather)
+//   warps TY, TY+1  : the halo rows above and below the tile
+//   warps TY+2, TY+3: the left and right halo columns (TY+2 lanes each)
+// so every warp but the last two reads contiguous shared memory.
 template <int TY>
 struct Tile {
     static constexpr int EX = TX + 2;             // extended (halo) columns in x
     static constexpr int EY = TY + 2;
     static constexpr int NEXT = EX * EY;
-    static constexpr int NT = ((NEXT + 31) / 32) * 32;
+    static constexpr int NT = (TY + 4) * 32;
     static constexpr int UY = TY + 4;             // u rows: y0-2 .. y0+TY+1
     static constexpr int PLANE = UY * UXP;
 };
@@ -60,172 +66,193 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-template <typename T, int TY, int MODE, bool BATCH>
+template <typename T, int TY, int MODE, int MAXI>
 __global__ void __launch_bounds__(Tile<TY>::NT, 1)
-k_fused(Inst<T> single, const Inst<T>* __restrict__ insts, int n_inst)
+k_fused(const __grid_constant__ Launch<T, MAXI> L)
 {
     using TL = Tile<TY>;
     constexpr int EX = TL::EX, NEXT = TL::NEXT, NT = TL::NT, UY = TL::UY, PLANE = TL::PLANE;
     constexpr int VEC = 16 / (int)sizeof(T);
     constexpr int NCH = UXP / VEC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* us = reinterpret_cast<T*>(smem_raw);   // [NBUF][UY][UXP]
-    T* fs = us + NBUF * PLANE;                 // [2][5][NEXT]
-    __shared__ double red[32 * NPART];
-
-    // ---- which problem and which tile
-    int local = blockIdx.x;
-    Inst<T> in;
-    if (BATCH) {
-        int lo = 0, hi = n_inst - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (insts[mid].first_block <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-        }
-        in = insts[lo];
-        local = blockIdx.x - in.first_block;
-    } else {
-        in = single;
-    }
-    const int nx = in.nx, ny = in.ny, nz = in.nz;
-    int b = local;
-    const int tile_x = b % in.tiles_x; b /= in.tiles_x;
-    const int tile_y = b % in.tiles_y; b /= in.tiles_y;
-    const int x0 = tile_x * TX, y0 = tile_y * TY, z0 = b * in.zc;
-    const int zend = min(z0 + in.zc, nz);        // exclusive
-    const int plast = zend + 1;                   // last u plane needed
-    const size_t plane_g = (size_t)nx * ny;
+    T* us = reinterpret_cast<T*>(smem_raw);            // [NBUF][UY][UXP]
+    T* fs = us + NBUF * PLANE;                          // [2][5][NEXT]
+    float* scr = reinterpret_cast<float*>(fs + 2 * 5 * NEXT);   // [NPART][NT]
+    __shared__ double tot[NPART];
 
     const int tid = threadIdx.x;
-    const int ex = tid % EX, ey = tid / EX;       // extended column of this thread
-    const bool active = tid < NEXT;
-    const int gx = x0 + ex - 1, gy = y0 + ey - 1;
-    const bool interior = active && ex >= 1 && ex <= TX && ey >= 1 && ey <= TY && gx < nx && gy < ny;
+    const int warp = tid >> 5, lane = tid & 31;
+    int ex, ey;                                   // extended column of this thread
+    bool active = true;
+    if (warp < TY) { ey = warp + 1; ex = lane + 1; }
+    else if (warp == TY) { ey = 0; ex = lane + 1; }
+    else if (warp == TY + 1) { ey = TY + 1; ex = lane + 1; }
+    else { ex = warp == TY + 2 ? 0 : EX - 1; ey = lane; active = lane < TY + 2; }
     const int uc = (ey + 1) * UXP + ex + 3;       // this column in a u plane
+    const int fc = ey * EX + ex;                  // this column in a field plane
 
-    // ---- loads: every u plane of the tile, periodic in x, y and z
-    int ld_off = -1, ld_dst = 0;
-    if (in.vec && tid < UY * NCH) {
-        const int r = tid / NCH, c = tid - (tid / NCH) * NCH;
-        ld_off = wrapi(y0 - 2 + r, ny) * nx + wrapi(x0 - 4 + c * VEC, nx);
-        ld_dst = r * UXP + c * VEC;
-    }
-    auto issue = [&](int p) {
-        if (p <= plast) {
-            T* dst = us + (p & (NBUF - 1)) * PLANE;
-            const T* src = in.u + (size_t)wrapi(p, nz) * plane_g;
-            if (in.vec) {
-                if (ld_off >= 0) cp_async16(dst + ld_dst, src + ld_off);
-            } else {
-                for (int i = tid; i < PLANE; i += NT) {
-                    const int r = i / UXP, c = i - (i / UXP) * UXP;
-                    cp_async_elem(dst + i, src + wrapi(y0 - 2 + r, ny) * nx + wrapi(x0 - 4 + c, nx));
-                }
+    // per-thread sums of the problem being processed, in the arithmetic type
+    // (a few hundred terms each), combined in FP64 across threads and CTAs
+    T se = 0, su = 0, sg = 0, sag = 0, gmax = 0, sout = 0;
+    int cur = -1;                                 // problem the sums belong to
+    auto flush = [&]() {
+        const T v[NPART] = { se, su, sg, sag, gmax, sout };
+        block_sums<NT>(v, scr, tot);
+        const Inst<T>& pin = L.inst[cur];
+        finish_problem(pin, (int)blockIdx.x - pin.first_block, MODE, tot);
+        se = su = sg = sag = gmax = sout = 0;
+    };
+
+    // this CTA's share of the work units
+    const long long W = L.units;
+    long long U = (long long)blockIdx.x * W / L.grid;
+    const long long Uend = ((long long)blockIdx.x + 1) * W / L.grid;
+    while (U < Uend) {
+        // ---- the run: one column tile of one problem, a contiguous z range
+        int k = 0;
+        if (MAXI > 1) {
+            int hi = L.n - 1;
+            while (k < hi) {
+                const int mid = (k + hi + 1) >> 1;
+                if (L.inst[mid].unit_base <= U) k = mid; else hi = mid - 1;
             }
         }
-        cp_async_commit();   // one group per plane slot, empty past the chunk
-    };
-
-    const double cind = (MODE == MODE_STEP) ? in.scal[S_C] : 0.0;
-    const T cin = (T)cind;
-
-    // ---- per-column state carried from plane to plane
-    T accC = 0, zdn = 0, hxz2 = 0, hyz2 = 0, hxz1 = 0, hyz1 = 0;
-    T fx1 = 0, fx2 = 0, fy1 = 0, fy2 = 0, fxy = 0, cpend = 0;
-    KSum<T> se, su, sg, sag, sout;
-    T gmax = 0;
-
-    auto gather = [&](int k) {
-        const T* F = fs + (k & 1) * 5 * NEXT;
-        const int c = tid;
-        const T g = cpend + F[c - 1] + F[NEXT + c + 1] + F[2 * NEXT + c - EX] + F[3 * NEXT + c + EX]
-                  + (F[4 * NEXT + c - 1 - EX] - F[4 * NEXT + c - 1 + EX])
-                  - (F[4 * NEXT + c + 1 - EX] - F[4 * NEXT + c + 1 + EX]);
-        const size_t gi = (size_t)k * plane_g + (size_t)gy * nx + gx;
-        const T ag = g < T(0) ? -g : g;
-        sg.add(g);
-        sag.add(ag);
-        gmax = ag > gmax ? ag : gmax;
-        if (MODE == MODE_GRAD) {
-            in.out[gi] = g;
-        } else {
-            const T u0 = us[(k & (NBUF - 1)) * PLANE + uc] + cin;
-            const T v = fma_(-in.tau, g, u0);
-            in.out[gi] = v;
-            su.add(u0);
-            sout.add(v);
+        const Inst<T>& in = L.inst[k];
+        const int nx = in.nx, ny = in.ny, nz = in.nz;
+        const long long rel = U - in.unit_base;
+        const int ct = (int)(rel / nz);
+        const int z0 = (int)(rel - (long long)ct * nz);
+        const long long run_end = min(Uend, in.unit_base + (long long)(ct + 1) * nz);
+        const int zend = z0 + (int)(run_end - U);      // exclusive
+        U = run_end;
+        if (k != cur) {
+            if (cur >= 0) flush();
+            cur = k;
         }
-    };
+        const int x0 = (ct % in.tiles_x) * TX, y0 = (ct / in.tiles_x) * TY;
+        const int plast = zend + 1;                    // last u plane needed
+        const size_t plane_g = (size_t)nx * ny;
+        const int gx = x0 + ex - 1, gy = y0 + ey - 1;
+        const bool interior = warp < TY && gx < nx && gy < ny;
 
-    for (int p = z0 - 2; p <= z0 + PD - 1; ++p) issue(p);
+        // ---- loads: every u plane of the tile, periodic in x, y and z
+        int ld_off = -1, ld_dst = 0;
+        if (in.vec && tid < UY * NCH) {
+            const int r = tid / NCH, c = tid - (tid / NCH) * NCH;
+            ld_off = wrapi(y0 - 2 + r, ny) * nx + wrapi(x0 - 4 + c * VEC, nx);
+            ld_dst = r * UXP + c * VEC;
+        }
+        int pz = wrapi(z0 - 2, nz);                // planes are issued in increasing order
+        auto issue = [&](int p) {
+            if (p <= plast) {
+                T* dst = us + (p & (NBUF - 1)) * PLANE;
+                const T* src = in.u + (size_t)pz * plane_g;
+                if (in.vec) {
+                    if (ld_off >= 0) cp_async16(dst + ld_dst, src + ld_off);
+                } else {
+                    for (int i = tid; i < PLANE; i += NT) {
+                        const int r = i / UXP, c = i - (i / UXP) * UXP;
+                        cp_async_elem(dst + i, src + wrapi(y0 - 2 + r, ny) * nx + wrapi(x0 - 4 + c, nx));
+                    }
+                }
+            }
+            cp_async_commit();   // one group per plane slot, empty past the run
+            pz = pz + 1 == nz ? 0 : pz + 1;
+        };
 
-    for (int m = z0 - 1; m <= zend; ++m) {
-        cp_async_wait<PD - 1>();
-        __syncthreads();
-        if (MODE != MODE_ENERGY && m - 2 >= z0 && interior) gather(m - 2);
-        issue(m + 1 + PD);
-        if (!active) continue;
-        const bool own = (m >= z0 && m < zend);
-        if (MODE == MODE_ENERGY && !(own && interior)) continue;
-        const T* pm = us + ((m - 1) & (NBUF - 1)) * PLANE + uc;
-        const T* p0 = us + (m & (NBUF - 1)) * PLANE + uc;
-        const T* pp = us + ((m + 1) & (NBUF - 1)) * PLANE + uc;
-        const T u0 = p0[0];
-        const T dx = p0[1] - p0[-1];
-        const T dy = p0[UXP] - p0[-UXP];
-        const T dz = pp[0] - pm[0];
-        const T hxx = (p0[1] + p0[-1]) - T(2) * u0;
-        const T hyy = (p0[UXP] + p0[-UXP]) - T(2) * u0;
-        const T hzz = (pp[0] + pm[0]) - T(2) * u0;
-        const T hxy = (p0[UXP + 1] - p0[UXP - 1]) - (p0[-UXP + 1] - p0[-UXP - 1]);
-        const T hxz = (pp[1] - pp[-1]) - (pm[1] - pm[-1]);
-        const T hyz = (pp[UXP] - pp[-UXP]) - (pm[UXP] - pm[-UXP]);
-        Cot<T> ct;
-        // FP64 re-evaluation of D from the exact float inputs (float path only)
-        auto refine = [&]() -> T { return (T)discriminant_fp64_at<T>(in.C.R, in.C.well, pm, p0, pp, UXP, cind); };
-        if (MODE == MODE_ENERGY) {
-            se.add(voxel_eval<T, false>(in.C, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ct, refine));
-            continue;
+        const double cind = (MODE == MODE_STEP) ? in.scal[S_C] : 0.0;
+        const T cin = (T)cind;
+
+        // ---- per-column state carried from plane to plane
+        T accC = 0, zdn = 0, hxz2 = 0, hyz2 = 0, hxz1 = 0, hyz1 = 0;
+        T fx1 = 0, fx2 = 0, fy1 = 0, fy2 = 0, fxy = 0, cpend = 0;
+
+        T* optr = in.out + (size_t)z0 * plane_g + (size_t)gy * nx + gx;   // planes gathered in order
+        auto gather = [&](int kz) {
+            const T* F = fs + (kz & 1) * 5 * NEXT;
+            const int c = fc;
+            const T g = cpend + F[c - 1] + F[NEXT + c + 1] + F[2 * NEXT + c - EX] + F[3 * NEXT + c + EX]
+                      + (F[4 * NEXT + c - 1 - EX] - F[4 * NEXT + c - 1 + EX])
+                      - (F[4 * NEXT + c + 1 - EX] - F[4 * NEXT + c + 1 + EX]);
+            const T ag = g < T(0) ? -g : g;
+            sg += g;
+            sag += ag;
+            gmax = ag > gmax ? ag : gmax;
+            if (MODE == MODE_GRAD) {
+                *optr = g;
+            } else {
+                const T u0 = us[(kz & (NBUF - 1)) * PLANE + uc] + cin;
+                const T v = fma_(-in.tau, g, u0);
+                *optr = v;
+                su += u0;
+                sout += v;
+            }
+            optr += plane_g;
+        };
+
+        for (int p = z0 - 2; p <= z0 + PD - 1; ++p) issue(p);
+
+        for (int m = z0 - 1; m <= zend; ++m) {
+            cp_async_wait<PD - 1>();
+            __syncthreads();
+            if (MODE != MODE_ENERGY && m - 2 >= z0 && interior) gather(m - 2);
+            issue(m + 1 + PD);
+            if (!active) continue;
+            const bool own = (m >= z0 && m < zend);
+            if (MODE == MODE_ENERGY && !(own && interior)) continue;
+            const T* pm = us + ((m - 1) & (NBUF - 1)) * PLANE + uc;
+            const T* p0 = us + (m & (NBUF - 1)) * PLANE + uc;
+            const T* pp = us + ((m + 1) & (NBUF - 1)) * PLANE + uc;
+            const T u0 = p0[0];
+            const T dx = p0[1] - p0[-1];
+            const T dy = p0[UXP] - p0[-UXP];
+            const T dz = pp[0] - pm[0];
+            const T hxx = (p0[1] + p0[-1]) - T(2) * u0;
+            const T hyy = (p0[UXP] + p0[-UXP]) - T(2) * u0;
+            const T hzz = (pp[0] + pm[0]) - T(2) * u0;
+            const T hxy = (p0[UXP + 1] - p0[UXP - 1]) - (p0[-UXP + 1] - p0[-UXP - 1]);
+            const T hxz = (pp[1] - pp[-1]) - (pm[1] - pm[-1]);
+            const T hyz = (pp[UXP] - pp[-UXP]) - (pm[UXP] - pm[-UXP]);
+            Cot<T> ctv;
+            // FP64 re-evaluation of D from the exact float inputs (float path only)
+            auto refine = [&]() -> T { return (T)discriminant_fp64_at<T>(in.C.R, in.C.well, pm, p0, pp, UXP, cind); };
+            if (MODE == MODE_ENERGY) {
+                se += voxel_eval<T, false>(in.C, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ctv, refine);
+                continue;
+            }
+            const T e = voxel_eval<T, true>(in.C, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ctv, refine);
+            if (own && interior) se += e;
+            // transposed-stencil pieces of this voxel (see the gather):
+            //   x/y first+second differences read from the left/right neighbour,
+            //   z pieces from the planes below/above, the centre term stays here
+            const T X1 = ctv.dx + ctv.hxx, X2 = ctv.hxx - ctv.dx;
+            const T Y1 = ctv.dy + ctv.hyy, Y2 = ctv.hyy - ctv.dy;
+            const T zd = ctv.dz + ctv.hzz, zu = ctv.hzz - ctv.dz;
+            const T cpart = ctv.u - T(2) * (ctv.hxx + ctv.hyy + ctv.hzz);
+            if (m - 1 >= z0) {   // plane m-1 is complete: publish its x/y fields
+                cpend = accC + zu;
+                const T dxz = hxz2 - ctv.hxz, dyz = hyz2 - ctv.hyz;
+                T* F = fs + ((m - 1) & 1) * 5 * NEXT + fc;
+                F[0] = fx1 + dxz;
+                F[NEXT] = fx2 - dxz;
+                F[2 * NEXT] = fy1 + dyz;
+                F[3 * NEXT] = fy2 - dyz;
+                F[4 * NEXT] = fxy;
+            }
+            accC = cpart + zdn;
+            zdn = zd;
+            hxz2 = hxz1; hyz2 = hyz1;
+            hxz1 = ctv.hxz; hyz1 = ctv.hyz;
+            fx1 = X1; fx2 = X2; fy1 = Y1; fy2 = Y2; fxy = ctv.hxy;
         }
-        const T e = voxel_eval<T, true>(in.C, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ct, refine);
-        if (own && interior) se.add(e);
-        // transposed-stencil pieces of this voxel (see the gather):
-        //   x/y first+second differences read from the left/right neighbour,
-        //   z pieces from the planes below/above, the centre term stays here
-        const T X1 = ct.dx + ct.hxx, X2 = ct.hxx - ct.dx;
-        const T Y1 = ct.dy + ct.hyy, Y2 = ct.hyy - ct.dy;
-        const T zd = ct.dz + ct.hzz, zu = ct.hzz - ct.dz;
-        const T cpart = ct.u - T(2) * (ct.hxx + ct.hyy + ct.hzz);
-        if (m - 1 >= z0) {   // plane m-1 is complete: publish its x/y fields
-            cpend = accC + zu;
-            const T dxz = hxz2 - ct.hxz, dyz = hyz2 - ct.hyz;
-            T* F = fs + ((m - 1) & 1) * 5 * NEXT;
-            F[tid] = fx1 + dxz;
-            F[NEXT + tid] = fx2 - dxz;
-            F[2 * NEXT + tid] = fy1 + dyz;
-            F[3 * NEXT + tid] = fy2 - dyz;
-            F[4 * NEXT + tid] = fxy;
+        if (MODE != MODE_ENERGY) {
+            __syncthreads();
+            if (interior) gather(zend - 1);
         }
-        accC = cpart + zdn;
-        zdn = zd;
-        hxz2 = hxz1; hyz2 = hyz1;
-        hxz1 = ct.hxz; hyz1 = ct.hyz;
-        fx1 = X1; fx2 = X2; fy1 = Y1; fy2 = Y2; fxy = ct.hxy;
+        cp_async_wait<0>();
+        __syncthreads();   // the ring and the field planes are reused by the next run
     }
-    if (MODE != MODE_ENERGY) {
-        __syncthreads();
-        if (interior) gather(zend - 1);
-    }
-    cp_async_wait<0>();
-
-    double v[NPART];
-    v[P_E] = se.get();
-    v[P_U] = su.get();
-    v[P_G] = sg.get();
-    v[P_AG] = sag.get();
-    v[P_GMAX] = (double)gmax;
-    v[P_OUT] = sout.get();
-    grid_finish(in, local, MODE, v, red);
+    if (cur >= 0) flush();
 }
 
 // ------------------------------------------------------------ small kernels
@@ -239,12 +266,18 @@ __global__ void k_add_offset(T* __restrict__ out, const T* __restrict__ in, long
 }
 
 // Batched form: blockIdx.y selects the problem; out[i] += its offset.
-__global__ void k_add_offset_batch(const Inst<float>* __restrict__ insts)
+struct OffsetLaunch {
+    int n;
+    float* out[BATCH_MAX];
+    const double* c[BATCH_MAX];
+    long len[BATCH_MAX];
+};
+__global__ void k_add_offset_batch(const __grid_constant__ OffsetLaunch L)
 {
-    const Inst<float>& in = insts[blockIdx.y];
-    const long n = (long)in.nx * in.ny * in.nz;
-    const float off = (float)in.scal[S_C];
-    float* out = in.out;
+    const int k = blockIdx.y;
+    const float off = (float)(*L.c[k]);
+    float* out = L.out[k];
+    const long n = L.len[k];
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
         out[i] += off;
 }
@@ -321,49 +354,106 @@ size_t fused_smem_bytes(int elem_size, int tile_y)
 {
     const int plane = tile_y == 8 ? Tile<8>::PLANE : Tile<16>::PLANE;
     const int next = tile_y == 8 ? Tile<8>::NEXT : Tile<16>::NEXT;
-    return (size_t)elem_size * ((size_t)NBUF * plane + 2 * 5 * (size_t)next);
+    const int nt = tile_y == 8 ? Tile<8>::NT : Tile<16>::NT;
+    return (size_t)elem_size * ((size_t)NBUF * plane + 2 * 5 * (size_t)next) + sizeof(float) * NPART * (size_t)nt;
 }
 
-template <typename T, int TY, int MODE, bool BATCH>
-static cudaError_t launch_one(const Inst<T>& in, const Inst<T>* insts, int n_inst, int blocks, cudaStream_t s)
+template <typename T, int TY, int MODE, int MAXI>
+static cudaError_t launch_one(const Launch<T, MAXI>& L, int blocks, cudaStream_t s)
 {
     const size_t smem = fused_smem_bytes(sizeof(T), TY);
     static bool attr_done = false;   // per instantiation; idempotent, so a race is harmless
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<T, TY, MODE, BATCH>,
+        cudaError_t e = cudaFuncSetAttribute(k_fused<T, TY, MODE, MAXI>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    k_fused<T, TY, MODE, BATCH><<<blocks, Tile<TY>::NT, smem, s>>>(in, insts, n_inst);
+    k_fused<T, TY, MODE, MAXI><<<blocks, Tile<TY>::NT, smem, s>>>(L);
     return cudaGetLastError();
 }
 
-template <typename T, int TY>
-static cudaError_t launch_mode(const Inst<T>& in, int mode, cudaStream_t s)
+static int sm_count_current()
 {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        (void)cudaGetLastError();
+        n = 152;
+    }
+    return n;
+}
+
+long long fused_grid(long long units, int max_run)
+{
+    long long G = sm_count_current();                   // one CTA per SM
+    if (max_run > 0 && (units + max_run - 1) / max_run > G) G = (units + max_run - 1) / max_run;
+    return G < units ? G : units;
+}
+
+// Split the launch's work units evenly over G CTAs and record, per problem,
+// the first CTA that holds a partial of it and how many do.
+template <typename T, int MAXI>
+static void plan(Launch<T, MAXI>& L, int tile_y, int max_run)
+{
+    long long W = 0;
+    for (int k = 0; k < L.n; ++k) {
+        Inst<T>& in = L.inst[k];
+        in.tiles_x = (in.nx + TX - 1) / TX;
+        in.tiles_y = (in.ny + tile_y - 1) / tile_y;
+        in.unit_base = W;
+        W += (long long)in.tiles_x * in.tiles_y * in.nz;
+    }
+    const long long G = fused_grid(W, max_run);
+    L.units = W;
+    L.grid = (int)G;
+    for (int k = 0; k < L.n; ++k) {
+        Inst<T>& in = L.inst[k];
+        const long long a = in.unit_base, b = a + (long long)in.tiles_x * in.tiles_y * in.nz - 1;
+        const int c0 = (int)(((a + 1) * G - 1) / W), c1 = (int)(((b + 1) * G - 1) / W);
+        in.first_block = c0;
+        in.nblocks = c1 - c0 + 1;
+    }
+}
+
+template <typename T, int TY>
+static cudaError_t launch_mode(const Inst<T>& in, int mode, int max_run, cudaStream_t s)
+{
+    Launch<T, 1> L;
+    L.n = 1;
+    L.inst[0] = in;
+    plan(L, TY, max_run);
     switch (mode) {
-    case MODE_ENERGY: return launch_one<T, TY, MODE_ENERGY, false>(in, nullptr, 1, in.nblocks, s);
-    case MODE_GRAD: return launch_one<T, TY, MODE_GRAD, false>(in, nullptr, 1, in.nblocks, s);
-    case MODE_STEP: return launch_one<T, TY, MODE_STEP, false>(in, nullptr, 1, in.nblocks, s);
+    case MODE_ENERGY: return launch_one<T, TY, MODE_ENERGY, 1>(L, L.grid, s);
+    case MODE_GRAD: return launch_one<T, TY, MODE_GRAD, 1>(L, L.grid, s);
+    case MODE_STEP: return launch_one<T, TY, MODE_STEP, 1>(L, L.grid, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
 template <typename T>
-cudaError_t launch_fused(const Inst<T>& in, int mode, int tile_y, cudaStream_t s)
+cudaError_t launch_fused(const Inst<T>& in, int mode, int tile_y, int max_run, cudaStream_t s)
 {
-    return tile_y == 8 ? launch_mode<T, 8>(in, mode, s) : launch_mode<T, 16>(in, mode, s);
+    return tile_y == 8 ? launch_mode<T, 8>(in, mode, max_run, s) : launch_mode<T, 16>(in, mode, max_run, s);
 }
-template cudaError_t launch_fused<float>(const Inst<float>&, int, int, cudaStream_t);
-template cudaError_t launch_fused<double>(const Inst<double>&, int, int, cudaStream_t);
+template cudaError_t launch_fused<float>(const Inst<float>&, int, int, int, cudaStream_t);
+template cudaError_t launch_fused<double>(const Inst<double>&, int, int, int, cudaStream_t);
 
-cudaError_t launch_fused_batch(const Inst<float>* insts_dev, int n_inst, int total_blocks, int tile_y,
-                               cudaStream_t s)
+// Batches of up to BATCH_MAX problems go in one launch (their descriptors
+// travel as kernel parameters); larger batches take one launch per group.
+cudaError_t launch_fused_batch(const Inst<float>* insts, int n_inst, int tile_y, int max_run, cudaStream_t s)
 {
-    Inst<float> dummy{};
-    return tile_y == 8 ? launch_one<float, 8, MODE_STEP, true>(dummy, insts_dev, n_inst, total_blocks, s)
-                       : launch_one<float, 16, MODE_STEP, true>(dummy, insts_dev, n_inst, total_blocks, s);
+    static Launch<float, BATCH_MAX> L;   // host staging; the launch copies it
+    for (int g0 = 0; g0 < n_inst; g0 += BATCH_MAX) {
+        const int cnt = n_inst - g0 < BATCH_MAX ? n_inst - g0 : BATCH_MAX;
+        L.n = cnt;
+        for (int k = 0; k < cnt; ++k) L.inst[k] = insts[g0 + k];
+        plan(L, tile_y, max_run);
+        cudaError_t e = tile_y == 8 ? launch_one<float, 8, MODE_STEP, BATCH_MAX>(L, L.grid, s)
+                                    : launch_one<float, 16, MODE_STEP, BATCH_MAX>(L, L.grid, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename T>
@@ -378,13 +468,25 @@ cudaError_t launch_add_offset(T* out, const T* in, long n, const double* c, cuda
 template cudaError_t launch_add_offset<float>(float*, const float*, long, const double*, cudaStream_t);
 template cudaError_t launch_add_offset<double>(double*, const double*, long, const double*, cudaStream_t);
 
-cudaError_t launch_add_offset_batch(const Inst<float>* insts_dev, int n_inst, cudaStream_t s)
+cudaError_t launch_add_offset_batch(const Inst<float>* insts, int n_inst, cudaStream_t s)
 {
-    if (n_inst <= 0) return cudaSuccess;
-    int bx = (152 * 8 + n_inst - 1) / n_inst;
-    if (bx < 8) bx = 8;
-    k_add_offset_batch<<<dim3(bx, n_inst), 256, 0, s>>>(insts_dev);
-    return cudaGetLastError();
+    static OffsetLaunch L;
+    for (int g0 = 0; g0 < n_inst; g0 += BATCH_MAX) {
+        const int cnt = n_inst - g0 < BATCH_MAX ? n_inst - g0 : BATCH_MAX;
+        L.n = cnt;
+        for (int k = 0; k < cnt; ++k) {
+            const Inst<float>& in = insts[g0 + k];
+            L.out[k] = in.out;
+            L.c[k] = in.scal + S_C;
+            L.len[k] = (long)in.nx * in.ny * in.nz;
+        }
+        int bx = (152 * 8 + cnt - 1) / cnt;
+        if (bx < 8) bx = 8;
+        k_add_offset_batch<<<dim3(bx, cnt), 256, 0, s>>>(L);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename T>

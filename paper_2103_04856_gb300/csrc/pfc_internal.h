@@ -52,8 +52,9 @@ struct Inst {
     int zc;              // planes per z-chunk
     int tiles_x, tiles_y, chunks_z;
     int vec;             // 1: 16-byte chunked loads are legal
-    int first_block;     // index of this problem's first CTA in the launch
-    int nblocks;
+    int first_block;     // plain path: unused; fused: first CTA holding a partial of this problem
+    int nblocks;         // number of FP64 partial slots (CTAs) of this problem in the launch
+    long long unit_base; // fused: first work unit (one plane of one column tile) of this problem
     Coef<T> C;
     T tau;
     double inv_N;
@@ -64,18 +65,36 @@ struct Inst {
     int trace_cap;
 };
 
+// Problems of one fused launch, passed by value as a kernel parameter (the
+// descriptors are read from the constant bank, uniformly per CTA).
+constexpr int BATCH_MAX = 64;
+// Work is split in units of one z-plane of one 32 x TY column tile,
+// enumerated problem by problem, tile by tile, plane by plane; CTA b of G
+// takes units [b W / G, (b+1) W / G).
+template <typename T, int MAXI>
+struct Launch {
+    int n;
+    int grid;            // G
+    long long units;     // W
+    Inst<T> inst[MAXI];
+};
+
 template <typename T>
 Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well);
 
 // fused kernels (pfc_fused.cu)
+// max_run > 0 caps the planes one CTA processes per problem (more CTAs);
+// 0 = one CTA per SM with equal shares.  Partial slots needed per problem:
+// at most fused_grid(units of the launch, max_run).
 template <typename T>
-cudaError_t launch_fused(const Inst<T>& in, int mode, int tile_y, cudaStream_t s);
-cudaError_t launch_fused_batch(const Inst<float>* insts_dev, int n_inst, int total_blocks,
-                               int tile_y, cudaStream_t s);
+cudaError_t launch_fused(const Inst<T>& in, int mode, int tile_y, int max_run, cudaStream_t s);
+// `insts`: host array of descriptors (copied into the launch parameters)
+cudaError_t launch_fused_batch(const Inst<float>* insts, int n_inst, int tile_y, int max_run, cudaStream_t s);
+long long fused_grid(long long units, int max_run);
 template <typename T>
 cudaError_t launch_add_offset(T* out, const T* in, long n, const double* c, cudaStream_t s);
-// out += scal[S_C] for every problem of a batch, in place, one launch
-cudaError_t launch_add_offset_batch(const Inst<float>* insts_dev, int n_inst, cudaStream_t s);
+// out += scal[S_C] for every problem of a batch (host descriptors), in place
+cudaError_t launch_add_offset_batch(const Inst<float>* insts, int n_inst, cudaStream_t s);
 template <typename T>
 cudaError_t launch_curvatures(const T* u, T* k1, T* k2, int nx, int ny, int nz, const Coef<T>& C,
                               double eps, cudaStream_t s);
