@@ -136,6 +136,26 @@ pfc_status pfc_batch_step(pfc_batch* batch, const void* const* u_in, void* const
 pfc_status pfc_batch_timing(pfc_batch* batch, int enable);
 pfc_status pfc_batch_last_timing(pfc_batch* batch, float* step_ms, float* sweep_ms);
 
+/* pfc_energy_and_grad without any device allocation, for callers that may not
+ * call cudaMalloc/cudaFree (graph-capture regions, host callbacks, plugins in
+ * a process that owns the device's memory budget, loops that must not take
+ * the allocator's implicit device-wide synchronisation).  The paper has no
+ * counterpart: this is an interface convenience.
+ *  - prob: the problem (impl must be PFC_IMPL_FUSED); u, g: caller-owned
+ *    device fields as for pfc_energy_and_grad; E_host may be NULL (then the
+ *    call only enqueues work).
+ *  - Scratch: a static device array in the library (49,256 bytes, held by
+ *    every GPU that loads the library until the process exits) with room for
+ *    1024 CTAs of FP64 partial sums; a problem that would need more CTAs
+ *    (only possible with a small tile_z) returns PFC_EINVAL.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls share the one array: calls that overlap on the GPU (two
+ *    streams, or two host threads) race and give wrong results.  Serialise
+ *    them, e.g. on one stream. */
+pfc_status pfc_energy_and_grad_noalloc(const pfc_problem* prob, const void* u, void* g, double* E_host,
+                                       pfc_stream stream);
+
 /* eq. redundant: b = (h2, H0, k1, alpha, kappa1_0, beta, kappa2_0) expanded
  * into a = (a20, a11, a02, a10, a01, a00).  Host only. */
 pfc_status pfc_b_to_a(const double b[7], double a_out[6]);

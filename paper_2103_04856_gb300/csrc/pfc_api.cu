@@ -26,6 +26,11 @@ static pfc_status fail(pfc_status s, const char* fmt, ...)
     return s;
 }
 
+namespace pfc {
+// lets other translation units of the library report through pfc_last_error
+void set_last_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+}  // namespace pfc
+
 #define PFC_CU(call)                                                                                 \
     do {                                                                                             \
         cudaError_t e_ = (call);                                                                     \

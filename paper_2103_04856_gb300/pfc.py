@@ -31,7 +31,8 @@ PFC_IMPL_FUSED, PFC_IMPL_PLAIN = 0, 1
 # every symbol include/pfc.h declares
 EXPORTED = ("pfc_create", "pfc_destroy", "pfc_energy", "pfc_energy_and_grad", "pfc_step", "pfc_run",
             "pfc_curvatures", "pfc_batch_create", "pfc_batch_destroy", "pfc_batch_run", "pfc_batch_step",
-            "pfc_batch_timing", "pfc_batch_last_timing", "pfc_b_to_a", "pfc_status_string", "pfc_last_error")
+            "pfc_batch_timing", "pfc_batch_last_timing", "pfc_energy_and_grad_noalloc", "pfc_b_to_a",
+            "pfc_status_string", "pfc_last_error")
 
 
 class PfcError(RuntimeError):
@@ -126,6 +127,7 @@ def load_library():
             "pfc_batch_timing": ([vp, ctypes.c_int], ctypes.c_int),
             "pfc_batch_last_timing": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
                                       ctypes.c_int),
+            "pfc_energy_and_grad_noalloc": ([P, vp, vp, dp, vp], ctypes.c_int),
             "pfc_b_to_a": ([dp, dp], ctypes.c_int),
             "pfc_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "pfc_last_error": ([], ctypes.c_char_p),
@@ -182,6 +184,17 @@ def pfc_b_to_a(b) -> np.ndarray:
     _check(load_library().pfc_b_to_a(b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                      a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return a
+
+
+def energy_and_grad_noalloc(prob: Problem, u: torch.Tensor, g: torch.Tensor, stream=None, sync=True):
+    """pfc_energy_and_grad_noalloc: the fused energy and gradient with no
+    device allocation at all (for callers that may not allocate); g is filled
+    in place.  Calls that overlap on the GPU race (one static scratch array)."""
+    E = ctypes.c_double()
+    _check(load_library().pfc_energy_and_grad_noalloc(ctypes.byref(prob._c()), _field(u, prob, "u"),
+                                                      _field(g, prob, "g"), ctypes.byref(E) if sync else None,
+                                                      _stream(stream)))
+    return E.value if sync else None
 
 
 class Context:
