@@ -277,16 +277,22 @@ class Batch:
         except Exception:
             pass
 
-    def run(self, fields, nsteps: int, taus, trace: bool = True, stream=None):
+    def run(self, fields, nsteps: int, taus, trace: bool = True, stream=None, allow_nonfinite: bool = False):
+        """Advance every field in place by nsteps steps.  Returns the trace
+        (n, nsteps, 5).  With allow_nonfinite, a problem that diverged does not
+        raise: (trace, finite) is returned, finite[k] False for those problems
+        (read from their trace rows)."""
         if len(fields) != len(self.probs):
             raise ValueError("one field per problem")
         ptrs = (ctypes.c_void_p * len(fields))(*[_field(f, p, f"u[{k}]").value
                                                  for k, (f, p) in enumerate(zip(fields, self.probs))])
         taus = np.ascontiguousarray(np.broadcast_to(np.asarray(taus, dtype=np.float64), (len(fields),)))
-        tr = np.empty((len(fields), max(int(nsteps), 0), 5), dtype=np.float64) if trace else None
+        tr = np.empty((len(fields), max(int(nsteps), 0), 5), dtype=np.float64) if (trace or allow_nonfinite) else None
         rc = self._lib.pfc_batch_run(self._h, ptrs, int(nsteps), taus.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                     tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if trace else None,
+                                     tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if tr is not None else None,
                                      _stream(stream))
+        if allow_nonfinite and rc in (PFC_OK, PFC_ENONFINITE):
+            return tr, np.all(np.isfinite(tr), axis=(1, 2))
         _check(rc)
         return tr
 
