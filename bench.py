@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile-y", type=int, default=0, help="0 = library default")
+    ap.add_argument("--max-run", type=int, default=0, help="cap on planes per CTA run (0 = equal shares)")
     return ap.parse_args()
 
 
@@ -253,7 +255,8 @@ def main():
     from paper_2103_04856_gb300 import pfc
 
     insts = I.validation_set_128()
-    probs = [pfc.Problem.from_shape(i.shape, eps=i.eps, a=i.a, prec="fp32") for i in insts]
+    probs = [pfc.Problem.from_shape(i.shape, eps=i.eps, a=i.a, prec="fp32", tile_y=args.tile_y, tile_z=args.max_run)
+             for i in insts]
     host = [i.field().astype(np.float32) for i in insts]
     taus = [i.tau for i in insts]
     A = [torch.tensor(h, device="cuda") for h in host]

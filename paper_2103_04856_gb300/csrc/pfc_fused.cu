@@ -16,6 +16,8 @@
 // cotangents are recomputed per tile instead of stored.  The energy and the
 // gradient sums are reduced per CTA in FP64 and combined by the last CTA of
 // the problem (pfc_device.cuh, grid_finish).
+#include <type_traits>
+
 #include "pfc_device.cuh"
 
 namespace pfc {
@@ -87,7 +89,15 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
     if (warp < TY) { ey = warp + 1; ex = lane + 1; }
     else if (warp == TY) { ey = 0; ex = lane + 1; }
     else if (warp == TY + 1) { ey = TY + 1; ex = lane + 1; }
-    else { ex = warp == TY + 2 ? 0 : EX - 1; ey = lane; active = lane < TY + 2; }
+    else {   // halo columns: lanes past the last row duplicate it and never publish
+        ex = warp == TY + 2 ? 0 : EX - 1;
+        ey = lane < TY + 2 ? lane : TY + 1;
+        active = lane < TY + 2;
+    }
+    const bool rowwarp = warp < TY;               // the warps that gather
+    // warps whose threads copy u planes (vector path: one 16-byte chunk per
+    // thread; element path: every warp)
+    constexpr int LOADWARPS = (UY * NCH + 31) / 32;
     const int uc = (ey + 1) * UXP + ex + 3;       // this column in a u plane
     const int fc = ey * EX + ex;                  // this column in a field plane
 
@@ -117,6 +127,10 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
                 if (L.inst[mid].unit_base <= U) k = mid; else hi = mid - 1;
             }
         }
+        if (k != cur) {
+            if (cur >= 0) flush();
+            cur = k;
+        }
         const Inst<T>& in = L.inst[k];
         const int nx = in.nx, ny = in.ny, nz = in.nz;
         const long long rel = U - in.unit_base;
@@ -125,15 +139,12 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
         const long long run_end = min(Uend, in.unit_base + (long long)(ct + 1) * nz);
         const int zend = z0 + (int)(run_end - U);      // exclusive
         U = run_end;
-        if (k != cur) {
-            if (cur >= 0) flush();
-            cur = k;
-        }
         const int x0 = (ct % in.tiles_x) * TX, y0 = (ct / in.tiles_x) * TY;
         const int plast = zend + 1;                    // last u plane needed
         const size_t plane_g = (size_t)nx * ny;
         const int gx = x0 + ex - 1, gy = y0 + ey - 1;
         const bool interior = warp < TY && gx < nx && gy < ny;
+        const bool loader = !in.vec || warp < LOADWARPS;
 
         // ---- loads: every u plane of the tile, periodic in x, y and z
         int ld_off = -1, ld_dst = 0;
@@ -144,6 +155,7 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
         }
         int pz = wrapi(z0 - 2, nz);                // planes are issued in increasing order
         auto issue = [&](int p) {
+            if (!loader) return;                   // warp-uniform: only loading warps copy, commit and wait
             if (p <= plast) {
                 T* dst = us + (p & (NBUF - 1)) * PLANE;
                 const T* src = in.u + (size_t)pz * plane_g;
@@ -168,38 +180,45 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
         T fx1 = 0, fx2 = 0, fy1 = 0, fy2 = 0, fxy = 0, cpend = 0;
 
         T* optr = in.out + (size_t)z0 * plane_g + (size_t)gy * nx + gx;   // planes gathered in order
-        auto gather = [&](int kz) {
+        auto gather = [&](int kz) {   // row warps; lanes past a ragged edge only skip the store
             const T* F = fs + (kz & 1) * 5 * NEXT;
             const int c = fc;
-            const T g = cpend + F[c - 1] + F[NEXT + c + 1] + F[2 * NEXT + c - EX] + F[3 * NEXT + c + EX]
-                      + (F[4 * NEXT + c - 1 - EX] - F[4 * NEXT + c - 1 + EX])
-                      - (F[4 * NEXT + c + 1 - EX] - F[4 * NEXT + c + 1 + EX]);
+            const T gv = cpend + F[c - 1] + F[NEXT + c + 1] + F[2 * NEXT + c - EX] + F[3 * NEXT + c + EX]
+                       + (F[4 * NEXT + c - 1 - EX] - F[4 * NEXT + c - 1 + EX])
+                       - (F[4 * NEXT + c + 1 - EX] - F[4 * NEXT + c + 1 + EX]);
+            const T g = interior ? gv : T(0);
             const T ag = g < T(0) ? -g : g;
             sg += g;
             sag += ag;
             gmax = ag > gmax ? ag : gmax;
             if (MODE == MODE_GRAD) {
-                *optr = g;
+                if (interior) *optr = g;
             } else {
                 const T u0 = us[(kz & (NBUF - 1)) * PLANE + uc] + cin;
                 const T v = fma_(-in.tau, g, u0);
-                *optr = v;
-                su += u0;
-                sout += v;
+                if (interior) *optr = v;
+                su += interior ? u0 : T(0);
+                sout += interior ? v : T(0);
             }
             optr += plane_g;
         };
 
         for (int p = z0 - 2; p <= z0 + PD - 1; ++p) issue(p);
 
-        for (int m = z0 - 1; m <= zend; ++m) {
-            cp_async_wait<PD - 1>();
+        // One plane m of the march.  GATHER: write plane m-2; PUBLISH: plane
+        // m-1 is complete, publish its x/y fields; OWN: plane m is in the
+        // run (its energy counts).  All three are compile-time constants, so
+        // the steady state (all true) has no phase tests.
+        auto plane = [&](int m, auto GATHER, auto PUBLISH, auto OWN) {
+            constexpr bool kGather = decltype(GATHER)::value, kPublish = decltype(PUBLISH)::value;
+            constexpr bool kOwn = decltype(OWN)::value;
+            if (loader) cp_async_wait<PD - 1>();
             __syncthreads();
-            if (MODE != MODE_ENERGY && m - 2 >= z0 && interior) gather(m - 2);
+            if constexpr (kGather && MODE != MODE_ENERGY) {
+                if (rowwarp) gather(m - 2);
+            }
             issue(m + 1 + PD);
-            if (!active) continue;
-            const bool own = (m >= z0 && m < zend);
-            if (MODE == MODE_ENERGY && !(own && interior)) continue;
+            if constexpr (MODE == MODE_ENERGY && !kOwn) return;
             const T* pm = us + ((m - 1) & (NBUF - 1)) * PLANE + uc;
             const T* p0 = us + (m & (NBUF - 1)) * PLANE + uc;
             const T* pp = us + ((m + 1) & (NBUF - 1)) * PLANE + uc;
@@ -216,38 +235,54 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
             Cot<T> ctv;
             // FP64 re-evaluation of D from the exact float inputs (float path only)
             auto refine = [&]() -> T { return (T)discriminant_fp64_at<T>(in.C.R, in.C.well, pm, p0, pp, UXP, cind); };
-            if (MODE == MODE_ENERGY) {
-                se += voxel_eval<T, false>(in.C, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ctv, refine);
-                continue;
+            if constexpr (MODE == MODE_ENERGY) {
+                const T e = voxel_eval<T, false>(in.C, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ctv, refine);
+                se += interior ? e : T(0);
+                return;
+            } else {
+                const T e = voxel_eval<T, true>(in.C, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ctv, refine);
+                if constexpr (kOwn) se += interior ? e : T(0);
+                // transposed-stencil pieces of this voxel (see the gather):
+                //   x/y first+second differences read from the left/right neighbour,
+                //   z pieces from the planes below/above, the centre term stays here
+                const T X1 = ctv.dx + ctv.hxx, X2 = ctv.hxx - ctv.dx;
+                const T Y1 = ctv.dy + ctv.hyy, Y2 = ctv.hyy - ctv.dy;
+                const T zd = ctv.dz + ctv.hzz, zu = ctv.hzz - ctv.dz;
+                const T cpart = ctv.u - T(2) * (ctv.hxx + ctv.hyy + ctv.hzz);
+                if constexpr (kPublish) {   // plane m-1 is complete
+                    cpend = accC + zu;
+                    const T dxz = hxz2 - ctv.hxz, dyz = hyz2 - ctv.hyz;
+                    T* F = fs + ((m - 1) & 1) * 5 * NEXT + fc;
+                    if (active) {
+                        F[0] = fx1 + dxz;
+                        F[NEXT] = fx2 - dxz;
+                        F[2 * NEXT] = fy1 + dyz;
+                        F[3 * NEXT] = fy2 - dyz;
+                        F[4 * NEXT] = fxy;
+                    }
+                }
+                accC = cpart + zdn;
+                zdn = zd;
+                hxz2 = hxz1; hyz2 = hyz1;
+                hxz1 = ctv.hxz; hyz1 = ctv.hyz;
+                fx1 = X1; fx2 = X2; fy1 = Y1; fy2 = Y2; fxy = ctv.hxy;
             }
-            const T e = voxel_eval<T, true>(in.C, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ctv, refine);
-            if (own && interior) se += e;
-            // transposed-stencil pieces of this voxel (see the gather):
-            //   x/y first+second differences read from the left/right neighbour,
-            //   z pieces from the planes below/above, the centre term stays here
-            const T X1 = ctv.dx + ctv.hxx, X2 = ctv.hxx - ctv.dx;
-            const T Y1 = ctv.dy + ctv.hyy, Y2 = ctv.hyy - ctv.dy;
-            const T zd = ctv.dz + ctv.hzz, zu = ctv.hzz - ctv.dz;
-            const T cpart = ctv.u - T(2) * (ctv.hxx + ctv.hyy + ctv.hzz);
-            if (m - 1 >= z0) {   // plane m-1 is complete: publish its x/y fields
-                cpend = accC + zu;
-                const T dxz = hxz2 - ctv.hxz, dyz = hyz2 - ctv.hyz;
-                T* F = fs + ((m - 1) & 1) * 5 * NEXT + fc;
-                F[0] = fx1 + dxz;
-                F[NEXT] = fx2 - dxz;
-                F[2 * NEXT] = fy1 + dyz;
-                F[3 * NEXT] = fy2 - dyz;
-                F[4 * NEXT] = fxy;
-            }
-            accC = cpart + zdn;
-            zdn = zd;
-            hxz2 = hxz1; hyz2 = hyz1;
-            hxz1 = ctv.hxz; hyz1 = ctv.hyz;
-            fx1 = X1; fx2 = X2; fy1 = Y1; fy2 = Y2; fxy = ctv.hxy;
+        };
+        using Y = std::true_type;
+        using N = std::false_type;
+        plane(z0 - 1, N{}, N{}, N{});
+        plane(z0, N{}, N{}, Y{});
+        if (zend - z0 == 1) {
+            plane(z0 + 1, N{}, Y{}, N{});
+        } else {
+            plane(z0 + 1, N{}, Y{}, Y{});
+#pragma unroll 1
+            for (int m = z0 + 2; m < zend; ++m) plane(m, Y{}, Y{}, Y{});
+            plane(zend, Y{}, Y{}, N{});
         }
         if (MODE != MODE_ENERGY) {
             __syncthreads();
-            if (interior) gather(zend - 1);
+            if (rowwarp) gather(zend - 1);
         }
         cp_async_wait<0>();
         __syncthreads();   // the ring and the field planes are reused by the next run
