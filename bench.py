@@ -52,8 +52,10 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=20)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--tile-y", type=int, default=0, help="0 = library default")
-    ap.add_argument("--max-run", type=int, default=0, help="cap on planes per CTA run (0 = equal shares)")
+    ap.add_argument("--tile-y", type=int, default=0, help="0 = autotuned (or library default)")
+    ap.add_argument("--max-run", type=int, default=-1, help="cap on planes per CTA run (-1 = autotuned)")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 64-instance batch and 512^3 lines")
     return ap.parse_args()
 
 
@@ -230,6 +232,33 @@ def cpu_baseline_oracle():
             "sample": f"{reps} FP64 oracle step(s) of the 128^3 tanh sphere (2,097,152 voxels each), single thread"}
 
 
+def extra_workload(pfc, insts, flush, steps):
+    """Steady-state batched FP32 steps of another workload (L2 flushed before
+    each): voxel-steps/s and the sweep's share of HBM and FP32 peaks."""
+    import torch
+    probs = [pfc.Problem.from_shape(i.shape, eps=i.eps, a=i.a, prec="fp32") for i in insts]
+    A = [torch.tensor(i.field().astype(np.float32), device="cuda") for i in insts]
+    B = [torch.empty_like(a) for a in A]
+    vox = sum(a.numel() for a in A)
+    b = pfc.Batch(probs)
+    b.timing(True)
+    st, sw = [], []
+    for k in range(steps + 3):
+        flush.zero_()
+        b.step(A, B, [i.tau for i in insts])
+        x, y = b.last_timing()
+        if k >= 3:
+            st.append(x)
+            sw.append(y)
+        A, B = B, A
+    b.close()
+    ms, msw = float(np.mean(st)), float(np.mean(sw))
+    return {"workload": f"{len(insts)} problem(s), {vox} voxels", "value": vox / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms, "sweep_ms": msw,
+            "alu_frac": FLOPS_PER_VOXEL_STEP * vox / (msw * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+            "hbm_gbs": 8.0 * vox / (msw * 1e-3) / 1e9}
+
+
 # Algorithmic FP32 flops of one voxel-step, counted from the arithmetic (FMA =
 # 2): stencils 18, forward (eq. Feps) 86, local reverse mode 75,
 # transposed-stencil pieces 19, gather 9, update and sums 4.
@@ -255,8 +284,14 @@ def main():
     from paper_2103_04856_gb300 import pfc
 
     insts = I.validation_set_128()
-    probs = [pfc.Problem.from_shape(i.shape, eps=i.eps, a=i.a, prec="fp32", tile_y=args.tile_y, tile_z=args.max_run)
-             for i in insts]
+    launch = {"tile_y": args.tile_y, "max_run": max(args.max_run, 0), "source": "command line"}
+    if not args.no_autotune and args.tile_y == 0 and args.max_run < 0:
+        from paper_2103_04856_gb300 import autotune
+        best = autotune.tune([i.shape for i in insts], cache=None)
+        launch = {"tile_y": best["tile_y"], "max_run": best["max_run"], "source": "autotuned",
+                  "tried": [{k: r[k] for k in ("tile_y", "max_run", "sweep_ms")} for r in best["tried"]]}
+    probs = [pfc.Problem.from_shape(i.shape, eps=i.eps, a=i.a, prec="fp32", tile_y=launch["tile_y"],
+                                    tile_z=launch["max_run"]) for i in insts]
     host = [i.field().astype(np.float32) for i in insts]
     taus = [i.tau for i in insts]
     A = [torch.tensor(h, device="cuda") for h in host]
@@ -378,6 +413,11 @@ def main():
     if traffic is None:
         roofline["traffic_note"] = traffic_note
 
+    extra = None
+    if not args.no_extra:
+        extra = {"batch64_mixed": extra_workload(pfc, I.batch_instances(64), flush, steps=20),
+                 "membrane_512": extra_workload(pfc, [I.membrane_descent_512()], flush, steps=10)}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_oracle()
@@ -393,7 +433,7 @@ def main():
             "rel_energy_err_fp32_vs_fp64": rel_err, "mass_drift": mass_err,
             "fp64_plain": fp64,
             "speedup_vs_fp64_plain": (value / ws) / fp64["value"] if fp64 else None,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "launch": launch, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "other_workloads": extra,
             "gpu_launches": 2 * args.steps, "clocks": clocks.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)

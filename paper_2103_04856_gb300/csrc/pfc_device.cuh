@@ -57,38 +57,45 @@ struct Cot {
     T hxy, hxz, hyz;        // 4-point mixed differences
 };
 
-// D = 2||M||^2 - (Tr M)^2 in FP64 from raw stencil values that are exact in
-// FP64 (differences of float inputs), for the float path's refinement.
-__device__ __forceinline__ double discriminant_fp64(const CoefD& R, int well, double u0, double dx, double dy,
-                                                    double dz, double hxx, double hyy, double hzz, double hxy,
-                                                    double hxz, double hyz)
+// rho^2 D = 2||rho M||^2 - (Tr rho M)^2 in FP64 from raw stencil values that
+// are exact in FP64 (differences of float inputs), for the float path's
+// refinement; rho M = rho kd Hess + w G G^T needs no division.
+__device__ __forceinline__ double discriminant_rho2_fp64(const CoefD& R, int well, double u0, double dx, double dy,
+                                                         double dz, double hxx, double hyy, double hzz, double hxy,
+                                                         double hxz, double hyz, double* rho_out)
 {
     const double Gx = dx * R.sg, Gy = dy * R.sg, Gz = dz * R.sg;
     const double rho = fma(Gx, Gx, fma(Gy, Gy, fma(Gz, Gz, R.xi2)));
-    const double wp = well == 0 ? 2.0 * (u0 - u0 * u0) * (1.0 - 2.0 * u0) : u0 * u0 * u0 - u0;
-    const double wr = wp * R.inv_eps / rho;
-    const double wx = wr * Gx, wy = wr * Gy, wz = wr * Gz;
-    const double Mxx = fma(R.kd, hxx, wx * Gx), Myy = fma(R.kd, hyy, wy * Gy), Mzz = fma(R.kd, hzz, wz * Gz);
-    const double Mxy = fma(R.ko, hxy, wx * Gy), Mxz = fma(R.ko, hxz, wx * Gz), Myz = fma(R.ko, hyz, wy * Gz);
+    const double w = (well == 0 ? 2.0 * (u0 - u0 * u0) * (1.0 - 2.0 * u0) : u0 * u0 * u0 - u0) * R.inv_eps;
+    const double ak = rho * R.kd, bk = rho * R.ko;
+    const double wx = w * Gx, wy = w * Gy, wz = w * Gz;
+    const double Mxx = fma(ak, hxx, wx * Gx), Myy = fma(ak, hyy, wy * Gy), Mzz = fma(ak, hzz, wz * Gz);
+    const double Mxy = fma(bk, hxy, wx * Gy), Mxz = fma(bk, hxz, wx * Gz), Myz = fma(bk, hyz, wy * Gz);
     const double Tr = Mxx + Myy + Mzz;
     const double S = Mxx * Mxx + Myy * Myy + Mzz * Mzz + 2.0 * (Mxy * Mxy + Mxz * Mxz + Myz * Myz);
+    *rho_out = rho;
     return 2.0 * S - Tr * Tr;
 }
 
-// Same, reading the 19 stencil inputs of a voxel from three u planes (pm, p0,
-// pp point at the voxel; `pitch` is the row pitch).  Kept out of line: it
-// runs for few voxels and must not add registers to the float hot path.
+// D for the voxel whose 19 stencil inputs sit in three u planes (pm, p0, pp
+// point at the voxel; `pitch` is the row pitch).  Kept out of line: it runs
+// for few voxels and must not add registers to the float hot path.
 template <typename T>
-__device__ __noinline__ double discriminant_fp64_at(const CoefD& R, int well, const T* pm, const T* p0,
-                                                    const T* pp, int pitch, double c)
+__device__ __noinline__ T discriminant_fp64_at(const CoefD& R, int well, const T* pm, const T* p0, const T* pp,
+                                               int pitch, double c)
 {
     auto d = [](T v) { return (double)v; };
     const double u0 = d(p0[0]);
-    return discriminant_fp64(
+    double rho;
+    const double Dr2 = discriminant_rho2_fp64(
         R, well, u0 + c, d(p0[1]) - d(p0[-1]), d(p0[pitch]) - d(p0[-pitch]), d(pp[0]) - d(pm[0]),
         (d(p0[1]) + d(p0[-1])) - 2.0 * u0, (d(p0[pitch]) + d(p0[-pitch])) - 2.0 * u0, (d(pp[0]) + d(pm[0])) - 2.0 * u0,
         (d(p0[pitch + 1]) - d(p0[pitch - 1])) - (d(p0[-pitch + 1]) - d(p0[-pitch - 1])),
-        (d(pp[1]) - d(pp[-1])) - (d(pm[1]) - d(pm[-1])), (d(pp[pitch]) - d(pp[-pitch])) - (d(pm[pitch]) - d(pm[-pitch])));
+        (d(pp[1]) - d(pp[-1])) - (d(pm[1]) - d(pm[-1])), (d(pp[pitch]) - d(pp[-pitch])) - (d(pm[pitch]) - d(pm[-pitch])),
+        &rho);
+    // the cancellation is resolved; the division keeps float's relative accuracy
+    const T r = (T)rho;
+    return (T)Dr2 / (r * r);
 }
 
 struct NoRefine {
@@ -101,10 +108,12 @@ struct NoRefine {
 //   hxy = u(x+1,y+1) - u(x+1,y-1) - u(x-1,y+1) + u(x-1,y-1), etc.
 //
 // float only: D is the difference of two O(||M||^2) numbers, so its FP32
-// error is about 2^-22 (2S + T^2).  Where that error is not small against
-// max(|D|, xi) -- near umbilics of strongly curved fields, and at the kink of
-// sqrt(D+) -- `refine()` recomputes D in FP64 from the exact float inputs
-// (rare on noise fields, never on the smooth validation shapes).
+// error is about 2^-22 (2S + T^2).  Only the sqrt(D+) terms, of weight
+// a3 = c3 T + c5 q (zero for polynomials symmetric in kappa1, kappa2), see
+// that error, and it matters only where it is more than 2^-6 of max(|D|, xi):
+// there `refine()` recomputes D in FP64 from the exact float inputs (about
+// one voxel in 10^4 on noise fields; the kernel's CTAs wait for the slowest
+// warp at every plane, so the test is kept tight).
 template <typename T, bool GRAD, class Refine = NoRefine>
 __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz, T hxx, T hyy,
                                         T hzz, T hxy, T hxz, T hyz, Cot<T>& ct, const Refine& refine = Refine())
@@ -142,16 +151,16 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
     const T t2 = Tr * Tr;
     const T t2e = fma_(Tr, Tr, -t2);
     T D = fma_(T(2), S, -t2) - t2e;
+    const T a3 = fma_(C.c3, Tr, C.c5 * q);              // c3 T + c5 q
     if (sizeof(T) == 4) {
         const T scale = fma_(T(2), S, t2);
-        if (scale > T(4096) * fmax(fabs(D), C.xi)) D = (T)refine();
+        if (a3 != T(0) && scale > T(65536) * fmax(fabs(D), C.xi)) D = (T)refine();
     }
     T P, Pp;
     softplus_(D, C, P, Pp);
     // float: one reciprocal square root gives both sqrt(P) and 1/(2 sqrt(P))
     const T rs = (sizeof(T) == 4 && P > T(0)) ? rsqrt_(P) : T(0);
     const T r = sizeof(T) == 4 ? P * rs : sqrt_(P);
-    const T a3 = fma_(C.c3, Tr, C.c5 * q);              // c3 T + c5 q
     const T e = fma_(C.c1, S, fma_(C.c2, t2, fma_(a3, r, fma_(C.c4 * q, Tr, C.c6 * g2))));
     if (!GRAD) return e;
 

@@ -234,7 +234,7 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
             const T hyz = (pp[UXP] - pp[-UXP]) - (pm[UXP] - pm[-UXP]);
             Cot<T> ctv;
             // FP64 re-evaluation of D from the exact float inputs (float path only)
-            auto refine = [&]() -> T { return (T)discriminant_fp64_at<T>(in.C.R, in.C.well, pm, p0, pp, UXP, cind); };
+            auto refine = [&]() -> T { return discriminant_fp64_at<T>(in.C.R, in.C.well, pm, p0, pp, UXP, cind); };
             if constexpr (MODE == MODE_ENERGY) {
                 const T e = voxel_eval<T, false>(in.C, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ctv, refine);
                 se += interior ? e : T(0);

@@ -1,0 +1,47 @@
+"""Autotuner: selection and caching logic on CPU (fake timings), a real tune
+on the GPU."""
+import json
+
+import pytest
+import torch
+
+
+def test_picks_fastest_and_caches(tmp_path, monkeypatch):
+    from paper_2103_04856_gb300 import autotune
+    fake = {(16, 0): 0.20, (8, 0): 0.25, (16, 64): 0.15, (16, 32): 0.30, (8, 64): 0.40}
+    calls = []
+
+    def timer(shapes, cand, steps=30, **kw):
+        calls.append((cand["tile_y"], cand["max_run"]))
+        return fake[(cand["tile_y"], cand["max_run"])]
+
+    monkeypatch.setattr(autotune, "time_candidate", timer)
+    cache = str(tmp_path / "cache.json")
+    best = autotune.tune([(64, 64, 64), (32, 32, 32)], cache=cache)
+    assert (best["tile_y"], best["max_run"]) == (16, 64)
+    assert len(calls) == len(autotune.CANDIDATES)
+    stored = json.load(open(cache))
+    assert list(stored.values())[0]["tile_y"] == 16
+    # second call: from the cache, no timing; the key ignores shape order
+    calls.clear()
+    again = autotune.tune([(32, 32, 32), (64, 64, 64)], cache=cache)
+    assert calls == [] and again["max_run"] == 64
+    # force re-times
+    autotune.tune([(32, 32, 32), (64, 64, 64)], cache=cache, force=True)
+    assert len(calls) == len(autotune.CANDIDATES)
+
+
+def test_rejects_fp64():
+    from paper_2103_04856_gb300 import autotune
+    with pytest.raises(ValueError):
+        autotune.tune([(8, 8, 8)], prec="fp64", cache=None)
+
+
+@pytest.mark.gpu
+def test_real_tune_small(tmp_path):
+    from paper_2103_04856_gb300 import autotune
+    shapes = [(32, 32, 64), (24, 40, 32)]
+    best = autotune.tune(shapes, cache=str(tmp_path / "c.json"), steps=3)
+    assert {"tile_y", "max_run", "sweep_ms"} <= set(best)
+    assert best["sweep_ms"] > 0 and len(best["tried"]) == len(autotune.CANDIDATES)
+    assert min(r["sweep_ms"] for r in best["tried"]) == best["sweep_ms"]
