@@ -20,6 +20,8 @@ Parity status per function (what pins it, in tests/test_oracle_pins.py):
   step / run       mass conservation, lambda = mean(g), descent of E
   curvatures       kappa1 + kappa2 = H^eps, kappa1 kappa2 <= K^eps, tanh sphere
   b_to_a           the eight printed rows of the paper's two parameter tables
+  hflow_*          (Alg. 1) mass = m0 exactly, blur moments and symmetry, the
+                   closed-form first Adam step, central differences of G(A)
 """
 from __future__ import annotations
 
@@ -35,6 +37,12 @@ _SRC = os.path.join(_HERE, "pf_oracle.c")
 _LIB = os.path.join(_HERE, "libpf_oracle.so")
 _lock = threading.Lock()
 _lib = None
+
+
+class _HFlow(ctypes.Structure):
+    _fields_ = [("m0", ctypes.c_double), ("lr", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("beta2", ctypes.c_double), ("adam_eps", ctypes.c_double), ("blur_sigma", ctypes.c_double),
+                ("blur_radius", ctypes.c_int)]
 
 
 class _Problem(ctypes.Structure):
@@ -74,6 +82,18 @@ def _load():
                 f = getattr(lib, name)
                 f.argtypes = args
                 f.restype = ctypes.c_int
+            H = ctypes.POINTER(_HFlow)
+            for name, args in [
+                ("pfo_blur", [P, H, D]),
+                ("pfo_hflow_field", [P, H, D, D]),
+                ("pfo_hflow_grad", [P, H, D, D, D]),
+                ("pfo_hflow_run", [P, H, D, D, D, ctypes.c_int, ctypes.POINTER(ctypes.c_int), D]),
+            ]:
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = ctypes.c_int
+            lib.pfo_gauss_weights.argtypes = [ctypes.c_double, ctypes.c_int, D]
+            lib.pfo_gauss_weights.restype = None
             lib.pfo_b_to_a.argtypes = [D, D]
             lib.pfo_b_to_a.restype = None
             _lib = lib
@@ -169,3 +189,60 @@ def b_to_a(b) -> np.ndarray:
     a = np.empty(6, dtype=np.float64)
     _load().pfo_b_to_a(_ptr(b), _ptr(a))
     return a
+
+
+# ---------------------------------------------------------------- Alg. 1
+
+def _flow(fp: dict) -> _HFlow:
+    sigma = float(fp.get("blur_sigma", 0.0))
+    R = int(fp.get("blur_radius", 0)) or (int(np.ceil(3.0 * sigma)) if sigma > 0 else 0)
+    return _HFlow(float(fp.get("m0", 0.0)), float(fp.get("lr", 1e-3)), float(fp.get("beta1", 0.9)),
+                  float(fp.get("beta2", 0.999)), float(fp.get("adam_eps", 1e-8)), sigma, R)
+
+
+def _A(A):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    if A.ndim != 4 or A.shape[0] != 3:
+        raise ValueError("A must be shaped (3, nz, ny, nx)")
+    return A
+
+
+def gauss_weights(sigma: float, R: int) -> np.ndarray:
+    w = np.empty(2 * R + 1)
+    _load().pfo_gauss_weights(float(sigma), int(R), _ptr(w))
+    return w
+
+
+def blur(a, p: dict, fp: dict) -> np.ndarray:
+    """k * a (periodic separable Gaussian of std fp['blur_sigma'])."""
+    a = _f64(a).copy()
+    _ok(_load().pfo_blur(ctypes.byref(_prob(a, p)), ctypes.byref(_flow(fp)), _ptr(a)), "blur")
+    return a
+
+
+def hflow_field(A, p: dict, fp: dict) -> np.ndarray:
+    """ut = k * (div A + m0) (Alg. 1, change of variable then blur)."""
+    A = _A(A)
+    ut = np.empty(A.shape[1:])
+    _ok(_load().pfo_hflow_field(ctypes.byref(_prob(ut, p)), ctypes.byref(_flow(fp)), _ptr(A), _ptr(ut)), "hflow_field")
+    return ut
+
+
+def hflow_grad(A, p: dict, fp: dict):
+    """(G, dG/dA) with G(A) = F_eps(k * (div A + m0))."""
+    A = _A(A)
+    gA = np.empty_like(A)
+    G = ctypes.c_double()
+    _ok(_load().pfo_hflow_grad(ctypes.byref(_prob(A[0], p)), ctypes.byref(_flow(fp)), _ptr(A), ctypes.byref(G),
+                               _ptr(gA)), "hflow_grad")
+    return G.value, gA
+
+
+def hflow_run(A, m, v, p: dict, fp: dict, nsteps: int, t: int = 0):
+    """nsteps Adam steps of Alg. 1; returns (A, m, v, t, trace[nsteps, 5])."""
+    A, m, v = _A(A).copy(), _A(m).copy(), _A(v).copy()
+    tt = ctypes.c_int(int(t))
+    tr = np.empty((max(int(nsteps), 0), 5))
+    _ok(_load().pfo_hflow_run(ctypes.byref(_prob(A[0], p)), ctypes.byref(_flow(fp)), _ptr(A), _ptr(m), _ptr(v),
+                              int(nsteps), ctypes.byref(tt), _ptr(tr)), "hflow_run")
+    return A, m, v, tt.value, tr

@@ -414,3 +414,146 @@ void pfo_b_to_a(const double b[7], double a[6])
     a[4] = -2.0 * h2 * H0 - 2.0 * be * k20;          /* kappa2          */
     a[5] = h2 * H0 * H0 + al * k10 * k10 + be * k20 * k20;
 }
+
+/* ------------------------------------------------------ Alg. 1: H^-1 flow */
+
+void pfo_gauss_weights(double sigma, int R, double* w)
+{
+    double s = 0.0;
+    for (int j = -R; j <= R; ++j) {
+        w[j + R] = exp(-(double)(j * j) / (2.0 * sigma * sigma));
+        s += w[j + R];
+    }
+    for (int j = 0; j <= 2 * R; ++j) w[j] /= s;
+}
+
+/* periodic 1-D convolution along axis `ax` (0 x, 1 y, 2 z) with weights w[0..2R] */
+static void convolve_axis(const pfo_problem* p, const double* in, double* out, int ax, const double* w, int R)
+{
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                double s = 0.0;
+                for (int j = -R; j <= R; ++j) {
+                    int xx = x + (ax == 0 ? j : 0), yy = y + (ax == 1 ? j : 0), zz = z + (ax == 2 ? j : 0);
+                    s += w[j + R] * in[vid(p, xx, yy, zz)];
+                }
+                out[vid(p, x, y, z)] = s;
+            }
+}
+
+/* k * a in place (separable Gaussian, x then y then z); no-op without blur */
+static int blur(const pfo_problem* p, const pfo_hflow* f, double* a)
+{
+    if (!(f->blur_sigma > 0.0)) return 0;
+    int R = f->blur_radius;
+    long N = (long)p->nx * p->ny * p->nz;
+    double* w = (double*)malloc(sizeof(double) * (2 * R + 1));
+    double* t = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!w || !t) { free(w); free(t); return -1; }
+    pfo_gauss_weights(f->blur_sigma, R, w);
+    convolve_axis(p, a, t, 0, w, R);
+    convolve_axis(p, t, a, 1, w, R);
+    convolve_axis(p, a, t, 2, w, R);
+    memcpy(a, t, sizeof(double) * (size_t)N);
+    free(w);
+    free(t);
+    return 0;
+}
+
+static int check_flow(const pfo_hflow* f)
+{
+    if (!f) return -1;
+    if (f->blur_sigma > 0.0 && f->blur_radius < 1) return -1;
+    return 0;
+}
+
+int pfo_blur(const pfo_problem* p, const pfo_hflow* f, double* a)
+{
+    if (check(p) || check_flow(f) || !a) return -1;
+    return blur(p, f, a);
+}
+
+int pfo_hflow_field(const pfo_problem* p, const pfo_hflow* f, const double* A, double* ut)
+{
+    if (check(p) || check_flow(f) || !A || !ut) return -1;
+    long N = (long)p->nx * p->ny * p->nz;
+    const int e[3][3] = { { 1, 0, 0 }, { 0, 1, 0 }, { 0, 0, 1 } };
+    /* eq. change_var: u = div A + m0 with periodic central differences */
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                double d = 0.0;
+                for (int c = 0; c < 3; ++c)
+                    d += (A[c * N + vid(p, x + e[c][0], y + e[c][1], z + e[c][2])]
+                          - A[c * N + vid(p, x - e[c][0], y - e[c][1], z - e[c][2])]) / (2.0 * p->h);
+                ut[vid(p, x, y, z)] = d + f->m0;
+            }
+    return blur(p, f, ut);   /* Alg. 1: small blur before the energy */
+}
+
+int pfo_hflow_grad(const pfo_problem* p, const pfo_hflow* f, const double* A, double* G, double* gA)
+{
+    if (check(p) || check_flow(f) || !A || !gA) return -1;
+    long N = (long)p->nx * p->ny * p->nz;
+    double* ut = (double*)malloc(sizeof(double) * (size_t)N);
+    double* g = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!ut || !g) { free(ut); free(g); return -1; }
+    double E = 0.0;
+    if (pfo_hflow_field(p, f, A, ut) || pfo_energy_and_grad(p, ut, &E, g) || blur(p, f, g)) {
+        free(ut); free(g); return -1;
+    }
+    /* the blur is symmetric and periodic, hence self-adjoint: g = k * dF/dut.
+     * dG/dA_c(j) = sum_i g_i du_i/dA_c(j) = (g(j - e_c) - g(j + e_c)) / 2h */
+    const int e[3][3] = { { 1, 0, 0 }, { 0, 1, 0 }, { 0, 0, 1 } };
+    for (int c = 0; c < 3; ++c)
+        for (int z = 0; z < p->nz; ++z)
+            for (int y = 0; y < p->ny; ++y)
+                for (int x = 0; x < p->nx; ++x)
+                    gA[c * N + vid(p, x, y, z)] = (g[vid(p, x - e[c][0], y - e[c][1], z - e[c][2])]
+                                                   - g[vid(p, x + e[c][0], y + e[c][1], z + e[c][2])]) / (2.0 * p->h);
+    if (G) *G = E;
+    free(ut);
+    free(g);
+    return 0;
+}
+
+int pfo_hflow_run(const pfo_problem* p, const pfo_hflow* f, double* A, double* m, double* v, int nsteps, int* t,
+                  double* trace)
+{
+    if (check(p) || check_flow(f) || !A || !m || !v || !t || nsteps < 0) return -1;
+    long N = (long)p->nx * p->ny * p->nz;
+    double* gA = (double*)malloc(sizeof(double) * 3 * (size_t)N);
+    double* ut = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!gA || !ut) { free(gA); free(ut); return -1; }
+    for (int s = 0; s < nsteps; ++s) {
+        double G = 0.0;
+        if (pfo_hflow_grad(p, f, A, &G, gA) || pfo_hflow_field(p, f, A, ut)) { free(gA); free(ut); return -1; }
+        *t += 1;
+        /* Adam (Kingma and Ba): moment updates with bias correction */
+        const double b1t = 1.0 - pow(f->beta1, *t), b2t = 1.0 - pow(f->beta2, *t);
+        nsum sa = { 0, 0 }, su = { 0, 0 };
+        double gmax = 0.0;
+        for (long i = 0; i < 3 * N; ++i) {
+            const double g = gA[i];
+            if (fabs(g) > gmax) gmax = fabs(g);
+            nsum_add(&sa, fabs(g));
+            m[i] = f->beta1 * m[i] + (1.0 - f->beta1) * g;
+            v[i] = f->beta2 * v[i] + (1.0 - f->beta2) * g * g;
+            const double mh = m[i] / b1t, vh = v[i] / b2t;
+            A[i] -= f->lr * mh / (sqrt(vh) + f->adam_eps);
+        }
+        for (long i = 0; i < N; ++i) nsum_add(&su, ut[i]);
+        if (trace) {
+            double* row = trace + 5 * (long)s;
+            row[0] = G;
+            row[1] = gmax;
+            row[2] = nsum_get(&sa) / (3.0 * (double)N);
+            row[3] = nsum_get(&su) / (double)N;
+            row[4] = (double)*t;
+        }
+    }
+    free(gA);
+    free(ut);
+    return 0;
+}

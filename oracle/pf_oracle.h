@@ -56,6 +56,32 @@ int pfo_run(const pfo_problem* p, double* u, int nsteps, double tau, double* tra
  * exact positive part and the xi-regularised |grad u|. */
 int pfo_curvatures(const pfo_problem* p, const double* u, double* k1, double* k2);
 
+/* ---- Alg. 1 (Sec. 4.1): H^-1 flow through u = div A + m0, blur, Adam ---- */
+typedef struct {
+    double m0;              /* mass: the mean of u                                        */
+    double lr, beta1, beta2, adam_eps;   /* Adam (Sec. 4.1: 1e-3, 0.9, 0.999, no decay)   */
+    double blur_sigma;      /* Gaussian blur std in voxels (Sec. 4.1: 2); 0 = no blur      */
+    int blur_radius;        /* taps on each side; the caller passes ceil(3 sigma)          */
+} pfo_hflow;
+
+/* Discrete Gaussian of std sigma, taps -R..R, normalised to sum 1: w[0..2R]. */
+void pfo_gauss_weights(double sigma, int R, double* w);
+
+/* a <- k * a in place (periodic separable Gaussian of the flow's sigma). */
+int pfo_blur(const pfo_problem* p, const pfo_hflow* f, double* a);
+
+/* ut = k * (div A + m0); A is 3 fields A_x, A_y, A_z of N voxels each (component-major). */
+int pfo_hflow_field(const pfo_problem* p, const pfo_hflow* f, const double* A, double* ut);
+
+/* G(A) = F_eps(k * (div A + m0)) and dG/dA (3 x N). */
+int pfo_hflow_grad(const pfo_problem* p, const pfo_hflow* f, const double* A, double* G, double* gA);
+
+/* nsteps Adam steps of Alg. 1 in place on A with moments m, v (3 x N) and the
+ * step counter *t (incremented per step).  trace (nsteps x 5, may be NULL):
+ * {G, max|dG/dA|, mean|dG/dA|, mean(ut), t}. */
+int pfo_hflow_run(const pfo_problem* p, const pfo_hflow* f, double* A, double* m, double* v, int nsteps, int* t,
+                  double* trace);
+
 /* Redundant parameters b = (h2, H0, k1, alpha, kappa1_0, beta, kappa2_0) of
  * eq. redundant expanded to the reduced coefficients a. */
 void pfo_b_to_a(const double b[7], double a[6]);
