@@ -136,6 +136,36 @@ pfc_status pfc_batch_step(pfc_batch* batch, const void* const* u_in, void* const
 pfc_status pfc_batch_timing(pfc_batch* batch, int enable);
 pfc_status pfc_batch_last_timing(pfc_batch* batch, float* step_ms, float* sweep_ms);
 
+/* ---- The paper's generator (Alg. 1, Sec. 4.1): the H^-1 flow of F_eps run as
+ * an L2 flow on a periodic vector field A through u = div A + m0 (eq.
+ * change_var), with a small Gaussian blur of u before the energy and Adam on
+ * A.  A, and the Adam moments m, v, are caller-owned device arrays of 3 x N
+ * values (component-major: A_x, A_y, A_z, each laid out like u) of the
+ * problem's type.  The mass of u = k * (div A + m0) is m0 exactly. */
+typedef struct {
+    double m0;              /* mean of u (Alg. 1: the mass)                             */
+    double lr, beta1, beta2, adam_eps;   /* Adam; Sec. 4.1: 1e-3, 0.9, 0.999, no decay  */
+    double blur_sigma;      /* Gaussian std in voxels (Sec. 4.1: 2); 0 = no blur        */
+    int32_t blur_radius;    /* taps per side; 0 = ceil(3 sigma); at most 32             */
+    int32_t reserved;
+} pfc_hflow_params;
+typedef struct pfc_hflow pfc_hflow;
+/* prob: grid, coefficients and precision (fused path); allocates 4 fields of
+ * scratch plus reduction slots. */
+pfc_status pfc_hflow_create(const pfc_problem* prob, const pfc_hflow_params* params, pfc_hflow** out);
+void pfc_hflow_destroy(pfc_hflow* flow);
+/* ut = k * (div A + m0): the phase field the flow evaluates (enqueue only). */
+pfc_status pfc_hflow_field(pfc_hflow* flow, const void* A, void* ut, pfc_stream stream);
+/* G(A) = F_eps(k * (div A + m0)) and gA = dG/dA (3 x N).  G_host may be NULL
+ * (then nothing is synchronised). */
+pfc_status pfc_hflow_grad(pfc_hflow* flow, const void* A, void* gA, double* G_host, pfc_stream stream);
+/* nsteps Adam steps of Alg. 1 in place on A, m, v; *t is Adam's step count
+ * (0 for fresh moments), advanced by nsteps.  trace_host (may be NULL):
+ * nsteps rows {G, max|dG/dA|, mean|dG/dA|, mean(u), t}.  The loop runs as
+ * CUDA-graph replays of 32 steps.  Synchronises the stream. */
+pfc_status pfc_hflow_run(pfc_hflow* flow, void* A, void* m, void* v, int32_t nsteps, int32_t* t,
+                         double* trace_host, pfc_stream stream);
+
 /* pfc_energy_and_grad without any device allocation, for callers that may not
  * call cudaMalloc/cudaFree (graph-capture regions, host callbacks, plugins in
  * a process that owns the device's memory budget, loops that must not take

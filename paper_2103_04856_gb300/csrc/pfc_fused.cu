@@ -211,6 +211,7 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
         // the steady state (all true) has no phase tests.
         auto plane = [&](int m, auto GATHER, auto PUBLISH, auto OWN) {
             constexpr bool kGather = decltype(GATHER)::value, kPublish = decltype(PUBLISH)::value;
+            (void)kPublish;
             constexpr bool kOwn = decltype(OWN)::value;
             if (loader) cp_async_wait<PD - 1>();
             __syncthreads();

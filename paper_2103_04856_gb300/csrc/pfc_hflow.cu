@@ -1,0 +1,554 @@
+// pfc_hflow.cu -- the paper's generator (Alg. 1, Sec. 4.1): the H^-1 flow of
+// F_eps written as an L2 flow on a periodic vector field A through the change
+// of variable u = div A + m0 (eq. change_var), a small Gaussian blur of u
+// before the energy, and Adam on A.  One step:
+//   div    : A (3 fields)  -> u = div A + m0          (plus the mass of u)
+//   blur   : u -> k * u     (three periodic 1-D passes, x, y, z)
+//   sweep  : k * u -> E, g = dF/du                    (the fused kernel)
+//   blur   : g -> k * g     (the blur is symmetric and periodic: self-adjoint)
+//   adam   : dG/dA_c = -(k*g)(j+e_c) + (k*g)(j-e_c), over 2h; moments; A update
+// The div, blur and Adam kernels are memory-bound grid-stride loops; the
+// sweep is the issue-bound kernel of pfc_fused.cu.
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <stdio.h>
+#include <vector>
+
+#include "../../include/pfc.h"
+#include "pfc_device.cuh"
+
+using namespace pfc;
+
+namespace pfc {
+void set_last_error(const char* msg);
+}
+
+namespace {
+
+constexpr int kMaxRadius = 32;
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ int wrap_h(int i, int n)
+{
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// Reduction slots of the flow's own kernels (the sweep has its own).
+enum { H_MASS = 0, H_GMAX, H_GABS, NH };
+
+struct Flow {
+    int nx, ny, nz;
+    long n;
+    double sg;          // 1 / (2h)
+    double m0;
+    double lr, beta1, beta2, adam_eps;
+    double* part;       // [blocks][NH] FP64 partials of the flow kernels
+    unsigned* ints;     // [0] ticket, [1] Adam step t, [2] trace row
+    double* hs;         // [NH] finished sums: mass, max|dG/dA|, mean|dG/dA|
+    const double* sweep_scal;   // the sweep's scalars (energy)
+    double* trace;      // [cap][5]
+    int trace_cap;
+};
+
+struct Weights {
+    int R;
+    float wf[2 * kMaxRadius + 1];
+    double wd[2 * kMaxRadius + 1];
+};
+
+template <typename T>
+__device__ __forceinline__ T wget(const Weights& w, int j);
+template <>
+__device__ __forceinline__ float wget<float>(const Weights& w, int j) { return w.wf[j]; }
+template <>
+__device__ __forceinline__ double wget<double>(const Weights& w, int j) { return w.wd[j]; }
+
+// Block totals of (sum, max, sum) -> partial of this block; the last block
+// combines all partials and runs `fin` with the totals (thread 0).
+template <class Fin>
+__device__ void flow_finish(const Flow& f, double a0, double a1, double a2, Fin fin)
+{
+    __shared__ double red[3 * (kThreads / 32)];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    a0 = warp_sum(a0);
+    a1 = warp_max(a1);
+    a2 = warp_sum(a2);
+    if (lane == 0) { red[3 * wid] = a0; red[3 * wid + 1] = a1; red[3 * wid + 2] = a2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0, s1 = 0, s2 = 0;
+        for (int w = 0; w < kThreads / 32; ++w) { s0 += red[3 * w]; s1 = fmax(s1, red[3 * w + 1]); s2 += red[3 * w + 2]; }
+        double* p = f.part + (size_t)blockIdx.x * NH;
+        p[0] = s0; p[1] = s1; p[2] = s2;
+        __threadfence();
+        last = atomicAdd(&f.ints[0], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (unsigned b = 0; b < gridDim.x; ++b) {
+        const double* p = f.part + (size_t)b * NH;
+        s0 += __ldcg(p);
+        s1 = fmax(s1, __ldcg(p + 1));
+        s2 += __ldcg(p + 2);
+    }
+    fin(s0, s1, s2);
+    __threadfence();
+    f.ints[0] = 0;
+}
+
+// u = div A + m0, periodic central differences (eq. change_var); mass of u.
+template <typename T>
+__global__ void k_div(const T* __restrict__ A, T* __restrict__ u, Flow f, int want_mass)
+{
+    const long n = f.n;
+    const T sg = (T)f.sg, m0 = (T)f.m0;
+    double s = 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % f.nx), y = (int)((i / f.nx) % f.ny), z = (int)(i / ((long)f.nx * f.ny));
+        const long row = i - x, pl = i - (long)y * f.nx - x;
+        const T dx = A[row + wrap_h(x + 1, f.nx)] - A[row + wrap_h(x - 1, f.nx)];
+        const T dy = A[n + pl + (long)wrap_h(y + 1, f.ny) * f.nx + x] - A[n + pl + (long)wrap_h(y - 1, f.ny) * f.nx + x];
+        const long zp = ((long)wrap_h(z + 1, f.nz) * f.ny + y) * f.nx + x, zm = ((long)wrap_h(z - 1, f.nz) * f.ny + y) * f.nx + x;
+        const T dz = A[2 * n + zp] - A[2 * n + zm];
+        const T v = sg * (dx + dy + dz) + m0;
+        u[i] = v;
+        s += (double)v;
+    }
+    if (!want_mass) return;
+    flow_finish(f, s, 0.0, 0.0, [&](double s0, double, double) { f.hs[H_MASS] = s0 / (double)f.n; });
+}
+
+// One periodic 1-D Gaussian pass along axis AX (0 x, 1 y, 2 z).
+template <typename T, int AX>
+__global__ void k_blur(const T* __restrict__ in, T* __restrict__ out, int nx, int ny, int nz, Weights w)
+{
+    const long n = (long)nx * ny * nz;
+    const int R = w.R;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long)nx * ny));
+        T s = 0;
+        if (AX == 0) {
+            const long row = i - x;
+            for (int j = -R; j <= R; ++j) s += wget<T>(w, j + R) * in[row + wrap_h(x + j, nx)];
+        } else if (AX == 1) {
+            const long pl = i - (long)y * nx;
+            for (int j = -R; j <= R; ++j) s += wget<T>(w, j + R) * in[pl + (long)wrap_h(y + j, ny) * nx];
+        } else {
+            const long col = (long)y * nx + x, pls = (long)nx * ny;
+            for (int j = -R; j <= R; ++j) s += wget<T>(w, j + R) * in[(long)wrap_h(z + j, nz) * pls + col];
+        }
+        out[i] = s;
+    }
+}
+
+// dG/dA from the blurred gradient gb, then Adam (Kingma and Ba) on A with
+// moments m, v; the step counter lives in f.ints[1].  `only_grad`: write
+// dG/dA to m and leave A, v alone (pfc_hflow_grad).
+template <typename T>
+__global__ void k_adam(const T* __restrict__ gb, T* __restrict__ A, T* __restrict__ m, T* __restrict__ v, Flow f,
+                       int only_grad)
+{
+    const long n = f.n;
+    const T sg = (T)f.sg;
+    const unsigned t = f.ints[1] + 1;
+    const T b1 = (T)f.beta1, b2 = (T)f.beta2;
+    const T c1 = (T)(1.0 / (1.0 - pow(f.beta1, (double)t))), c2 = (T)(1.0 / (1.0 - pow(f.beta2, (double)t)));
+    const T lr = (T)f.lr, ae = (T)f.adam_eps;
+    double sabs = 0.0, gmax = 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % f.nx), y = (int)((i / f.nx) % f.ny), z = (int)(i / ((long)f.nx * f.ny));
+        const long row = i - x, pl = i - (long)y * f.nx - x;
+        T g[3];
+        g[0] = sg * (gb[row + wrap_h(x - 1, f.nx)] - gb[row + wrap_h(x + 1, f.nx)]);
+        g[1] = sg * (gb[pl + (long)wrap_h(y - 1, f.ny) * f.nx + x] - gb[pl + (long)wrap_h(y + 1, f.ny) * f.nx + x]);
+        g[2] = sg * (gb[((long)wrap_h(z - 1, f.nz) * f.ny + y) * f.nx + x] - gb[((long)wrap_h(z + 1, f.nz) * f.ny + y) * f.nx + x]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long k = c * n + i;
+            const T gc = g[c];
+            const T ag = gc < T(0) ? -gc : gc;
+            sabs += (double)ag;
+            gmax = fmax(gmax, (double)ag);
+            if (only_grad) {
+                m[k] = gc;
+                continue;
+            }
+            const T mk = b1 * m[k] + (T(1) - b1) * gc;
+            const T vk = b2 * v[k] + (T(1) - b2) * gc * gc;
+            m[k] = mk;
+            v[k] = vk;
+            A[k] -= lr * (mk * c1) / (sqrt(vk * c2) + ae);
+        }
+    }
+    flow_finish(f, sabs, gmax, 0.0, [&](double s0, double s1, double) {
+        f.hs[H_GMAX] = s1;
+        f.hs[H_GABS] = s0 / (3.0 * (double)f.n);
+        if (only_grad) return;
+        f.ints[1] = t;
+        const unsigned row = f.ints[2];
+        if (f.trace && (int)row < f.trace_cap) {
+            double* r = f.trace + (size_t)row * 5;
+            r[0] = f.sweep_scal[S_E];
+            r[1] = s1;
+            r[2] = s0 / (3.0 * (double)f.n);
+            r[3] = f.hs[H_MASS];
+            r[4] = (double)t;
+        }
+        f.ints[2] = row + 1;
+    });
+}
+
+int flow_blocks(long n)
+{
+    long b = (n + kThreads - 1) / kThreads;
+    return (int)(b < 152 * 8 ? b : 152 * 8);
+}
+
+}  // namespace
+
+struct pfc_hflow {
+    pfc_problem P;
+    pfc_hflow_params H;
+    int device = 0;
+    long N = 0;
+    int esz = 4;
+    int tile_y = 16;
+    Weights W{};
+    void* buf[4] = { nullptr, nullptr, nullptr, nullptr };   // ut, g, two blur temporaries
+    double* spart = nullptr;    // sweep partials
+    unsigned* sints = nullptr;  // sweep counters
+    double* sscal = nullptr;    // sweep scalars
+    double* fpart = nullptr;    // flow partials
+    unsigned* fints = nullptr;
+    double* hs = nullptr;
+    double* trace = nullptr;
+    int trace_cap = 0;
+    int sweep_slots = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const void* gA = nullptr;
+    const void* gm = nullptr;
+    const void* gv = nullptr;
+    int glen = 0;
+    double* gtrace = nullptr;
+};
+
+static pfc_status hfail(pfc_status s, const char* msg)
+{
+    pfc::set_last_error(msg);
+    return s;
+}
+
+#define HCU(call)                                                              \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) {                                               \
+            (void)cudaGetLastError();                                          \
+            char b_[256];                                                      \
+            snprintf(b_, sizeof b_, "%s: %s", #call, cudaGetErrorString(e_));  \
+            return hfail(PFC_ECUDA, b_);                                       \
+        }                                                                      \
+    } while (0)
+
+static bool dev_ptr(const void* p)
+{
+    cudaPointerAttributes at;
+    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static void free_flow(pfc_hflow* h)
+{
+    for (void* b : h->buf) cudaFree(b);
+    cudaFree(h->spart);
+    cudaFree(h->sints);
+    cudaFree(h->sscal);
+    cudaFree(h->fpart);
+    cudaFree(h->fints);
+    cudaFree(h->hs);
+    cudaFree(h->trace);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->cap) cudaStreamDestroy(h->cap);
+}
+
+extern "C" pfc_status pfc_hflow_create(const pfc_problem* prob, const pfc_hflow_params* hp, pfc_hflow** out)
+{
+    if (!out || !prob || !hp) return hfail(PFC_EINVAL, "hflow: problem, params and out are required");
+    *out = nullptr;
+    const pfc_problem& p = *prob;
+    if (p.nx < 1 || p.ny < 1 || p.nz < 1 || (double)p.nx * p.ny * p.nz > 2.0e9)
+        return hfail(PFC_EINVAL, "hflow: grid sizes must be >= 1 and hold at most 2e9 voxels");
+    if (!(p.h > 0) || !(p.eps > 0) || !(p.xi > 0)) return hfail(PFC_EINVAL, "hflow: h, eps, xi must be > 0");
+    if (p.prec != PFC_FP32 && p.prec != PFC_FP64) return hfail(PFC_EINVAL, "hflow: unknown precision");
+    if (p.well != PFC_WELL_01 && p.well != PFC_WELL_PM1) return hfail(PFC_EINVAL, "hflow: unknown double well");
+    if (p.impl != PFC_IMPL_FUSED) return hfail(PFC_EUNSUPPORTED, "hflow: runs on the fused path");
+    if (p.tile_y != 0 && p.tile_y != 8 && p.tile_y != 16) return hfail(PFC_EINVAL, "hflow: tile_y must be 0, 8 or 16");
+    for (int i = 0; i < 6; ++i)
+        if (!isfinite(p.a[i])) return hfail(PFC_EINVAL, "hflow: a coefficient is not finite");
+    if (!isfinite(hp->m0) || !(hp->lr >= 0) || !(hp->beta1 >= 0 && hp->beta1 < 1) || !(hp->beta2 >= 0 && hp->beta2 < 1) ||
+        !(hp->adam_eps >= 0) || !(hp->blur_sigma >= 0))
+        return hfail(PFC_EINVAL, "hflow: m0 finite, lr >= 0, betas in [0,1), eps >= 0, sigma >= 0 required");
+    int R = 0;
+    if (hp->blur_sigma > 0) {
+        R = hp->blur_radius > 0 ? hp->blur_radius : (int)ceil(3.0 * hp->blur_sigma);
+        if (R > kMaxRadius) return hfail(PFC_EINVAL, "hflow: blur radius above 32 taps");
+    }
+    pfc_hflow* h = new (std::nothrow) pfc_hflow();
+    if (!h) return hfail(PFC_ENOMEM, "hflow: host allocation failed");
+    h->P = p;
+    h->H = *hp;
+    h->H.blur_radius = R;
+    h->N = (long)p.nx * p.ny * p.nz;
+    h->esz = p.prec == PFC_FP64 ? 8 : 4;
+    h->tile_y = p.tile_y ? p.tile_y : (p.prec == PFC_FP64 ? 8 : 16);
+    h->W.R = R;
+    if (R > 0) {   // discrete Gaussian, normalised to sum 1
+        double s = 0;
+        for (int j = -R; j <= R; ++j) s += exp(-(double)j * j / (2.0 * hp->blur_sigma * hp->blur_sigma));
+        for (int j = -R; j <= R; ++j) {
+            h->W.wd[j + R] = exp(-(double)j * j / (2.0 * hp->blur_sigma * hp->blur_sigma)) / s;
+            h->W.wf[j + R] = (float)h->W.wd[j + R];
+        }
+    }
+    cudaGetDevice(&h->device);
+    const long long units = (long long)((p.nx + 31) / 32) * ((p.ny + h->tile_y - 1) / h->tile_y) * p.nz;
+    h->sweep_slots = (int)fused_grid(units, p.tile_z);
+    bool ok = true;
+    for (void*& b : h->buf) ok = ok && cudaMalloc(&b, (size_t)h->esz * h->N) == cudaSuccess;
+    ok = ok && cudaMalloc((void**)&h->spart, sizeof(double) * NPART * (size_t)h->sweep_slots) == cudaSuccess &&
+         cudaMalloc((void**)&h->sints, sizeof(unsigned) * NINTS) == cudaSuccess &&
+         cudaMalloc((void**)&h->sscal, sizeof(double) * NSCAL) == cudaSuccess &&
+         cudaMalloc((void**)&h->fpart, sizeof(double) * NH * (size_t)flow_blocks(h->N)) == cudaSuccess &&
+         cudaMalloc((void**)&h->fints, sizeof(unsigned) * 4) == cudaSuccess &&
+         cudaMalloc((void**)&h->hs, sizeof(double) * NH) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) ok = cudaMemset(h->sints, 0, sizeof(unsigned) * NINTS) == cudaSuccess &&
+                 cudaMemset(h->fints, 0, sizeof(unsigned) * 4) == cudaSuccess &&
+                 cudaMemset(h->hs, 0, sizeof(double) * NH) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+    if (!ok) {
+        (void)cudaGetLastError();
+        free_flow(h);
+        delete h;
+        return hfail(PFC_ENOMEM, "hflow: device allocation failed");
+    }
+    *out = h;
+    return PFC_OK;
+}
+
+extern "C" void pfc_hflow_destroy(pfc_hflow* h)
+{
+    if (!h) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    free_flow(h);
+    cudaSetDevice(prev);
+    delete h;
+}
+
+static Flow flow_desc(const pfc_hflow* h)
+{
+    Flow f;
+    f.nx = h->P.nx; f.ny = h->P.ny; f.nz = h->P.nz;
+    f.n = h->N;
+    f.sg = 1.0 / (2.0 * h->P.h);
+    f.m0 = h->H.m0;
+    f.lr = h->H.lr; f.beta1 = h->H.beta1; f.beta2 = h->H.beta2; f.adam_eps = h->H.adam_eps;
+    f.part = h->fpart;
+    f.ints = h->fints;
+    f.hs = h->hs;
+    f.sweep_scal = h->sscal;
+    f.trace = h->trace;
+    f.trace_cap = h->trace_cap;
+    return f;
+}
+
+// in -> k * in through the two temporaries; returns the buffer holding the result
+template <typename T>
+static cudaError_t blur3(const pfc_hflow* h, T* in, T* t1, T* t2, T** result, cudaStream_t s)
+{
+    if (h->W.R == 0) {
+        *result = in;
+        return cudaSuccess;
+    }
+    const int nb = flow_blocks(h->N);
+    k_blur<T, 0><<<nb, kThreads, 0, s>>>(in, t1, h->P.nx, h->P.ny, h->P.nz, h->W);
+    k_blur<T, 1><<<nb, kThreads, 0, s>>>(t1, t2, h->P.nx, h->P.ny, h->P.nz, h->W);
+    k_blur<T, 2><<<nb, kThreads, 0, s>>>(t2, t1, h->P.nx, h->P.ny, h->P.nz, h->W);
+    *result = t1;
+    return cudaGetLastError();
+}
+
+// ut = k * (div A + m0) into buf[0] (or the returned buffer)
+template <typename T>
+static cudaError_t field(const pfc_hflow* h, const T* A, T** ut, int want_mass, cudaStream_t s)
+{
+    T* b0 = (T*)h->buf[0];
+    T* b2 = (T*)h->buf[2];
+    T* b3 = (T*)h->buf[3];
+    const int nb = flow_blocks(h->N);
+    if (h->W.R == 0) {
+        k_div<T><<<nb, kThreads, 0, s>>>(A, b0, flow_desc(h), want_mass);
+        *ut = b0;
+        return cudaGetLastError();
+    }
+    k_div<T><<<nb, kThreads, 0, s>>>(A, b2, flow_desc(h), want_mass);
+    k_blur<T, 0><<<nb, kThreads, 0, s>>>(b2, b3, h->P.nx, h->P.ny, h->P.nz, h->W);
+    k_blur<T, 1><<<nb, kThreads, 0, s>>>(b3, b2, h->P.nx, h->P.ny, h->P.nz, h->W);
+    k_blur<T, 2><<<nb, kThreads, 0, s>>>(b2, b0, h->P.nx, h->P.ny, h->P.nz, h->W);
+    *ut = b0;
+    return cudaGetLastError();
+}
+
+// one evaluation: E and k * dF/du in a buffer (returned)
+template <typename T>
+static cudaError_t eval(pfc_hflow* h, const T* A, T** gb, cudaStream_t s)
+{
+    T* ut = nullptr;
+    cudaError_t e = field<T>(h, A, &ut, 1, s);
+    if (e != cudaSuccess) return e;
+    Inst<T> in{};
+    in.u = ut;
+    in.out = (T*)h->buf[1];
+    in.nx = h->P.nx; in.ny = h->P.ny; in.nz = h->P.nz;
+    in.vec = (h->P.nx % (16 / (int)sizeof(T)) == 0);
+    in.C = make_coef<T>(h->P.a, h->P.h, h->P.eps, h->P.xi, h->P.well);
+    in.inv_N = 1.0 / (double)h->N;
+    in.partials = h->spart;
+    in.ints = h->sints;
+    in.scal = h->sscal;
+    e = launch_fused<T>(in, MODE_GRAD, h->tile_y, h->P.tile_z, s);
+    if (e != cudaSuccess) return e;
+    return blur3<T>(h, (T*)h->buf[1], (T*)h->buf[2], (T*)h->buf[3], gb, s);
+}
+
+template <typename T>
+static cudaError_t step(pfc_hflow* h, T* A, T* m, T* v, cudaStream_t s)
+{
+    T* gb = nullptr;
+    cudaError_t e = eval<T>(h, A, &gb, s);
+    if (e != cudaSuccess) return e;
+    k_adam<T><<<flow_blocks(h->N), kThreads, 0, s>>>(gb, A, m, v, flow_desc(h), 0);
+    return cudaGetLastError();
+}
+
+extern "C" pfc_status pfc_hflow_field(pfc_hflow* h, const void* A, void* ut, pfc_stream stream)
+{
+    if (!h) return hfail(PFC_EINVAL, "hflow: handle is NULL");
+    if (!dev_ptr(A) || !dev_ptr(ut)) return hfail(PFC_EINVAL, "hflow: A and ut must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->P.prec == PFC_FP64) {
+        double* r = nullptr;
+        HCU(field<double>(h, (const double*)A, &r, 0, s));
+        HCU(cudaMemcpyAsync(ut, r, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, s));
+    } else {
+        float* r = nullptr;
+        HCU(field<float>(h, (const float*)A, &r, 0, s));
+        HCU(cudaMemcpyAsync(ut, r, sizeof(float) * h->N, cudaMemcpyDeviceToDevice, s));
+    }
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_hflow_grad(pfc_hflow* h, const void* A, void* gA, double* G_host, pfc_stream stream)
+{
+    if (!h) return hfail(PFC_EINVAL, "hflow: handle is NULL");
+    if (!dev_ptr(A) || !dev_ptr(gA)) return hfail(PFC_EINVAL, "hflow: A and gA must be device memory");
+    if (A == gA) return hfail(PFC_EINVAL, "hflow: gA must not alias A");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Flow f = flow_desc(h);
+    if (h->P.prec == PFC_FP64) {
+        double* gb = nullptr;
+        HCU(eval<double>(h, (const double*)A, &gb, s));
+        k_adam<double><<<flow_blocks(h->N), kThreads, 0, s>>>(gb, nullptr, (double*)gA, nullptr, f, 1);
+    } else {
+        float* gb = nullptr;
+        HCU(eval<float>(h, (const float*)A, &gb, s));
+        k_adam<float><<<flow_blocks(h->N), kThreads, 0, s>>>(gb, nullptr, (float*)gA, nullptr, f, 1);
+    }
+    HCU(cudaGetLastError());
+    if (G_host) {
+        HCU(cudaMemcpyAsync(G_host, h->sscal + S_E, sizeof(double), cudaMemcpyDeviceToHost, s));
+        HCU(cudaStreamSynchronize(s));
+        if (!isfinite(*G_host)) return hfail(PFC_ENONFINITE, "hflow: energy is not finite");
+    }
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_hflow_run(pfc_hflow* h, void* A, void* m, void* v, int32_t nsteps, int32_t* t,
+                                    double* trace_host, pfc_stream stream)
+{
+    if (!h) return hfail(PFC_EINVAL, "hflow: handle is NULL");
+    if (!dev_ptr(A) || !dev_ptr(m) || !dev_ptr(v)) return hfail(PFC_EINVAL, "hflow: A, m, v must be device memory");
+    if (A == m || A == v || m == v) return hfail(PFC_EINVAL, "hflow: A, m and v must be distinct");
+    if (!t || *t < 0 || nsteps < 0) return hfail(PFC_EINVAL, "hflow: nsteps >= 0 and a step counter >= 0 required");
+    if (nsteps == 0) return PFC_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nsteps > h->trace_cap) {
+        if (h->gexec) {
+            cudaGraphExecDestroy(h->gexec);
+            h->gexec = nullptr;
+        }
+        HCU(cudaDeviceSynchronize());
+        cudaFree(h->trace);
+        h->trace = nullptr;
+        h->trace_cap = 0;
+        HCU(cudaMalloc((void**)&h->trace, sizeof(double) * 5 * (size_t)nsteps));
+        h->trace_cap = nsteps;
+    }
+    const unsigned tt[2] = { (unsigned)*t, 0u };
+    HCU(cudaMemsetAsync(h->fints, 0, sizeof(unsigned), s));
+    HCU(cudaMemcpyAsync(h->fints + 1, tt, sizeof tt, cudaMemcpyHostToDevice, s));
+    auto enqueue = [&](int cnt, cudaStream_t st) -> cudaError_t {
+        for (int i = 0; i < cnt; ++i) {
+            cudaError_t e = h->P.prec == PFC_FP64 ? step<double>(h, (double*)A, (double*)m, (double*)v, st)
+                                                  : step<float>(h, (float*)A, (float*)m, (float*)v, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    const int G = nsteps >= 32 ? 32 : 0;
+    if (G) {
+        if (!(h->gexec && h->gA == A && h->gm == m && h->gv == v && h->glen == G && h->gtrace == h->trace)) {
+            if (h->gexec) {
+                cudaGraphExecDestroy(h->gexec);
+                h->gexec = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            HCU(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue(G, h->cap);
+            cudaError_t e2 = cudaStreamEndCapture(h->cap, &graph);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                (void)cudaGetLastError();
+                return hfail(PFC_ECUDA, "hflow: graph capture failed");
+            }
+            e = cudaGraphInstantiate(&h->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                h->gexec = nullptr;
+                (void)cudaGetLastError();
+                return hfail(PFC_ECUDA, "hflow: graph instantiation failed");
+            }
+            h->gA = A; h->gm = m; h->gv = v; h->glen = G; h->gtrace = h->trace;
+        }
+        for (int k = 0; k + G <= nsteps; k += G) HCU(cudaGraphLaunch(h->gexec, s));
+    }
+    const int done = G ? (nsteps / G) * G : 0;
+    HCU(enqueue(nsteps - done, s));
+    unsigned back[2];
+    HCU(cudaMemcpyAsync(back, h->fints + 1, sizeof back, cudaMemcpyDeviceToHost, s));
+    if (trace_host) HCU(cudaMemcpyAsync(trace_host, h->trace, sizeof(double) * 5 * (size_t)nsteps, cudaMemcpyDeviceToHost, s));
+    HCU(cudaStreamSynchronize(s));
+    *t = (int32_t)back[0];
+    if (back[1] != (unsigned)nsteps) return hfail(PFC_ECUDA, "hflow: step count mismatch");
+    return PFC_OK;
+}

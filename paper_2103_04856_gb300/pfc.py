@@ -31,7 +31,8 @@ PFC_IMPL_FUSED, PFC_IMPL_PLAIN = 0, 1
 # every symbol include/pfc.h declares
 EXPORTED = ("pfc_create", "pfc_destroy", "pfc_energy", "pfc_energy_and_grad", "pfc_step", "pfc_run",
             "pfc_curvatures", "pfc_batch_create", "pfc_batch_destroy", "pfc_batch_run", "pfc_batch_step",
-            "pfc_batch_timing", "pfc_batch_last_timing", "pfc_energy_and_grad_noalloc", "pfc_b_to_a",
+            "pfc_batch_timing", "pfc_batch_last_timing", "pfc_hflow_create", "pfc_hflow_destroy",
+            "pfc_hflow_field", "pfc_hflow_grad", "pfc_hflow_run", "pfc_energy_and_grad_noalloc", "pfc_b_to_a",
             "pfc_status_string", "pfc_last_error")
 
 
@@ -43,6 +44,12 @@ class PfcError(RuntimeError):
 
 class NonFiniteError(PfcError):
     pass
+
+
+class _CHFlow(ctypes.Structure):
+    _fields_ = [("m0", ctypes.c_double), ("lr", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("beta2", ctypes.c_double), ("adam_eps", ctypes.c_double), ("blur_sigma", ctypes.c_double),
+                ("blur_radius", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class _CProblem(ctypes.Structure):
@@ -128,6 +135,12 @@ def load_library():
             "pfc_batch_last_timing": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
                                       ctypes.c_int),
             "pfc_energy_and_grad_noalloc": ([P, vp, vp, dp, vp], ctypes.c_int),
+            "pfc_hflow_create": ([P, ctypes.POINTER(_CHFlow), ctypes.POINTER(vp)], ctypes.c_int),
+            "pfc_hflow_destroy": ([vp], None),
+            "pfc_hflow_field": ([vp, vp, vp, vp], ctypes.c_int),
+            "pfc_hflow_grad": ([vp, vp, vp, dp, vp], ctypes.c_int),
+            "pfc_hflow_run": ([vp, vp, vp, vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), dp, vp],
+                              ctypes.c_int),
             "pfc_b_to_a": ([dp, dp], ctypes.c_int),
             "pfc_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "pfc_last_error": ([], ctypes.c_char_p),
@@ -320,6 +333,62 @@ class Batch:
         a, b = ctypes.c_float(), ctypes.c_float()
         _check(self._lib.pfc_batch_last_timing(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+
+class HFlow:
+    """The paper's generator (Alg. 1): Adam on a periodic vector field A with
+    u = k * (div A + m0).  A, m, v: CUDA tensors shaped (3, nz, ny, nx)."""
+
+    def __init__(self, prob: Problem, m0: float, lr: float = 1e-3, betas=(0.9, 0.999), adam_eps: float = 1e-8,
+                 blur_sigma: float = 2.0, blur_radius: int = 0):
+        self.prob = prob
+        self._lib = load_library()
+        self._h = ctypes.c_void_p()
+        hp = _CHFlow(float(m0), float(lr), float(betas[0]), float(betas[1]), float(adam_eps), float(blur_sigma),
+                     int(blur_radius), 0)
+        _check(self._lib.pfc_hflow_create(ctypes.byref(prob._c()), ctypes.byref(hp), ctypes.byref(self._h)))
+        self.t = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pfc_hflow_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _vec(self, t, name):
+        p = self.prob
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != p.dtype:
+            raise TypeError(f"{name} must be a CUDA {p.dtype} tensor")
+        if tuple(t.shape) != (3, p.nz, p.ny, p.nx) or not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous with shape {(3, p.nz, p.ny, p.nx)}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def field(self, A, stream=None):
+        p = self.prob
+        ut = torch.empty((p.nz, p.ny, p.nx), dtype=p.dtype, device="cuda")
+        _check(self._lib.pfc_hflow_field(self._h, self._vec(A, "A"), _field(ut, p, "ut"), _stream(stream)))
+        return ut
+
+    def grad(self, A, stream=None):
+        gA = torch.empty_like(A)
+        G = ctypes.c_double()
+        _check(self._lib.pfc_hflow_grad(self._h, self._vec(A, "A"), self._vec(gA, "gA"), ctypes.byref(G),
+                                        _stream(stream)))
+        return G.value, gA
+
+    def run(self, A, m, v, nsteps: int, trace: bool = True, stream=None):
+        tr = np.empty((max(int(nsteps), 0), 5)) if trace else None
+        t = ctypes.c_int32(self.t)
+        _check(self._lib.pfc_hflow_run(self._h, self._vec(A, "A"), self._vec(m, "m"), self._vec(v, "v"), int(nsteps),
+                                       ctypes.byref(t), tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                                       if trace else None, _stream(stream)))
+        self.t = t.value
+        return tr
 
 
 class PhaseFieldEnergy(torch.autograd.Function):

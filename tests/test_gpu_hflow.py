@@ -1,0 +1,94 @@
+"""Alg. 1 on the GPU (pfc_hflow_*) against the oracle's restatement."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2103_04856_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_2103_04856_gb300 import pfc
+
+
+def setup(shape, prec="fp64", sigma=1.5, xi=1e-6, a=(1.0, 0.4, 0.8, 0.3, -0.2, 0.1), seed=0, m0=0.3, lr=1e-3):
+    nz, ny, nx = shape
+    p = pfc.Problem(nx=nx, ny=ny, nz=nz, eps=1.5, a=a, xi=xi, prec=prec)
+    rng = np.random.default_rng(seed)
+    A = 0.04 * rng.standard_normal((3,) + tuple(shape))
+    if prec == "fp32":
+        A = A.astype(np.float32).astype(np.float64)
+    op = {"a": a, "eps": 1.5, "xi": xi, "h": 1.0, "well": 0}
+    fp = {"m0": m0, "blur_sigma": sigma, "lr": lr}
+    flow = pfc.HFlow(p, m0=m0, lr=lr, blur_sigma=sigma)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    return flow, torch.tensor(A, dtype=dt, device="cuda"), A, op, fp
+
+
+@pytest.mark.parametrize("shape,sigma", [((12, 10, 16), 1.5), ((7, 9, 11), 0.0), ((20, 24, 40), 2.0)])
+def test_field_and_grad_vs_oracle(shape, sigma):
+    flow, Ad, A, op, fp = setup(shape, sigma=sigma)
+    ut = flow.field(Ad).cpu().numpy()
+    uo = oracle.hflow_field(A, op, fp)
+    assert np.max(np.abs(ut - uo)) < 1e-13
+    assert abs(ut.mean() - 0.3) < 1e-14
+    G, gA = flow.grad(Ad)
+    Go, gAo = oracle.hflow_grad(A, op, fp)
+    assert G == pytest.approx(Go, rel=1e-10)
+    gA = gA.cpu().numpy()
+    assert np.linalg.norm(gA - gAo) / np.linalg.norm(gAo) < 1e-10
+
+
+def test_run_vs_oracle_short_horizon():
+    """5 Adam steps (fresh moments), then 3 more continuing the step count."""
+    shape = (12, 10, 16)
+    flow, Ad, A, op, fp = setup(shape)
+    md, vd = torch.zeros_like(Ad), torch.zeros_like(Ad)
+    tr = flow.run(Ad, md, vd, 5)
+    Ao, mo, vo, to, tro = oracle.hflow_run(A, np.zeros_like(A), np.zeros_like(A), op, fp, 5)
+    assert flow.t == to == 5
+    for d, o in ((Ad, Ao), (md, mo), (vd, vo)):
+        assert np.linalg.norm(d.cpu().numpy() - o) / np.linalg.norm(o) < 1e-10
+    np.testing.assert_allclose(tr, tro, rtol=1e-10, atol=1e-14)
+    tr2 = flow.run(Ad, md, vd, 3)
+    Ao, mo, vo, to, tro = oracle.hflow_run(Ao, mo, vo, op, fp, 3, t=5)
+    assert flow.t == to == 8
+    assert np.linalg.norm(Ad.cpu().numpy() - Ao) / np.linalg.norm(Ao) < 1e-10
+    np.testing.assert_allclose(tr2, tro, rtol=1e-10, atol=1e-14)
+
+
+def test_run_graph_replays_smooth_xi():
+    """70 steps = two 32-step graph replays plus 6 direct steps (smooth xi, so
+    the long trajectory is comparable)."""
+    shape = (8, 12, 16)
+    flow, Ad, A, op, fp = setup(shape, xi=1e-2, lr=2e-3)
+    md, vd = torch.zeros_like(Ad), torch.zeros_like(Ad)
+    tr = flow.run(Ad, md, vd, 70)
+    Ao, mo, vo, to, tro = oracle.hflow_run(A, np.zeros_like(A), np.zeros_like(A), op, fp, 70)
+    assert np.linalg.norm(Ad.cpu().numpy() - Ao) / np.linalg.norm(Ao) < 1e-8
+    np.testing.assert_allclose(tr[:, 0], tro[:, 0], rtol=1e-8)
+    np.testing.assert_allclose(tr[:, 3], 0.3, atol=1e-14)
+    assert tr[-1, 0] < tr[0, 0]
+
+
+def test_fp32_matches_fp64():
+    shape = (20, 24, 32)
+    f64, A64, A, op, fp = setup(shape, seed=3)
+    f32, A32, _, _, _ = setup(shape, prec="fp32", seed=3)
+    A64 = A32.double()
+    G64, g64 = f64.grad(A64)
+    G32, g32 = f32.grad(A32)
+    assert abs(G32 - G64) / abs(G64) < 1e-4
+    assert (torch.linalg.norm(g32.double() - g64) / torch.linalg.norm(g64)).item() < 1e-3
+    assert torch.max(torch.abs(f32.field(A32).double() - f64.field(A64))).item() < 1e-6
+
+
+def test_errors():
+    shape = (8, 8, 8)
+    flow, Ad, A, op, fp = setup(shape)
+    with pytest.raises(ValueError):
+        flow.field(Ad[:2].contiguous())
+    with pytest.raises(pfc.PfcError):
+        pfc.HFlow(pfc.Problem(nx=8, ny=8, nz=8, eps=1.5, a=(1, 0, 1, 0, 0, 0), prec="fp64"), m0=0.3,
+                  blur_sigma=20.0)                                  # radius 60 > 32
