@@ -259,6 +259,35 @@ def extra_workload(pfc, insts, flush, steps):
             "hbm_gbs": 8.0 * vox / (msw * 1e-3) / 1e9}
 
 
+def alg1_workload(pfc, I, steps):
+    """The paper's generator (Alg. 1) in its own setting (100^3, Fig. cvg_1
+    parameters, blur of 2 voxels, Adam), FP32: Adam iterations per second."""
+    import torch
+    pd, fd, A0 = I.paper_flow_100()
+    nz, ny, nx = pd["shape"]
+    prob = pfc.Problem(nx=nx, ny=ny, nz=nz, h=pd["h"], eps=pd["eps"], xi=pd["xi"], a=pd["a"], well=pd["well"],
+                       prec="fp32")
+    flow = pfc.HFlow(prob, m0=fd["m0"], lr=fd["lr"], betas=(fd["beta1"], fd["beta2"]), adam_eps=fd["adam_eps"],
+                     blur_sigma=fd["blur_sigma"])
+    A = torch.tensor(A0.astype(np.float32), device="cuda")
+    m, v = torch.zeros_like(A), torch.zeros_like(A)
+    flow.run(A, m, v, 64)                       # warm-up: graph capture
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    tr = flow.run(A, m, v, steps)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    flow.close()
+    n = nx * ny * nz
+    return {"workload": "Alg. 1 at 100^3, h=0.01, eps=0.02, a=(1,2.4,9,30,170,-195), m0=-0.66, blur 2 px, Adam 1e-3",
+            "iterations_per_s": 1e3 / ms, "ms_per_iteration": ms, "value": n * 1e3 / ms, "unit": "voxel-iterations/s",
+            "energy_first_last": [float(tr[0, 0]), float(tr[-1, 0])], "mass": float(tr[-1, 3]),
+            "paper_context": "up to 150 s for ~8000 iterations at 100^3 (~53 iterations/s) on an unnamed GPU, "
+                             "PyTorch autograd (Sec. 4.1)"}
+
+
 # Algorithmic FP32 flops of one voxel-step, counted from the arithmetic (FMA =
 # 2): stencils 18, forward (eq. Feps) 86, local reverse mode 75,
 # transposed-stencil pieces 19, gather 9, update and sums 4.
@@ -416,7 +445,8 @@ def main():
     extra = None
     if not args.no_extra:
         extra = {"batch64_mixed": extra_workload(pfc, I.batch_instances(64), flush, steps=20),
-                 "membrane_512": extra_workload(pfc, [I.membrane_descent_512()], flush, steps=10)}
+                 "membrane_512": extra_workload(pfc, [I.membrane_descent_512()], flush, steps=10),
+                 "alg1_flow_100": alg1_workload(pfc, I, steps=400)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -7,7 +7,9 @@
 //   sweep  : k * u -> E, g = dF/du                    (the fused kernel)
 //   blur   : g -> k * g     (the blur is symmetric and periodic: self-adjoint)
 //   adam   : dG/dA_c = -(k*g)(j+e_c) + (k*g)(j-e_c), over 2h; moments; A update
-// The div, blur and Adam kernels are memory-bound grid-stride loops; the
+// The div, blur and Adam kernels are memory-bound (x along threads, blocks
+// looping over rows, FP32 sums per thread and FP64 only across warps and
+// blocks: FP64 runs at a small fraction of the FP32 rate on this GPU); the
 // sweep is the issue-bound kernel of pfc_fused.cu.
 #include <cuda_runtime.h>
 
@@ -27,7 +29,8 @@ void set_last_error(const char* msg);
 namespace {
 
 constexpr int kMaxRadius = 32;
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;
+constexpr int kRowBlocks = 1024;   // block rows; each loops over (y, z) rows
 
 __device__ __forceinline__ int wrap_h(int i, int n)
 {
@@ -65,84 +68,125 @@ __device__ __forceinline__ float wget<float>(const Weights& w, int j) { return w
 template <>
 __device__ __forceinline__ double wget<double>(const Weights& w, int j) { return w.wd[j]; }
 
-// Block totals of (sum, max, sum) -> partial of this block; the last block
-// combines all partials and runs `fin` with the totals (thread 0).
-template <class Fin>
-__device__ void flow_finish(const Flow& f, double a0, double a1, double a2, Fin fin)
+// Neighbour index along one axis: i + d wrapped into [0, n) without a
+// division when |d| < n (every case but tiny grids with wide blurs).
+__device__ __forceinline__ int nb(int i, int d, int n)
 {
-    __shared__ double red[3 * (kThreads / 32)];
+    int j = i + d;
+    if (j < 0) j += n;
+    if (j >= n) j -= n;
+    return (j >= 0 && j < n) ? j : wrap_h(i + d, n);
+}
+
+template <typename T> __device__ __forceinline__ T pow_(T b, T e);
+template <> __device__ __forceinline__ float pow_<float>(float b, float e) { return powf(b, e); }
+template <> __device__ __forceinline__ double pow_<double>(double b, double e) { return pow(b, e); }
+
+// Block totals of (sum, max) in the arithmetic type per thread, FP64 across
+// warps and blocks; the last block combines all partials in a fixed order
+// and runs `fin` with the totals (thread 0).
+template <typename T, class Fin>
+__device__ void flow_finish(const Flow& f, T a0, T a1, Fin fin)
+{
+    __shared__ double red[2 * (kThreads / 32)];
     __shared__ int last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    a0 = warp_sum(a0);
-    a1 = warp_max(a1);
-    a2 = warp_sum(a2);
-    if (lane == 0) { red[3 * wid] = a0; red[3 * wid + 1] = a1; red[3 * wid + 2] = a2; }
+    const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 = fmax(a1, __shfl_xor_sync(0xffffffffu, a1, o));
+    }
+    if (lane == 0) { red[2 * wid] = (double)a0; red[2 * wid + 1] = (double)a1; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s0 = 0, s1 = 0, s2 = 0;
-        for (int w = 0; w < kThreads / 32; ++w) { s0 += red[3 * w]; s1 = fmax(s1, red[3 * w + 1]); s2 += red[3 * w + 2]; }
-        double* p = f.part + (size_t)blockIdx.x * NH;
-        p[0] = s0; p[1] = s1; p[2] = s2;
+        double s0 = 0, s1 = 0;
+        for (int w = 0; w < kThreads / 32; ++w) { s0 += red[2 * w]; s1 = fmax(s1, red[2 * w + 1]); }
+        double* p = f.part + (size_t)bid * 2;
+        p[0] = s0; p[1] = s1;
         __threadfence();
-        last = atomicAdd(&f.ints[0], 1u) == gridDim.x - 1;
+        last = atomicAdd(&f.ints[0], 1u) == (unsigned)nblocks - 1u;
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
     __threadfence();
-    double s0 = 0, s1 = 0, s2 = 0;
-    for (unsigned b = 0; b < gridDim.x; ++b) {
-        const double* p = f.part + (size_t)b * NH;
-        s0 += __ldcg(p);
-        s1 = fmax(s1, __ldcg(p + 1));
-        s2 += __ldcg(p + 2);
+    double s0 = 0, s1 = 0;
+    for (int b = threadIdx.x; b < nblocks; b += kThreads) {
+        s0 += __ldcg(f.part + (size_t)b * 2);
+        s1 = fmax(s1, __ldcg(f.part + (size_t)b * 2 + 1));
     }
-    fin(s0, s1, s2);
+    s0 = warp_sum(s0);
+    s1 = warp_max(s1);
+    __syncthreads();
+    if (lane == 0) { red[2 * wid] = s0; red[2 * wid + 1] = s1; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    s0 = 0; s1 = 0;
+    for (int w = 0; w < kThreads / 32; ++w) { s0 += red[2 * w]; s1 = fmax(s1, red[2 * w + 1]); }
+    fin(s0, s1);
     __threadfence();
     f.ints[0] = 0;
 }
+
+// Launch: x along threads (kThreads wide); block row b handles the (y, z)
+// rows b, b + gridDim.y, ...
+inline dim3 flow_grid(int nx, int ny, int nz)
+{
+    const long rows = (long)ny * nz;
+    return dim3((nx + kThreads - 1) / kThreads, (unsigned)(rows < kRowBlocks ? rows : kRowBlocks), 1);
+}
+#define FLOW_ROWS(f_ny, f_nz)                                                                        \
+    for (long r_ = blockIdx.y; r_ < (long)(f_ny) * (f_nz); r_ += gridDim.y)                          \
+        for (int y = (int)(r_ % (f_ny)), z = (int)(r_ / (f_ny)), once_ = 1; once_; once_ = 0)
 
 // u = div A + m0, periodic central differences (eq. change_var); mass of u.
 template <typename T>
 __global__ void k_div(const T* __restrict__ A, T* __restrict__ u, Flow f, int want_mass)
 {
-    const long n = f.n;
-    const T sg = (T)f.sg, m0 = (T)f.m0;
-    double s = 0.0;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % f.nx), y = (int)((i / f.nx) % f.ny), z = (int)(i / ((long)f.nx * f.ny));
-        const long row = i - x, pl = i - (long)y * f.nx - x;
-        const T dx = A[row + wrap_h(x + 1, f.nx)] - A[row + wrap_h(x - 1, f.nx)];
-        const T dy = A[n + pl + (long)wrap_h(y + 1, f.ny) * f.nx + x] - A[n + pl + (long)wrap_h(y - 1, f.ny) * f.nx + x];
-        const long zp = ((long)wrap_h(z + 1, f.nz) * f.ny + y) * f.nx + x, zm = ((long)wrap_h(z - 1, f.nz) * f.ny + y) * f.nx + x;
-        const T dz = A[2 * n + zp] - A[2 * n + zm];
-        const T v = sg * (dx + dy + dz) + m0;
-        u[i] = v;
-        s += (double)v;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const long n = f.n, pls = (long)f.nx * f.ny;
+    T ms = 0;
+    if (x < f.nx) {
+        FLOW_ROWS(f.ny, f.nz)
+        {
+            const long row = (long)z * pls + (long)y * f.nx;
+            const T dx = A[row + nb(x, 1, f.nx)] - A[row + nb(x, -1, f.nx)];
+            const long pl = (long)z * pls;
+            const T dy = A[n + pl + (long)nb(y, 1, f.ny) * f.nx + x] - A[n + pl + (long)nb(y, -1, f.ny) * f.nx + x];
+            const long col = (long)y * f.nx + x;
+            const T dz = A[2 * n + (long)nb(z, 1, f.nz) * pls + col] - A[2 * n + (long)nb(z, -1, f.nz) * pls + col];
+            const T v = (T)f.sg * (dx + dy + dz) + (T)f.m0;
+            u[row + x] = v;
+            ms += v;
+        }
     }
     if (!want_mass) return;
-    flow_finish(f, s, 0.0, 0.0, [&](double s0, double, double) { f.hs[H_MASS] = s0 / (double)f.n; });
+    flow_finish<T>(f, ms, T(0), [&](double s0, double) { f.hs[H_MASS] = s0 / (double)f.n; });
 }
 
 // One periodic 1-D Gaussian pass along axis AX (0 x, 1 y, 2 z).
 template <typename T, int AX>
 __global__ void k_blur(const T* __restrict__ in, T* __restrict__ out, int nx, int ny, int nz, Weights w)
 {
-    const long n = (long)nx * ny * nz;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nx) return;
     const int R = w.R;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((long)nx * ny));
+    const long pls = (long)nx * ny;
+    FLOW_ROWS(ny, nz)
+    {
+        const long row = (long)z * pls + (long)y * nx;
         T s = 0;
         if (AX == 0) {
-            const long row = i - x;
-            for (int j = -R; j <= R; ++j) s += wget<T>(w, j + R) * in[row + wrap_h(x + j, nx)];
+            for (int j = -R; j <= R; ++j) s += wget<T>(w, j + R) * in[row + nb(x, j, nx)];
         } else if (AX == 1) {
-            const long pl = i - (long)y * nx;
-            for (int j = -R; j <= R; ++j) s += wget<T>(w, j + R) * in[pl + (long)wrap_h(y + j, ny) * nx];
+            const long pl = (long)z * pls;
+            for (int j = -R; j <= R; ++j) s += wget<T>(w, j + R) * in[pl + (long)nb(y, j, ny) * nx + x];
         } else {
-            const long col = (long)y * nx + x, pls = (long)nx * ny;
-            for (int j = -R; j <= R; ++j) s += wget<T>(w, j + R) * in[(long)wrap_h(z + j, nz) * pls + col];
+            const long col = (long)y * nx + x;
+            for (int j = -R; j <= R; ++j) s += wget<T>(w, j + R) * in[(long)nb(z, j, nz) * pls + col];
         }
-        out[i] = s;
+        out[row + x] = s;
     }
 }
 
@@ -153,60 +197,62 @@ template <typename T>
 __global__ void k_adam(const T* __restrict__ gb, T* __restrict__ A, T* __restrict__ m, T* __restrict__ v, Flow f,
                        int only_grad)
 {
-    const long n = f.n;
-    const T sg = (T)f.sg;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const long n = f.n, pls = (long)f.nx * f.ny;
     const unsigned t = f.ints[1] + 1;
     const T b1 = (T)f.beta1, b2 = (T)f.beta2;
-    const T c1 = (T)(1.0 / (1.0 - pow(f.beta1, (double)t))), c2 = (T)(1.0 / (1.0 - pow(f.beta2, (double)t)));
-    const T lr = (T)f.lr, ae = (T)f.adam_eps;
-    double sabs = 0.0, gmax = 0.0;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % f.nx), y = (int)((i / f.nx) % f.ny), z = (int)(i / ((long)f.nx * f.ny));
-        const long row = i - x, pl = i - (long)y * f.nx - x;
-        T g[3];
-        g[0] = sg * (gb[row + wrap_h(x - 1, f.nx)] - gb[row + wrap_h(x + 1, f.nx)]);
-        g[1] = sg * (gb[pl + (long)wrap_h(y - 1, f.ny) * f.nx + x] - gb[pl + (long)wrap_h(y + 1, f.ny) * f.nx + x]);
-        g[2] = sg * (gb[((long)wrap_h(z - 1, f.nz) * f.ny + y) * f.nx + x] - gb[((long)wrap_h(z + 1, f.nz) * f.ny + y) * f.nx + x]);
+    const T c1 = T(1) / (T(1) - pow_<T>(b1, (T)t)), c2 = T(1) / (T(1) - pow_<T>(b2, (T)t));
+    const T lr = (T)f.lr, ae = (T)f.adam_eps, sg = (T)f.sg;
+    T sabs = 0, gmax = 0;
+    if (x < f.nx) {
+        FLOW_ROWS(f.ny, f.nz)
+        {
+            const long row = (long)z * pls + (long)y * f.nx, i = row + x;
+            T g[3];
+            g[0] = sg * (gb[row + nb(x, -1, f.nx)] - gb[row + nb(x, 1, f.nx)]);
+            g[1] = sg * (gb[(long)z * pls + (long)nb(y, -1, f.ny) * f.nx + x] - gb[(long)z * pls + (long)nb(y, 1, f.ny) * f.nx + x]);
+            g[2] = sg * (gb[(long)nb(z, -1, f.nz) * pls + (long)y * f.nx + x] - gb[(long)nb(z, 1, f.nz) * pls + (long)y * f.nx + x]);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const long k = c * n + i;
-            const T gc = g[c];
-            const T ag = gc < T(0) ? -gc : gc;
-            sabs += (double)ag;
-            gmax = fmax(gmax, (double)ag);
-            if (only_grad) {
-                m[k] = gc;
-                continue;
+            for (int c = 0; c < 3; ++c) {
+                const long k = c * n + i;
+                const T gc = g[c];
+                const T ag = gc < T(0) ? -gc : gc;
+                sabs += ag;
+                gmax = ag > gmax ? ag : gmax;
+                if (only_grad) {
+                    m[k] = gc;
+                    continue;
+                }
+                const T mk = b1 * m[k] + (T(1) - b1) * gc;
+                const T vk = b2 * v[k] + (T(1) - b2) * gc * gc;
+                m[k] = mk;
+                v[k] = vk;
+                A[k] -= lr * (mk * c1) / (sqrt(vk * c2) + ae);
             }
-            const T mk = b1 * m[k] + (T(1) - b1) * gc;
-            const T vk = b2 * v[k] + (T(1) - b2) * gc * gc;
-            m[k] = mk;
-            v[k] = vk;
-            A[k] -= lr * (mk * c1) / (sqrt(vk * c2) + ae);
         }
     }
-    flow_finish(f, sabs, gmax, 0.0, [&](double s0, double s1, double) {
+    flow_finish<T>(f, sabs, gmax, [&](double s0, double s1) {
         f.hs[H_GMAX] = s1;
         f.hs[H_GABS] = s0 / (3.0 * (double)f.n);
         if (only_grad) return;
         f.ints[1] = t;
-        const unsigned row = f.ints[2];
-        if (f.trace && (int)row < f.trace_cap) {
-            double* r = f.trace + (size_t)row * 5;
+        const unsigned rowi = f.ints[2];
+        if (f.trace && (int)rowi < f.trace_cap) {
+            double* r = f.trace + (size_t)rowi * 5;
             r[0] = f.sweep_scal[S_E];
             r[1] = s1;
             r[2] = s0 / (3.0 * (double)f.n);
             r[3] = f.hs[H_MASS];
             r[4] = (double)t;
         }
-        f.ints[2] = row + 1;
+        f.ints[2] = rowi + 1;
     });
 }
 
-int flow_blocks(long n)
+long flow_blocks(int nx, int ny, int nz)
 {
-    long b = (n + kThreads - 1) / kThreads;
-    return (int)(b < 152 * 8 ? b : 152 * 8);
+    const dim3 g = flow_grid(nx, ny, nz);
+    return (long)g.x * g.y;
 }
 
 }  // namespace
@@ -326,7 +372,7 @@ extern "C" pfc_status pfc_hflow_create(const pfc_problem* prob, const pfc_hflow_
     ok = ok && cudaMalloc((void**)&h->spart, sizeof(double) * NPART * (size_t)h->sweep_slots) == cudaSuccess &&
          cudaMalloc((void**)&h->sints, sizeof(unsigned) * NINTS) == cudaSuccess &&
          cudaMalloc((void**)&h->sscal, sizeof(double) * NSCAL) == cudaSuccess &&
-         cudaMalloc((void**)&h->fpart, sizeof(double) * NH * (size_t)flow_blocks(h->N)) == cudaSuccess &&
+         cudaMalloc((void**)&h->fpart, sizeof(double) * 2 * (size_t)flow_blocks(p.nx, p.ny, p.nz)) == cudaSuccess &&
          cudaMalloc((void**)&h->fints, sizeof(unsigned) * 4) == cudaSuccess &&
          cudaMalloc((void**)&h->hs, sizeof(double) * NH) == cudaSuccess &&
          cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) == cudaSuccess;
@@ -380,10 +426,10 @@ static cudaError_t blur3(const pfc_hflow* h, T* in, T* t1, T* t2, T** result, cu
         *result = in;
         return cudaSuccess;
     }
-    const int nb = flow_blocks(h->N);
-    k_blur<T, 0><<<nb, kThreads, 0, s>>>(in, t1, h->P.nx, h->P.ny, h->P.nz, h->W);
-    k_blur<T, 1><<<nb, kThreads, 0, s>>>(t1, t2, h->P.nx, h->P.ny, h->P.nz, h->W);
-    k_blur<T, 2><<<nb, kThreads, 0, s>>>(t2, t1, h->P.nx, h->P.ny, h->P.nz, h->W);
+    const dim3 gr = flow_grid(h->P.nx, h->P.ny, h->P.nz);
+    k_blur<T, 0><<<gr, kThreads, 0, s>>>(in, t1, h->P.nx, h->P.ny, h->P.nz, h->W);
+    k_blur<T, 1><<<gr, kThreads, 0, s>>>(t1, t2, h->P.nx, h->P.ny, h->P.nz, h->W);
+    k_blur<T, 2><<<gr, kThreads, 0, s>>>(t2, t1, h->P.nx, h->P.ny, h->P.nz, h->W);
     *result = t1;
     return cudaGetLastError();
 }
@@ -395,16 +441,16 @@ static cudaError_t field(const pfc_hflow* h, const T* A, T** ut, int want_mass, 
     T* b0 = (T*)h->buf[0];
     T* b2 = (T*)h->buf[2];
     T* b3 = (T*)h->buf[3];
-    const int nb = flow_blocks(h->N);
+    const dim3 gr = flow_grid(h->P.nx, h->P.ny, h->P.nz);
     if (h->W.R == 0) {
-        k_div<T><<<nb, kThreads, 0, s>>>(A, b0, flow_desc(h), want_mass);
+        k_div<T><<<gr, kThreads, 0, s>>>(A, b0, flow_desc(h), want_mass);
         *ut = b0;
         return cudaGetLastError();
     }
-    k_div<T><<<nb, kThreads, 0, s>>>(A, b2, flow_desc(h), want_mass);
-    k_blur<T, 0><<<nb, kThreads, 0, s>>>(b2, b3, h->P.nx, h->P.ny, h->P.nz, h->W);
-    k_blur<T, 1><<<nb, kThreads, 0, s>>>(b3, b2, h->P.nx, h->P.ny, h->P.nz, h->W);
-    k_blur<T, 2><<<nb, kThreads, 0, s>>>(b2, b0, h->P.nx, h->P.ny, h->P.nz, h->W);
+    k_div<T><<<gr, kThreads, 0, s>>>(A, b2, flow_desc(h), want_mass);
+    k_blur<T, 0><<<gr, kThreads, 0, s>>>(b2, b3, h->P.nx, h->P.ny, h->P.nz, h->W);
+    k_blur<T, 1><<<gr, kThreads, 0, s>>>(b3, b2, h->P.nx, h->P.ny, h->P.nz, h->W);
+    k_blur<T, 2><<<gr, kThreads, 0, s>>>(b2, b0, h->P.nx, h->P.ny, h->P.nz, h->W);
     *ut = b0;
     return cudaGetLastError();
 }
@@ -437,7 +483,7 @@ static cudaError_t step(pfc_hflow* h, T* A, T* m, T* v, cudaStream_t s)
     T* gb = nullptr;
     cudaError_t e = eval<T>(h, A, &gb, s);
     if (e != cudaSuccess) return e;
-    k_adam<T><<<flow_blocks(h->N), kThreads, 0, s>>>(gb, A, m, v, flow_desc(h), 0);
+    k_adam<T><<<flow_grid(h->P.nx, h->P.ny, h->P.nz), kThreads, 0, s>>>(gb, A, m, v, flow_desc(h), 0);
     return cudaGetLastError();
 }
 
@@ -468,11 +514,11 @@ extern "C" pfc_status pfc_hflow_grad(pfc_hflow* h, const void* A, void* gA, doub
     if (h->P.prec == PFC_FP64) {
         double* gb = nullptr;
         HCU(eval<double>(h, (const double*)A, &gb, s));
-        k_adam<double><<<flow_blocks(h->N), kThreads, 0, s>>>(gb, nullptr, (double*)gA, nullptr, f, 1);
+        k_adam<double><<<flow_grid(h->P.nx, h->P.ny, h->P.nz), kThreads, 0, s>>>(gb, nullptr, (double*)gA, nullptr, f, 1);
     } else {
         float* gb = nullptr;
         HCU(eval<float>(h, (const float*)A, &gb, s));
-        k_adam<float><<<flow_blocks(h->N), kThreads, 0, s>>>(gb, nullptr, (float*)gA, nullptr, f, 1);
+        k_adam<float><<<flow_grid(h->P.nx, h->P.ny, h->P.nz), kThreads, 0, s>>>(gb, nullptr, (float*)gA, nullptr, f, 1);
     }
     HCU(cudaGetLastError());
     if (G_host) {

@@ -161,3 +161,19 @@ def batch_instances(n_inst: int = 64, sizes=(64, 96, 128), seed: int = 12345):
         out.append(Instance(f"batch_{k}", (n, n, n), 1.5, baseline_poly_to_a(a_, b_, c_, d_, e_),
                             init={"kind": "noise", "mean": float(vf), "std": 0.1, "seed": 100 + k}))
     return out
+
+
+def paper_flow_100(seed: int = 0):
+    """The generator's setting of Sec. 4.1 and Fig. cvg_1: a 100^3 grid with
+    spacing 0.01, eps = 0.02, the paper's double well (wells -1 and 1),
+    a = (1, 2.4, 9, 30, 170, -195), mass m0 = -0.66, blur of 2 voxels, Adam with
+    lr 1e-3 and betas (0.9, 0.999).  A0 is white noise scaled so that div A0
+    has a standard deviation of about 0.1 (the paper does not give the scale).
+    Returns (problem dict, flow dict, A0 of shape (3, 100, 100, 100))."""
+    n, h = 100, 0.01
+    prob = {"shape": (n, n, n), "h": h, "eps": 0.02, "xi": 1e-6, "a": (1.0, 2.4, 9.0, 30.0, 170.0, -195.0), "well": 1}
+    flow = {"m0": -0.66, "lr": 1e-3, "beta1": 0.9, "beta2": 0.999, "adam_eps": 1e-8, "blur_sigma": 2.0}
+    scale = 2.0 * h * 0.1 / math.sqrt(6.0)
+    rng = np.random.default_rng(seed)
+    A0 = scale * rng.standard_normal((3, n, n, n))
+    return prob, flow, A0

@@ -92,3 +92,27 @@ def test_errors():
     with pytest.raises(pfc.PfcError):
         pfc.HFlow(pfc.Problem(nx=8, ny=8, nz=8, eps=1.5, a=(1, 0, 1, 0, 0, 0), prec="fp64"), m0=0.3,
                   blur_sigma=20.0)                                  # radius 60 > 32
+
+
+def test_paper_setting_100():
+    """Alg. 1 in the paper's own setting (Sec. 4.1, Fig. cvg_1 parameters at
+    100^3, h = 0.01, eps = 0.02, the +-1 well, blur 2 voxels): FP32 against
+    the FP64 oracle for 2 steps, then 300 steps stay finite, keep the mass
+    and lower the energy."""
+    pd, fd, A0 = I.paper_flow_100()
+    nz, ny, nx = pd["shape"]
+    prob = pfc.Problem(nx=nx, ny=ny, nz=nz, h=pd["h"], eps=pd["eps"], xi=pd["xi"], a=pd["a"], well=pd["well"],
+                       prec="fp32")
+    flow = pfc.HFlow(prob, m0=fd["m0"], lr=fd["lr"], blur_sigma=fd["blur_sigma"])
+    A32 = A0.astype(np.float32)
+    A = torch.tensor(A32, device="cuda")
+    m, v = torch.zeros_like(A), torch.zeros_like(A)
+    tr = flow.run(A, m, v, 2)
+    op = {"a": pd["a"], "eps": pd["eps"], "xi": pd["xi"], "h": pd["h"], "well": pd["well"]}
+    _, _, _, _, tro = oracle.hflow_run(A32.astype(np.float64), np.zeros_like(A0), np.zeros_like(A0), op, fd, 2)
+    np.testing.assert_allclose(tr[:, 0], tro[:, 0], rtol=1e-4)
+    np.testing.assert_allclose(tr[:, 1:3], tro[:, 1:3], rtol=1e-3)
+    tr = flow.run(A, m, v, 300)
+    assert np.all(np.isfinite(tr))
+    assert np.max(np.abs(tr[:, 3] - fd["m0"])) < 1e-6
+    assert tr[-1, 0] < tr[0, 0]
