@@ -20,6 +20,11 @@ Parity status per function (what pins it, in tests/test_oracle_pins.py):
   step / run       mass conservation, lambda = mean(g), descent of E
   curvatures       kappa1 + kappa2 = H^eps, kappa1 kappa2 <= K^eps, tanh sphere
   b_to_a           the eight printed rows of the paper's two parameter tables
+  mu, theta        (Sec. 5.2 orientation term) closed form on a sine field, the
+                   axis-sum identity with the a00 term, central differences
+  a_field          (Sec. 5.2 a(x)) linearity in a: E equals the sum of the
+                   per-coefficient densities weighted by a(x); central differences
+  diagnostics      (Sec. 4.5) constant field and tanh-slab closed forms
   hflow_*          (Alg. 1) mass = m0 exactly, blur moments and symmetry, the
                    closed-form first Adam step, central differences of G(A)
 """
@@ -42,7 +47,7 @@ _lib = None
 class _HFlow(ctypes.Structure):
     _fields_ = [("m0", ctypes.c_double), ("lr", ctypes.c_double), ("beta1", ctypes.c_double),
                 ("beta2", ctypes.c_double), ("adam_eps", ctypes.c_double), ("blur_sigma", ctypes.c_double),
-                ("blur_radius", ctypes.c_int)]
+                ("blur_radius", ctypes.c_int), ("m_field", ctypes.POINTER(ctypes.c_double))]
 
 
 class _Problem(ctypes.Structure):
@@ -50,6 +55,7 @@ class _Problem(ctypes.Structure):
         ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
         ("h", ctypes.c_double), ("eps", ctypes.c_double), ("xi", ctypes.c_double),
         ("a", ctypes.c_double * 6), ("well", ctypes.c_int),
+        ("mu", ctypes.c_double), ("theta", ctypes.c_double * 3), ("a_field", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -78,6 +84,7 @@ def _load():
                 ("pfo_step", [P, D, D, ctypes.c_double, D]),
                 ("pfo_run", [P, D, ctypes.c_int, ctypes.c_double, D]),
                 ("pfo_curvatures", [P, D, D, D]),
+                ("pfo_diagnostics", [P, D, D]),
             ]:
                 f = getattr(lib, name)
                 f.argtypes = args
@@ -101,11 +108,22 @@ def _load():
 
 
 def _prob(u: np.ndarray, p: dict) -> _Problem:
+    """Problem keys: h, eps, xi, a, well; optional (Sec. 5.2) mu, theta (3
+    values, x y z) and a_field (shape (6, nz, ny, nx): a(x))."""
     nz, ny, nx = u.shape
     a = p["a"]
-    return _Problem(nx, ny, nz, float(p.get("h", 1.0)), float(p["eps"]),
-                    float(p.get("xi", 1e-6)), (ctypes.c_double * 6)(*[float(v) for v in a]),
-                    int(p.get("well", 0)))
+    s = _Problem(nx, ny, nz, float(p.get("h", 1.0)), float(p["eps"]),
+                 float(p.get("xi", 1e-6)), (ctypes.c_double * 6)(*[float(v) for v in a]),
+                 int(p.get("well", 0)), float(p.get("mu", 0.0)),
+                 (ctypes.c_double * 3)(*[float(v) for v in p.get("theta", (0.0, 0.0, 0.0))]), None)
+    af = p.get("a_field")
+    if af is not None:
+        af = np.ascontiguousarray(af, dtype=np.float64)
+        if af.shape != (6, nz, ny, nx):
+            raise ValueError("a_field must be shaped (6, nz, ny, nx)")
+        s.a_field = _ptr(af)
+        s._keep = af          # the array must outlive the call
+    return s
 
 
 def _f64(u):
@@ -182,6 +200,15 @@ def curvatures(u, p):
     return k1, k2
 
 
+def diagnostics(u, p) -> dict:
+    """Sec. 4.5 viability quantities: discrepancy and Cahn-Hilliard integrals,
+    their ratio, max and min of u."""
+    u = _f64(u)
+    out = np.empty(5)
+    _ok(_load().pfo_diagnostics(ctypes.byref(_prob(u, p)), _ptr(u), _ptr(out)), "diagnostics")
+    return {"discrepancy": out[0], "cahn_hilliard": out[1], "ratio": out[2], "max": out[3], "min": out[4]}
+
+
 def b_to_a(b) -> np.ndarray:
     b = np.ascontiguousarray(b, dtype=np.float64)
     if b.shape != (7,):
@@ -194,10 +221,18 @@ def b_to_a(b) -> np.ndarray:
 # ---------------------------------------------------------------- Alg. 1
 
 def _flow(fp: dict) -> _HFlow:
+    """Flow keys: m0, lr, beta1, beta2, adam_eps, blur_sigma, blur_radius;
+    optional m_field (shape (nz, ny, nx): the spatialised mass of Sec. 5.2)."""
     sigma = float(fp.get("blur_sigma", 0.0))
     R = int(fp.get("blur_radius", 0)) or (int(np.ceil(3.0 * sigma)) if sigma > 0 else 0)
-    return _HFlow(float(fp.get("m0", 0.0)), float(fp.get("lr", 1e-3)), float(fp.get("beta1", 0.9)),
-                  float(fp.get("beta2", 0.999)), float(fp.get("adam_eps", 1e-8)), sigma, R)
+    s = _HFlow(float(fp.get("m0", 0.0)), float(fp.get("lr", 1e-3)), float(fp.get("beta1", 0.9)),
+               float(fp.get("beta2", 0.999)), float(fp.get("adam_eps", 1e-8)), sigma, R, None)
+    mf = fp.get("m_field")
+    if mf is not None:
+        mf = np.ascontiguousarray(mf, dtype=np.float64)
+        s.m_field = _ptr(mf)
+        s._keep = mf
+    return s
 
 
 def _A(A):

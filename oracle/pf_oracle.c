@@ -86,8 +86,12 @@ static double softplus_xi_prime(double x, double xi)
     return t / (1.0 + t);
 }
 
+/* coefficients of eq. Feps */
+typedef struct { double c1, c2, c3, c4, c5, c6; } coefs;
+
 /* Per-voxel state of the forward evaluation. */
 typedef struct {
+    coefs cf;        /* eq. Feps coefficients at this voxel (a, or a(x)) */
     double u;        /* centre value                                   */
     double G[3];     /* grad u                                          */
     double Hs[3][3]; /* Hess u (symmetric, all nine entries stored)     */
@@ -96,15 +100,12 @@ typedef struct {
     double M[3][3];  /* eq. Meps with the regularised normal            */
     double T, S, D;  /* Tr M, ||M||^2, 2||M||^2 - (Tr M)^2             */
     double P, r;     /* smooth positive part of D and its square root   */
-    double e;        /* integrand of eq. Feps                           */
+    double tg;       /* theta . grad u (orientation term, Sec. 5.2)     */
+    double e;        /* integrand of eq. Feps (plus the orientation term) */
 } voxel;
 
-/* coefficients of eq. Feps */
-typedef struct { double c1, c2, c3, c4, c5, c6; } coefs;
-
-static coefs make_coefs(const pfo_problem* p)
+static coefs make_coefs(const pfo_problem* p, const double* a)   /* a20 a11 a02 a10 a01 a00 */
 {
-    const double* a = p->a;   /* a20 a11 a02 a10 a01 a00 */
     coefs c;
     c.c1 = (a[0] + a[2] - a[1]) / (2.0 * p->eps);
     c.c2 = a[1] / (2.0 * p->eps);
@@ -113,6 +114,16 @@ static coefs make_coefs(const pfo_problem* p)
     c.c5 = (a[3] - a[4]) / 2.0;
     c.c6 = a[5] * p->eps;
     return c;
+}
+
+/* The coefficients at voxel i: the constant a, or a(x) of Sec. 5.2. */
+static coefs coefs_at(const pfo_problem* p, long i)
+{
+    if (!p->a_field) return make_coefs(p, p->a);
+    const long N = (long)p->nx * p->ny * p->nz;
+    double a[6];
+    for (int k = 0; k < 6; ++k) a[k] = p->a_field[k * N + i];
+    return make_coefs(p, a);
 }
 
 /* Finite differences of Sec. 4.1 (reading: second-order central stencils). */
@@ -143,10 +154,11 @@ static void stencils(const pfo_problem* p, const double* u, int x, int y, int z,
 
 /* Forward evaluation of one voxel: eq. Meps, the invariants of Sec. 3.1 and
  * the integrand of eq. Feps. */
-static void forward(const pfo_problem* p, const coefs* cf, const double* u,
-                    int x, int y, int z, voxel* v)
+static void forward(const pfo_problem* p, const double* u, int x, int y, int z, voxel* v)
 {
     stencils(p, u, x, y, z, v);
+    v->cf = coefs_at(p, vid(p, x, y, z));
+    const coefs* cf = &v->cf;
     double g2 = v->G[0] * v->G[0] + v->G[1] * v->G[1] + v->G[2] * v->G[2];
     v->rho = g2 + p->xi * p->xi;
     v->q = sqrt(v->rho);
@@ -164,6 +176,9 @@ static void forward(const pfo_problem* p, const coefs* cf, const double* u,
     v->r = sqrt(v->P);
     v->e = cf->c1 * v->S + cf->c2 * v->T * v->T + cf->c3 * v->T * v->r
          + cf->c4 * v->q * v->T + cf->c5 * v->q * v->r + cf->c6 * g2;
+    /* Sec. 5.2: the orientation term eps mu (theta . grad u)^2 */
+    v->tg = p->theta[0] * v->G[0] + p->theta[1] * v->G[1] + p->theta[2] * v->G[2];
+    v->e += p->eps * p->mu * v->tg * v->tg;
 }
 
 /* Cotangents of one voxel's integrand with respect to its stencil outputs:
@@ -171,9 +186,9 @@ static void forward(const pfo_problem* p, const coefs* cf, const double* u,
  * (Hbar holds the derivative with respect to each of the nine entries; the
  * stencil transpose below visits each unordered pair once and adds both).
  * Chain: e(S, T, r(D(S,T)), q(G), |G|^2), M(Hs, w(u), G). */
-static void local_adjoint(const pfo_problem* p, const coefs* cf, const voxel* v,
-                          double* ubar, double Gbar[3], double Hbar[3][3])
+static void local_adjoint(const pfo_problem* p, const voxel* v, double* ubar, double Gbar[3], double Hbar[3][3])
 {
+    const coefs* cf = &v->cf;
     double rp = 0.0;     /* dr/dD, defined as 0 where r == 0 */
     if (v->r > 0.0) rp = softplus_xi_prime(v->D, p->xi) / (2.0 * v->r);
     double k = (cf->c3 * v->T + cf->c5 * v->q) * rp;   /* de/dD */
@@ -196,7 +211,8 @@ static void local_adjoint(const pfo_problem* p, const coefs* cf, const voxel* v,
     /* M depends on G through w G G^T / rho; q and |G|^2 depend on G too */
     for (int a = 0; a < 3; ++a)
         Gbar[a] = 2.0 * v->w / v->rho * (LG[a] - GLG / v->rho * v->G[a])
-                + dq * v->G[a] / v->q + 2.0 * cf->c6 * v->G[a];
+                + dq * v->G[a] / v->q + 2.0 * cf->c6 * v->G[a]
+                + 2.0 * p->eps * p->mu * v->tg * p->theta[a];
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) Hbar[a][b] = -p->eps * L[a][b];
 }
@@ -206,12 +222,11 @@ static void local_adjoint(const pfo_problem* p, const coefs* cf, const voxel* v,
 int pfo_density(const pfo_problem* p, const double* u, double* e)
 {
     if (check(p) || !u || !e) return -1;
-    coefs cf = make_coefs(p);
     voxel v;
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
-                forward(p, &cf, u, x, y, z, &v);
+                forward(p, u, x, y, z, &v);
                 e[vid(p, x, y, z)] = v.e;
             }
     return 0;
@@ -220,13 +235,12 @@ int pfo_density(const pfo_problem* p, const double* u, double* e)
 int pfo_energy(const pfo_problem* p, const double* u, double* E)
 {
     if (check(p) || !u || !E) return -1;
-    coefs cf = make_coefs(p);
     nsum acc = { 0.0, 0.0 };
     voxel v;
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
-                forward(p, &cf, u, x, y, z, &v);
+                forward(p, u, x, y, z, &v);
                 nsum_add(&acc, v.e);
             }
     *E = p->h * p->h * p->h * nsum_get(&acc);
@@ -236,10 +250,10 @@ int pfo_energy(const pfo_problem* p, const double* u, double* E)
 /* cotangent fields, one record per voxel: ubar, Gbar[3], Hbar (xx yy zz xy xz yz) */
 enum { CT_U = 0, CT_GX, CT_GY, CT_GZ, CT_HXX, CT_HYY, CT_HZZ, CT_HXY, CT_HXZ, CT_HYZ, CT_N };
 
-static void cotangent_record(const pfo_problem* p, const coefs* cf, const voxel* v, double* rec)
+static void cotangent_record(const pfo_problem* p, const voxel* v, double* rec)
 {
     double ub, Gb[3], Hb[3][3];
-    local_adjoint(p, cf, v, &ub, Gb, Hb);
+    local_adjoint(p, v, &ub, Gb, Hb);
     rec[CT_U] = ub;
     rec[CT_GX] = Gb[0]; rec[CT_GY] = Gb[1]; rec[CT_GZ] = Gb[2];
     rec[CT_HXX] = Hb[0][0]; rec[CT_HYY] = Hb[1][1]; rec[CT_HZZ] = Hb[2][2];
@@ -289,16 +303,15 @@ int pfo_energy_and_grad(const pfo_problem* p, const double* u, double* E, double
     long N = (long)p->nx * p->ny * p->nz;
     double* ct = (double*)malloc(sizeof(double) * CT_N * (size_t)N);
     if (!ct) return -1;
-    coefs cf = make_coefs(p);
     nsum acc = { 0.0, 0.0 };
     voxel v;
     /* pass 1: forward and local reverse mode, voxel by voxel */
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
-                forward(p, &cf, u, x, y, z, &v);
+                forward(p, u, x, y, z, &v);
                 nsum_add(&acc, v.e);
-                cotangent_record(p, &cf, &v, ct + vid(p, x, y, z) * CT_N);
+                cotangent_record(p, &v, ct + vid(p, x, y, z) * CT_N);
             }
     /* pass 2: transposed stencils */
     for (int z = 0; z < p->nz; ++z)
@@ -313,7 +326,6 @@ int pfo_grad_sampled(const pfo_problem* p, const double* u, int n, const long* i
 {
     if (check(p) || !u || (n > 0 && (!idx || !g))) return -1;
     long N = (long)p->nx * p->ny * p->nz;
-    coefs cf = make_coefs(p);
     /* the gradient at j reads cotangents at offsets in {-1,0,1}^3 only;
      * compute those 27 records into a small local block */
     double* ct = (double*)malloc(sizeof(double) * CT_N * 27);
@@ -327,9 +339,9 @@ int pfo_grad_sampled(const pfo_problem* p, const double* u, int n, const long* i
         for (int dz = -1; dz <= 1; ++dz)
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dx = -1; dx <= 1; ++dx) {
-                    forward(p, &cf, u, x + dx, y + dy, z + dz, &v);
+                    forward(p, u, x + dx, y + dy, z + dz, &v);
                     int l = ((dz + 1) * 3 + (dy + 1)) * 3 + (dx + 1);
-                    cotangent_record(p, &cf, &v, ct + l * CT_N);
+                    cotangent_record(p, &v, ct + l * CT_N);
                 }
         /* gather on the 3x3x3 block around its centre: every offset it
          * visits lies inside the block, so its wrap never triggers */
@@ -388,17 +400,48 @@ int pfo_run(const pfo_problem* p, double* u, int nsteps, double tau, double* tra
 int pfo_curvatures(const pfo_problem* p, const double* u, double* k1, double* k2)
 {
     if (check(p) || !u || !k1 || !k2) return -1;
-    coefs cf = make_coefs(p);
     voxel v;
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
-                forward(p, &cf, u, x, y, z, &v);
+                forward(p, u, x, y, z, &v);
                 double root = sqrt(v.D > 0.0 ? v.D : 0.0);
                 double den = 2.0 * p->eps * v.q;
                 k1[vid(p, x, y, z)] = (v.T + root) / den;
                 k2[vid(p, x, y, z)] = (v.T - root) / den;
             }
+    return 0;
+}
+
+static double W(int well, double u)
+{
+    if (well == 1) return 0.25 * (1.0 - u * u) * (1.0 - u * u);
+    return u * u * (1.0 - u) * (1.0 - u);
+}
+
+int pfo_diagnostics(const pfo_problem* p, const double* u, double out[5])
+{
+    if (check(p) || !u || !out) return -1;
+    nsum dis = { 0, 0 }, ch = { 0, 0 };
+    double umax = -HUGE_VAL, umin = HUGE_VAL;
+    voxel v;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                stencils(p, u, x, y, z, &v);
+                const double g2 = v.G[0] * v.G[0] + v.G[1] * v.G[1] + v.G[2] * v.G[2];
+                const double kin = 0.5 * p->eps * g2, pot = W(p->well, v.u) / p->eps;
+                nsum_add(&dis, fabs(kin - pot));
+                nsum_add(&ch, kin + pot);
+                if (v.u > umax) umax = v.u;
+                if (v.u < umin) umin = v.u;
+            }
+    const double h3 = p->h * p->h * p->h;
+    out[0] = h3 * nsum_get(&dis);
+    out[1] = h3 * nsum_get(&ch);
+    out[2] = out[1] > 0.0 ? out[0] / out[1] : 0.0;
+    out[3] = umax;
+    out[4] = umin;
     return 0;
 }
 
@@ -479,7 +522,8 @@ int pfo_hflow_field(const pfo_problem* p, const pfo_hflow* f, const double* A, d
     if (check(p) || check_flow(f) || !A || !ut) return -1;
     long N = (long)p->nx * p->ny * p->nz;
     const int e[3][3] = { { 1, 0, 0 }, { 0, 1, 0 }, { 0, 0, 1 } };
-    /* eq. change_var: u = div A + m0 with periodic central differences */
+    /* eq. change_var: u = div A + m0 with periodic central differences
+     * (Sec. 5.2: + m(x) when the mass is spatialised) */
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
@@ -487,7 +531,8 @@ int pfo_hflow_field(const pfo_problem* p, const pfo_hflow* f, const double* A, d
                 for (int c = 0; c < 3; ++c)
                     d += (A[c * N + vid(p, x + e[c][0], y + e[c][1], z + e[c][2])]
                           - A[c * N + vid(p, x - e[c][0], y - e[c][1], z - e[c][2])]) / (2.0 * p->h);
-                ut[vid(p, x, y, z)] = d + f->m0;
+                const long i = vid(p, x, y, z);
+                ut[i] = d + (f->m_field ? f->m_field[i] : f->m0);
             }
     return blur(p, f, ut);   /* Alg. 1: small blur before the energy */
 }

@@ -26,6 +26,10 @@ typedef struct {
     double xi;     /* regularisation offset of |grad u| and of x^+ (Sec. 4.1)    */
     double a[6];   /* a20, a11, a02, a10, a01, a00 (eq. F)                       */
     int well;      /* 0: W(u)=u^2(1-u)^2, wells 0 and 1; 1: W(s)=(1-s^2)^2/4 (Sec. 2.3) */
+    /* extensions of Sec. 5.2 (all zero / NULL: the plain eq. Feps) */
+    double mu;            /* orientation weight: eps*mu*(theta . grad u)^2 joins the integrand */
+    double theta[3];      /* orientation direction (x, y, z), used as given (Sec. 5.2 takes |theta| = 1) */
+    const double* a_field;/* NULL, or spatialised coefficients a(x): a_field[k*N + i] is a_k at voxel i */
 } pfo_problem;
 
 /* All functions return 0 on success, -1 on invalid arguments. */
@@ -56,12 +60,20 @@ int pfo_run(const pfo_problem* p, double* u, int nsteps, double tau, double* tra
  * exact positive part and the xi-regularised |grad u|. */
 int pfo_curvatures(const pfo_problem* p, const double* u, double* k1, double* k2);
 
+/* Viability diagnostics of Sec. 4.5 with the plain central-difference
+ * gradient: out = {int |eps/2 |grad u|^2 - W(u)/eps|, int (eps/2 |grad u|^2 +
+ * W(u)/eps) (the Cahn-Hilliard energy, i.e. the diffuse area), their ratio
+ * (the normalised discrepancy, in [0, 1]), max u, min u}; integrals are h^3
+ * times the sums over voxels. */
+int pfo_diagnostics(const pfo_problem* p, const double* u, double out[5]);
+
 /* ---- Alg. 1 (Sec. 4.1): H^-1 flow through u = div A + m0, blur, Adam ---- */
 typedef struct {
     double m0;              /* mass: the mean of u                                        */
     double lr, beta1, beta2, adam_eps;   /* Adam (Sec. 4.1: 1e-3, 0.9, 0.999, no decay)   */
     double blur_sigma;      /* Gaussian blur std in voxels (Sec. 4.1: 2); 0 = no blur      */
     int blur_radius;        /* taps on each side; the caller passes ceil(3 sigma)          */
+    const double* m_field;  /* NULL, or a spatialised mass m(x) (Sec. 5.2): u = div A + m(x)  */
 } pfo_hflow;
 
 /* Discrete Gaussian of std sigma, taps -R..R, normalised to sum 1: w[0..2R]. */
@@ -70,7 +82,7 @@ void pfo_gauss_weights(double sigma, int R, double* w);
 /* a <- k * a in place (periodic separable Gaussian of the flow's sigma). */
 int pfo_blur(const pfo_problem* p, const pfo_hflow* f, double* a);
 
-/* ut = k * (div A + m0); A is 3 fields A_x, A_y, A_z of N voxels each (component-major). */
+/* ut = k * (div A + m0) (or + m(x)); A is 3 fields A_x, A_y, A_z of N voxels each (component-major). */
 int pfo_hflow_field(const pfo_problem* p, const pfo_hflow* f, const double* A, double* ut);
 
 /* G(A) = F_eps(k * (div A + m0)) and dG/dA (3 x N). */

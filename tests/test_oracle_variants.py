@@ -1,0 +1,176 @@
+"""Pins of the oracle's extensions (Sec. 5.2) and diagnostics (Sec. 4.5).
+
+  orientation term  eps mu (theta . grad u)^2: closed form on a sine field (the
+                    central difference of sin is sin(k) cos(kx)), the axis-sum
+                    identity sum over theta = e_x, e_y, e_z equals the a00 term
+                    with a00 = mu, and central differences of the gradient
+  a(x)              the integrand is linear in a, so E(a(x)) equals the sum over
+                    k of a_k(x) times the density with a = e_k; central
+                    differences of the gradient with a random a(x)
+  m(x)              u = div A + m(x): with A = 0 and no blur u is m(x), and the
+                    mean of u is the mean of m for any A
+  diagnostics       constant field (discrepancy = Cahn-Hilliard = N h^3 W(c)/eps),
+                    tanh slab (equipartition: the ratio vanishes like (h/eps)^2
+                    and the Cahn-Hilliard energy tends to sigma times the area)
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2103_04856_gb300 import inputs as I
+
+
+def prob(a, eps=1.5, h=1.0, xi=1e-6, well=0, **kw):
+    d = {"a": tuple(float(x) for x in a), "eps": eps, "h": h, "xi": xi, "well": well}
+    d.update(kw)
+    return d
+
+
+def _fd_grad(u, p, delta):
+    g = np.empty_like(u)
+    flat = u.reshape(-1)
+    for i in range(flat.size):
+        v = flat[i]
+        flat[i] = v + delta
+        ep = oracle.energy(u, p)
+        flat[i] = v - delta
+        em = oracle.energy(u, p)
+        flat[i] = v
+        g.reshape(-1)[i] = (ep - em) / (2 * delta)
+    return g
+
+
+# ------------------------------------------------------------ orientation
+
+@pytest.mark.parametrize("h", [1.0, 0.7])
+def test_orientation_sine_closed_form(h):
+    """u = c + s sin(2 pi x / L): G_x = s sin(2 pi / L) cos(2 pi x / L) / h, so
+    h^3 sum eps mu (theta . G)^2 = h eps mu s^2 sin^2(2 pi / L) theta_x^2 N / 2."""
+    nz, ny, nx = 3, 4, 10
+    s, c, eps, mu = 0.3, 0.4, 1.3, 2.5
+    x = np.arange(nx)
+    u = np.broadcast_to(c + s * np.sin(2 * math.pi * x / nx), (nz, ny, nx)).copy()
+    a = (0.7, -0.2, 0.4, 0.3, -0.1, 0.2)
+    base = oracle.energy(u, prob(a, eps=eps, h=h))
+    N = nx * ny * nz
+    for phi in (0.0, 0.4, 1.1, math.pi / 2):
+        th = (math.cos(phi), math.sin(phi) * 0.6, math.sin(phi) * 0.8)
+        E = oracle.energy(u, prob(a, eps=eps, h=h, mu=mu, theta=th))
+        want = h * eps * mu * s * s * math.sin(2 * math.pi / nx) ** 2 * th[0] ** 2 * N / 2
+        assert E - base == pytest.approx(want, rel=1e-10, abs=1e-12)
+
+
+def test_orientation_axis_sum_equals_a00_term():
+    rng = np.random.default_rng(5)
+    u = I.noise((5, 6, 7), 0.3, 0.2, 4)
+    a = rng.uniform(-1, 1, 6)
+    mu = 1.7
+    p0 = prob(a, h=0.8)
+    E0, g0 = oracle.energy_and_grad(u, p0)
+    Es, gs = 0.0, np.zeros_like(u)
+    for th in ((1, 0, 0), (0, 1, 0), (0, 0, 1)):
+        E, g = oracle.energy_and_grad(u, prob(a, h=0.8, mu=mu, theta=th))
+        Es += E - E0
+        gs += g - g0
+    Ea, ga = oracle.energy_and_grad(u, prob((0, 0, 0, 0, 0, mu), h=0.8))
+    assert Es == pytest.approx(Ea, rel=1e-11)
+    np.testing.assert_allclose(gs, ga, rtol=0, atol=1e-11 * np.max(np.abs(ga)))
+
+
+def test_orientation_gradient_central_differences():
+    rng = np.random.default_rng(8)
+    u = I.noise((6, 7, 8), 0.3, 0.1, 21)
+    th = rng.normal(size=3)
+    th /= np.linalg.norm(th)
+    p = prob(rng.uniform(-1, 1, 6), eps=1.5, h=0.9, xi=1e-2, mu=3.0, theta=tuple(th))
+    _, g = oracle.energy_and_grad(u, p)
+    gfd = _fd_grad(u.copy(), p, 1e-5)
+    assert np.max(np.abs(g - gfd)) < 1e-6 * np.max(np.abs(g))
+
+
+# ------------------------------------------------------------ a(x)
+
+def test_spatial_coefficients_linearity():
+    rng = np.random.default_rng(9)
+    shape = (5, 6, 7)
+    u = I.noise(shape, 0.3, 0.15, 6)
+    af = rng.uniform(-1, 1, (6,) + shape)
+    h = 0.9
+    E = oracle.energy(u, prob((0,) * 6, h=h, a_field=af))
+    want = 0.0
+    for k in range(6):
+        ek = np.zeros(6)
+        ek[k] = 1.0
+        want += np.sum(af[k] * oracle.density(u, prob(ek, h=h)))
+    assert E == pytest.approx(h ** 3 * want, rel=1e-12)
+    # a constant field is the constant a
+    a = rng.uniform(-1, 1, 6)
+    afc = np.broadcast_to(a[:, None, None, None], (6,) + shape).copy()
+    Ec, gc = oracle.energy_and_grad(u, prob((0,) * 6, h=h, a_field=afc))
+    Ea, ga = oracle.energy_and_grad(u, prob(a, h=h))
+    assert Ec == Ea
+    np.testing.assert_array_equal(gc, ga)
+
+
+def test_spatial_coefficients_gradient_central_differences():
+    rng = np.random.default_rng(10)
+    shape = (6, 7, 8)
+    u = I.noise(shape, 0.3, 0.1, 22)
+    af = rng.uniform(-1, 1, (6,) + shape)
+    p = prob((0,) * 6, eps=1.5, h=1.1, xi=1e-2, a_field=af)
+    _, g = oracle.energy_and_grad(u, p)
+    gfd = _fd_grad(u.copy(), p, 1e-5)
+    assert np.max(np.abs(g - gfd)) < 1e-6 * np.max(np.abs(g))
+
+
+# ------------------------------------------------------------ m(x)
+
+def test_spatial_mass_field():
+    rng = np.random.default_rng(11)
+    shape = (6, 7, 8)
+    m = rng.uniform(-0.7, -0.3, shape)
+    p = prob((1, 0, 1, 0, 0, 0))
+    A0 = np.zeros((3,) + shape)
+    np.testing.assert_array_equal(oracle.hflow_field(A0, p, {"m_field": m}), m)
+    A = rng.normal(size=(3,) + shape)
+    ut = oracle.hflow_field(A, p, {"m_field": m, "blur_sigma": 1.0})
+    assert ut.mean() == pytest.approx(m.mean(), abs=1e-13)
+    np.testing.assert_allclose(oracle.hflow_field(A0, p, {"m_field": m, "blur_sigma": 1.0}),
+                               oracle.blur(m, p, {"blur_sigma": 1.0}), rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------------------ diagnostics
+
+@pytest.mark.parametrize("well", [0, 1])
+def test_diagnostics_constant_field(well):
+    c, eps, h = 0.37, 1.3, 0.8
+    u = np.full((4, 5, 6), c)
+    W = c * c * (1 - c) ** 2 if well == 0 else (1 - c * c) ** 2 / 4
+    d = oracle.diagnostics(u, prob((0,) * 6, eps=eps, h=h, well=well))
+    want = 120 * h ** 3 * W / eps
+    assert d["discrepancy"] == pytest.approx(want, rel=1e-13)
+    assert d["cahn_hilliard"] == pytest.approx(want, rel=1e-13)
+    assert d["ratio"] == pytest.approx(1.0, rel=1e-13)
+    assert d["max"] == d["min"] == c
+
+
+@pytest.mark.parametrize("well", [0, 1])
+def test_diagnostics_tanh_slab_equipartition(well):
+    """On the tanh profile eps/2 |grad u|^2 = W(u)/eps (equipartition), so the
+    normalised discrepancy vanishes like (h/eps)^2, and the Cahn-Hilliard
+    energy tends to sigma x area (two interfaces of 8 x 8)."""
+    sigma = math.sqrt(2) / 6 if well == 0 else 2 * math.sqrt(2) / 3
+    ratios, areas = [], []
+    for n, eps in ((32, 2.0), (48, 3.0), (64, 4.0)):
+        u = I.tanh_slab((n, 8, 8), n / 2, eps, 1.0, well=well)
+        d = oracle.diagnostics(u, prob((0,) * 6, eps=eps, well=well))
+        ratios.append(d["ratio"])
+        areas.append(d["cahn_hilliard"] / (sigma * 2 * 64))
+        assert 0.0 <= d["ratio"] <= 1.0
+    assert ratios[0] < 0.03 and ratios[0] > ratios[1] > ratios[2]
+    scaled = [r * e * e for r, e in zip(ratios, (2.0, 3.0, 4.0))]
+    assert max(scaled) / min(scaled) < 1.1
+    assert abs(areas[0] - 1) < 0.02 and abs(areas[2] - 1) < 0.005
+    assert abs(areas[0] - 1) > abs(areas[1] - 1) > abs(areas[2] - 1)
