@@ -69,6 +69,13 @@ typedef struct {
     double a[6];            /* a20 a11 a02 a10 a01 a00 of eq. F, kappa1 >= kappa2         */
     int32_t tile_y;         /* 0 = automatic; else 8 or 16 rows per CTA tile             */
     int32_t tile_z;         /* 0 = automatic; else planes per CTA z-chunk (>= 1)         */
+    /* Orientation term of Sec. 5.2: eps mu (theta . grad u)^2 joins the
+     * integrand (grad u the central-difference gradient).  mu = 0 (with any
+     * theta) is the plain eq. Feps.  theta (x, y, z) is used as given; the
+     * paper takes it of unit norm.  Fused path only (PFC_EUNSUPPORTED on the
+     * plain path and in batches); it runs the extended sweep (8-row tiles). */
+    double mu;
+    double theta[3];
 } pfc_problem;
 
 typedef struct pfc_ctx pfc_ctx;
@@ -102,6 +109,25 @@ pfc_status pfc_step(pfc_ctx* ctx, const void* u_in, void* u_out, double tau,
  * Returns PFC_ENONFINITE if any step produced a non-finite scalar. */
 pfc_status pfc_run(pfc_ctx* ctx, void* u, int32_t nsteps, double tau, double* trace_host,
                    pfc_stream stream);
+
+/* Spatialised coefficients a(x) of Sec. 5.2: a_field (device, the context's
+ * element type) holds 6 planes of N values, a_field[k*N + i] = a_k at voxel i,
+ * k in the order of pfc_problem.a.  From the next call on, every evaluation
+ * (energy, gradient, step, run) uses a(x) instead of the constant a.  The
+ * library converts a(x) into its own copy on `stream`: a_field may be freed
+ * or reused once the stream has passed this call.  a_field = NULL returns
+ * to the constant a.  The first call allocates 6 fields of scratch.  Fused
+ * path only (PFC_EUNSUPPORTED on the plain path); runs the extended sweep. */
+pfc_status pfc_set_coefficient_field(pfc_ctx* ctx, const void* a_field, pfc_stream stream);
+
+/* Viability diagnostics of Sec. 4.5 with the central-difference gradient
+ * (no xi):  out_host[0] = h^3 sum |eps/2 |grad u|^2 - W(u)/eps| (discrepancy),
+ * out_host[1] = h^3 sum (eps/2 |grad u|^2 + W(u)/eps) (Cahn-Hilliard energy,
+ * the diffuse area), out_host[2] = out[0]/out[1] (in [0, 1]; 0 when out[1]
+ * is 0), out_host[3] = max u, out_host[4] = min u.  The paper deems a shape
+ * viable when the ratio is below 0.75 and max u > 0.1 > -0.1 > min u (wells
+ * -1 and 1).  Synchronises the stream. */
+pfc_status pfc_diagnostics(pfc_ctx* ctx, const void* u, double out_host[5], pfc_stream stream);
 
 /* Diffuse principal curvatures kappa1 >= kappa2 at every voxel (Sec. 3.1,
  * eqs. kepsa/kepsb, exact positive part, regularised |grad u|).  k1 and k2
@@ -165,6 +191,14 @@ pfc_status pfc_hflow_grad(pfc_hflow* flow, const void* A, void* gA, double* G_ho
  * CUDA-graph replays of 32 steps.  Synchronises the stream. */
 pfc_status pfc_hflow_run(pfc_hflow* flow, void* A, void* m, void* v, int32_t nsteps, int32_t* t,
                          double* trace_host, pfc_stream stream);
+
+/* Spatialised generation parameters (Sec. 5.2) for the flow: a(x) as for
+ * pfc_set_coefficient_field, and m(x) (device, N values of the problem's
+ * type): u = k * (div A + m(x)), whose mean is mean(m).  Both are copied on
+ * `stream` (the caller's buffers may be freed once the stream has passed the
+ * call); NULL returns to the constant a / m0. */
+pfc_status pfc_hflow_set_coefficient_field(pfc_hflow* flow, const void* a_field, pfc_stream stream);
+pfc_status pfc_hflow_set_mass_field(pfc_hflow* flow, const void* m_field, pfc_stream stream);
 
 /* pfc_energy_and_grad without any device allocation, for callers that may not
  * call cudaMalloc/cudaFree (graph-capture regions, host callbacks, plugins in

@@ -57,12 +57,18 @@ struct pfc_ctx {
     double* trace = nullptr;
     int trace_cap = 0;
     void* plain_mem = nullptr;       // 21 fields for the plain path
+    void* cfield = nullptr;          // c(x) from pfc_set_coefficient_field (NCF fields)
+    bool cf_on = false;
+    double* dpart = nullptr;         // diagnostics: block partials, ticket, 5 results
+    unsigned* dticket = nullptr;
+    double* dout = nullptr;
     // cached step-loop graph
     cudaGraphExec_t gexec = nullptr;
     const void* g_u = nullptr;
     double g_tau = 0.0;
     int g_len = 0;
     double* g_trace = nullptr;
+    bool g_cf = false;
     cudaStream_t cap = nullptr;
 };
 
@@ -88,6 +94,10 @@ static pfc_status check_problem(const pfc_problem* p)
     if (p->impl != PFC_IMPL_FUSED && p->impl != PFC_IMPL_PLAIN) return fail(PFC_EINVAL, "unknown implementation %d", p->impl);
     if (p->tile_y != 0 && p->tile_y != 8 && p->tile_y != 16) return fail(PFC_EINVAL, "tile_y must be 0, 8 or 16");
     if (p->tile_z < 0) return fail(PFC_EINVAL, "tile_z must be >= 0");
+    if (!isfinite(p->mu) || !isfinite(p->theta[0]) || !isfinite(p->theta[1]) || !isfinite(p->theta[2]))
+        return fail(PFC_EINVAL, "mu and theta must be finite");
+    if (p->mu != 0.0 && p->impl != PFC_IMPL_FUSED)
+        return fail(PFC_EUNSUPPORTED, "the orientation term (mu != 0) runs on the fused path only");
     return PFC_OK;
 }
 
@@ -132,6 +142,10 @@ static void free_ctx_mem(pfc_ctx* c)
     cudaFree(c->scal);
     cudaFree(c->trace);
     cudaFree(c->plain_mem);
+    cudaFree(c->cfield);
+    cudaFree(c->dpart);
+    cudaFree(c->dticket);
+    cudaFree(c->dout);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap) cudaStreamDestroy(c->cap);
 }
@@ -154,7 +168,7 @@ extern "C" pfc_status pfc_create(const pfc_problem* prob, pfc_ctx** out)
         return fail(PFC_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     }
     geometry(prob, sm_count(c->device), &c->tile_y, &c->zc, &c->tiles_x, &c->tiles_y, &c->chunks_z);
-    c->nblocks = (int)fused_grid((long long)c->tiles_x * c->tiles_y * prob->nz, prob->tile_z);
+    c->nblocks = (int)fused_slots(prob->nx, prob->ny, prob->nz, c->tile_y, prob->tile_z);
     c->plain_nblocks = plain_blocks(c->N);
     const int nparts = c->nblocks > c->plain_nblocks ? c->nblocks : c->plain_nblocks;
     bool ok = cudaMalloc(&c->ping, (size_t)c->esz * c->N) == cudaSuccess &&
@@ -203,7 +217,8 @@ static Inst<T> make_inst(const pfc_ctx* c, const void* u, void* out, double tau)
     in.vec = (P.nx % vecw == 0) && (((uintptr_t)u) % 16 == 0);
     in.first_block = 0;
     in.nblocks = c->nblocks;
-    in.C = make_coef<T>(P.a, P.h, P.eps, P.xi, P.well);
+    in.C = make_coef<T>(P.a, P.h, P.eps, P.xi, P.well, P.mu, P.theta);
+    in.cf = c->cf_on ? (const T*)c->cfield : nullptr;
     in.tau = (T)tau;
     in.inv_N = 1.0 / (double)c->N;
     in.partials = c->partials;
@@ -233,11 +248,11 @@ static cudaError_t enqueue(pfc_ctx* c, int mode, const void* u, void* out, doubl
     if (c->P.impl == PFC_IMPL_PLAIN) {
         if (c->P.prec == PFC_FP64)
             return launch_plain<double>((const double*)u, (double*)out, plain_bufs<double>(c), c->P.nx, c->P.ny,
-                                        c->P.nz, make_coef<double>(c->P.a, c->P.h, c->P.eps, c->P.xi, c->P.well),
+                                        c->P.nz, make_coef<double>(c->P.a, c->P.h, c->P.eps, c->P.xi, c->P.well, c->P.mu, c->P.theta),
                                         mode, tau, 1.0 / (double)c->N, c->partials, c->plain_nblocks, c->ints,
                                         c->scal, c->trace, c->trace_cap, s);
         return launch_plain<float>((const float*)u, (float*)out, plain_bufs<float>(c), c->P.nx, c->P.ny, c->P.nz,
-                                   make_coef<float>(c->P.a, c->P.h, c->P.eps, c->P.xi, c->P.well), mode,
+                                   make_coef<float>(c->P.a, c->P.h, c->P.eps, c->P.xi, c->P.well, c->P.mu, c->P.theta), mode,
                                    (float)tau, 1.0 / (double)c->N, c->partials, c->plain_nblocks, c->ints, c->scal,
                                    c->trace, c->trace_cap, s);
     }
@@ -359,7 +374,8 @@ extern "C" pfc_status pfc_run(pfc_ctx* c, void* u, int32_t nsteps, double tau, d
     // a CUDA graph of G steps (G even) replayed; the remainder is launched directly
     const int G = nsteps >= 64 ? 64 : (nsteps & ~1);
     if (G >= 2) {
-        if (!(c->gexec && c->g_u == u && c->g_tau == tau && c->g_len == G && c->g_trace == c->trace)) {
+        if (!(c->gexec && c->g_u == u && c->g_tau == tau && c->g_len == G && c->g_trace == c->trace &&
+              c->g_cf == c->cf_on)) {
             if (c->gexec) {
                 cudaGraphExecDestroy(c->gexec);
                 c->gexec = nullptr;
@@ -385,6 +401,7 @@ extern "C" pfc_status pfc_run(pfc_ctx* c, void* u, int32_t nsteps, double tau, d
             c->g_tau = tau;
             c->g_len = G;
             c->g_trace = c->trace;
+            c->g_cf = c->cf_on;
         }
         for (int k = 0; k + G <= nsteps; k += G) PFC_CU(cudaGraphLaunch(c->gexec, s));
     }
@@ -425,6 +442,51 @@ extern "C" pfc_status pfc_curvatures(pfc_ctx* c, const void* u, void* k1, void* 
     else
         PFC_CU(launch_curvatures<float>((const float*)u, (float*)k1, (float*)k2, P.nx, P.ny, P.nz,
                                         make_coef<float>(P.a, P.h, P.eps, P.xi, P.well), P.eps, s));
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_set_coefficient_field(pfc_ctx* c, const void* a_field, pfc_stream stream)
+{
+    if (!c) return fail(PFC_EINVAL, "context is NULL");
+    if (c->P.impl != PFC_IMPL_FUSED) return fail(PFC_EUNSUPPORTED, "a(x) runs on the fused path only");
+    if (!a_field) {
+        c->cf_on = false;
+        return PFC_OK;
+    }
+    pfc_status st = check_dev_ptr(c, a_field, "a_field");
+    if (st) return st;
+    if (!c->cfield) PFC_CU(cudaMalloc(&c->cfield, (size_t)c->esz * NCF * c->N));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->P.prec == PFC_FP64)
+        PFC_CU(launch_coef_field<double>((const double*)a_field, (double*)c->cfield, c->N, c->P.h, c->P.eps, s));
+    else
+        PFC_CU(launch_coef_field<float>((const float*)a_field, (float*)c->cfield, c->N, c->P.h, c->P.eps, s));
+    c->cf_on = true;
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_diagnostics(pfc_ctx* c, const void* u, double out_host[5], pfc_stream stream)
+{
+    if (!c) return fail(PFC_EINVAL, "context is NULL");
+    if (!out_host) return fail(PFC_EINVAL, "out_host is NULL");
+    pfc_status st = check_dev_ptr(c, u, "u");
+    if (st) return st;
+    if (!c->dpart) {
+        PFC_CU(cudaMalloc((void**)&c->dpart, sizeof(double) * 4 * (size_t)diag_blocks(c->N)));
+        PFC_CU(cudaMalloc((void**)&c->dticket, sizeof(unsigned)));
+        PFC_CU(cudaMalloc((void**)&c->dout, sizeof(double) * 5));
+        PFC_CU(cudaMemset(c->dticket, 0, sizeof(unsigned)));
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const pfc_problem& P = c->P;
+    if (P.prec == PFC_FP64)
+        PFC_CU(launch_diagnostics<double>((const double*)u, P.nx, P.ny, P.nz, P.h, P.eps, P.well, c->dpart,
+                                          c->dticket, c->dout, s));
+    else
+        PFC_CU(launch_diagnostics<float>((const float*)u, P.nx, P.ny, P.nz, P.h, P.eps, P.well, c->dpart,
+                                         c->dticket, c->dout, s));
+    PFC_CU(cudaMemcpyAsync(out_host, c->dout, sizeof(double) * 5, cudaMemcpyDeviceToHost, s));
+    PFC_CU(cudaStreamSynchronize(s));
     return PFC_OK;
 }
 
@@ -477,6 +539,8 @@ extern "C" pfc_status pfc_batch_create(const pfc_problem* probs, int32_t n, pfc_
         if (st) return fail(st, "problem %d: %s", k, g_err);
         if (probs[k].prec != PFC_FP32 || probs[k].impl != PFC_IMPL_FUSED)
             return fail(PFC_EUNSUPPORTED, "problem %d: batches run FP32 on the fused path only", k);
+        if (probs[k].mu != 0.0)
+            return fail(PFC_EUNSUPPORTED, "problem %d: the orientation term is not available in batches", k);
     }
     pfc_batch* b = new (std::nothrow) pfc_batch();
     if (!b) return fail(PFC_ENOMEM, "host allocation failed");

@@ -114,7 +114,10 @@ struct NoRefine {
 // there `refine()` recomputes D in FP64 from the exact float inputs (about
 // one voxel in 10^4 on noise fields; the kernel's CTAs wait for the slowest
 // warp at every plane, so the test is kept tight).
-template <typename T, bool GRAD, class Refine = NoRefine>
+//
+// ORIENT adds the orientation term of Sec. 5.2, c7 (theta . G)^2, and its
+// cotangent 2 c7 (theta . G) theta on G.
+template <typename T, bool GRAD, bool ORIENT = false, class Refine = NoRefine>
 __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz, T hxx, T hyy,
                                         T hzz, T hxy, T hxz, T hyz, Cot<T>& ct, const Refine& refine = Refine())
 {
@@ -161,7 +164,12 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
     // float: one reciprocal square root gives both sqrt(P) and 1/(2 sqrt(P))
     const T rs = (sizeof(T) == 4 && P > T(0)) ? rsqrt_(P) : T(0);
     const T r = sizeof(T) == 4 ? P * rs : sqrt_(P);
-    const T e = fma_(C.c1, S, fma_(C.c2, t2, fma_(a3, r, fma_(C.c4 * q, Tr, C.c6 * g2))));
+    T e = fma_(C.c1, S, fma_(C.c2, t2, fma_(a3, r, fma_(C.c4 * q, Tr, C.c6 * g2))));
+    T tg = T(0);
+    if (ORIENT) {
+        tg = fma_(C.th0, Gx, fma_(C.th1, Gy, C.th2 * Gz));
+        e = fma_(C.c7 * tg, tg, e);
+    }
     if (!GRAD) return e;
 
     // local reverse mode: e(S, T, r(D(S,T)), q(G), |G|^2), M(Hess, w(u), G)
@@ -185,6 +193,12 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
     ct.dx = C.sg * fma_(al, LGx, be * Gx);
     ct.dy = C.sg * fma_(al, LGy, be * Gy);
     ct.dz = C.sg * fma_(al, LGz, be * Gz);
+    if (ORIENT) {
+        const T ot = T(2) * C.c7 * tg * C.sg;
+        ct.dx = fma_(ot, C.th0, ct.dx);
+        ct.dy = fma_(ot, C.th1, ct.dy);
+        ct.dz = fma_(ot, C.th2, ct.dz);
+    }
     ct.hxx = C.kd * Lxx;
     ct.hyy = C.kd * Lyy;
     ct.hzz = C.kd * Lzz;
@@ -194,6 +208,46 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
     ct.hyz = ko2 * Lyz;
     return e;
 }
+
+// ------------------------------------------------------------ grid walks
+
+// Neighbour index along one axis: i + d wrapped into [0, n) (periodic),
+// without a division when |d| < n.
+__device__ __forceinline__ int nbr(int i, int d, int n)
+{
+    int j = i + d;
+    if (j < 0) j += n;
+    if (j >= n) j -= n;
+    if (j >= 0 && j < n) return j;
+    const int r = (i + d) % n;
+    return r < 0 ? r + n : r;
+}
+
+// A thread's position in a grid-stride loop over the flattened voxel index
+// i = (z ny + y) nx + x: the coordinates advance by the stride's own (sx, sy,
+// sz) with two carries instead of two divisions per voxel.
+struct Walk {
+    int x, y, z;            // coordinates of voxel i
+    int sx, sy, sz;         // the grid stride as (x, y, z) steps
+    long i, stride;
+    __device__ Walk(int nx, int ny, long i0, long s) : i(i0), stride(s)
+    {
+        const long pls = (long)nx * ny;
+        z = (int)(i0 / pls); y = (int)((i0 - (long)z * pls) / nx); x = (int)(i0 - (long)z * pls - (long)y * nx);
+        sz = (int)(s / pls); sy = (int)((s - (long)sz * pls) / nx); sx = (int)(s - (long)sz * pls - (long)sy * nx);
+    }
+    __device__ void next(int nx, int ny)
+    {
+        i += stride;
+        x += sx;
+        int c = x >= nx;
+        x -= c ? nx : 0;
+        y += sy + c;
+        c = y >= ny;
+        y -= c ? ny : 0;
+        z += sz + c;
+    }
+};
 
 // ------------------------------------------------------------ accumulators
 

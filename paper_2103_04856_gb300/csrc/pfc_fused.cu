@@ -16,6 +16,10 @@
 // cotangents are recomputed per tile instead of stored.  The energy and the
 // gradient sums are reduced per CTA in FP64 and combined by the last CTA of
 // the problem (pfc_device.cuh, grid_finish).
+//
+// EXT (the extended sweep, Sec. 5.2): the orientation term, and coefficients
+// read per voxel from a field c(x); each thread loads the six coefficients
+// of its column one plane ahead of their use.
 #include <type_traits>
 
 #include "pfc_device.cuh"
@@ -68,7 +72,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-template <typename T, int TY, int MODE, int MAXI>
+template <typename T, int TY, int MODE, int MAXI, bool EXT = false>
 __global__ void __launch_bounds__(Tile<TY>::NT, 1)
 k_fused(const __grid_constant__ Launch<T, MAXI> L)
 {
@@ -175,6 +179,27 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
         const double cind = (MODE == MODE_STEP) ? in.scal[S_C] : 0.0;
         const T cin = (T)cind;
 
+        // EXT: c(x) of this thread's (wrapped) column, one plane ahead
+        const T* cfp = nullptr;
+        size_t cf_stride = 0;
+        T ccn[NCF];
+        if constexpr (EXT) {
+            if (in.cf) {
+                cfp = in.cf + (size_t)wrapi(gy, ny) * nx + wrapi(gx, nx);
+                cf_stride = plane_g * nz;
+            }
+        }
+        auto load_c = [&](int m) {
+            if constexpr (EXT) {
+                if (cfp) {
+                    const T* q = cfp + (size_t)wrapi(m, nz) * plane_g;
+#pragma unroll
+                    for (int k = 0; k < NCF; ++k) ccn[k] = __ldg(q + k * cf_stride);
+                }
+            }
+        };
+        load_c(z0 - 1);
+
         // ---- per-column state carried from plane to plane
         T accC = 0, zdn = 0, hxz2 = 0, hyz2 = 0, hxz1 = 0, hyz1 = 0;
         T fx1 = 0, fx2 = 0, fy1 = 0, fy2 = 0, fxy = 0, cpend = 0;
@@ -213,6 +238,16 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
             constexpr bool kGather = decltype(GATHER)::value, kPublish = decltype(PUBLISH)::value;
             (void)kPublish;
             constexpr bool kOwn = decltype(OWN)::value;
+            // EXT: this plane's coefficients; start the next plane's loads
+            Coef<T> Cv;
+            if constexpr (EXT) {
+                Cv = in.C;
+                if (cfp) {
+                    Cv.c1 = ccn[0]; Cv.c2 = ccn[1]; Cv.c3 = ccn[2];
+                    Cv.c4 = ccn[3]; Cv.c5 = ccn[4]; Cv.c6 = ccn[5];
+                }
+                load_c(m + 1);
+            }
             if (loader) cp_async_wait<PD - 1>();
             __syncthreads();
             if constexpr (kGather && MODE != MODE_ENERGY) {
@@ -234,14 +269,18 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
             const T hxz = (pp[1] - pp[-1]) - (pm[1] - pm[-1]);
             const T hyz = (pp[UXP] - pp[-UXP]) - (pm[UXP] - pm[-UXP]);
             Cot<T> ctv;
+            const Coef<T>& CC = [&]() -> const Coef<T>& {
+                if constexpr (EXT) return Cv;
+                else return in.C;
+            }();
             // FP64 re-evaluation of D from the exact float inputs (float path only)
             auto refine = [&]() -> T { return discriminant_fp64_at<T>(in.C.R, in.C.well, pm, p0, pp, UXP, cind); };
             if constexpr (MODE == MODE_ENERGY) {
-                const T e = voxel_eval<T, false>(in.C, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ctv, refine);
+                const T e = voxel_eval<T, false, EXT>(CC, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ctv, refine);
                 se += interior ? e : T(0);
                 return;
             } else {
-                const T e = voxel_eval<T, true>(in.C, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ctv, refine);
+                const T e = voxel_eval<T, true, EXT>(CC, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ctv, refine);
                 if constexpr (kOwn) se += interior ? e : T(0);
                 // transposed-stencil pieces of this voxel (see the gather):
                 //   x/y first+second differences read from the left/right neighbour,
@@ -356,7 +395,7 @@ __global__ void k_curvatures(const T* __restrict__ u, T* __restrict__ k1, T* __r
 // ------------------------------------------------------------ host side
 
 template <typename T>
-Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well)
+Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well, double mu, const double* theta)
 {
     const double h3 = h * h * h;
     Coef<T> C;
@@ -379,10 +418,41 @@ Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well)
     C.R.sg = 1.0 / (2.0 * h);
     C.R.inv_eps = 1.0 / eps;
     C.R.xi2 = xi * xi;
+    C.c7 = (T)(eps * mu * h3);
+    C.th0 = (T)(theta ? theta[0] : 0.0);
+    C.th1 = (T)(theta ? theta[1] : 0.0);
+    C.th2 = (T)(theta ? theta[2] : 0.0);
     return C;
 }
-template Coef<float> make_coef<float>(const double*, double, double, double, int);
-template Coef<double> make_coef<double>(const double*, double, double, double, int);
+template Coef<float> make_coef<float>(const double*, double, double, double, int, double, const double*);
+template Coef<double> make_coef<double>(const double*, double, double, double, int, double, const double*);
+
+// c(x) from a(x): the coefficients of eq. Feps (times h^3) per voxel, in FP64
+// then rounded to the arithmetic type, exactly as make_coef does for a constant a.
+template <typename T>
+__global__ void k_coef_field(const T* __restrict__ a, T* __restrict__ c, long n, double h3, double eps)
+{
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double a20 = a[i], a11 = a[n + i], a02 = a[2 * n + i];
+        const double a10 = a[3 * n + i], a01 = a[4 * n + i], a00 = a[5 * n + i];
+        c[i] = (T)((a20 + a02 - a11) / (2.0 * eps) * h3);
+        c[n + i] = (T)(a11 / (2.0 * eps) * h3);
+        c[2 * n + i] = (T)((a20 - a02) / (2.0 * eps) * h3);
+        c[3 * n + i] = (T)((a10 + a01) / 2.0 * h3);
+        c[4 * n + i] = (T)((a10 - a01) / 2.0 * h3);
+        c[5 * n + i] = (T)(a00 * eps * h3);
+    }
+}
+
+template <typename T>
+cudaError_t launch_coef_field(const T* a_field, T* c_field, long n, double h, double eps, cudaStream_t s)
+{
+    const long b = (n + 255) / 256;
+    k_coef_field<T><<<(unsigned)(b < 4096 ? b : 4096), 256, 0, s>>>(a_field, c_field, n, h * h * h, eps);
+    return cudaGetLastError();
+}
+template cudaError_t launch_coef_field<float>(const float*, float*, long, double, double, cudaStream_t);
+template cudaError_t launch_coef_field<double>(const double*, double*, long, double, double, cudaStream_t);
 
 int fused_threads(int tile_y) { return tile_y == 8 ? Tile<8>::NT : Tile<16>::NT; }
 
@@ -394,18 +464,18 @@ size_t fused_smem_bytes(int elem_size, int tile_y)
     return (size_t)elem_size * ((size_t)NBUF * plane + 2 * 5 * (size_t)next) + sizeof(float) * NPART * (size_t)nt;
 }
 
-template <typename T, int TY, int MODE, int MAXI>
+template <typename T, int TY, int MODE, int MAXI, bool EXT = false>
 static cudaError_t launch_one(const Launch<T, MAXI>& L, int blocks, cudaStream_t s)
 {
     const size_t smem = fused_smem_bytes(sizeof(T), TY);
     static bool attr_done = false;   // per instantiation; idempotent, so a race is harmless
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<T, TY, MODE, MAXI>,
+        cudaError_t e = cudaFuncSetAttribute(k_fused<T, TY, MODE, MAXI, EXT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    k_fused<T, TY, MODE, MAXI><<<blocks, Tile<TY>::NT, smem, s>>>(L);
+    k_fused<T, TY, MODE, MAXI, EXT><<<blocks, Tile<TY>::NT, smem, s>>>(L);
     return cudaGetLastError();
 }
 
@@ -425,6 +495,14 @@ long long fused_grid(long long units, int max_run)
     long long G = sm_count_current();                   // one CTA per SM
     if (max_run > 0 && (units + max_run - 1) / max_run > G) G = (units + max_run - 1) / max_run;
     return G < units ? G : units;
+}
+
+long long fused_slots(int nx, int ny, int nz, int tile_y, int max_run)
+{
+    const long long tx = (nx + TX - 1) / TX;
+    const long long a = fused_grid(tx * ((ny + tile_y - 1) / tile_y) * nz, max_run);
+    const long long b = fused_grid(tx * ((ny + EXT_TILE_Y - 1) / EXT_TILE_Y) * nz, max_run);
+    return a > b ? a : b;
 }
 
 // Split the launch's work units evenly over G CTAs and record, per problem,
@@ -452,7 +530,7 @@ static void plan(Launch<T, MAXI>& L, int tile_y, int max_run)
     }
 }
 
-template <typename T, int TY>
+template <typename T, int TY, bool EXT = false>
 static cudaError_t launch_mode(const Inst<T>& in, int mode, int max_run, cudaStream_t s)
 {
     Launch<T, 1> L;
@@ -460,9 +538,9 @@ static cudaError_t launch_mode(const Inst<T>& in, int mode, int max_run, cudaStr
     L.inst[0] = in;
     plan(L, TY, max_run);
     switch (mode) {
-    case MODE_ENERGY: return launch_one<T, TY, MODE_ENERGY, 1>(L, L.grid, s);
-    case MODE_GRAD: return launch_one<T, TY, MODE_GRAD, 1>(L, L.grid, s);
-    case MODE_STEP: return launch_one<T, TY, MODE_STEP, 1>(L, L.grid, s);
+    case MODE_ENERGY: return launch_one<T, TY, MODE_ENERGY, 1, EXT>(L, L.grid, s);
+    case MODE_GRAD: return launch_one<T, TY, MODE_GRAD, 1, EXT>(L, L.grid, s);
+    case MODE_STEP: return launch_one<T, TY, MODE_STEP, 1, EXT>(L, L.grid, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -470,6 +548,7 @@ static cudaError_t launch_mode(const Inst<T>& in, int mode, int max_run, cudaStr
 template <typename T>
 cudaError_t launch_fused(const Inst<T>& in, int mode, int tile_y, int max_run, cudaStream_t s)
 {
+    if (needs_ext(in)) return launch_mode<T, EXT_TILE_Y, true>(in, mode, max_run, s);
     return tile_y == 8 ? launch_mode<T, 8>(in, mode, max_run, s) : launch_mode<T, 16>(in, mode, max_run, s);
 }
 template cudaError_t launch_fused<float>(const Inst<float>&, int, int, int, cudaStream_t);

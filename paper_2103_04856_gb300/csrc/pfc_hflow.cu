@@ -7,9 +7,10 @@
 //   sweep  : k * u -> E, g = dF/du                    (the fused kernel)
 //   blur   : g -> k * g     (the blur is symmetric and periodic: self-adjoint)
 //   adam   : dG/dA_c = -(k*g)(j+e_c) + (k*g)(j-e_c), over 2h; moments; A update
-// The div, blur and Adam kernels are memory-bound (x along threads, blocks
-// looping over rows, FP32 sums per thread and FP64 only across warps and
-// blocks: FP64 runs at a small fraction of the FP32 rate on this GPU); the
+// The div, blur and Adam kernels are memory-bound (grid-stride loops over
+// the voxels, or shared-memory tiles for the blur; FP32 sums per thread and
+// FP64 only across warps and blocks: FP64 runs at a small fraction of the
+// FP32 rate on this GPU); the
 // sweep is the issue-bound kernel of pfc_fused.cu.
 #include <cuda_runtime.h>
 
@@ -30,13 +31,7 @@ namespace {
 
 constexpr int kMaxRadius = 32;
 constexpr int kThreads = 128;
-constexpr int kRowBlocks = 1024;   // block rows; each loops over (y, z) rows
-
-__device__ __forceinline__ int wrap_h(int i, int n)
-{
-    int r = i % n;
-    return r < 0 ? r + n : r;
-}
+constexpr int kTileAx = 64;        // blur outputs per tile along the blurred axis
 
 // Reduction slots of the flow's own kernels (the sweep has its own).
 enum { H_MASS = 0, H_GMAX, H_GABS, NH };
@@ -46,6 +41,7 @@ struct Flow {
     long n;
     double sg;          // 1 / (2h)
     double m0;
+    const void* mf;     // null, or m(x) (N values of the arithmetic type, Sec. 5.2)
     double lr, beta1, beta2, adam_eps;
     double* part;       // [blocks][NH] FP64 partials of the flow kernels
     unsigned* ints;     // [0] ticket, [1] Adam step t, [2] trace row
@@ -67,16 +63,6 @@ template <>
 __device__ __forceinline__ float wget<float>(const Weights& w, int j) { return w.wf[j]; }
 template <>
 __device__ __forceinline__ double wget<double>(const Weights& w, int j) { return w.wd[j]; }
-
-// Neighbour index along one axis: i + d wrapped into [0, n) without a
-// division when |d| < n (every case but tiny grids with wide blurs).
-__device__ __forceinline__ int nb(int i, int d, int n)
-{
-    int j = i + d;
-    if (j < 0) j += n;
-    if (j >= n) j -= n;
-    return (j >= 0 && j < n) ? j : wrap_h(i + d, n);
-}
 
 template <typename T> __device__ __forceinline__ T pow_(T b, T e);
 template <> __device__ __forceinline__ float pow_<float>(float b, float e) { return powf(b, e); }
@@ -129,106 +115,136 @@ __device__ void flow_finish(const Flow& f, T a0, T a1, Fin fin)
     f.ints[0] = 0;
 }
 
-// Launch: x along threads (kThreads wide); block row b handles the (y, z)
-// rows b, b + gridDim.y, ...
-inline dim3 flow_grid(int nx, int ny, int nz)
+// Launch of the pointwise kernels: a 1-D grid of at most kFlowBlocks blocks
+// striding over the flattened voxel index; each thread carries its (x, y, z)
+// and advances it by the stride's own (sx, sy, sz) with two carries.
+constexpr int kFlowBlocks = 152 * 8;
+inline dim3 flow_grid(long n)
 {
-    const long rows = (long)ny * nz;
-    return dim3((nx + kThreads - 1) / kThreads, (unsigned)(rows < kRowBlocks ? rows : kRowBlocks), 1);
+    const long b = (n + kThreads - 1) / kThreads;
+    return dim3((unsigned)(b < kFlowBlocks ? b : kFlowBlocks));
 }
-#define FLOW_ROWS(f_ny, f_nz)                                                                        \
-    for (long r_ = blockIdx.y; r_ < (long)(f_ny) * (f_nz); r_ += gridDim.y)                          \
-        for (int y = (int)(r_ % (f_ny)), z = (int)(r_ / (f_ny)), once_ = 1; once_; once_ = 0)
 
-// u = div A + m0, periodic central differences (eq. change_var); mass of u.
+
+// u = div A + m0 (or + m(x)), periodic central differences (eq.
+// change_var); mass of u.
 template <typename T>
-__global__ void k_div(const T* __restrict__ A, T* __restrict__ u, Flow f, int want_mass)
+__global__ void __launch_bounds__(kThreads) k_div(const T* __restrict__ A, T* __restrict__ u, Flow f, int want_mass)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const long n = f.n, pls = (long)f.nx * f.ny;
     T ms = 0;
-    if (x < f.nx) {
-        FLOW_ROWS(f.ny, f.nz)
-        {
-            const long row = (long)z * pls + (long)y * f.nx;
-            const T dx = A[row + nb(x, 1, f.nx)] - A[row + nb(x, -1, f.nx)];
-            const long pl = (long)z * pls;
-            const T dy = A[n + pl + (long)nb(y, 1, f.ny) * f.nx + x] - A[n + pl + (long)nb(y, -1, f.ny) * f.nx + x];
-            const long col = (long)y * f.nx + x;
-            const T dz = A[2 * n + (long)nb(z, 1, f.nz) * pls + col] - A[2 * n + (long)nb(z, -1, f.nz) * pls + col];
-            const T v = (T)f.sg * (dx + dy + dz) + (T)f.m0;
-            u[row + x] = v;
-            ms += v;
-        }
+    for (Walk w(f.nx, f.ny, (long)blockIdx.x * kThreads + threadIdx.x, (long)gridDim.x * kThreads); w.i < n;
+         w.next(f.nx, f.ny)) {
+        const long row = w.i - w.x, pl = (long)w.z * pls, col = w.i - pl;
+        const T dx = A[row + nbr(w.x, 1, f.nx)] - A[row + nbr(w.x, -1, f.nx)];
+        const T dy = A[n + pl + (long)nbr(w.y, 1, f.ny) * f.nx + w.x] - A[n + pl + (long)nbr(w.y, -1, f.ny) * f.nx + w.x];
+        const T dz = A[2 * n + (long)nbr(w.z, 1, f.nz) * pls + col] - A[2 * n + (long)nbr(w.z, -1, f.nz) * pls + col];
+        const T m = f.mf ? ((const T*)f.mf)[w.i] : (T)f.m0;
+        const T v = (T)f.sg * (dx + dy + dz) + m;
+        u[w.i] = v;
+        ms += v;
     }
     if (!want_mass) return;
     flow_finish<T>(f, ms, T(0), [&](double s0, double) { f.hs[H_MASS] = s0 / (double)f.n; });
 }
 
-// One periodic 1-D Gaussian pass along axis AX (0 x, 1 y, 2 z).
+// One periodic 1-D Gaussian pass along axis AX (0 x, 1 y, 2 z), staged in
+// shared memory: a block of 32 x 8 threads loads kTileAx + 2R lines of the
+// axis once (each line a coalesced run along x; along x itself, kTileAx + 2R
+// consecutive values of 8 rows) and writes kTileAx outputs per line, so each
+// input is read about (kTileAx + 2R) / kTileAx times instead of 2R + 1.
+// Grid: x = tiles across x (32 wide, or kTileAx wide for AX 0), y = tiles
+// along the blurred axis (for AX 0: groups of 8 rows), z = the remaining
+// axis (looped when above the grid limit).
 template <typename T, int AX>
-__global__ void k_blur(const T* __restrict__ in, T* __restrict__ out, int nx, int ny, int nz, Weights w)
+__global__ void __launch_bounds__(256) k_blur(const T* __restrict__ in, T* __restrict__ out, int nx, int ny, int nz,
+                                              const __grid_constant__ Weights w)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= nx) return;
+    constexpr int L = kTileAx + 2 * kMaxRadius;
+    __shared__ T s[AX == 0 ? 8 : L][AX == 0 ? L : 32];
+    const int tx = threadIdx.x, ty = threadIdx.y;
     const int R = w.R;
     const long pls = (long)nx * ny;
-    FLOW_ROWS(ny, nz)
-    {
-        const long row = (long)z * pls + (long)y * nx;
-        T s = 0;
+    const int n_other = AX == 2 ? ny : nz;
+    for (int o = blockIdx.z; o < n_other; o += gridDim.z) {
         if (AX == 0) {
-            for (int j = -R; j <= R; ++j) s += wget<T>(w, j + R) * in[row + nb(x, j, nx)];
-        } else if (AX == 1) {
-            const long pl = (long)z * pls;
-            for (int j = -R; j <= R; ++j) s += wget<T>(w, j + R) * in[pl + (long)nb(y, j, ny) * nx + x];
+            const int x0 = blockIdx.x * kTileAx, y = blockIdx.y * 8 + ty;
+            const long row = (long)o * pls + (long)y * nx;
+            if (y < ny)
+                for (int k = tx; k < kTileAx + 2 * R; k += 32) s[ty][k] = in[row + nbr(x0, k - R, nx)];
+            __syncthreads();
+            if (y < ny)
+                for (int k = tx; k < kTileAx && x0 + k < nx; k += 32) {
+                    T acc = 0;
+                    for (int j = 0; j <= 2 * R; ++j) acc += wget<T>(w, j) * s[ty][k + j];
+                    out[row + x0 + k] = acc;
+                }
         } else {
-            const long col = (long)y * nx + x;
-            for (int j = -R; j <= R; ++j) s += wget<T>(w, j + R) * in[(long)nb(z, j, nz) * pls + col];
+            const int x = blockIdx.x * 32 + tx, c0 = blockIdx.y * kTileAx;
+            const int n_ax = AX == 1 ? ny : nz;
+            // element (x, axis index c, other index o)
+            const long stride = AX == 1 ? (long)nx : pls;
+            const long base = AX == 1 ? (long)o * pls + x : (long)o * nx + x;
+            if (x < nx)
+                for (int k = ty; k < kTileAx + 2 * R; k += 8) s[k][tx] = in[base + (long)nbr(c0, k - R, n_ax) * stride];
+            __syncthreads();
+            if (x < nx)
+                for (int k = ty; k < kTileAx && c0 + k < n_ax; k += 8) {
+                    T acc = 0;
+                    for (int j = 0; j <= 2 * R; ++j) acc += wget<T>(w, j) * s[k + j][tx];
+                    out[base + (long)(c0 + k) * stride] = acc;
+                }
         }
-        out[row + x] = s;
+        __syncthreads();
     }
+}
+
+template <typename T, int AX>
+static void launch_blur(const T* in, T* out, int nx, int ny, int nz, const Weights& w, cudaStream_t s)
+{
+    const int n_other = AX == 2 ? ny : nz;
+    const dim3 grid = AX == 0 ? dim3((nx + kTileAx - 1) / kTileAx, (ny + 7) / 8, n_other < 65535 ? n_other : 65535)
+                              : dim3((nx + 31) / 32, ((AX == 1 ? ny : nz) + kTileAx - 1) / kTileAx,
+                                     n_other < 65535 ? n_other : 65535);
+    k_blur<T, AX><<<grid, dim3(32, 8), 0, s>>>(in, out, nx, ny, nz, w);
 }
 
 // dG/dA from the blurred gradient gb, then Adam (Kingma and Ba) on A with
 // moments m, v; the step counter lives in f.ints[1].  `only_grad`: write
 // dG/dA to m and leave A, v alone (pfc_hflow_grad).
 template <typename T>
-__global__ void k_adam(const T* __restrict__ gb, T* __restrict__ A, T* __restrict__ m, T* __restrict__ v, Flow f,
-                       int only_grad)
+__global__ void __launch_bounds__(kThreads) k_adam(const T* __restrict__ gb, T* __restrict__ A, T* __restrict__ m,
+                                                   T* __restrict__ v, Flow f, int only_grad)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const long n = f.n, pls = (long)f.nx * f.ny;
     const unsigned t = f.ints[1] + 1;
     const T b1 = (T)f.beta1, b2 = (T)f.beta2;
     const T c1 = T(1) / (T(1) - pow_<T>(b1, (T)t)), c2 = T(1) / (T(1) - pow_<T>(b2, (T)t));
     const T lr = (T)f.lr, ae = (T)f.adam_eps, sg = (T)f.sg;
     T sabs = 0, gmax = 0;
-    if (x < f.nx) {
-        FLOW_ROWS(f.ny, f.nz)
-        {
-            const long row = (long)z * pls + (long)y * f.nx, i = row + x;
-            T g[3];
-            g[0] = sg * (gb[row + nb(x, -1, f.nx)] - gb[row + nb(x, 1, f.nx)]);
-            g[1] = sg * (gb[(long)z * pls + (long)nb(y, -1, f.ny) * f.nx + x] - gb[(long)z * pls + (long)nb(y, 1, f.ny) * f.nx + x]);
-            g[2] = sg * (gb[(long)nb(z, -1, f.nz) * pls + (long)y * f.nx + x] - gb[(long)nb(z, 1, f.nz) * pls + (long)y * f.nx + x]);
+    for (Walk w(f.nx, f.ny, (long)blockIdx.x * kThreads + threadIdx.x, (long)gridDim.x * kThreads); w.i < n;
+         w.next(f.nx, f.ny)) {
+        const long row = w.i - w.x, pl = (long)w.z * pls, col = w.i - pl;
+        T g[3];
+        g[0] = sg * (gb[row + nbr(w.x, -1, f.nx)] - gb[row + nbr(w.x, 1, f.nx)]);
+        g[1] = sg * (gb[pl + (long)nbr(w.y, -1, f.ny) * f.nx + w.x] - gb[pl + (long)nbr(w.y, 1, f.ny) * f.nx + w.x]);
+        g[2] = sg * (gb[(long)nbr(w.z, -1, f.nz) * pls + col] - gb[(long)nbr(w.z, 1, f.nz) * pls + col]);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const long k = c * n + i;
-                const T gc = g[c];
-                const T ag = gc < T(0) ? -gc : gc;
-                sabs += ag;
-                gmax = ag > gmax ? ag : gmax;
-                if (only_grad) {
-                    m[k] = gc;
-                    continue;
-                }
-                const T mk = b1 * m[k] + (T(1) - b1) * gc;
-                const T vk = b2 * v[k] + (T(1) - b2) * gc * gc;
-                m[k] = mk;
-                v[k] = vk;
-                A[k] -= lr * (mk * c1) / (sqrt(vk * c2) + ae);
+        for (int c = 0; c < 3; ++c) {
+            const long k = c * n + w.i;
+            const T gc = g[c];
+            const T ag = gc < T(0) ? -gc : gc;
+            sabs += ag;
+            gmax = ag > gmax ? ag : gmax;
+            if (only_grad) {
+                m[k] = gc;
+                continue;
             }
+            const T mk = b1 * m[k] + (T(1) - b1) * gc;
+            const T vk = b2 * v[k] + (T(1) - b2) * gc * gc;
+            m[k] = mk;
+            v[k] = vk;
+            A[k] -= lr * (mk * c1) / (sqrt(vk * c2) + ae);
         }
     }
     flow_finish<T>(f, sabs, gmax, [&](double s0, double s1) {
@@ -249,11 +265,7 @@ __global__ void k_adam(const T* __restrict__ gb, T* __restrict__ A, T* __restric
     });
 }
 
-long flow_blocks(int nx, int ny, int nz)
-{
-    const dim3 g = flow_grid(nx, ny, nz);
-    return (long)g.x * g.y;
-}
+long flow_blocks(long n) { return flow_grid(n).x; }
 
 }  // namespace
 
@@ -275,6 +287,10 @@ struct pfc_hflow {
     double* trace = nullptr;
     int trace_cap = 0;
     int sweep_slots = 0;
+    void* cfield = nullptr;     // c(x) (NCF fields), when a(x) is set
+    bool cf_on = false;
+    void* mfield = nullptr;     // m(x), when set
+    bool mf_on = false;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t gexec = nullptr;
     const void* gA = nullptr;
@@ -282,6 +298,7 @@ struct pfc_hflow {
     const void* gv = nullptr;
     int glen = 0;
     double* gtrace = nullptr;
+    bool gcf = false, gmf = false;
 };
 
 static pfc_status hfail(pfc_status s, const char* msg)
@@ -321,6 +338,8 @@ static void free_flow(pfc_hflow* h)
     cudaFree(h->fints);
     cudaFree(h->hs);
     cudaFree(h->trace);
+    cudaFree(h->cfield);
+    cudaFree(h->mfield);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->cap) cudaStreamDestroy(h->cap);
 }
@@ -339,6 +358,8 @@ extern "C" pfc_status pfc_hflow_create(const pfc_problem* prob, const pfc_hflow_
     if (p.tile_y != 0 && p.tile_y != 8 && p.tile_y != 16) return hfail(PFC_EINVAL, "hflow: tile_y must be 0, 8 or 16");
     for (int i = 0; i < 6; ++i)
         if (!isfinite(p.a[i])) return hfail(PFC_EINVAL, "hflow: a coefficient is not finite");
+    if (!isfinite(p.mu) || !isfinite(p.theta[0]) || !isfinite(p.theta[1]) || !isfinite(p.theta[2]))
+        return hfail(PFC_EINVAL, "hflow: mu and theta must be finite");
     if (!isfinite(hp->m0) || !(hp->lr >= 0) || !(hp->beta1 >= 0 && hp->beta1 < 1) || !(hp->beta2 >= 0 && hp->beta2 < 1) ||
         !(hp->adam_eps >= 0) || !(hp->blur_sigma >= 0))
         return hfail(PFC_EINVAL, "hflow: m0 finite, lr >= 0, betas in [0,1), eps >= 0, sigma >= 0 required");
@@ -365,14 +386,13 @@ extern "C" pfc_status pfc_hflow_create(const pfc_problem* prob, const pfc_hflow_
         }
     }
     cudaGetDevice(&h->device);
-    const long long units = (long long)((p.nx + 31) / 32) * ((p.ny + h->tile_y - 1) / h->tile_y) * p.nz;
-    h->sweep_slots = (int)fused_grid(units, p.tile_z);
+    h->sweep_slots = (int)fused_slots(p.nx, p.ny, p.nz, h->tile_y, p.tile_z);
     bool ok = true;
     for (void*& b : h->buf) ok = ok && cudaMalloc(&b, (size_t)h->esz * h->N) == cudaSuccess;
     ok = ok && cudaMalloc((void**)&h->spart, sizeof(double) * NPART * (size_t)h->sweep_slots) == cudaSuccess &&
          cudaMalloc((void**)&h->sints, sizeof(unsigned) * NINTS) == cudaSuccess &&
          cudaMalloc((void**)&h->sscal, sizeof(double) * NSCAL) == cudaSuccess &&
-         cudaMalloc((void**)&h->fpart, sizeof(double) * 2 * (size_t)flow_blocks(p.nx, p.ny, p.nz)) == cudaSuccess &&
+         cudaMalloc((void**)&h->fpart, sizeof(double) * 2 * (size_t)flow_blocks((long)p.nx * p.ny * p.nz)) == cudaSuccess &&
          cudaMalloc((void**)&h->fints, sizeof(unsigned) * 4) == cudaSuccess &&
          cudaMalloc((void**)&h->hs, sizeof(double) * NH) == cudaSuccess &&
          cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) == cudaSuccess;
@@ -408,6 +428,7 @@ static Flow flow_desc(const pfc_hflow* h)
     f.n = h->N;
     f.sg = 1.0 / (2.0 * h->P.h);
     f.m0 = h->H.m0;
+    f.mf = h->mf_on ? h->mfield : nullptr;
     f.lr = h->H.lr; f.beta1 = h->H.beta1; f.beta2 = h->H.beta2; f.adam_eps = h->H.adam_eps;
     f.part = h->fpart;
     f.ints = h->fints;
@@ -426,10 +447,9 @@ static cudaError_t blur3(const pfc_hflow* h, T* in, T* t1, T* t2, T** result, cu
         *result = in;
         return cudaSuccess;
     }
-    const dim3 gr = flow_grid(h->P.nx, h->P.ny, h->P.nz);
-    k_blur<T, 0><<<gr, kThreads, 0, s>>>(in, t1, h->P.nx, h->P.ny, h->P.nz, h->W);
-    k_blur<T, 1><<<gr, kThreads, 0, s>>>(t1, t2, h->P.nx, h->P.ny, h->P.nz, h->W);
-    k_blur<T, 2><<<gr, kThreads, 0, s>>>(t2, t1, h->P.nx, h->P.ny, h->P.nz, h->W);
+    launch_blur<T, 0>(in, t1, h->P.nx, h->P.ny, h->P.nz, h->W, s);
+    launch_blur<T, 1>(t1, t2, h->P.nx, h->P.ny, h->P.nz, h->W, s);
+    launch_blur<T, 2>(t2, t1, h->P.nx, h->P.ny, h->P.nz, h->W, s);
     *result = t1;
     return cudaGetLastError();
 }
@@ -441,16 +461,16 @@ static cudaError_t field(const pfc_hflow* h, const T* A, T** ut, int want_mass, 
     T* b0 = (T*)h->buf[0];
     T* b2 = (T*)h->buf[2];
     T* b3 = (T*)h->buf[3];
-    const dim3 gr = flow_grid(h->P.nx, h->P.ny, h->P.nz);
+    const dim3 gr = flow_grid(h->N);
     if (h->W.R == 0) {
         k_div<T><<<gr, kThreads, 0, s>>>(A, b0, flow_desc(h), want_mass);
         *ut = b0;
         return cudaGetLastError();
     }
     k_div<T><<<gr, kThreads, 0, s>>>(A, b2, flow_desc(h), want_mass);
-    k_blur<T, 0><<<gr, kThreads, 0, s>>>(b2, b3, h->P.nx, h->P.ny, h->P.nz, h->W);
-    k_blur<T, 1><<<gr, kThreads, 0, s>>>(b3, b2, h->P.nx, h->P.ny, h->P.nz, h->W);
-    k_blur<T, 2><<<gr, kThreads, 0, s>>>(b2, b0, h->P.nx, h->P.ny, h->P.nz, h->W);
+    launch_blur<T, 0>(b2, b3, h->P.nx, h->P.ny, h->P.nz, h->W, s);
+    launch_blur<T, 1>(b3, b2, h->P.nx, h->P.ny, h->P.nz, h->W, s);
+    launch_blur<T, 2>(b2, b0, h->P.nx, h->P.ny, h->P.nz, h->W, s);
     *ut = b0;
     return cudaGetLastError();
 }
@@ -467,7 +487,8 @@ static cudaError_t eval(pfc_hflow* h, const T* A, T** gb, cudaStream_t s)
     in.out = (T*)h->buf[1];
     in.nx = h->P.nx; in.ny = h->P.ny; in.nz = h->P.nz;
     in.vec = (h->P.nx % (16 / (int)sizeof(T)) == 0);
-    in.C = make_coef<T>(h->P.a, h->P.h, h->P.eps, h->P.xi, h->P.well);
+    in.C = make_coef<T>(h->P.a, h->P.h, h->P.eps, h->P.xi, h->P.well, h->P.mu, h->P.theta);
+    in.cf = h->cf_on ? (const T*)h->cfield : nullptr;
     in.inv_N = 1.0 / (double)h->N;
     in.partials = h->spart;
     in.ints = h->sints;
@@ -483,7 +504,7 @@ static cudaError_t step(pfc_hflow* h, T* A, T* m, T* v, cudaStream_t s)
     T* gb = nullptr;
     cudaError_t e = eval<T>(h, A, &gb, s);
     if (e != cudaSuccess) return e;
-    k_adam<T><<<flow_grid(h->P.nx, h->P.ny, h->P.nz), kThreads, 0, s>>>(gb, A, m, v, flow_desc(h), 0);
+    k_adam<T><<<flow_grid(h->N), kThreads, 0, s>>>(gb, A, m, v, flow_desc(h), 0);
     return cudaGetLastError();
 }
 
@@ -514,11 +535,11 @@ extern "C" pfc_status pfc_hflow_grad(pfc_hflow* h, const void* A, void* gA, doub
     if (h->P.prec == PFC_FP64) {
         double* gb = nullptr;
         HCU(eval<double>(h, (const double*)A, &gb, s));
-        k_adam<double><<<flow_grid(h->P.nx, h->P.ny, h->P.nz), kThreads, 0, s>>>(gb, nullptr, (double*)gA, nullptr, f, 1);
+        k_adam<double><<<flow_grid(h->N), kThreads, 0, s>>>(gb, nullptr, (double*)gA, nullptr, f, 1);
     } else {
         float* gb = nullptr;
         HCU(eval<float>(h, (const float*)A, &gb, s));
-        k_adam<float><<<flow_grid(h->P.nx, h->P.ny, h->P.nz), kThreads, 0, s>>>(gb, nullptr, (float*)gA, nullptr, f, 1);
+        k_adam<float><<<flow_grid(h->N), kThreads, 0, s>>>(gb, nullptr, (float*)gA, nullptr, f, 1);
     }
     HCU(cudaGetLastError());
     if (G_host) {
@@ -563,7 +584,8 @@ extern "C" pfc_status pfc_hflow_run(pfc_hflow* h, void* A, void* m, void* v, int
     };
     const int G = nsteps >= 32 ? 32 : 0;
     if (G) {
-        if (!(h->gexec && h->gA == A && h->gm == m && h->gv == v && h->glen == G && h->gtrace == h->trace)) {
+        if (!(h->gexec && h->gA == A && h->gm == m && h->gv == v && h->glen == G && h->gtrace == h->trace &&
+              h->gcf == h->cf_on && h->gmf == h->mf_on)) {
             if (h->gexec) {
                 cudaGraphExecDestroy(h->gexec);
                 h->gexec = nullptr;
@@ -585,6 +607,7 @@ extern "C" pfc_status pfc_hflow_run(pfc_hflow* h, void* A, void* m, void* v, int
                 return hfail(PFC_ECUDA, "hflow: graph instantiation failed");
             }
             h->gA = A; h->gm = m; h->gv = v; h->glen = G; h->gtrace = h->trace;
+            h->gcf = h->cf_on; h->gmf = h->mf_on;
         }
         for (int k = 0; k + G <= nsteps; k += G) HCU(cudaGraphLaunch(h->gexec, s));
     }
@@ -596,5 +619,37 @@ extern "C" pfc_status pfc_hflow_run(pfc_hflow* h, void* A, void* m, void* v, int
     HCU(cudaStreamSynchronize(s));
     *t = (int32_t)back[0];
     if (back[1] != (unsigned)nsteps) return hfail(PFC_ECUDA, "hflow: step count mismatch");
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_hflow_set_coefficient_field(pfc_hflow* h, const void* a_field, pfc_stream stream)
+{
+    if (!h) return hfail(PFC_EINVAL, "hflow: handle is NULL");
+    if (!a_field) {
+        h->cf_on = false;
+        return PFC_OK;
+    }
+    if (!dev_ptr(a_field)) return hfail(PFC_EINVAL, "hflow: a_field must be device memory");
+    if (!h->cfield) HCU(cudaMalloc(&h->cfield, (size_t)h->esz * NCF * h->N));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->P.prec == PFC_FP64)
+        HCU(launch_coef_field<double>((const double*)a_field, (double*)h->cfield, h->N, h->P.h, h->P.eps, s));
+    else
+        HCU(launch_coef_field<float>((const float*)a_field, (float*)h->cfield, h->N, h->P.h, h->P.eps, s));
+    h->cf_on = true;
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_hflow_set_mass_field(pfc_hflow* h, const void* m_field, pfc_stream stream)
+{
+    if (!h) return hfail(PFC_EINVAL, "hflow: handle is NULL");
+    if (!m_field) {
+        h->mf_on = false;
+        return PFC_OK;
+    }
+    if (!dev_ptr(m_field)) return hfail(PFC_EINVAL, "hflow: m_field must be device memory");
+    if (!h->mfield) HCU(cudaMalloc(&h->mfield, (size_t)h->esz * h->N));
+    HCU(cudaMemcpyAsync(h->mfield, m_field, (size_t)h->esz * h->N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    h->mf_on = true;
     return PFC_OK;
 }

@@ -41,7 +41,13 @@ struct Coef {
     T xi, xi2, inv_xi;
     int well;   // 0: u^2(1-u)^2, 1: (1-s^2)^2/4
     CoefD R;
+    // orientation term of Sec. 5.2, eps mu (theta . grad u)^2: c7 = eps mu h^3
+    T c7, th0, th1, th2;
 };
+
+// Coefficient fields: c(x) = (c1..c6)(a(x)) as 6 component planes of N
+// values each, built from a user's a(x) (Sec. 5.2) by launch_coef_field.
+constexpr int NCF = 6;
 
 // One problem as seen by a fused launch.
 template <typename T>
@@ -56,6 +62,7 @@ struct Inst {
     int nblocks;         // number of FP64 partial slots (CTAs) of this problem in the launch
     long long unit_base; // fused: first work unit (one plane of one column tile) of this problem
     Coef<T> C;
+    const T* cf;         // null, or the coefficient field c(x) [NCF][nz][ny][nx] replacing C.c1..c6
     T tau;
     double inv_N;
     double* partials;    // [nblocks][NPART]
@@ -80,7 +87,16 @@ struct Launch {
 };
 
 template <typename T>
-Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well);
+Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well, double mu = 0.0,
+                  const double* theta = nullptr);
+
+// The extended sweep (orientation term and/or c(x)) runs with 8-row tiles.
+template <typename T>
+inline bool needs_ext(const Inst<T>& in) { return in.cf != nullptr || in.C.c7 != T(0); }
+constexpr int EXT_TILE_Y = 8;
+// c(x) from a(x) (both [6][n], the arithmetic type; a in the paper's order)
+template <typename T>
+cudaError_t launch_coef_field(const T* a_field, T* c_field, long n, double h, double eps, cudaStream_t s);
 
 // fused kernels (pfc_fused.cu)
 // max_run > 0 caps the planes one CTA processes per problem (more CTAs);
@@ -91,6 +107,9 @@ cudaError_t launch_fused(const Inst<T>& in, int mode, int tile_y, int max_run, c
 // `insts`: host array of descriptors (copied into the launch parameters)
 cudaError_t launch_fused_batch(const Inst<float>* insts, int n_inst, int tile_y, int max_run, cudaStream_t s);
 long long fused_grid(long long units, int max_run);
+// partial slots a single problem can need: both the requested tile height and
+// the extended sweep's
+long long fused_slots(int nx, int ny, int nz, int tile_y, int max_run);
 template <typename T>
 cudaError_t launch_add_offset(T* out, const T* in, long n, const double* c, cudaStream_t s);
 // out += scal[S_C] for every problem of a batch (host descriptors), in place
@@ -100,6 +119,13 @@ cudaError_t launch_curvatures(const T* u, T* k1, T* k2, int nx, int ny, int nz, 
                               double eps, cudaStream_t s);
 size_t fused_smem_bytes(int elem_size, int tile_y);
 int fused_threads(int tile_y);
+
+// viability diagnostics (pfc_diag.cu): part holds 4 doubles per block
+// (diag_blocks), *ticket starts at 0 and is left at 0, out receives 5 doubles
+long diag_blocks(long n);
+template <typename T>
+cudaError_t launch_diagnostics(const T* u, int nx, int ny, int nz, double h, double eps, int well, double* part,
+                               unsigned* ticket, double* out, cudaStream_t s);
 
 // plain unfused path (pfc_plain.cu)
 template <typename T>

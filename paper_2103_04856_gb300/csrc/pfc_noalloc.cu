@@ -104,7 +104,8 @@ static pfc_status run_noalloc(const pfc_problem* p, const void* u, void* g, doub
     in.zc = p->nz;
     in.chunks_z = 1;
     in.vec = (p->nx % (16 / (int)sizeof(T)) == 0) && ((uintptr_t)u) % 16 == 0;
-    in.C = make_coef<T>(p->a, p->h, p->eps, p->xi, p->well);
+    in.C = make_coef<T>(p->a, p->h, p->eps, p->xi, p->well, p->mu, p->theta);
+    in.cf = nullptr;
     in.tau = T(0);
     in.inv_N = 1.0 / ((double)p->nx * p->ny * p->nz);
     in.partials = (double*)base;
@@ -112,8 +113,7 @@ static pfc_status run_noalloc(const pfc_problem* p, const void* u, void* g, doub
     in.ints = (unsigned*)(base + kPartBytes + kScalBytes);
     in.trace = nullptr;
     in.trace_cap = 0;
-    const long long units = (long long)in.tiles_x * in.tiles_y * p->nz;
-    if (fused_grid(units, p->tile_z) > kMaxCtas)
+    if (fused_slots(p->nx, p->ny, p->nz, tile_y, p->tile_z) > kMaxCtas)
         return na_fail(PFC_EINVAL, "noalloc: the launch would need more than 1024 CTAs of scratch "
                                    "(lower tile_z or use pfc_energy_and_grad)");
     // the counters must start at zero; everything else is written before it is read
@@ -142,6 +142,8 @@ extern "C" pfc_status pfc_energy_and_grad_noalloc(const pfc_problem* prob, const
         return na_fail(PFC_EINVAL, "noalloc: h, eps and xi must be finite and > 0");
     for (int i = 0; i < 6; ++i)
         if (!isfinite(p.a[i])) return na_fail(PFC_EINVAL, "noalloc: a coefficient is not finite");
+    if (!isfinite(p.mu) || !isfinite(p.theta[0]) || !isfinite(p.theta[1]) || !isfinite(p.theta[2]))
+        return na_fail(PFC_EINVAL, "noalloc: mu and theta must be finite");
     if (p.well != PFC_WELL_01 && p.well != PFC_WELL_PM1) return na_fail(PFC_EINVAL, "noalloc: unknown double well");
     if (p.prec != PFC_FP32 && p.prec != PFC_FP64) return na_fail(PFC_EINVAL, "noalloc: unknown precision");
     if (p.impl != PFC_IMPL_FUSED) return na_fail(PFC_EUNSUPPORTED, "noalloc: only the fused path needs no allocation");

@@ -177,3 +177,37 @@ def paper_flow_100(seed: int = 0):
     rng = np.random.default_rng(seed)
     A0 = scale * rng.standard_normal((3, n, n, n))
     return prob, flow, A0
+
+
+# The four generation parameters of the paper's spatialised example (Sec. 5.2,
+# Table in_spatialized): a in the paper's order, and the mass m0.
+SPATIALIZED_TABLE = (
+    ((2.0, 2.0, 2.0, 0.0, 0.0, 0.0), -0.4),
+    ((1.0, 2.0, 6.0, -40.0, -40.0, 400.0), -0.6),
+    ((2.0, 2.0, 2.0, -75.0, -75.0, 937.5), -0.7),
+    ((2.0, 2.0, 11.0, -180.0, -90.0, 4050.0), -0.7),
+)
+
+
+def spatialized_fields(n_cube: int, table=SPATIALIZED_TABLE):
+    """a(x) and m(x) of the spatialised example (Sec. 5.2): six cubes of edge
+    n_cube along x carry (p1, p1, p2, p3, p4, p4) at their mid-planes
+    x = (k + 1/2) n_cube, linearly interpolated in between and periodically
+    across the wrap.  Returns (a_field (6, n, n, 6n), m_field (n, n, 6n)),
+    float64."""
+    nodes = [table[0], table[0], table[1], table[2], table[3], table[3]]
+    nx = 6 * n_cube
+    xs = np.arange(nx, dtype=np.float64)
+    a_line = np.empty((6, nx))
+    m_line = np.empty(nx)
+    for i, x in enumerate(xs):
+        t = x / n_cube - 0.5                 # node coordinate
+        k0 = int(math.floor(t)) % 6
+        k1 = (k0 + 1) % 6
+        w = t - math.floor(t)
+        a_line[:, i] = (1 - w) * np.asarray(nodes[k0][0]) + w * np.asarray(nodes[k1][0])
+        m_line[i] = (1 - w) * nodes[k0][1] + w * nodes[k1][1]
+    shape = (n_cube, n_cube, nx)
+    a_field = np.broadcast_to(a_line[:, None, None, :], (6,) + shape).copy()
+    m_field = np.broadcast_to(m_line[None, None, :], shape).copy()
+    return a_field, m_field

@@ -33,7 +33,8 @@ EXPORTED = ("pfc_create", "pfc_destroy", "pfc_energy", "pfc_energy_and_grad", "p
             "pfc_curvatures", "pfc_batch_create", "pfc_batch_destroy", "pfc_batch_run", "pfc_batch_step",
             "pfc_batch_timing", "pfc_batch_last_timing", "pfc_hflow_create", "pfc_hflow_destroy",
             "pfc_hflow_field", "pfc_hflow_grad", "pfc_hflow_run", "pfc_energy_and_grad_noalloc", "pfc_b_to_a",
-            "pfc_status_string", "pfc_last_error")
+            "pfc_status_string", "pfc_last_error", "pfc_set_coefficient_field", "pfc_diagnostics",
+            "pfc_hflow_set_coefficient_field", "pfc_hflow_set_mass_field")
 
 
 class PfcError(RuntimeError):
@@ -59,13 +60,16 @@ class _CProblem(ctypes.Structure):
         ("h", ctypes.c_double), ("eps", ctypes.c_double), ("xi", ctypes.c_double),
         ("a", ctypes.c_double * 6),
         ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32),
+        ("mu", ctypes.c_double), ("theta", ctypes.c_double * 3),
     ]
 
 
 @dataclass
 class Problem:
     """Grid and parameters of eq. Feps; ``a`` in the paper's order (a20 a11 a02 a10 a01 a00),
-    kappa1 >= kappa2.  ``prec`` is "fp32" or "fp64", ``impl`` "fused" or "plain"."""
+    kappa1 >= kappa2.  ``prec`` is "fp32" or "fp64", ``impl`` "fused" or "plain".
+    ``mu``, ``theta`` (x, y, z): the orientation term eps mu (theta . grad u)^2
+    of Sec. 5.2 (mu = 0: none)."""
     nx: int
     ny: int
     nz: int
@@ -78,6 +82,8 @@ class Problem:
     impl: str = "fused"
     tile_y: int = 0
     tile_z: int = 0
+    mu: float = 0.0
+    theta: tuple = (0.0, 0.0, 0.0)
 
     @classmethod
     def from_shape(cls, shape, **kw):
@@ -95,12 +101,15 @@ class Problem:
             raise ValueError("impl must be 'fused' or 'plain'")
         if len(self.a) != 6:
             raise ValueError("a needs 6 coefficients")
+        if len(self.theta) != 3:
+            raise ValueError("theta needs 3 components")
         return _CProblem(int(self.nx), int(self.ny), int(self.nz), int(self.well),
                          PFC_FP64 if self.prec == "fp64" else PFC_FP32,
                          PFC_IMPL_PLAIN if self.impl == "plain" else PFC_IMPL_FUSED,
                          float(self.h), float(self.eps), float(self.xi),
                          (ctypes.c_double * 6)(*[float(x) for x in self.a]),
-                         int(self.tile_y), int(self.tile_z))
+                         int(self.tile_y), int(self.tile_z), float(self.mu),
+                         (ctypes.c_double * 3)(*[float(x) for x in self.theta]))
 
 
 _lib = None
@@ -142,6 +151,10 @@ def load_library():
             "pfc_hflow_run": ([vp, vp, vp, vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), dp, vp],
                               ctypes.c_int),
             "pfc_b_to_a": ([dp, dp], ctypes.c_int),
+            "pfc_set_coefficient_field": ([vp, vp, vp], ctypes.c_int),
+            "pfc_diagnostics": ([vp, vp, dp, vp], ctypes.c_int),
+            "pfc_hflow_set_coefficient_field": ([vp, vp, vp], ctypes.c_int),
+            "pfc_hflow_set_mass_field": ([vp, vp, vp], ctypes.c_int),
             "pfc_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "pfc_last_error": ([], ctypes.c_char_p),
         }
@@ -163,6 +176,18 @@ def _check(rc: int):
 def _stream(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def _coef_field(t, prob: Problem):
+    """a(x) (Sec. 5.2): a CUDA tensor shaped (6, nz, ny, nx) of the problem's
+    dtype, a[k] the k-th coefficient in the order of Problem.a; None clears."""
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != prob.dtype:
+        raise TypeError(f"a_field must be a CUDA {prob.dtype} tensor")
+    if tuple(t.shape) != (6, prob.nz, prob.ny, prob.nx) or not t.is_contiguous():
+        raise ValueError(f"a_field must be contiguous with shape {(6, prob.nz, prob.ny, prob.nx)}")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _field(t: torch.Tensor, prob: Problem, name: str):
@@ -261,6 +286,20 @@ class Context:
                                  tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if trace else None,
                                  _stream(stream)))
         return tr
+
+    def set_coefficient_field(self, a_field, stream=None):
+        """Spatialised coefficients a(x) (Sec. 5.2) for every later evaluation;
+        None returns to the constant a.  The library keeps its own copy."""
+        _check(self._lib.pfc_set_coefficient_field(self._h, _coef_field(a_field, self.prob), _stream(stream)))
+
+    def diagnostics(self, u: torch.Tensor, stream=None) -> dict:
+        """Sec. 4.5 viability quantities of u (discrepancy, Cahn-Hilliard
+        energy, their ratio, max and min of u)."""
+        out = np.empty(5)
+        _check(self._lib.pfc_diagnostics(self._h, _field(u, self.prob, "u"),
+                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)))
+        return {"discrepancy": float(out[0]), "cahn_hilliard": float(out[1]), "ratio": float(out[2]),
+                "max": float(out[3]), "min": float(out[4])}
 
     def curvatures(self, u: torch.Tensor, stream=None):
         k1, k2 = self.new_field(), self.new_field()
@@ -367,6 +406,15 @@ class HFlow:
         if tuple(t.shape) != (3, p.nz, p.ny, p.nx) or not t.is_contiguous():
             raise ValueError(f"{name} must be contiguous with shape {(3, p.nz, p.ny, p.nx)}")
         return ctypes.c_void_p(t.data_ptr())
+
+    def set_coefficient_field(self, a_field, stream=None):
+        """a(x) of Sec. 5.2 for the flow's energy (None: the constant a)."""
+        _check(self._lib.pfc_hflow_set_coefficient_field(self._h, _coef_field(a_field, self.prob), _stream(stream)))
+
+    def set_mass_field(self, m_field, stream=None):
+        """m(x) of Sec. 5.2: u = k * (div A + m(x)) (None: the constant m0)."""
+        ptr = None if m_field is None else _field(m_field, self.prob, "m_field")
+        _check(self._lib.pfc_hflow_set_mass_field(self._h, ptr, _stream(stream)))
 
     def field(self, A, stream=None):
         p = self.prob

@@ -36,11 +36,37 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
-def test_problem_struct_layout_matches_header():
+def _c_layout(tmp_path, struct, fields):
+    """sizeof and offsetof as the C compiler lays out `struct` of pfc.h."""
+    import subprocess
+    src = tmp_path / "layout.c"
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "pfc.h"', "int main(void) {",
+             f'  printf("%zu\\n", sizeof({struct}));']
+    lines += [f'  printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    return [int(v) for v in out]
+
+
+def test_problem_struct_layout_matches_header(tmp_path):
     from paper_2103_04856_gb300 import pfc
-    # int32 x6, double x3, double[6], int32 x2  -> 24 + 24 + 48 + 8 = 104 bytes
-    assert ctypes.sizeof(pfc._CProblem) == 104
-    assert pfc._CProblem.h.offset == 24 and pfc._CProblem.a.offset == 48 and pfc._CProblem.tile_y.offset == 96
+    fields = [name for name, _ in pfc._CProblem._fields_]
+    got = _c_layout(tmp_path, "pfc_problem", fields)
+    assert ctypes.sizeof(pfc._CProblem) == got[0]
+    for name, off in zip(fields, got[1:]):
+        assert getattr(pfc._CProblem, name).offset == off, name
+
+
+def test_hflow_params_layout_matches_header(tmp_path):
+    from paper_2103_04856_gb300 import pfc
+    fields = [name for name, _ in pfc._CHFlow._fields_]
+    got = _c_layout(tmp_path, "pfc_hflow_params", fields)
+    assert ctypes.sizeof(pfc._CHFlow) == got[0]
+    for name, off in zip(fields, got[1:]):
+        assert getattr(pfc._CHFlow, name).offset == off, name
 
 
 def test_status_strings_and_b_to_a(lib):
@@ -54,7 +80,8 @@ def test_status_strings_and_b_to_a(lib):
 def test_create_rejects_bad_problems_without_touching_the_gpu(lib):
     from paper_2103_04856_gb300 import pfc
     h = ctypes.c_void_p()
-    bad = [dict(eps=0.0), dict(nx=0), dict(xi=-1.0), dict(tile_y=12), dict(h=float("nan"))]
+    bad = [dict(eps=0.0), dict(nx=0), dict(xi=-1.0), dict(tile_y=12), dict(h=float("nan")),
+           dict(mu=float("inf")), dict(theta=(0.0, float("nan"), 1.0))]
     for kw in bad:
         base = dict(nx=8, ny=8, nz=8, eps=1.5, a=(1, 0, 1, 0, 0, 0))
         base.update(kw)
@@ -67,6 +94,9 @@ def test_create_rejects_bad_problems_without_touching_the_gpu(lib):
     c.well = 7
     assert lib.pfc_create(ctypes.byref(c), ctypes.byref(h)) == pfc.PFC_EINVAL
     assert lib.pfc_energy(None, None, None, None) == pfc.PFC_EINVAL
+    # the orientation term is a fused-path feature
+    p = pfc.Problem(nx=8, ny=8, nz=8, eps=1.5, a=(1, 0, 1, 0, 0, 0), impl="plain", mu=1.0, theta=(0, 0, 1))
+    assert lib.pfc_create(ctypes.byref(p._c()), ctypes.byref(h)) == pfc.PFC_EUNSUPPORTED
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):

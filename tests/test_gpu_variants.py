@@ -1,0 +1,219 @@
+"""Extensions of Sec. 5.2 (orientation term, a(x), m(x)) and the viability
+diagnostics of Sec. 4.5 on the GPU, against the FP64 oracle, through the C ABI.
+
+Bars: FP64 1e-10 relative (energy, gradient 2-norm, trajectories), FP32 vs
+FP64 on the same state 1e-4 relative energy and 1e-3 relative gradient
+2-norm, as for the plain eq. Feps.  Diagnostics: FP64 1e-12 relative, FP32
+1e-5 relative (sums of positive terms) and exact extremes.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2103_04856_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_2103_04856_gb300 import pfc
+
+
+def P(shape, a, eps=1.5, prec="fp64", h=1.0, xi=1e-6, well=0, **kw):
+    nz, ny, nx = shape
+    return pfc.Problem(nx=nx, ny=ny, nz=nz, eps=eps, a=tuple(a), h=h, xi=xi, well=well, prec=prec, **kw)
+
+
+def oprob(p, **kw):
+    d = {"a": p.a, "eps": p.eps, "h": p.h, "xi": p.xi, "well": p.well, "mu": p.mu, "theta": p.theta}
+    d.update(kw)
+    return d
+
+
+def dev(x, prec):
+    return torch.tensor(x, dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda").contiguous()
+
+
+def rel(g, gref):
+    return float(np.linalg.norm(g - gref) / max(np.linalg.norm(gref), 1e-300))
+
+
+SHAPES = [(7, 9, 11), (20, 24, 40), (33, 17, 64), (2, 3, 5)]
+
+
+def _unit(rng):
+    t = rng.normal(size=3)
+    return tuple(t / np.linalg.norm(t))
+
+
+# ------------------------------------------------------------ orientation
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_orientation_fp64_vs_oracle(shape):
+    rng = np.random.default_rng(sum(shape))
+    for well in (0, 1):
+        p = P(shape, rng.uniform(-1, 1, 6), eps=1.3, h=0.9, well=well, mu=2.5, theta=_unit(rng))
+        u = I.noise(shape, 0.3 if well == 0 else -0.1, 0.1 if well == 0 else 0.3, 5)
+        Eo, go = oracle.energy_and_grad(u, oprob(p))
+        ctx = pfc.Context(p)
+        E, g = ctx.energy_and_grad(dev(u, "fp64"))
+        assert E == pytest.approx(Eo, rel=1e-10, abs=1e-12)
+        assert rel(g.cpu().numpy(), go) < 1e-10
+        assert ctx.energy(dev(u, "fp64")) == pytest.approx(Eo, rel=1e-10, abs=1e-12)
+
+
+def test_orientation_run_vs_oracle():
+    shape = (12, 16, 20)
+    rng = np.random.default_rng(4)
+    p = P(shape, (1, 0, 1, 0, 0, 0), xi=1e-2, mu=1.5, theta=_unit(rng))
+    u = I.noise(shape, 0.3, 0.1, 6)
+    ud = dev(u, "fp64")
+    tr = pfc.Context(p).run(ud, 70, 1e-3)          # graph replay + remainder
+    uo, tro = oracle.run(u, oprob(p), 70, 1e-3)
+    assert rel(ud.cpu().numpy(), uo) < 1e-10
+    np.testing.assert_allclose(tr, tro, rtol=1e-9, atol=1e-12)
+
+
+def test_orientation_fp32_vs_fp64():
+    shape = (24, 40, 48)
+    rng = np.random.default_rng(9)
+    th = _unit(rng)
+    u = I.noise(shape, 0.3, 0.1, 7).astype(np.float32).astype(np.float64)
+    a = (0.2, 0, 1, 0, -0.5, 0)
+    E64, g64 = pfc.Context(P(shape, a, mu=3.0, theta=th)).energy_and_grad(dev(u, "fp64"))
+    E32, g32 = pfc.Context(P(shape, a, mu=3.0, theta=th, prec="fp32")).energy_and_grad(dev(u, "fp32"))
+    assert abs(E32 - E64) / abs(E64) < 1e-4
+    assert rel(g32.double().cpu().numpy(), g64.cpu().numpy()) < 1e-3
+
+
+def test_orientation_noalloc():
+    shape = (10, 20, 36)
+    rng = np.random.default_rng(10)
+    p = P(shape, rng.uniform(-1, 1, 6), mu=0.8, theta=_unit(rng))
+    u = I.noise(shape, 0.3, 0.1, 8)
+    Eo, go = oracle.energy_and_grad(u, oprob(p))
+    g = torch.empty(shape, dtype=torch.float64, device="cuda")
+    E = pfc.energy_and_grad_noalloc(p, dev(u, "fp64"), g)
+    assert E == pytest.approx(Eo, rel=1e-10)
+    assert rel(g.cpu().numpy(), go) < 1e-10
+
+
+# ------------------------------------------------------------ a(x)
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_coefficient_field_fp64_vs_oracle(shape):
+    rng = np.random.default_rng(100 + sum(shape))
+    af = rng.uniform(-1, 1, (6,) + shape)
+    p = P(shape, (0,) * 6, eps=1.4, h=1.1)
+    u = I.noise(shape, 0.3, 0.1, 11)
+    Eo, go = oracle.energy_and_grad(u, oprob(p, a_field=af))
+    ctx = pfc.Context(p)
+    ctx.set_coefficient_field(dev(af, "fp64"))
+    E, g = ctx.energy_and_grad(dev(u, "fp64"))
+    assert E == pytest.approx(Eo, rel=1e-10, abs=1e-12)
+    assert rel(g.cpu().numpy(), go) < 1e-10
+    # cleared: the constant a again
+    ctx.set_coefficient_field(None)
+    E0 = ctx.energy(dev(u, "fp64"))
+    assert E0 == pytest.approx(oracle.energy(u, oprob(p)), rel=1e-10, abs=1e-12)
+
+
+def test_coefficient_field_with_orientation_and_run():
+    """The paper's spatialised example (Table in_spatialized, h = 0.01,
+    eps = 0.02) on 4-voxel cubes, with an orientation term: 40 steps (graph
+    replays + remainder) against the oracle."""
+    n = 4
+    af, _ = I.spatialized_fields(n)
+    shape = af.shape[1:]
+    p = P(shape, (0,) * 6, eps=0.02, h=0.01, xi=1e-2, well=1, mu=50.0, theta=(0.0, 0.6, 0.8))
+    u = I.noise(shape, -0.5, 0.3, 12)
+    ctx = pfc.Context(p)
+    ctx.set_coefficient_field(dev(af, "fp64"))
+    ud = dev(u, "fp64")
+    tr = ctx.run(ud, 40, 2e-6)
+    uo, tro = oracle.run(u, oprob(p, a_field=af), 40, 2e-6)
+    assert rel(ud.cpu().numpy(), uo) < 1e-10
+    np.testing.assert_allclose(tr, tro, rtol=1e-9, atol=1e-12)
+
+
+def test_coefficient_field_fp32_vs_fp64():
+    n = 16
+    af, _ = I.spatialized_fields(n)
+    shape = af.shape[1:]
+    u = I.noise(shape, -0.5, 0.3, 13).astype(np.float32).astype(np.float64)
+    af32 = af.astype(np.float32).astype(np.float64)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        ctx = pfc.Context(P(shape, (0,) * 6, eps=0.02, h=0.01, well=1, prec=prec))
+        ctx.set_coefficient_field(dev(af32, prec))
+        E, g = ctx.energy_and_grad(dev(u, prec))
+        out[prec] = (E, g.double().cpu().numpy())
+    assert abs(out["fp32"][0] - out["fp64"][0]) / abs(out["fp64"][0]) < 1e-4
+    assert rel(out["fp32"][1], out["fp64"][1]) < 1e-3
+
+
+# ------------------------------------------------------------ flow with a(x), m(x)
+
+def test_flow_with_spatialised_parameters_vs_oracle():
+    n = 4
+    af, mf = I.spatialized_fields(n)
+    shape = af.shape[1:]
+    nz, ny, nx = shape
+    p = pfc.Problem(nx=nx, ny=ny, nz=nz, eps=0.02, h=0.01, xi=1e-6, a=(0,) * 6, well=1, prec="fp64",
+                    mu=20.0, theta=(1.0, 0.0, 0.0))
+    flow = pfc.HFlow(p, m0=0.0, lr=1e-3, blur_sigma=1.0)
+    flow.set_coefficient_field(dev(af, "fp64"))
+    flow.set_mass_field(dev(mf, "fp64"))
+    rng = np.random.default_rng(14)
+    A = 2e-4 * rng.standard_normal((3,) + shape)
+    Ad = dev(A, "fp64")
+    op = {"a": (0,) * 6, "eps": 0.02, "h": 0.01, "xi": 1e-6, "well": 1, "mu": 20.0, "theta": (1.0, 0.0, 0.0),
+          "a_field": af}
+    fp = {"m0": 0.0, "lr": 1e-3, "blur_sigma": 1.0, "m_field": mf}
+    ut = flow.field(Ad).cpu().numpy()
+    assert np.max(np.abs(ut - oracle.hflow_field(A, op, fp))) < 1e-13
+    assert abs(ut.mean() - mf.mean()) < 1e-13
+    md, vd = torch.zeros_like(Ad), torch.zeros_like(Ad)
+    tr = flow.run(Ad, md, vd, 5)
+    Ao, mo, vo, to, tro = oracle.hflow_run(A, np.zeros_like(A), np.zeros_like(A), op, fp, 5)
+    assert rel(Ad.cpu().numpy(), Ao) < 1e-10
+    np.testing.assert_allclose(tr, tro, rtol=1e-10, atol=1e-14)
+    # cleared: the constant m0 and a again
+    flow.set_mass_field(None)
+    flow.set_coefficient_field(None)
+    assert abs(flow.field(Ad).cpu().numpy().mean()) < 1e-13
+
+
+# ------------------------------------------------------------ diagnostics
+
+@pytest.mark.parametrize("shape", [(7, 9, 11), (40, 33, 64), (1, 4, 8)])
+def test_diagnostics_vs_oracle(shape):
+    for well in (0, 1):
+        u = I.noise(shape, 0.3 if well == 0 else -0.1, 0.2, 15)
+        p64 = P(shape, (1, 0, 1, 0, 0, 0), eps=1.7, h=0.8, well=well)
+        want = oracle.diagnostics(u, oprob(p64))
+        got = pfc.Context(p64).diagnostics(dev(u, "fp64"))
+        for k in ("discrepancy", "cahn_hilliard", "ratio"):
+            assert got[k] == pytest.approx(want[k], rel=1e-12), k
+        assert got["max"] == want["max"] and got["min"] == want["min"]
+        u32 = u.astype(np.float32).astype(np.float64)
+        want = oracle.diagnostics(u32, oprob(p64))
+        got = pfc.Context(P(shape, (1, 0, 1, 0, 0, 0), eps=1.7, h=0.8, well=well, prec="fp32")).diagnostics(
+            dev(u32, "fp32"))
+        for k in ("discrepancy", "cahn_hilliard", "ratio"):
+            assert got[k] == pytest.approx(want[k], rel=1e-5), k
+        assert got["max"] == want["max"] and got["min"] == want["min"]
+
+
+def test_diagnostics_tanh_slab_and_constant():
+    u = I.tanh_slab((64, 8, 8), 32.0, 4.0, 1.0, well=1)
+    d = pfc.Context(P(u.shape, (0,) * 6, eps=4.0, well=1)).diagnostics(dev(u, "fp64"))
+    sigma = 2 * math.sqrt(2) / 3
+    assert d["ratio"] < 0.01
+    assert d["cahn_hilliard"] / (sigma * 2 * 64) == pytest.approx(1.0, abs=0.005)
+    c = np.full((5, 6, 7), 0.37)
+    d = pfc.Context(P(c.shape, (0,) * 6, eps=1.3)).diagnostics(dev(c, "fp64"))
+    assert d["ratio"] == pytest.approx(1.0, rel=1e-13)
+    assert d["discrepancy"] == pytest.approx(210 * 0.37 ** 2 * 0.63 ** 2 / 1.3, rel=1e-13)
