@@ -281,11 +281,97 @@ def alg1_workload(pfc, I, steps):
     ms = e0.elapsed_time(e1) / steps
     flow.close()
     n = nx * ny * nz
+    peaks, peak_kind = load_peaks()
+    # Adam state (A, m, v: 9 FP32 values) read and written once per iteration
+    state_gbs = 72.0 * n / (ms * 1e-3) / 1e9
     return {"workload": "Alg. 1 at 100^3, h=0.01, eps=0.02, a=(1,2.4,9,30,170,-195), m0=-0.66, blur 2 px, Adam 1e-3",
             "iterations_per_s": 1e3 / ms, "ms_per_iteration": ms, "value": n * 1e3 / ms, "unit": "voxel-iterations/s",
+            "state_bytes_per_voxel_iteration": 72, "state_GBps": state_gbs,
+            "state_frac_of_hbm": state_gbs / peaks["hbm_gbs"], "hbm_peak_kind": peak_kind,
+            "note": "the 100^3 working set (about 60 MB) stays in the 129 MB L2",
             "energy_first_last": [float(tr[0, 0]), float(tr[-1, 0])], "mass": float(tr[-1, 3]),
             "paper_context": "up to 150 s for ~8000 iterations at 100^3 (~53 iterations/s) on an unnamed GPU, "
                              "PyTorch autograd (Sec. 4.1)"}
+
+
+def _timed(fn, reps):
+    import torch
+    fn()                                        # warm-up (graph capture, allocation)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extended_sweep_workload(pfc, I, steps):
+    """The Sec. 5.2 extensions on the 128^3 tanh sphere (p = k1^2 + k2^2),
+    FP32 descent steps (pfc_run, graph replays): the plain sweep, with the
+    orientation term, and with a(x) (a constant field equal to a, so that the
+    three compute the same problem up to the orientation term)."""
+    import torch
+    inst = I.validation_128("sphere", "k1^2+k2^2")
+    u0 = torch.tensor(inst.field().astype(np.float32), device="cuda")
+    n = u0.numel()
+    out = {}
+    for name, kw, field in (("plain", {}, False), ("orientation", {"mu": 1.0, "theta": (0.0, 0.6, 0.8)}, False),
+                            ("a_of_x", {}, True)):
+        ctx = pfc.Context(pfc.Problem.from_shape(inst.shape, eps=inst.eps, a=inst.a, prec="fp32", **kw))
+        if field:
+            af = torch.tensor(np.broadcast_to(np.asarray(inst.a, dtype=np.float32)[:, None, None, None],
+                                              (6,) + inst.shape).copy(), device="cuda")
+            ctx.set_coefficient_field(af)
+        u = u0.clone()
+        ms = _timed(lambda: ctx.run(u, steps, 1e-3, trace=False), 3) / steps
+        out[name] = {"ms_per_step": ms, "voxel_steps_per_s": n * 1e3 / ms}
+        ctx.close()
+    return {"workload": "128^3 tanh sphere R=32, eps=2, FP32 descent steps (Sec. 5.2 extensions)", **out}
+
+
+def spatialized_flow_workload(pfc, I, steps):
+    """The paper's spatialised example (Sec. 5.2, Table in_spatialized): Alg. 1
+    on six 100^3 cubes along x (600 x 100 x 100, h = 0.01, eps = 0.02, the +-1
+    well) with a(x) and m(x) interpolated between the table's four
+    parameters, blur 2 voxels, Adam 1e-3, FP32."""
+    import torch
+    af, mf = I.spatialized_fields(100)
+    nz, ny, nx = mf.shape
+    prob = pfc.Problem(nx=nx, ny=ny, nz=nz, h=0.01, eps=0.02, xi=1e-6, a=(0.0,) * 6, well=1, prec="fp32")
+    flow = pfc.HFlow(prob, m0=0.0, lr=1e-3, blur_sigma=2.0)
+    flow.set_coefficient_field(torch.tensor(af.astype(np.float32), device="cuda"))
+    flow.set_mass_field(torch.tensor(mf.astype(np.float32), device="cuda"))
+    rng = np.random.default_rng(0)
+    A = torch.tensor((2.0 * 0.01 * 0.1 / math.sqrt(6.0) * rng.standard_normal((3, nz, ny, nx))).astype(np.float32),
+                     device="cuda")
+    m, v = torch.zeros_like(A), torch.zeros_like(A)
+    trs = []
+    ms = _timed(lambda: trs.append(flow.run(A, m, v, steps)), 1) / steps
+    flow.close()
+    n = nx * ny * nz
+    return {"workload": "Alg. 1 with a(x), m(x): 600x100x100, h=0.01, eps=0.02, blur 2 px, Adam 1e-3",
+            "iterations_per_s": 1e3 / ms, "ms_per_iteration": ms, "value": n * 1e3 / ms,
+            "unit": "voxel-iterations/s", "energy_last": float(trs[-1][-1, 0]), "mass_last": float(trs[-1][-1, 3]),
+            "mass_target": float(mf.mean())}
+
+
+def diagnostics_workload(pfc, I):
+    """Sec. 4.5 viability diagnostics of a 512^3 FP32 field: one HBM-bound
+    pass (4 B/voxel read)."""
+    import torch
+    inst = I.membrane_descent_512()
+    u = torch.tensor(inst.field().astype(np.float32), device="cuda")
+    ctx = pfc.Context(pfc.Problem.from_shape(inst.shape, eps=inst.eps, a=inst.a, prec="fp32"))
+    res = {}
+    ms = _timed(lambda: res.update(ctx.diagnostics(u)), 10)
+    ctx.close()
+    peaks, kind = load_peaks()
+    gbs = 4.0 * u.numel() / (ms * 1e-3) / 1e9
+    return {"workload": "viability diagnostics of a 512^3 FP32 noise field", "ms_per_call_incl_sync": ms,
+            "GBps_of_4B_per_voxel": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"], "hbm_peak_kind": kind,
+            "ratio": res["ratio"]}
 
 
 # Algorithmic FP32 flops of one voxel-step, counted from the arithmetic (FMA =
@@ -446,7 +532,10 @@ def main():
     if not args.no_extra:
         extra = {"batch64_mixed": extra_workload(pfc, I.batch_instances(64), flush, steps=20),
                  "membrane_512": extra_workload(pfc, [I.membrane_descent_512()], flush, steps=10),
-                 "alg1_flow_100": alg1_workload(pfc, I, steps=400)}
+                 "alg1_flow_100": alg1_workload(pfc, I, steps=400),
+                 "extended_sweep_128": extended_sweep_workload(pfc, I, steps=64),
+                 "alg1_spatialized_600x100x100": spatialized_flow_workload(pfc, I, steps=64),
+                 "diagnostics_512": diagnostics_workload(pfc, I)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -472,7 +472,7 @@ extern "C" pfc_status pfc_diagnostics(pfc_ctx* c, const void* u, double out_host
     pfc_status st = check_dev_ptr(c, u, "u");
     if (st) return st;
     if (!c->dpart) {
-        PFC_CU(cudaMalloc((void**)&c->dpart, sizeof(double) * 4 * (size_t)diag_blocks(c->N)));
+        PFC_CU(cudaMalloc((void**)&c->dpart, sizeof(double) * 4 * (size_t)diag_blocks(c->P.nx, c->P.ny, c->P.nz)));
         PFC_CU(cudaMalloc((void**)&c->dticket, sizeof(unsigned)));
         PFC_CU(cudaMalloc((void**)&c->dout, sizeof(double) * 5));
         PFC_CU(cudaMemset(c->dticket, 0, sizeof(unsigned)));

@@ -122,7 +122,7 @@ int fused_threads(int tile_y);
 
 // viability diagnostics (pfc_diag.cu): part holds 4 doubles per block
 // (diag_blocks), *ticket starts at 0 and is left at 0, out receives 5 doubles
-long diag_blocks(long n);
+long diag_blocks(int nx, int ny, int nz);
 template <typename T>
 cudaError_t launch_diagnostics(const T* u, int nx, int ny, int nz, double h, double eps, int well, double* part,
                                unsigned* ticket, double* out, cudaStream_t s);
