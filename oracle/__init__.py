@@ -25,6 +25,9 @@ Parity status per function (what pins it, in tests/test_oracle_pins.py):
   a_field          (Sec. 5.2 a(x)) linearity in a: E equals the sum of the
                    per-coefficient densities weighted by a(x); central differences
   diagnostics      (Sec. 4.5) constant field and tanh-slab closed forms
+  surface_cells    (Sec. 4.1) flat interfaces: exact area, zero curvature; tanh
+                   sphere and cylinder: area and curvatures converge to the
+                   sharp values; every triangle lies in its cube
   hflow_*          (Alg. 1) mass = m0 exactly, blur moments and symmetry, the
                    closed-form first Adam step, central differences of G(A)
 """
@@ -99,6 +102,8 @@ def _load():
                 f = getattr(lib, name)
                 f.argtypes = args
                 f.restype = ctypes.c_int
+            lib.pfo_surface_cells.argtypes = [P, D, ctypes.c_double, ctypes.c_long, D, ctypes.POINTER(ctypes.c_long)]
+            lib.pfo_surface_cells.restype = ctypes.c_int
             lib.pfo_gauss_weights.argtypes = [ctypes.c_double, ctypes.c_int, D]
             lib.pfo_gauss_weights.restype = None
             lib.pfo_b_to_a.argtypes = [D, D]
@@ -207,6 +212,20 @@ def diagnostics(u, p) -> dict:
     out = np.empty(5)
     _ok(_load().pfo_diagnostics(ctypes.byref(_prob(u, p)), _ptr(u), _ptr(out)), "diagnostics")
     return {"discrepancy": out[0], "cahn_hilliard": out[1], "ratio": out[2], "max": out[3], "min": out[4]}
+
+
+def surface_cells(u, p, level: float) -> np.ndarray:
+    """Cells of the curvature diagram (Sec. 4.1): rows (area, kappa1, kappa2)
+    of the triangles of {u = level}, in cube / tetrahedron / triangle order."""
+    u = _f64(u)
+    lib = _load()
+    n = ctypes.c_long()
+    _ok(lib.pfo_surface_cells(ctypes.byref(_prob(u, p)), _ptr(u), float(level), 0, None, ctypes.byref(n)),
+        "surface_cells")
+    cells = np.empty((max(n.value, 1), 3))
+    _ok(lib.pfo_surface_cells(ctypes.byref(_prob(u, p)), _ptr(u), float(level), n.value, _ptr(cells),
+                              ctypes.byref(n)), "surface_cells")
+    return cells[: n.value]
 
 
 def b_to_a(b) -> np.ndarray:

@@ -413,6 +413,119 @@ int pfo_curvatures(const pfo_problem* p, const double* u, double* k1, double* k2
     return 0;
 }
 
+/* ------------------------------------------ curvature diagram (Sec. 4.1) */
+
+/* Corner c = (i, j, k) of a cube is bit i + 2j + 4k.  The six tetrahedra of
+ * the Freudenthal split run from corner 0 to corner 7 along the three axes
+ * taken in each of the six orders. */
+static const int tet_axes[6][3] = { { 0, 1, 2 }, { 0, 2, 1 }, { 1, 0, 2 }, { 1, 2, 0 }, { 2, 0, 1 }, { 2, 1, 0 } };
+
+static void corner_pos(int c, double q[3])
+{
+    q[0] = (double)(c & 1);
+    q[1] = (double)((c >> 1) & 1);
+    q[2] = (double)((c >> 2) & 1);
+}
+
+/* the point where u - level changes sign on the edge from corner a (above
+ * the level) to corner b (not above), by linear interpolation */
+static void edge_point(const double f[8], int a, int b, double q[3])
+{
+    double qa[3], qb[3];
+    corner_pos(a, qa);
+    corner_pos(b, qb);
+    const double t = f[a] / (f[a] - f[b]);
+    for (int k = 0; k < 3; ++k) q[k] = qa[k] + t * (qb[k] - qa[k]);
+}
+
+static void emit_triangle(const pfo_problem* p, const double P0[3], const double P1[3], const double P2[3],
+                          const double k1c[8], const double k2c[8], long* n, long cap, double* cells)
+{
+    double a[3], b[3], cr[3], bc[3];
+    for (int k = 0; k < 3; ++k) {
+        a[k] = P1[k] - P0[k];
+        b[k] = P2[k] - P0[k];
+        bc[k] = (P0[k] + P1[k] + P2[k]) / 3.0;
+    }
+    cr[0] = a[1] * b[2] - a[2] * b[1];
+    cr[1] = a[2] * b[0] - a[0] * b[2];
+    cr[2] = a[0] * b[1] - a[1] * b[0];
+    const double area = 0.5 * sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]) * p->h * p->h;
+    /* trilinear interpolation of the corner curvatures at the barycenter */
+    double s1 = 0.0, s2 = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        const double wx = (c & 1) ? bc[0] : 1.0 - bc[0];
+        const double wy = ((c >> 1) & 1) ? bc[1] : 1.0 - bc[1];
+        const double wz = ((c >> 2) & 1) ? bc[2] : 1.0 - bc[2];
+        s1 += wx * wy * wz * k1c[c];
+        s2 += wx * wy * wz * k2c[c];
+    }
+    if (*n < cap) {
+        cells[3 * *n + 0] = area;
+        cells[3 * *n + 1] = s1;
+        cells[3 * *n + 2] = s2;
+    }
+    *n += 1;
+}
+
+int pfo_surface_cells(const pfo_problem* p, const double* u, double level, long cap, double* cells, long* count)
+{
+    if (check(p) || !u || !count || cap < 0 || (cap > 0 && !cells)) return -1;
+    const long N = (long)p->nx * p->ny * p->nz;
+    double* k1 = (double*)malloc(sizeof(double) * (size_t)N);
+    double* k2 = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!k1 || !k2 || pfo_curvatures(p, u, k1, k2)) { free(k1); free(k2); return -1; }
+    long n = 0;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                double f[8], k1c[8], k2c[8];
+                int above[8];
+                for (int c = 0; c < 8; ++c) {
+                    const long i = vid(p, x + (c & 1), y + ((c >> 1) & 1), z + ((c >> 2) & 1));
+                    above[c] = u[i] > level;
+                    f[c] = u[i] - level;
+                    k1c[c] = k1[i];
+                    k2c[c] = k2[i];
+                }
+                for (int t = 0; t < 6; ++t) {
+                    int v[4];
+                    v[0] = 0;
+                    v[1] = 1 << tet_axes[t][0];
+                    v[2] = v[1] | (1 << tet_axes[t][1]);
+                    v[3] = 7;
+                    int pos[4], neg[4], np = 0, nn = 0;
+                    for (int k = 0; k < 4; ++k) {
+                        if (above[v[k]]) pos[np++] = v[k];
+                        else neg[nn++] = v[k];
+                    }
+                    double A[3], B[3], C[3], D[3];
+                    if (np == 1) {          /* one corner above: a triangle around it */
+                        edge_point(f, pos[0], neg[0], A);
+                        edge_point(f, pos[0], neg[1], B);
+                        edge_point(f, pos[0], neg[2], C);
+                        emit_triangle(p, A, B, C, k1c, k2c, &n, cap, cells);
+                    } else if (np == 3) {   /* one corner below: a triangle around it */
+                        edge_point(f, pos[0], neg[0], A);
+                        edge_point(f, pos[1], neg[0], B);
+                        edge_point(f, pos[2], neg[0], C);
+                        emit_triangle(p, A, B, C, k1c, k2c, &n, cap, cells);
+                    } else if (np == 2) {   /* a quadrilateral, split along (p0 q0)-(p1 q1) */
+                        edge_point(f, pos[0], neg[0], A);
+                        edge_point(f, pos[0], neg[1], B);
+                        edge_point(f, pos[1], neg[1], C);
+                        edge_point(f, pos[1], neg[0], D);
+                        emit_triangle(p, A, B, C, k1c, k2c, &n, cap, cells);
+                        emit_triangle(p, A, C, D, k1c, k2c, &n, cap, cells);
+                    }
+                }
+            }
+    free(k1);
+    free(k2);
+    *count = n;
+    return 0;
+}
+
 static double W(int well, double u)
 {
     if (well == 1) return 0.25 * (1.0 - u * u) * (1.0 - u * u);

@@ -67,6 +67,16 @@ int pfo_curvatures(const pfo_problem* p, const double* u, double* k1, double* k2
  * times the sums over voxels. */
 int pfo_diagnostics(const pfo_problem* p, const double* u, double out[5]);
 
+/* Cells of the curvature diagram (Sec. 4.1, eq. curva_diagram): the surface
+ * {u = level} triangulated by marching tetrahedra on the Freudenthal split of
+ * every voxel cube (the cube at voxel (x, y, z) spans to (x+1, y+1, z+1),
+ * periodically), each triangle giving one record {area, kappa1, kappa2}:
+ * its area (h^2 units) and the diffuse curvatures of pfo_curvatures
+ * interpolated trilinearly at its barycenter.  Records come in cube order
+ * (z, y, x), then tetrahedron order, then triangle order; at most cap are
+ * written, *count receives the total. */
+int pfo_surface_cells(const pfo_problem* p, const double* u, double level, long cap, double* cells, long* count);
+
 /* ---- Alg. 1 (Sec. 4.1): H^-1 flow through u = div A + m0, blur, Adam ---- */
 typedef struct {
     double m0;              /* mass: the mean of u                                        */

@@ -12,6 +12,10 @@
   diagnostics       constant field (discrepancy = Cahn-Hilliard = N h^3 W(c)/eps),
                     tanh slab (equipartition: the ratio vanishes like (h/eps)^2
                     and the Cahn-Hilliard energy tends to sigma times the area)
+  surface cells     flat interfaces along each axis: exact area, zero curvature;
+                    tanh sphere: area -> 4 pi R^2 under refinement, mean of
+                    kappa1 + kappa2 -> 2/R; tanh cylinder: area -> 2 pi r L,
+                    kappa1 -> 1/r, kappa2 -> 0
 """
 import math
 
@@ -174,3 +178,50 @@ def test_diagnostics_tanh_slab_equipartition(well):
     assert max(scaled) / min(scaled) < 1.1
     assert abs(areas[0] - 1) < 0.02 and abs(areas[2] - 1) < 0.005
     assert abs(areas[0] - 1) > abs(areas[1] - 1) > abs(areas[2] - 1)
+
+
+# ------------------------------------------------------------ curvature diagram
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("well", [0, 1])
+def test_surface_cells_flat_interfaces_exact(axis, well):
+    """A slab normal to one axis: {u = level} is two flat planes, which the
+    linear edge interpolation reproduces exactly: area 2 L1 L2 h^2, zero
+    diffuse curvature (the profile varies along one axis only)."""
+    L, h = 32, 0.7
+    prof = I.tanh_slab((L, 1, 1), 16.0, 2.0, 1.0, well=well)[:, 0, 0]
+    shape = {0: (10, 12, L), 1: (10, L, 12), 2: (L, 10, 12)}[axis]      # (nz, ny, nx)
+    bshape = [1, 1, 1]
+    bshape[2 - axis] = L
+    u = np.broadcast_to(prof.reshape(bshape), shape).copy()
+    cells = oracle.surface_cells(u, prob((0,) * 6, eps=2.0 * h, h=h, well=well), 0.5 if well == 0 else 0.0)
+    other = [s for k, s in enumerate(shape) if k != 2 - axis]
+    assert cells[:, 0].sum() == pytest.approx(2 * other[0] * other[1] * h * h, rel=1e-12)
+    assert np.max(np.abs(cells[:, 1:])) < 1e-9
+
+
+def test_surface_cells_sphere_area_and_mean_curvature():
+    """tanh sphere (off-grid centre): area -> 4 pi R^2 under refinement, the
+    area-weighted mean of kappa1 + kappa2 -> 2/R, kappa1 >= kappa2 per cell."""
+    errs = []
+    for R, n, eps in ((12, 48, 2.0), (16, 64, 2.0), (24, 96, 3.0)):
+        u = I.tanh_sphere((n, n, n), R, eps, 1.0, center=(n / 2 + 0.31, n / 2 + 0.17, n / 2 + 0.23), well=1)
+        c = oracle.surface_cells(u, prob((0,) * 6, eps=eps, well=1), 0.0)
+        A = c[:, 0].sum()
+        errs.append(abs(A / (4 * math.pi * R * R) - 1))
+        H = (c[:, 0] * (c[:, 1] + c[:, 2])).sum() / A
+        assert H * R == pytest.approx(2.0, rel=0.01)
+        assert np.all(c[:, 1] >= c[:, 2])
+    assert errs[0] < 2e-3 and errs[0] > errs[1] > errs[2]
+
+
+def test_surface_cells_cylinder_curvatures():
+    """z-periodic tanh cylinder: area -> 2 pi r L, kappa1 -> 1/r, kappa2 -> 0."""
+    for r, n, eps in ((10, 40, 2.0), (24, 96, 3.0)):
+        L = 8
+        u = I.tanh_cylinder((L, n, n), r, eps, 1.0, center=(n / 2 + 0.31, n / 2 + 0.17), well=0)
+        c = oracle.surface_cells(u, prob((0,) * 6, eps=eps), 0.5)
+        A = c[:, 0].sum()
+        assert A / (2 * math.pi * r * L) == pytest.approx(1.0, abs=5e-4)
+        assert (c[:, 0] * c[:, 1]).sum() / A * r == pytest.approx(1.0, abs=0.02)
+        assert abs((c[:, 0] * c[:, 2]).sum() / A * r) < 0.02
