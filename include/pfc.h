@@ -129,6 +129,27 @@ pfc_status pfc_set_coefficient_field(pfc_ctx* ctx, const void* a_field, pfc_stre
  * -1 and 1).  Synchronises the stream. */
 pfc_status pfc_diagnostics(pfc_ctx* ctx, const void* u, double out_host[5], pfc_stream stream);
 
+/* Cells of the curvature diagram (Sec. 4.1, eq. curva_diagram): the surface
+ * {u = level} (0 for the paper's wells -1/1, 0.5 for wells 0/1) triangulated
+ * by marching tetrahedra on the Freudenthal split of every voxel cube
+ * (periodic), one record (area, kappa1, kappa2) per triangle: its area in
+ * h^2 units and the diffuse curvatures of pfc_curvatures interpolated
+ * trilinearly at its barycenter.  cells (device, the context's type, 3 x cap
+ * values) receives the first min(total, cap) records in cube order (z, y,
+ * x), then tetrahedron, then triangle order (deterministic); *count_host
+ * receives the total, so a call with cap = 0 sizes the buffer.  The first
+ * call allocates 2 fields of scratch.  Synchronises the stream. */
+pfc_status pfc_surface_cells(pfc_ctx* ctx, const void* u, double level, void* cells, int64_t cap,
+                             int64_t* count_host, pfc_stream stream);
+/* Area-weighted 2-D histogram of n cells (as written by pfc_surface_cells):
+ * hist_dev (device, FP64, nbins x nbins, zeroed by the call) [b1 * nbins + b2]
+ * sums the areas of the cells whose kappa1 falls in bin b1 and kappa2 in bin
+ * b2 of [lo, hi) split in nbins; values outside are clamped into the edge bins
+ * (the paper truncates its diagrams to [-100, 100]).  FP64 atomics: the sums
+ * are exact up to rounding order.  Enqueue only. */
+pfc_status pfc_curvature_histogram(pfc_ctx* ctx, const void* cells, int64_t n, int32_t nbins, double lo,
+                                   double hi, double* hist_dev, pfc_stream stream);
+
 /* Diffuse principal curvatures kappa1 >= kappa2 at every voxel (Sec. 3.1,
  * eqs. kepsa/kepsb, exact positive part, regularised |grad u|).  k1 and k2
  * have the type and layout of u. */

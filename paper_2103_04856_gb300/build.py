@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libpfc.so")
-SOURCES = ["pfc_fused.cu", "pfc_plain.cu", "pfc_api.cu", "pfc_noalloc.cu", "pfc_hflow.cu", "pfc_diag.cu"]
+SOURCES = ["pfc_fused.cu", "pfc_plain.cu", "pfc_api.cu", "pfc_noalloc.cu", "pfc_hflow.cu", "pfc_diag.cu", "pfc_surface.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

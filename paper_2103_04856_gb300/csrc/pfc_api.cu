@@ -62,6 +62,9 @@ struct pfc_ctx {
     double* dpart = nullptr;         // diagnostics: block partials, ticket, 5 results
     unsigned* dticket = nullptr;
     double* dout = nullptr;
+    void* skap = nullptr;            // surface cells: kappa1, kappa2 fields, block counts, offsets
+    unsigned* sblk = nullptr;
+    long long* soff = nullptr;
     // cached step-loop graph
     cudaGraphExec_t gexec = nullptr;
     const void* g_u = nullptr;
@@ -146,6 +149,9 @@ static void free_ctx_mem(pfc_ctx* c)
     cudaFree(c->dpart);
     cudaFree(c->dticket);
     cudaFree(c->dout);
+    cudaFree(c->skap);
+    cudaFree(c->sblk);
+    cudaFree(c->soff);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->cap) cudaStreamDestroy(c->cap);
 }
@@ -487,6 +493,63 @@ extern "C" pfc_status pfc_diagnostics(pfc_ctx* c, const void* u, double out_host
                                          c->dticket, c->dout, s));
     PFC_CU(cudaMemcpyAsync(out_host, c->dout, sizeof(double) * 5, cudaMemcpyDeviceToHost, s));
     PFC_CU(cudaStreamSynchronize(s));
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_surface_cells(pfc_ctx* c, const void* u, double level, void* cells, int64_t cap,
+                                        int64_t* count_host, pfc_stream stream)
+{
+    if (!c) return fail(PFC_EINVAL, "context is NULL");
+    if (!count_host) return fail(PFC_EINVAL, "count_host is NULL");
+    if (!isfinite(level)) return fail(PFC_EINVAL, "level is not finite");
+    if (cap < 0) return fail(PFC_EINVAL, "cap must be >= 0");
+    pfc_status st = check_dev_ptr(c, u, "u");
+    if (st) return st;
+    if (cap > 0 && (st = check_dev_ptr(c, cells, "cells"))) return st;
+    const long nb = surface_blocks(c->N);
+    if (!c->skap) {
+        PFC_CU(cudaMalloc(&c->skap, (size_t)c->esz * 2 * c->N));
+        PFC_CU(cudaMalloc((void**)&c->sblk, sizeof(unsigned) * (size_t)nb));
+        PFC_CU(cudaMalloc((void**)&c->soff, sizeof(long long) * (size_t)(nb + 1)));
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const pfc_problem& P = c->P;
+    if (P.prec == PFC_FP64) {
+        double* k1 = (double*)c->skap;
+        double* k2 = k1 + c->N;
+        PFC_CU(launch_curvatures<double>((const double*)u, k1, k2, P.nx, P.ny, P.nz,
+                                         make_coef<double>(P.a, P.h, P.eps, P.xi, P.well), P.eps, s));
+        PFC_CU(launch_surface_cells<double>((const double*)u, k1, k2, P.nx, P.ny, P.nz, P.h, level, c->sblk, c->soff,
+                                            (double*)cells, cap, s));
+    } else {
+        float* k1 = (float*)c->skap;
+        float* k2 = k1 + c->N;
+        PFC_CU(launch_curvatures<float>((const float*)u, k1, k2, P.nx, P.ny, P.nz,
+                                        make_coef<float>(P.a, P.h, P.eps, P.xi, P.well), P.eps, s));
+        PFC_CU(launch_surface_cells<float>((const float*)u, k1, k2, P.nx, P.ny, P.nz, P.h, level, c->sblk, c->soff,
+                                           (float*)cells, cap, s));
+    }
+    long long total = 0;
+    PFC_CU(cudaMemcpyAsync(&total, c->soff + nb, sizeof total, cudaMemcpyDeviceToHost, s));
+    PFC_CU(cudaStreamSynchronize(s));
+    *count_host = (int64_t)total;
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_curvature_histogram(pfc_ctx* c, const void* cells, int64_t n, int32_t nbins, double lo,
+                                              double hi, double* hist_dev, pfc_stream stream)
+{
+    if (!c) return fail(PFC_EINVAL, "context is NULL");
+    if (n < 0 || nbins < 1 || !(hi > lo) || !isfinite(lo) || !isfinite(hi))
+        return fail(PFC_EINVAL, "need n >= 0, nbins >= 1 and finite lo < hi");
+    pfc_status st = check_dev_ptr(c, hist_dev, "hist_dev");
+    if (st) return st;
+    if (n > 0 && (st = check_dev_ptr(c, cells, "cells"))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (c->P.prec == PFC_FP64)
+        PFC_CU(launch_curvature_histogram<double>((const double*)cells, n, nbins, lo, hi, hist_dev, s));
+    else
+        PFC_CU(launch_curvature_histogram<float>((const float*)cells, n, nbins, lo, hi, hist_dev, s));
     return PFC_OK;
 }
 

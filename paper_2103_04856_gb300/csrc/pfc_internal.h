@@ -127,6 +127,17 @@ template <typename T>
 cudaError_t launch_diagnostics(const T* u, int nx, int ny, int nz, double h, double eps, int well, double* part,
                                unsigned* ticket, double* out, cudaStream_t s);
 
+// curvature-diagram cells (pfc_surface.cu): block_counts holds
+// surface_blocks(n) values, offsets surface_blocks(n) + 1 (the total last);
+// cells receive min(total, cap) records (area, kappa1, kappa2)
+long surface_blocks(long n);
+template <typename T>
+cudaError_t launch_surface_cells(const T* u, const T* k1, const T* k2, int nx, int ny, int nz, double h, double level,
+                                 unsigned* block_counts, long long* offsets, T* cells, long long cap, cudaStream_t s);
+template <typename T>
+cudaError_t launch_curvature_histogram(const T* cells, long long n, int nbins, double lo, double hi, double* hist,
+                                       cudaStream_t s);
+
 // plain unfused path (pfc_plain.cu)
 template <typename T>
 struct PlainBufs {

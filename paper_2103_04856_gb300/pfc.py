@@ -34,7 +34,8 @@ EXPORTED = ("pfc_create", "pfc_destroy", "pfc_energy", "pfc_energy_and_grad", "p
             "pfc_batch_timing", "pfc_batch_last_timing", "pfc_hflow_create", "pfc_hflow_destroy",
             "pfc_hflow_field", "pfc_hflow_grad", "pfc_hflow_run", "pfc_energy_and_grad_noalloc", "pfc_b_to_a",
             "pfc_status_string", "pfc_last_error", "pfc_set_coefficient_field", "pfc_diagnostics",
-            "pfc_hflow_set_coefficient_field", "pfc_hflow_set_mass_field")
+            "pfc_hflow_set_coefficient_field", "pfc_hflow_set_mass_field", "pfc_surface_cells",
+            "pfc_curvature_histogram")
 
 
 class PfcError(RuntimeError):
@@ -155,6 +156,10 @@ def load_library():
             "pfc_diagnostics": ([vp, vp, dp, vp], ctypes.c_int),
             "pfc_hflow_set_coefficient_field": ([vp, vp, vp], ctypes.c_int),
             "pfc_hflow_set_mass_field": ([vp, vp, vp], ctypes.c_int),
+            "pfc_surface_cells": ([vp, vp, ctypes.c_double, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), vp],
+                                  ctypes.c_int),
+            "pfc_curvature_histogram": ([vp, vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_double, vp,
+                                         vp], ctypes.c_int),
             "pfc_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "pfc_last_error": ([], ctypes.c_char_p),
         }
@@ -300,6 +305,33 @@ class Context:
                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)))
         return {"discrepancy": float(out[0]), "cahn_hilliard": float(out[1]), "ratio": float(out[2]),
                 "max": float(out[3]), "min": float(out[4])}
+
+    def surface_cells(self, u: torch.Tensor, level: float | None = None, stream=None) -> torch.Tensor:
+        """Cells (area, kappa1, kappa2) of the curvature diagram of {u = level}
+        (Sec. 4.1); level defaults to the middle of the double well's two
+        phases.  Returns a CUDA tensor shaped (n, 3)."""
+        if level is None:
+            level = 0.5 if self.prob.well == PFC_WELL_01 else 0.0
+        n = ctypes.c_int64()
+        up = _field(u, self.prob, "u")
+        _check(self._lib.pfc_surface_cells(self._h, up, float(level), None, 0, ctypes.byref(n), _stream(stream)))
+        cells = torch.empty((max(n.value, 1), 3), dtype=self.prob.dtype, device="cuda")
+        _check(self._lib.pfc_surface_cells(self._h, up, float(level), ctypes.c_void_p(cells.data_ptr()), n.value,
+                                           ctypes.byref(n), _stream(stream)))
+        return cells[: n.value]
+
+    def curvature_histogram(self, cells: torch.Tensor, nbins: int = 100, lo: float = -100.0, hi: float = 100.0,
+                            stream=None) -> torch.Tensor:
+        """Area-weighted (kappa1, kappa2) histogram of surface cells,
+        (nbins, nbins) FP64 on the device; row = kappa1 bin."""
+        if cells.dtype != self.prob.dtype or not cells.is_cuda or cells.dim() != 2 or cells.shape[1] != 3:
+            raise TypeError("cells must be a CUDA tensor (n, 3) of the problem's dtype")
+        cells = cells.contiguous()
+        hist = torch.empty((nbins, nbins), dtype=torch.float64, device="cuda")
+        _check(self._lib.pfc_curvature_histogram(self._h, ctypes.c_void_p(cells.data_ptr()) if cells.numel() else None,
+                                                 cells.shape[0], int(nbins), float(lo), float(hi),
+                                                 ctypes.c_void_p(hist.data_ptr()), _stream(stream)))
+        return hist
 
     def curvatures(self, u: torch.Tensor, stream=None):
         k1, k2 = self.new_field(), self.new_field()

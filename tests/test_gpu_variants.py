@@ -217,3 +217,64 @@ def test_diagnostics_tanh_slab_and_constant():
     d = pfc.Context(P(c.shape, (0,) * 6, eps=1.3)).diagnostics(dev(c, "fp64"))
     assert d["ratio"] == pytest.approx(1.0, rel=1e-13)
     assert d["discrepancy"] == pytest.approx(210 * 0.37 ** 2 * 0.63 ** 2 / 1.3, rel=1e-13)
+
+
+# ------------------------------------------------------------ curvature diagram
+
+def _hist_ref(cells, nbins, lo, hi):
+    w = (hi - lo) / nbins
+    b1 = np.clip(np.floor((cells[:, 1] - lo) / w).astype(int), 0, nbins - 1)
+    b2 = np.clip(np.floor((cells[:, 2] - lo) / w).astype(int), 0, nbins - 1)
+    h = np.zeros((nbins, nbins))
+    np.add.at(h, (b1, b2), cells[:, 0])
+    return h
+
+
+@pytest.mark.parametrize("case", ["sphere", "noise"])
+def test_surface_cells_fp64_vs_oracle(case):
+    if case == "sphere":
+        n = 40
+        u = I.tanh_sphere((n, n, n), 12.0, 2.0, 1.0, center=(20.31, 19.17, 20.23), well=1)
+        p = P(u.shape, (0,) * 6, eps=2.0, well=1, h=0.5)
+        level = 0.0
+    else:
+        u = I.noise((13, 17, 19), 0.5, 0.2, 16)
+        p = P(u.shape, (0,) * 6, eps=1.5)
+        level = 0.5
+    want = oracle.surface_cells(u, oprob(p), level)
+    ctx = pfc.Context(p)
+    got = ctx.surface_cells(dev(u, "fp64"), level).cpu().numpy()
+    assert got.shape == want.shape and len(want) > 100
+    np.testing.assert_allclose(got[:, 0], want[:, 0], rtol=1e-12, atol=0)
+    # curvatures: sqrt(D+) of a nearly umbilic point amplifies rounding (as for pfc_curvatures)
+    scale = np.max(np.abs(want[:, 1:]))
+    np.testing.assert_allclose(got[:, 1:], want[:, 1:], rtol=0, atol=1e-6 * scale)
+    hist = ctx.curvature_histogram(torch.tensor(got, device="cuda"), 40, -2.0, 2.0).cpu().numpy()
+    np.testing.assert_allclose(hist, _hist_ref(got, 40, -2.0, 2.0), rtol=1e-12, atol=1e-14)
+    assert hist.sum() == pytest.approx(want[:, 0].sum(), rel=1e-12)
+    # a short buffer gets the first records and the full count
+    small = torch.zeros((10, 3), dtype=torch.float64, device="cuda")
+    import ctypes
+    cnt = ctypes.c_int64()
+    lib = pfc.load_library()
+    rc = lib.pfc_surface_cells(ctx._h, ctypes.c_void_p(dev(u, "fp64").data_ptr()), level,
+                               ctypes.c_void_p(small.data_ptr()), 10, ctypes.byref(cnt), None)
+    torch.cuda.synchronize()
+    assert rc == 0 and cnt.value == len(want)
+    np.testing.assert_allclose(small.cpu().numpy()[:, 0], want[:10, 0], rtol=1e-12)
+
+
+def test_surface_cells_fp32():
+    n = 48
+    u = I.tanh_sphere((n, n, n), 14.0, 2.0, 1.0, center=(24.31, 23.17, 24.23), well=0)
+    u = u.astype(np.float32).astype(np.float64)
+    p64 = P(u.shape, (0,) * 6, eps=2.0)
+    want = oracle.surface_cells(u, oprob(p64), 0.5)
+    got = pfc.Context(P(u.shape, (0,) * 6, eps=2.0, prec="fp32")).surface_cells(dev(u, "fp32"), 0.5)
+    got = got.double().cpu().numpy()
+    assert got.shape == want.shape
+    assert got[:, 0].sum() == pytest.approx(want[:, 0].sum(), rel=1e-5)
+    assert np.max(np.abs(got[:, 0] - want[:, 0])) < 1e-4 * np.max(want[:, 0])
+    A = want[:, 0].sum()
+    for k in (1, 2):
+        assert (got[:, 0] * got[:, k]).sum() / A == pytest.approx((want[:, 0] * want[:, k]).sum() / A, rel=1e-3)
