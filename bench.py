@@ -55,7 +55,10 @@ def parse():
     ap.add_argument("--tile-y", type=int, default=0, help="0 = autotuned (or library default)")
     ap.add_argument("--max-run", type=int, default=-1, help="cap on planes per CTA run (-1 = autotuned)")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the 64-instance batch and 512^3 lines")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other_workloads lines")
+    ap.add_argument("--only", default=None,
+                    choices=["alg1_flow_100", "extended_sweep_128", "alg1_spatialized", "diagnostics_512"],
+                    help="run just this one of the other workloads and print its line (for profiling)")
     return ap.parse_args()
 
 
@@ -279,7 +282,21 @@ def alg1_workload(pfc, I, steps):
     e1.record()
     e1.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    # the curvature diagram of the generated shape (Sec. 4.1): cells of {u = 0}
+    ut = flow.field(A)
     flow.close()
+    ctx = pfc.Context(prob)
+    cells = []
+    ms_cells = _timed(lambda: cells.append(ctx.surface_cells(ut, 0.0)), 5)
+    hist = ctx.curvature_histogram(cells[-1], 100, -100.0, 100.0)
+    torch.cuda.synchronize()
+    c = cells[-1].double()
+    area = float(c[:, 0].sum())
+    diagram = {"cells": int(c.shape[0]), "area": area, "ms_cells_incl_sync": ms_cells,
+               "mean_kappa1": float((c[:, 0] * c[:, 1]).sum()) / area if area > 0 else None,
+               "mean_kappa2": float((c[:, 0] * c[:, 2]).sum()) / area if area > 0 else None,
+               "hist_area": float(hist.sum())}
+    ctx.close()
     n = nx * ny * nz
     peaks, peak_kind = load_peaks()
     # Adam state (A, m, v: 9 FP32 values) read and written once per iteration
@@ -290,6 +307,7 @@ def alg1_workload(pfc, I, steps):
             "state_frac_of_hbm": state_gbs / peaks["hbm_gbs"], "hbm_peak_kind": peak_kind,
             "note": "the 100^3 working set (about 60 MB) stays in the 129 MB L2",
             "energy_first_last": [float(tr[0, 0]), float(tr[-1, 0])], "mass": float(tr[-1, 3]),
+            "curvature_diagram": diagram,
             "paper_context": "up to 150 s for ~8000 iterations at 100^3 (~53 iterations/s) on an unnamed GPU, "
                              "PyTorch autograd (Sec. 4.1)"}
 
@@ -397,6 +415,14 @@ def main():
     torch.cuda.set_device(local)
     from paper_2103_04856_gb300 import inputs as I
     from paper_2103_04856_gb300 import pfc
+
+    if args.only:
+        run = {"alg1_flow_100": lambda: alg1_workload(pfc, I, steps=args.steps),
+               "extended_sweep_128": lambda: extended_sweep_workload(pfc, I, steps=args.steps),
+               "alg1_spatialized": lambda: spatialized_flow_workload(pfc, I, steps=args.steps),
+               "diagnostics_512": lambda: diagnostics_workload(pfc, I)}[args.only]
+        print(json.dumps({"only": args.only, **run()}), flush=True)
+        return 0
 
     insts = I.validation_set_128()
     launch = {"tile_y": args.tile_y, "max_run": max(args.max_run, 0), "source": "command line"}
