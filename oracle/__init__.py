@@ -25,6 +25,9 @@ Parity status per function (what pins it, in tests/test_oracle_pins.py):
   a_field          (Sec. 5.2 a(x)) linearity in a: E equals the sum of the
                    per-coefficient densities weighted by a(x); central differences
   diagnostics      (Sec. 4.5) constant field and tanh-slab closed forms
+  proj (M_P)       planar profiles give M_P = 0 (closed form of E), tanh
+                   sphere F/(sigma 8 pi) -> 1, axis permutations, central
+                   differences of the gradient, torch autograd
   surface_cells    (Sec. 4.1) flat interfaces: exact area, zero curvature; tanh
                    sphere and cylinder: area and curvatures converge to the
                    sharp values; every triangle lies in its cube
@@ -59,6 +62,7 @@ class _Problem(ctypes.Structure):
         ("h", ctypes.c_double), ("eps", ctypes.c_double), ("xi", ctypes.c_double),
         ("a", ctypes.c_double * 6), ("well", ctypes.c_int),
         ("mu", ctypes.c_double), ("theta", ctypes.c_double * 3), ("a_field", ctypes.POINTER(ctypes.c_double)),
+        ("proj", ctypes.c_int),
     ]
 
 
@@ -114,13 +118,15 @@ def _load():
 
 def _prob(u: np.ndarray, p: dict) -> _Problem:
     """Problem keys: h, eps, xi, a, well; optional (Sec. 5.2) mu, theta (3
-    values, x y z) and a_field (shape (6, nz, ny, nx): a(x))."""
+    values, x y z) and a_field (shape (6, nz, ny, nx): a(x)); proj = 1 for the
+    tangent-projected M = -eps P Hess u P."""
     nz, ny, nx = u.shape
     a = p["a"]
     s = _Problem(nx, ny, nz, float(p.get("h", 1.0)), float(p["eps"]),
                  float(p.get("xi", 1e-6)), (ctypes.c_double * 6)(*[float(v) for v in a]),
                  int(p.get("well", 0)), float(p.get("mu", 0.0)),
-                 (ctypes.c_double * 3)(*[float(v) for v in p.get("theta", (0.0, 0.0, 0.0))]), None)
+                 (ctypes.c_double * 3)(*[float(v) for v in p.get("theta", (0.0, 0.0, 0.0))]), None,
+                 int(p.get("proj", 0)))
     af = p.get("a_field")
     if af is not None:
         af = np.ascontiguousarray(af, dtype=np.float64)

@@ -163,10 +163,28 @@ static void forward(const pfo_problem* p, const double* u, int x, int y, int z, 
     v->rho = g2 + p->xi * p->xi;
     v->q = sqrt(v->rho);
     v->w = Wp(p->well, v->u) / p->eps;
-    /* M = -eps Hess u + (W'(u)/eps) n (x) n, with n (x) n = G G^T / rho */
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-            v->M[a][b] = -p->eps * v->Hs[a][b] + v->w * v->G[a] * v->G[b] / v->rho;
+    if (p->proj) {
+        /* M = -eps P Hess u P, P = I - n (x) n with n (x) n = G G^T / rho */
+        double P[3][3], PH[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) P[a][b] = (a == b ? 1.0 : 0.0) - v->G[a] * v->G[b] / v->rho;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                PH[a][b] = 0.0;
+                for (int c = 0; c < 3; ++c) PH[a][b] += P[a][c] * v->Hs[c][b];
+            }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double s = 0.0;
+                for (int c = 0; c < 3; ++c) s += PH[a][c] * P[c][b];
+                v->M[a][b] = -p->eps * s;
+            }
+    } else {
+        /* M = -eps Hess u + (W'(u)/eps) n (x) n, with n (x) n = G G^T / rho */
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                v->M[a][b] = -p->eps * v->Hs[a][b] + v->w * v->G[a] * v->G[b] / v->rho;
+    }
     v->T = v->M[0][0] + v->M[1][1] + v->M[2][2];
     v->S = 0.0;
     for (int a = 0; a < 3; ++a)
@@ -199,6 +217,51 @@ static void local_adjoint(const pfo_problem* p, const voxel* v, double* ubar, do
     double L[3][3];      /* de/dM_ab */
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) L[a][b] = 2.0 * dS * v->M[a][b] + (a == b ? dT : 0.0);
+
+    if (p->proj) {
+        /* M = P K P with K = -eps Hess u and P = I - G G^T / rho:
+         *   dE/dK = P L P;  dE/dP = L P K + K P L =: B;
+         *   dP = -(dG G^T + G dG^T)/rho + 2 (G.dG) G G^T / rho^2  gives
+         *   dE/dG (through P) = -2 B G / rho + 2 (G^T B G) G / rho^2. */
+        double P[3][3], K[3][3], PL[3][3], LP[3][3], B[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                P[a][b] = (a == b ? 1.0 : 0.0) - v->G[a] * v->G[b] / v->rho;
+                K[a][b] = -p->eps * v->Hs[a][b];
+            }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                PL[a][b] = 0.0;
+                LP[a][b] = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    PL[a][b] += P[a][c] * L[c][b];
+                    LP[a][b] += L[a][c] * P[c][b];
+                }
+            }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double s = 0.0, t = 0.0, q = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    s += PL[a][c] * P[c][b];                /* (P L P)_ab     */
+                    t += LP[a][c] * K[c][b];                /* (L P K)_ab     */
+                    q += K[a][c] * PL[c][b];                /* (K P L)_ab     */
+                }
+                Hbar[a][b] = -p->eps * s;
+                B[a][b] = t + q;
+            }
+        double BG[3], GBG = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            BG[a] = 0.0;
+            for (int b = 0; b < 3; ++b) BG[a] += B[a][b] * v->G[b];
+            GBG += v->G[a] * BG[a];
+        }
+        *ubar = 0.0;     /* M no longer depends on u itself */
+        for (int a = 0; a < 3; ++a)
+            Gbar[a] = -2.0 * BG[a] / v->rho + 2.0 * GBG * v->G[a] / (v->rho * v->rho)
+                    + dq * v->G[a] / v->q + 2.0 * cf->c6 * v->G[a]
+                    + 2.0 * p->eps * p->mu * v->tg * p->theta[a];
+        return;
+    }
 
     double LG[3], GLG = 0.0;
     for (int a = 0; a < 3; ++a) {

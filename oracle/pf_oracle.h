@@ -30,6 +30,9 @@ typedef struct {
     double mu;            /* orientation weight: eps*mu*(theta . grad u)^2 joins the integrand */
     double theta[3];      /* orientation direction (x, y, z), used as given (Sec. 5.2 takes |theta| = 1) */
     const double* a_field;/* NULL, or spatialised coefficients a(x): a_field[k*N + i] is a_k at voxel i */
+    int proj;             /* 1: M = -eps P Hess u P with P = I - n (x) n (the Hessian projected on the
+                           * tangent plane, the form M takes on the tanh profile, Sec. 3.1) instead
+                           * of eq. Meps; 0: eq. Meps */
 } pfo_problem;
 
 /* All functions return 0 on success, -1 on invalid arguments. */

@@ -225,3 +225,58 @@ def test_surface_cells_cylinder_curvatures():
         assert A / (2 * math.pi * r * L) == pytest.approx(1.0, abs=5e-4)
         assert (c[:, 0] * c[:, 1]).sum() / A * r == pytest.approx(1.0, abs=0.02)
         assert abs((c[:, 0] * c[:, 2]).sum() / A * r) < 0.02
+
+
+# ------------------------------------------------------------ tangent-projected M
+
+def test_projected_planar_profile_closed_form():
+    """u depends on z only: Hess u = H e_z e_z^T and G = G e_z, so
+    P Hess P = (xi^2/rho)^2 H e_z e_z^T: M_P is rank one with T = -eps
+    (xi^2/rho)^2 H, S = D = T^2 (M_P vanishes where G != 0 and is -eps Hess u
+    where G = 0, the slab's mid-planes), and
+    e = (c1 + c2) T^2 + c3 T r + c4 q T + c5 q r + c6 G^2, r = sqrt(softplus(T^2))."""
+    rng = np.random.default_rng(12)
+    h, eps, xi = 0.8, 1.6, 1e-6
+    u = I.tanh_slab((32, 5, 6), 16.0, eps / h, 1.0, well=0)
+    a = rng.uniform(-1, 1, 6)
+    E = oracle.energy(u, prob(a, eps=eps, h=h, xi=xi, proj=1))
+    G = (np.roll(u, -1, axis=0) - np.roll(u, 1, axis=0)) / (2 * h)
+    H = (np.roll(u, -1, axis=0) - 2 * u + np.roll(u, 1, axis=0)) / (h * h)
+    rho = G * G + xi * xi
+    q = np.sqrt(rho)
+    T = -eps * (xi * xi / rho) ** 2 * H
+    D = T * T
+    r = np.sqrt(D + xi * np.log1p(np.exp(-D / xi)))
+    c1, c2, c3 = (a[0] + a[2] - a[1]) / (2 * eps), a[1] / (2 * eps), (a[0] - a[2]) / (2 * eps)
+    c4, c5, c6 = (a[3] + a[4]) / 2, (a[3] - a[4]) / 2, a[5] * eps
+    e = (c1 + c2) * T * T + c3 * T * r + c4 * q * T + c5 * q * r + c6 * G * G
+    assert np.any(G == 0) and np.any(np.abs(T) > 1e-3)      # both regimes occur
+    assert E == pytest.approx(h ** 3 * e.sum(), rel=1e-12)
+
+
+def test_projected_sphere_and_permutations():
+    """tanh sphere R = 32, eps = 2h, p = k1^2 + k2^2: F/(sigma 8 pi) close to 1
+    (the W' term of eq. Meps is replaced by the projection, which removes the
+    normal direction exactly); axis permutations leave E unchanged."""
+    n = 128
+    u = I.tanh_sphere((n, n, n), 32.0, 2.0, 1.0, center=(64.3, 64.1, 64.2))
+    ratio = oracle.energy(u, prob((1, 0, 1, 0, 0, 0), eps=2.0, proj=1)) / (math.sqrt(2) / 6 * 8 * math.pi)
+    assert abs(ratio - 1) < 0.01
+    rng = np.random.default_rng(13)
+    v = I.noise((5, 6, 7), 0.3, 0.2, 14)
+    p = prob(rng.uniform(-1, 1, 6), h=0.9, proj=1)
+    E = oracle.energy(v, p)
+    for perm in ((0, 2, 1), (1, 0, 2), (2, 1, 0)):
+        assert oracle.energy(np.ascontiguousarray(np.transpose(v, perm)), p) == pytest.approx(E, rel=1e-12)
+
+
+@pytest.mark.parametrize("well", [0, 1])
+def test_projected_gradient_central_differences(well):
+    rng = np.random.default_rng(15 + well)
+    u = I.noise((6, 7, 8), 0.3 if well == 0 else -0.1, 0.1 if well == 0 else 0.3, 23)
+    th = rng.normal(size=3)
+    p = prob(rng.uniform(-1, 1, 6), eps=1.5, h=0.9, xi=1e-2, well=well, proj=1, mu=0.7,
+             theta=tuple(th / np.linalg.norm(th)))
+    _, g = oracle.energy_and_grad(u, p)
+    gfd = _fd_grad(u.copy(), p, 1e-5)
+    assert np.max(np.abs(g - gfd)) < 1e-6 * np.max(np.abs(g))
