@@ -76,6 +76,12 @@ typedef struct {
      * plain path and in batches); it runs the extended sweep (8-row tiles). */
     double mu;
     double theta[3];
+    /* 1: the tangent-projected M = -eps P Hess u P, P = I - n (x) n (the form
+     * eq. Meps takes on the tanh profile, Sec. 3.1, with no double-well term)
+     * replaces eq. Meps in the energy, its gradient and the curvatures; 0:
+     * eq. Meps.  Fused path only; runs the extended sweep. */
+    int32_t proj;
+    int32_t reserved;       /* must be 0 */
 } pfc_problem;
 
 typedef struct pfc_ctx pfc_ctx;

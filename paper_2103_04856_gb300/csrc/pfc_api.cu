@@ -101,6 +101,10 @@ static pfc_status check_problem(const pfc_problem* p)
         return fail(PFC_EINVAL, "mu and theta must be finite");
     if (p->mu != 0.0 && p->impl != PFC_IMPL_FUSED)
         return fail(PFC_EUNSUPPORTED, "the orientation term (mu != 0) runs on the fused path only");
+    if (p->proj != 0 && p->proj != 1) return fail(PFC_EINVAL, "proj must be 0 or 1");
+    if (p->reserved != 0) return fail(PFC_EINVAL, "reserved must be 0");
+    if (p->proj && p->impl != PFC_IMPL_FUSED)
+        return fail(PFC_EUNSUPPORTED, "the projected M runs on the fused path only");
     return PFC_OK;
 }
 
@@ -223,7 +227,7 @@ static Inst<T> make_inst(const pfc_ctx* c, const void* u, void* out, double tau)
     in.vec = (P.nx % vecw == 0) && (((uintptr_t)u) % 16 == 0);
     in.first_block = 0;
     in.nblocks = c->nblocks;
-    in.C = make_coef<T>(P.a, P.h, P.eps, P.xi, P.well, P.mu, P.theta);
+    in.C = make_coef<T>(P.a, P.h, P.eps, P.xi, P.well, P.mu, P.theta, P.proj);
     in.cf = c->cf_on ? (const T*)c->cfield : nullptr;
     in.tau = (T)tau;
     in.inv_N = 1.0 / (double)c->N;
@@ -254,11 +258,11 @@ static cudaError_t enqueue(pfc_ctx* c, int mode, const void* u, void* out, doubl
     if (c->P.impl == PFC_IMPL_PLAIN) {
         if (c->P.prec == PFC_FP64)
             return launch_plain<double>((const double*)u, (double*)out, plain_bufs<double>(c), c->P.nx, c->P.ny,
-                                        c->P.nz, make_coef<double>(c->P.a, c->P.h, c->P.eps, c->P.xi, c->P.well, c->P.mu, c->P.theta),
+                                        c->P.nz, make_coef<double>(c->P.a, c->P.h, c->P.eps, c->P.xi, c->P.well, c->P.mu, c->P.theta, c->P.proj),
                                         mode, tau, 1.0 / (double)c->N, c->partials, c->plain_nblocks, c->ints,
                                         c->scal, c->trace, c->trace_cap, s);
         return launch_plain<float>((const float*)u, (float*)out, plain_bufs<float>(c), c->P.nx, c->P.ny, c->P.nz,
-                                   make_coef<float>(c->P.a, c->P.h, c->P.eps, c->P.xi, c->P.well, c->P.mu, c->P.theta), mode,
+                                   make_coef<float>(c->P.a, c->P.h, c->P.eps, c->P.xi, c->P.well, c->P.mu, c->P.theta, c->P.proj), mode,
                                    (float)tau, 1.0 / (double)c->N, c->partials, c->plain_nblocks, c->ints, c->scal,
                                    c->trace, c->trace_cap, s);
     }
@@ -444,10 +448,10 @@ extern "C" pfc_status pfc_curvatures(pfc_ctx* c, const void* u, void* k1, void* 
     const pfc_problem& P = c->P;
     if (P.prec == PFC_FP64)
         PFC_CU(launch_curvatures<double>((const double*)u, (double*)k1, (double*)k2, P.nx, P.ny, P.nz,
-                                         make_coef<double>(P.a, P.h, P.eps, P.xi, P.well), P.eps, s));
+                                         make_coef<double>(P.a, P.h, P.eps, P.xi, P.well, 0.0, nullptr, P.proj), P.eps, s));
     else
         PFC_CU(launch_curvatures<float>((const float*)u, (float*)k1, (float*)k2, P.nx, P.ny, P.nz,
-                                        make_coef<float>(P.a, P.h, P.eps, P.xi, P.well), P.eps, s));
+                                        make_coef<float>(P.a, P.h, P.eps, P.xi, P.well, 0.0, nullptr, P.proj), P.eps, s));
     return PFC_OK;
 }
 
@@ -518,14 +522,14 @@ extern "C" pfc_status pfc_surface_cells(pfc_ctx* c, const void* u, double level,
         double* k1 = (double*)c->skap;
         double* k2 = k1 + c->N;
         PFC_CU(launch_curvatures<double>((const double*)u, k1, k2, P.nx, P.ny, P.nz,
-                                         make_coef<double>(P.a, P.h, P.eps, P.xi, P.well), P.eps, s));
+                                         make_coef<double>(P.a, P.h, P.eps, P.xi, P.well, 0.0, nullptr, P.proj), P.eps, s));
         PFC_CU(launch_surface_cells<double>((const double*)u, k1, k2, P.nx, P.ny, P.nz, P.h, level, c->sblk, c->soff,
                                             (double*)cells, cap, s));
     } else {
         float* k1 = (float*)c->skap;
         float* k2 = k1 + c->N;
         PFC_CU(launch_curvatures<float>((const float*)u, k1, k2, P.nx, P.ny, P.nz,
-                                        make_coef<float>(P.a, P.h, P.eps, P.xi, P.well), P.eps, s));
+                                        make_coef<float>(P.a, P.h, P.eps, P.xi, P.well, 0.0, nullptr, P.proj), P.eps, s));
         PFC_CU(launch_surface_cells<float>((const float*)u, k1, k2, P.nx, P.ny, P.nz, P.h, level, c->sblk, c->soff,
                                            (float*)cells, cap, s));
     }
@@ -602,8 +606,9 @@ extern "C" pfc_status pfc_batch_create(const pfc_problem* probs, int32_t n, pfc_
         if (st) return fail(st, "problem %d: %s", k, g_err);
         if (probs[k].prec != PFC_FP32 || probs[k].impl != PFC_IMPL_FUSED)
             return fail(PFC_EUNSUPPORTED, "problem %d: batches run FP32 on the fused path only", k);
-        if (probs[k].mu != 0.0)
-            return fail(PFC_EUNSUPPORTED, "problem %d: the orientation term is not available in batches", k);
+        if (probs[k].mu != 0.0 || probs[k].proj)
+            return fail(PFC_EUNSUPPORTED, "problem %d: the orientation term and the projected M are not available "
+                        "in batches", k);
     }
     pfc_batch* b = new (std::nothrow) pfc_batch();
     if (!b) return fail(PFC_ENOMEM, "host allocation failed");

@@ -98,6 +98,38 @@ __device__ __noinline__ T discriminant_fp64_at(const CoefD& R, int well, const T
     return (T)Dr2 / (r * r);
 }
 
+// rho^4 D of the tangent-projected M, in FP64 from the exact raw stencil
+// values: rho^2 M = rho^2 K - rho (G k^T + k G^T) + s G G^T needs no division.
+template <typename T>
+__device__ __noinline__ T discriminant_fp64_proj_at(const CoefD& R, const T* pm, const T* p0, const T* pp, int pitch)
+{
+    auto d = [](T v) { return (double)v; };
+    const double u0 = d(p0[0]);
+    const double Gx = (d(p0[1]) - d(p0[-1])) * R.sg, Gy = (d(p0[pitch]) - d(p0[-pitch])) * R.sg;
+    const double Gz = (d(pp[0]) - d(pm[0])) * R.sg;
+    const double Kxx = R.kd * ((d(p0[1]) + d(p0[-1])) - 2.0 * u0);
+    const double Kyy = R.kd * ((d(p0[pitch]) + d(p0[-pitch])) - 2.0 * u0);
+    const double Kzz = R.kd * ((d(pp[0]) + d(pm[0])) - 2.0 * u0);
+    const double Kxy = R.ko * ((d(p0[pitch + 1]) - d(p0[pitch - 1])) - (d(p0[-pitch + 1]) - d(p0[-pitch - 1])));
+    const double Kxz = R.ko * ((d(pp[1]) - d(pp[-1])) - (d(pm[1]) - d(pm[-1])));
+    const double Kyz = R.ko * ((d(pp[pitch]) - d(pp[-pitch])) - (d(pm[pitch]) - d(pm[-pitch])));
+    const double rho = fma(Gx, Gx, fma(Gy, Gy, fma(Gz, Gz, R.xi2)));
+    const double kx = Kxx * Gx + Kxy * Gy + Kxz * Gz, ky = Kxy * Gx + Kyy * Gy + Kyz * Gz;
+    const double kz = Kxz * Gx + Kyz * Gy + Kzz * Gz;
+    const double s = Gx * kx + Gy * ky + Gz * kz;
+    const double r2 = rho * rho;
+    const double Mxx = r2 * Kxx - 2.0 * rho * Gx * kx + s * Gx * Gx;
+    const double Myy = r2 * Kyy - 2.0 * rho * Gy * ky + s * Gy * Gy;
+    const double Mzz = r2 * Kzz - 2.0 * rho * Gz * kz + s * Gz * Gz;
+    const double Mxy = r2 * Kxy - rho * (Gx * ky + kx * Gy) + s * Gx * Gy;
+    const double Mxz = r2 * Kxz - rho * (Gx * kz + kx * Gz) + s * Gx * Gz;
+    const double Myz = r2 * Kyz - rho * (Gy * kz + ky * Gz) + s * Gy * Gz;
+    const double Tr = Mxx + Myy + Mzz;
+    const double S = Mxx * Mxx + Myy * Myy + Mzz * Mzz + 2.0 * (Mxy * Mxy + Mxz * Mxz + Myz * Myz);
+    // the cancellation is resolved; divide in FP64 (rho^4 can be below float's range)
+    return (T)((2.0 * S - Tr * Tr) / (r2 * r2));
+}
+
 struct NoRefine {
     __device__ __forceinline__ float operator()() const { return 0.0f; }
 };
@@ -117,7 +149,11 @@ struct NoRefine {
 //
 // ORIENT adds the orientation term of Sec. 5.2, c7 (theta . G)^2, and its
 // cotangent 2 c7 (theta . G) theta on G.
-template <typename T, bool GRAD, bool ORIENT = false, class Refine = NoRefine>
+//
+// PROJ replaces eq. Meps by the tangent-projected M = P K P, K = -eps Hess u,
+// P = I - G G^T / rho (no double-well term): with k = K G and
+// s = G.k, M = K - (G m^T + m G^T)/rho, m = k - (s / 2rho) G.
+template <typename T, bool GRAD, bool ORIENT = false, bool PROJ = false, class Refine = NoRefine>
 __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz, T hxx, T hyy,
                                         T hzz, T hxy, T hxz, T hyz, Cot<T>& ct, const Refine& refine = Refine())
 {
@@ -127,26 +163,47 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
     const T iq = rsqrt_(rho);
     const T q = rho * iq;
     const T irho = sizeof(T) == 4 ? iq * iq : rcp_(rho);
-    // W'(u)/eps and W''(u)/eps for the chosen double well
-    T wp, wpp;
-    if (C.well == 0) {
-        const T t = u0 - u0 * u0;                       // u (1 - u)
-        wp = T(2) * t * (T(1) - T(2) * u0);
-        wpp = T(2) - T(12) * t;                         // 2 (1 - 6u + 6u^2)
+    T wpp = T(0), wr = T(0);
+    T Mxx, Myy, Mzz, Mxy, Mxz, Myz;
+    // PROJ only: K = -eps Hess u and k = K G
+    T Kxx = T(0), Kyy = T(0), Kzz = T(0), Kxy = T(0), Kxz = T(0), Kyz = T(0);
+    T kx = T(0), ky = T(0), kz = T(0), sk = T(0);
+    if (PROJ) {
+        Kxx = C.kd * hxx; Kyy = C.kd * hyy; Kzz = C.kd * hzz;
+        Kxy = C.ko * hxy; Kxz = C.ko * hxz; Kyz = C.ko * hyz;
+        kx = fma_(Kxx, Gx, fma_(Kxy, Gy, Kxz * Gz));
+        ky = fma_(Kxy, Gx, fma_(Kyy, Gy, Kyz * Gz));
+        kz = fma_(Kxz, Gx, fma_(Kyz, Gy, Kzz * Gz));
+        sk = fma_(Gx, kx, fma_(Gy, ky, Gz * kz));
+        const T hs = T(0.5) * sk * irho;
+        const T mx = fma_(-hs, Gx, kx), my = fma_(-hs, Gy, ky), mz = fma_(-hs, Gz, kz);
+        Mxx = fma_(-T(2) * irho * Gx, mx, Kxx);
+        Myy = fma_(-T(2) * irho * Gy, my, Kyy);
+        Mzz = fma_(-T(2) * irho * Gz, mz, Kzz);
+        Mxy = Kxy - irho * fma_(Gx, my, mx * Gy);
+        Mxz = Kxz - irho * fma_(Gx, mz, mx * Gz);
+        Myz = Kyz - irho * fma_(Gy, mz, my * Gz);
     } else {
-        wp = u0 * u0 * u0 - u0;
-        wpp = T(3) * u0 * u0 - T(1);
+        // W'(u)/eps and W''(u)/eps for the chosen double well
+        T wp;
+        if (C.well == 0) {
+            const T t = u0 - u0 * u0;                       // u (1 - u)
+            wp = T(2) * t * (T(1) - T(2) * u0);
+            wpp = T(2) - T(12) * t;                         // 2 (1 - 6u + 6u^2)
+        } else {
+            wp = u0 * u0 * u0 - u0;
+            wpp = T(3) * u0 * u0 - T(1);
+        }
+        wr = wp * C.inv_eps * irho;                         // (W'/eps) / rho
+        // M = -eps Hess u + (W'/eps) G G^T / rho
+        const T wx = wr * Gx, wy = wr * Gy, wz = wr * Gz;
+        Mxx = fma_(C.kd, hxx, wx * Gx);
+        Myy = fma_(C.kd, hyy, wy * Gy);
+        Mzz = fma_(C.kd, hzz, wz * Gz);
+        Mxy = fma_(C.ko, hxy, wx * Gy);
+        Mxz = fma_(C.ko, hxz, wx * Gz);
+        Myz = fma_(C.ko, hyz, wy * Gz);
     }
-    const T w = wp * C.inv_eps;
-    const T wr = w * irho;                              // (W'/eps) / rho
-    // M = -eps Hess u + (W'/eps) G G^T / rho
-    const T wx = wr * Gx, wy = wr * Gy, wz = wr * Gz;
-    const T Mxx = fma_(C.kd, hxx, wx * Gx);
-    const T Myy = fma_(C.kd, hyy, wy * Gy);
-    const T Mzz = fma_(C.kd, hzz, wz * Gz);
-    const T Mxy = fma_(C.ko, hxy, wx * Gy);
-    const T Mxz = fma_(C.ko, hxz, wx * Gz);
-    const T Myz = fma_(C.ko, hyz, wy * Gz);
     const T Tr = Mxx + Myy + Mzz;
     const T off = fma_(Mxy, Mxy, fma_(Mxz, Mxz, Myz * Myz));
     const T S = fma_(Mxx, Mxx, fma_(Myy, Myy, fma_(Mzz, Mzz, T(2) * off)));
@@ -187,6 +244,46 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
     const T LGy = fma_(Lxy, Gx, fma_(Lyy, Gy, Lyz * Gz));
     const T LGz = fma_(Lxz, Gx, fma_(Lyz, Gy, Lzz * Gz));
     const T GLG = fma_(Gx, LGx, fma_(Gy, LGy, Gz * LGz));
+    if (PROJ) {
+        // dE/dK = P L P = L - (G n^T + n G^T)/rho, n = LG - (G.LG / 2rho) G;
+        // dE/dG through P: -2 B G / rho + 2 (G^T B G) G / rho^2 with
+        // B G = L P k + K P (LG) and G^T B G = 2 (LG.k - s G.LG / rho)
+        const T hl = T(0.5) * GLG * irho;
+        const T nx = fma_(-hl, Gx, LGx), ny = fma_(-hl, Gy, LGy), nz = fma_(-hl, Gz, LGz);
+        const T Pxx = fma_(-T(2) * irho * Gx, nx, Lxx);
+        const T Pyy = fma_(-T(2) * irho * Gy, ny, Lyy);
+        const T Pzz = fma_(-T(2) * irho * Gz, nz, Lzz);
+        const T Pxy = Lxy - irho * fma_(Gx, ny, nx * Gy);
+        const T Pxz = Lxz - irho * fma_(Gx, nz, nx * Gz);
+        const T Pyz = Lyz - irho * fma_(Gy, nz, ny * Gz);
+        const T si = sk * irho, gi = GLG * irho;
+        const T pkx = fma_(-si, Gx, kx), pky = fma_(-si, Gy, ky), pkz = fma_(-si, Gz, kz);      // P k
+        const T plx = fma_(-gi, Gx, LGx), ply = fma_(-gi, Gy, LGy), plz = fma_(-gi, Gz, LGz);  // P LG
+        const T BGx = fma_(Lxx, pkx, fma_(Lxy, pky, Lxz * pkz)) + fma_(Kxx, plx, fma_(Kxy, ply, Kxz * plz));
+        const T BGy = fma_(Lxy, pkx, fma_(Lyy, pky, Lyz * pkz)) + fma_(Kxy, plx, fma_(Kyy, ply, Kyz * plz));
+        const T BGz = fma_(Lxz, pkx, fma_(Lyz, pky, Lzz * pkz)) + fma_(Kxz, plx, fma_(Kyz, ply, Kzz * plz));
+        const T GBG = T(2) * fma_(LGx, kx, fma_(LGy, ky, fma_(LGz, kz, -si * GLG)));
+        const T al = -T(2) * irho;
+        const T be = fma_(T(2) * GBG * irho, irho, fma_(dq, iq, T(2) * C.c6));
+        ct.u = T(0);
+        ct.dx = C.sg * fma_(al, BGx, be * Gx);
+        ct.dy = C.sg * fma_(al, BGy, be * Gy);
+        ct.dz = C.sg * fma_(al, BGz, be * Gz);
+        if (ORIENT) {
+            const T ot = T(2) * C.c7 * tg * C.sg;
+            ct.dx = fma_(ot, C.th0, ct.dx);
+            ct.dy = fma_(ot, C.th1, ct.dy);
+            ct.dz = fma_(ot, C.th2, ct.dz);
+        }
+        ct.hxx = C.kd * Pxx;
+        ct.hyy = C.kd * Pyy;
+        ct.hzz = C.kd * Pzz;
+        const T ko2p = T(2) * C.ko;
+        ct.hxy = ko2p * Pxy;
+        ct.hxz = ko2p * Pxz;
+        ct.hyz = ko2p * Pyz;
+        return e;
+    }
     ct.u = wpp * C.inv_eps * GLG * irho;
     const T al = T(2) * wr;
     const T be = fma_(-al * GLG, irho, fma_(dq, iq, T(2) * C.c6));

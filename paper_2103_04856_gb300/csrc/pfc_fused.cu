@@ -17,9 +17,10 @@
 // gradient sums are reduced per CTA in FP64 and combined by the last CTA of
 // the problem (pfc_device.cuh, grid_finish).
 //
-// EXT (the extended sweep, Sec. 5.2): the orientation term, and coefficients
-// read per voxel from a field c(x); each thread loads the six coefficients
-// of its column one plane ahead of their use.
+// EXT (the extended sweep): 1 = the orientation term of Sec. 5.2 and
+// coefficients read per voxel from a field c(x) (each thread loads the six
+// coefficients of its column one plane ahead of their use); 2 = the same
+// with the tangent-projected M = -eps P Hess u P.
 #include <type_traits>
 
 #include "pfc_device.cuh"
@@ -72,7 +73,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-template <typename T, int TY, int MODE, int MAXI, bool EXT = false>
+template <typename T, int TY, int MODE, int MAXI, int EXT = 0>
 __global__ void __launch_bounds__(Tile<TY>::NT, 1)
 k_fused(const __grid_constant__ Launch<T, MAXI> L)
 {
@@ -274,13 +275,16 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
                 else return in.C;
             }();
             // FP64 re-evaluation of D from the exact float inputs (float path only)
-            auto refine = [&]() -> T { return discriminant_fp64_at<T>(in.C.R, in.C.well, pm, p0, pp, UXP, cind); };
+            auto refine = [&]() -> T {
+                if constexpr (EXT == 2) return discriminant_fp64_proj_at<T>(in.C.R, pm, p0, pp, UXP);
+                else return discriminant_fp64_at<T>(in.C.R, in.C.well, pm, p0, pp, UXP, cind);
+            };
             if constexpr (MODE == MODE_ENERGY) {
-                const T e = voxel_eval<T, false, EXT>(CC, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ctv, refine);
+                const T e = voxel_eval<T, false, EXT != 0, EXT == 2>(CC, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ctv, refine);
                 se += interior ? e : T(0);
                 return;
             } else {
-                const T e = voxel_eval<T, true, EXT>(CC, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ctv, refine);
+                const T e = voxel_eval<T, true, EXT != 0, EXT == 2>(CC, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ctv, refine);
                 if constexpr (kOwn) se += interior ? e : T(0);
                 // transposed-stencil pieces of this voxel (see the gather):
                 //   x/y first+second differences read from the left/right neighbour,
@@ -378,10 +382,26 @@ __global__ void k_curvatures(const T* __restrict__ u, T* __restrict__ k1, T* __r
         const T hyz = at(0, 1, 1) - at(0, 1, -1) - at(0, -1, 1) + at(0, -1, -1);
         const T Gx = dx * C.sg, Gy = dy * C.sg, Gz = dz * C.sg;
         const T rho = Gx * Gx + Gy * Gy + Gz * Gz + C.xi2;
-        const T wp = C.well == 0 ? T(2) * u0 * (T(1) - u0) * (T(1) - T(2) * u0) : u0 * u0 * u0 - u0;
-        const T wr = wp * C.inv_eps / rho;
-        const T Mxx = C.kd * hxx + wr * Gx * Gx, Myy = C.kd * hyy + wr * Gy * Gy, Mzz = C.kd * hzz + wr * Gz * Gz;
-        const T Mxy = C.ko * hxy + wr * Gx * Gy, Mxz = C.ko * hxz + wr * Gx * Gz, Myz = C.ko * hyz + wr * Gy * Gz;
+        T Mxx, Myy, Mzz, Mxy, Mxz, Myz;
+        if (C.proj) {   // M = P K P, K = -eps Hess u, P = I - G G^T / rho
+            const T Kxx = C.kd * hxx, Kyy = C.kd * hyy, Kzz = C.kd * hzz;
+            const T Kxy = C.ko * hxy, Kxz = C.ko * hxz, Kyz = C.ko * hyz;
+            const T kx = Kxx * Gx + Kxy * Gy + Kxz * Gz, ky = Kxy * Gx + Kyy * Gy + Kyz * Gz;
+            const T kz = Kxz * Gx + Kyz * Gy + Kzz * Gz;
+            const T s = Gx * kx + Gy * ky + Gz * kz;
+            const T ir = T(1) / rho, s2 = s * ir * ir;
+            Mxx = Kxx - T(2) * ir * Gx * kx + s2 * Gx * Gx;
+            Myy = Kyy - T(2) * ir * Gy * ky + s2 * Gy * Gy;
+            Mzz = Kzz - T(2) * ir * Gz * kz + s2 * Gz * Gz;
+            Mxy = Kxy - ir * (Gx * ky + kx * Gy) + s2 * Gx * Gy;
+            Mxz = Kxz - ir * (Gx * kz + kx * Gz) + s2 * Gx * Gz;
+            Myz = Kyz - ir * (Gy * kz + ky * Gz) + s2 * Gy * Gz;
+        } else {
+            const T wp = C.well == 0 ? T(2) * u0 * (T(1) - u0) * (T(1) - T(2) * u0) : u0 * u0 * u0 - u0;
+            const T wr = wp * C.inv_eps / rho;
+            Mxx = C.kd * hxx + wr * Gx * Gx; Myy = C.kd * hyy + wr * Gy * Gy; Mzz = C.kd * hzz + wr * Gz * Gz;
+            Mxy = C.ko * hxy + wr * Gx * Gy; Mxz = C.ko * hxz + wr * Gx * Gz; Myz = C.ko * hyz + wr * Gy * Gz;
+        }
         const T Tr = Mxx + Myy + Mzz;
         const T S = Mxx * Mxx + Myy * Myy + Mzz * Mzz + T(2) * (Mxy * Mxy + Mxz * Mxz + Myz * Myz);
         const T D = T(2) * S - Tr * Tr;
@@ -395,7 +415,8 @@ __global__ void k_curvatures(const T* __restrict__ u, T* __restrict__ k1, T* __r
 // ------------------------------------------------------------ host side
 
 template <typename T>
-Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well, double mu, const double* theta)
+Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well, double mu, const double* theta,
+                  int proj)
 {
     const double h3 = h * h * h;
     Coef<T> C;
@@ -422,10 +443,11 @@ Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well, 
     C.th0 = (T)(theta ? theta[0] : 0.0);
     C.th1 = (T)(theta ? theta[1] : 0.0);
     C.th2 = (T)(theta ? theta[2] : 0.0);
+    C.proj = proj ? 1 : 0;
     return C;
 }
-template Coef<float> make_coef<float>(const double*, double, double, double, int, double, const double*);
-template Coef<double> make_coef<double>(const double*, double, double, double, int, double, const double*);
+template Coef<float> make_coef<float>(const double*, double, double, double, int, double, const double*, int);
+template Coef<double> make_coef<double>(const double*, double, double, double, int, double, const double*, int);
 
 // c(x) from a(x): the coefficients of eq. Feps (times h^3) per voxel, in FP64
 // then rounded to the arithmetic type, exactly as make_coef does for a constant a.
@@ -464,7 +486,7 @@ size_t fused_smem_bytes(int elem_size, int tile_y)
     return (size_t)elem_size * ((size_t)NBUF * plane + 2 * 5 * (size_t)next) + sizeof(float) * NPART * (size_t)nt;
 }
 
-template <typename T, int TY, int MODE, int MAXI, bool EXT = false>
+template <typename T, int TY, int MODE, int MAXI, int EXT = 0>
 static cudaError_t launch_one(const Launch<T, MAXI>& L, int blocks, cudaStream_t s)
 {
     const size_t smem = fused_smem_bytes(sizeof(T), TY);
@@ -530,7 +552,7 @@ static void plan(Launch<T, MAXI>& L, int tile_y, int max_run)
     }
 }
 
-template <typename T, int TY, bool EXT = false>
+template <typename T, int TY, int EXT = 0>
 static cudaError_t launch_mode(const Inst<T>& in, int mode, int max_run, cudaStream_t s)
 {
     Launch<T, 1> L;
@@ -548,7 +570,8 @@ static cudaError_t launch_mode(const Inst<T>& in, int mode, int max_run, cudaStr
 template <typename T>
 cudaError_t launch_fused(const Inst<T>& in, int mode, int tile_y, int max_run, cudaStream_t s)
 {
-    if (needs_ext(in)) return launch_mode<T, EXT_TILE_Y, true>(in, mode, max_run, s);
+    if (in.C.proj) return launch_mode<T, EXT_TILE_Y, 2>(in, mode, max_run, s);
+    if (needs_ext(in)) return launch_mode<T, EXT_TILE_Y, 1>(in, mode, max_run, s);
     return tile_y == 8 ? launch_mode<T, 8>(in, mode, max_run, s) : launch_mode<T, 16>(in, mode, max_run, s);
 }
 template cudaError_t launch_fused<float>(const Inst<float>&, int, int, int, cudaStream_t);

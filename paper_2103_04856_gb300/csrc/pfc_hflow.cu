@@ -360,6 +360,7 @@ extern "C" pfc_status pfc_hflow_create(const pfc_problem* prob, const pfc_hflow_
         if (!isfinite(p.a[i])) return hfail(PFC_EINVAL, "hflow: a coefficient is not finite");
     if (!isfinite(p.mu) || !isfinite(p.theta[0]) || !isfinite(p.theta[1]) || !isfinite(p.theta[2]))
         return hfail(PFC_EINVAL, "hflow: mu and theta must be finite");
+    if ((p.proj != 0 && p.proj != 1) || p.reserved != 0) return hfail(PFC_EINVAL, "hflow: proj 0 or 1, reserved 0");
     if (!isfinite(hp->m0) || !(hp->lr >= 0) || !(hp->beta1 >= 0 && hp->beta1 < 1) || !(hp->beta2 >= 0 && hp->beta2 < 1) ||
         !(hp->adam_eps >= 0) || !(hp->blur_sigma >= 0))
         return hfail(PFC_EINVAL, "hflow: m0 finite, lr >= 0, betas in [0,1), eps >= 0, sigma >= 0 required");
@@ -487,7 +488,7 @@ static cudaError_t eval(pfc_hflow* h, const T* A, T** gb, cudaStream_t s)
     in.out = (T*)h->buf[1];
     in.nx = h->P.nx; in.ny = h->P.ny; in.nz = h->P.nz;
     in.vec = (h->P.nx % (16 / (int)sizeof(T)) == 0);
-    in.C = make_coef<T>(h->P.a, h->P.h, h->P.eps, h->P.xi, h->P.well, h->P.mu, h->P.theta);
+    in.C = make_coef<T>(h->P.a, h->P.h, h->P.eps, h->P.xi, h->P.well, h->P.mu, h->P.theta, h->P.proj);
     in.cf = h->cf_on ? (const T*)h->cfield : nullptr;
     in.inv_N = 1.0 / (double)h->N;
     in.partials = h->spart;

@@ -43,6 +43,7 @@ struct Coef {
     CoefD R;
     // orientation term of Sec. 5.2, eps mu (theta . grad u)^2: c7 = eps mu h^3
     T c7, th0, th1, th2;
+    int proj;   // 1: tangent-projected M = -eps P Hess u P instead of eq. Meps
 };
 
 // Coefficient fields: c(x) = (c1..c6)(a(x)) as 6 component planes of N
@@ -88,11 +89,11 @@ struct Launch {
 
 template <typename T>
 Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well, double mu = 0.0,
-                  const double* theta = nullptr);
+                  const double* theta = nullptr, int proj = 0);
 
-// The extended sweep (orientation term and/or c(x)) runs with 8-row tiles.
+// The extended sweep (orientation term, c(x), projected M) runs with 8-row tiles.
 template <typename T>
-inline bool needs_ext(const Inst<T>& in) { return in.cf != nullptr || in.C.c7 != T(0); }
+inline bool needs_ext(const Inst<T>& in) { return in.cf != nullptr || in.C.c7 != T(0) || in.C.proj != 0; }
 constexpr int EXT_TILE_Y = 8;
 // c(x) from a(x) (both [6][n], the arithmetic type; a in the paper's order)
 template <typename T>

@@ -104,7 +104,7 @@ static pfc_status run_noalloc(const pfc_problem* p, const void* u, void* g, doub
     in.zc = p->nz;
     in.chunks_z = 1;
     in.vec = (p->nx % (16 / (int)sizeof(T)) == 0) && ((uintptr_t)u) % 16 == 0;
-    in.C = make_coef<T>(p->a, p->h, p->eps, p->xi, p->well, p->mu, p->theta);
+    in.C = make_coef<T>(p->a, p->h, p->eps, p->xi, p->well, p->mu, p->theta, p->proj);
     in.cf = nullptr;
     in.tau = T(0);
     in.inv_N = 1.0 / ((double)p->nx * p->ny * p->nz);
@@ -144,6 +144,7 @@ extern "C" pfc_status pfc_energy_and_grad_noalloc(const pfc_problem* prob, const
         if (!isfinite(p.a[i])) return na_fail(PFC_EINVAL, "noalloc: a coefficient is not finite");
     if (!isfinite(p.mu) || !isfinite(p.theta[0]) || !isfinite(p.theta[1]) || !isfinite(p.theta[2]))
         return na_fail(PFC_EINVAL, "noalloc: mu and theta must be finite");
+    if ((p.proj != 0 && p.proj != 1) || p.reserved != 0) return na_fail(PFC_EINVAL, "noalloc: proj 0 or 1, reserved 0");
     if (p.well != PFC_WELL_01 && p.well != PFC_WELL_PM1) return na_fail(PFC_EINVAL, "noalloc: unknown double well");
     if (p.prec != PFC_FP32 && p.prec != PFC_FP64) return na_fail(PFC_EINVAL, "noalloc: unknown precision");
     if (p.impl != PFC_IMPL_FUSED) return na_fail(PFC_EUNSUPPORTED, "noalloc: only the fused path needs no allocation");

@@ -62,6 +62,7 @@ class _CProblem(ctypes.Structure):
         ("a", ctypes.c_double * 6),
         ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32),
         ("mu", ctypes.c_double), ("theta", ctypes.c_double * 3),
+        ("proj", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -70,7 +71,8 @@ class Problem:
     """Grid and parameters of eq. Feps; ``a`` in the paper's order (a20 a11 a02 a10 a01 a00),
     kappa1 >= kappa2.  ``prec`` is "fp32" or "fp64", ``impl`` "fused" or "plain".
     ``mu``, ``theta`` (x, y, z): the orientation term eps mu (theta . grad u)^2
-    of Sec. 5.2 (mu = 0: none)."""
+    of Sec. 5.2 (mu = 0: none).  ``proj`` = 1: the tangent-projected
+    M = -eps P Hess u P instead of eq. Meps."""
     nx: int
     ny: int
     nz: int
@@ -85,6 +87,7 @@ class Problem:
     tile_z: int = 0
     mu: float = 0.0
     theta: tuple = (0.0, 0.0, 0.0)
+    proj: int = 0
 
     @classmethod
     def from_shape(cls, shape, **kw):
@@ -110,7 +113,7 @@ class Problem:
                          float(self.h), float(self.eps), float(self.xi),
                          (ctypes.c_double * 6)(*[float(x) for x in self.a]),
                          int(self.tile_y), int(self.tile_z), float(self.mu),
-                         (ctypes.c_double * 3)(*[float(x) for x in self.theta]))
+                         (ctypes.c_double * 3)(*[float(x) for x in self.theta]), int(self.proj), 0)
 
 
 _lib = None

@@ -278,3 +278,73 @@ def test_surface_cells_fp32():
     A = want[:, 0].sum()
     for k in (1, 2):
         assert (got[:, 0] * got[:, k]).sum() / A == pytest.approx((want[:, 0] * want[:, k]).sum() / A, rel=1e-3)
+
+
+# ------------------------------------------------------------ tangent-projected M
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_projected_fp64_vs_oracle(shape):
+    rng = np.random.default_rng(200 + sum(shape))
+    for well, mu in ((0, 0.0), (1, 1.3)):
+        p = P(shape, rng.uniform(-1, 1, 6), eps=1.3, h=0.9, well=well, proj=1, mu=mu, theta=_unit(rng))
+        u = I.noise(shape, 0.3 if well == 0 else -0.1, 0.1 if well == 0 else 0.3, 17)
+        Eo, go = oracle.energy_and_grad(u, oprob(p, proj=1))
+        ctx = pfc.Context(p)
+        E, g = ctx.energy_and_grad(dev(u, "fp64"))
+        assert E == pytest.approx(Eo, rel=1e-10, abs=1e-12)
+        assert rel(g.cpu().numpy(), go) < 1e-10
+        assert ctx.energy(dev(u, "fp64")) == pytest.approx(Eo, rel=1e-10, abs=1e-12)
+
+
+def test_projected_with_coefficient_field_and_run():
+    """70 steps with a(x) near p = k1^2 + k2^2 (a well-posed descent: with
+    random-sign coefficients the field grows and the oracle itself moves by
+    1e-3 under a 1e-13 perturbation of u0, so no two implementations agree)."""
+    shape = (12, 16, 20)
+    rng = np.random.default_rng(18)
+    af = np.array([1, 0, 1, 0, 0, 0.0])[:, None, None, None] + 0.2 * rng.uniform(-1, 1, (6,) + shape)
+    p = P(shape, (0,) * 6, xi=1e-2, proj=1)
+    u = I.noise(shape, 0.3, 0.1, 19)
+    ctx = pfc.Context(p)
+    ctx.set_coefficient_field(dev(af, "fp64"))
+    ud = dev(u, "fp64")
+    tr = ctx.run(ud, 70, 1e-3)
+    uo, tro = oracle.run(u, oprob(p, proj=1, a_field=af), 70, 1e-3)
+    assert rel(ud.cpu().numpy(), uo) < 1e-10
+    np.testing.assert_allclose(tr, tro, rtol=1e-9, atol=1e-12)
+
+
+def test_projected_fp32_vs_fp64_and_sphere():
+    """FP32 against FP64 on the same state (noise, asymmetric p), and the
+    128^3 tanh sphere R = 32, eps = 2 (p = k1^2 + k2^2): FP32 energy against
+    the oracle, whose ratio to sigma 8 pi is 1.0077."""
+    shape = (24, 40, 48)
+    u = I.noise(shape, 0.3, 0.1, 20).astype(np.float32).astype(np.float64)
+    a = (0.2, 0, 1, 0, -0.5, 0)
+    E64, g64 = pfc.Context(P(shape, a, proj=1)).energy_and_grad(dev(u, "fp64"))
+    E32, g32 = pfc.Context(P(shape, a, proj=1, prec="fp32")).energy_and_grad(dev(u, "fp32"))
+    assert abs(E32 - E64) / abs(E64) < 1e-4
+    assert rel(g32.double().cpu().numpy(), g64.cpu().numpy()) < 1e-3
+    n = 128
+    s = I.tanh_sphere((n, n, n), 32.0, 2.0, 1.0, center=(64.3, 64.1, 64.2)).astype(np.float32).astype(np.float64)
+    p32 = P(s.shape, (1, 0, 1, 0, 0, 0), eps=2.0, proj=1, prec="fp32")
+    Eo = oracle.energy(s, oprob(p32, proj=1))
+    assert pfc.Context(p32).energy(dev(s, "fp32")) == pytest.approx(Eo, rel=1e-4)
+
+
+def test_projected_curvatures_and_flow_vs_oracle():
+    shape = (10, 12, 14)
+    u = I.noise(shape, 0.3, 0.15, 21)
+    p = P(shape, (1.0, 0.4, 0.8, 0.3, -0.2, 0.1), proj=1)
+    k1, k2 = pfc.Context(p).curvatures(dev(u, "fp64"))
+    o1, o2 = oracle.curvatures(u, oprob(p, proj=1))
+    sc = np.max(np.abs(o1))
+    assert np.max(np.abs(k1.cpu().numpy() - o1)) < 1e-6 * sc
+    assert np.max(np.abs(k2.cpu().numpy() - o2)) < 1e-6 * sc
+    flow = pfc.HFlow(p, m0=0.3, lr=1e-3, blur_sigma=1.0)
+    rng = np.random.default_rng(22)
+    A = 0.04 * rng.standard_normal((3,) + shape)
+    G, gA = flow.grad(dev(A, "fp64"))
+    Go, gAo = oracle.hflow_grad(A, oprob(p, proj=1), {"m0": 0.3, "blur_sigma": 1.0})
+    assert G == pytest.approx(Go, rel=1e-10)
+    assert rel(gA.cpu().numpy(), gAo) < 1e-10
