@@ -116,3 +116,28 @@ def test_paper_setting_100():
     assert np.all(np.isfinite(tr))
     assert np.max(np.abs(tr[:, 3] - fd["m0"])) < 1e-6
     assert tr[-1, 0] < tr[0, 0]
+
+
+def test_paper_setting_generates_a_viable_shape():
+    """The generator from white noise in the paper's setting (Sec. 4.1, Fig.
+    cvg_1 parameters): within 2000 Adam iterations the field separates into
+    the two phases and passes the paper's viability test (Sec. 4.5:
+    normalised discrepancy below 0.75, max u > 0.1, min u < -0.1), the energy
+    has dropped, the mass is kept and {u = 0} has a surface."""
+    pd, fd, A0 = I.paper_flow_100()
+    nz, ny, nx = pd["shape"]
+    prob = pfc.Problem(nx=nx, ny=ny, nz=nz, h=pd["h"], eps=pd["eps"], xi=pd["xi"], a=pd["a"], well=pd["well"],
+                       prec="fp32")
+    flow = pfc.HFlow(prob, m0=fd["m0"], lr=fd["lr"], blur_sigma=fd["blur_sigma"])
+    A = torch.tensor(A0.astype(np.float32), device="cuda")
+    m, v = torch.zeros_like(A), torch.zeros_like(A)
+    tr = flow.run(A, m, v, 2000)
+    assert np.all(np.isfinite(tr))
+    np.testing.assert_allclose(tr[:, 3], fd["m0"], atol=1e-6)
+    assert tr[-1, 0] < 0.2 * tr[0, 0]
+    ctx = pfc.Context(prob)
+    ut = flow.field(A)
+    d = ctx.diagnostics(ut)
+    assert d["ratio"] < 0.75 and d["max"] > 0.1 and d["min"] < -0.1
+    cells = ctx.surface_cells(ut)
+    assert cells.shape[0] > 1000 and float(cells[:, 0].double().sum()) > 1.0
