@@ -182,6 +182,21 @@ pfc_status pfc_batch_run(pfc_batch* batch, void* const* u, int32_t nsteps, const
  * receives n_inst rows of the 5 scalars of pfc_step. */
 pfc_status pfc_batch_step(pfc_batch* batch, const void* const* u_in, void* const* u_out, const double* tau,
                           double* scalars_dev, pfc_stream stream);
+/* pfc_batch_step from and to HOST memory: u_in_host[k] is copied to the
+ * device, stepped, and the result copied to u_out_host[k] (host arrays of
+ * the instances' sizes, float; page-locked memory lets the copies overlap,
+ * pageable memory works but serialises them).  Enqueue only: the instances
+ * are pipelined over two internal copy streams beside `stream` (which runs
+ * the steps, one fused launch plus its projection per instance), and
+ * consecutive calls overlap (the copies out of one step with the copies in
+ * of the next).  u_out_host[k] holds the result once pfc_batch_host_wait
+ * returns; the caller must not change u_in_host / u_out_host before then.
+ * The first call allocates one device field per instance. */
+pfc_status pfc_batch_step_host(pfc_batch* batch, const void* const* u_in_host, void* const* u_out_host,
+                               const double* tau, pfc_stream stream);
+/* Waits for every step enqueued by pfc_batch_step_host (on `stream` and on
+ * the copy streams). */
+pfc_status pfc_batch_host_wait(pfc_batch* batch, pfc_stream stream);
 /* Optional device timing of pfc_batch_step: when enabled, the library records
  * CUDA events on the stream around the whole step and around its fused
  * sweep kernel; pfc_batch_last_timing waits for them and returns the two

@@ -581,6 +581,11 @@ struct pfc_batch {
     cudaStream_t cap = nullptr;
     cudaEvent_t ev[4] = { nullptr, nullptr, nullptr, nullptr };
     bool timing = false;
+    // pfc_batch_step_host: device staging and the copy pipeline
+    std::vector<void*> hin;
+    cudaStream_t hs[2] = { nullptr, nullptr };    // host-to-device, device-to-host
+    // per instance: copied in, stepped (staging input free), result ready, copied out (result buffer free)
+    std::vector<cudaEvent_t> evin, evstep, evres, evdone;
 };
 
 static void free_batch_mem(pfc_batch* b)
@@ -592,6 +597,12 @@ static void free_batch_mem(pfc_batch* b)
     cudaFree(b->trace);
     for (cudaEvent_t e : b->ev)
         if (e) cudaEventDestroy(e);
+    for (void* p : b->hin) cudaFree(p);
+    for (cudaStream_t s : b->hs)
+        if (s) cudaStreamDestroy(s);
+    for (auto* v : { &b->evin, &b->evstep, &b->evres, &b->evdone })
+        for (cudaEvent_t e : *v)
+            if (e) cudaEventDestroy(e);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->cap) cudaStreamDestroy(b->cap);
 }
@@ -824,6 +835,85 @@ extern "C" pfc_status pfc_batch_step(pfc_batch* b, const void* const* u_in, void
         PFC_CU(cudaMemcpy2DAsync(scalars_dev, 5 * sizeof(double), b->scal, NSCAL * sizeof(double), 5 * sizeof(double),
                                  b->n, cudaMemcpyDeviceToDevice, s));
     if (b->timing) PFC_CU(cudaEventRecord(b->ev[3], s));
+    return PFC_OK;
+}
+
+// One step of every instance from and to host memory, pipelined per
+// instance over three streams: copies in on hs[0], the steps on `stream`,
+// copies out on hs[1].  Nothing waits for the host: the copy of instance k
+// into its staging buffer waits only until the previous step of k has read
+// it, and the step of k only until the previous copy out of k has left its
+// result buffer, so consecutive calls overlap (the copies out of one step
+// with the copies in of the next).
+extern "C" pfc_status pfc_batch_step_host(pfc_batch* b, const void* const* u_in_host, void* const* u_out_host,
+                                          const double* tau, pfc_stream stream)
+{
+    if (!b) return fail(PFC_EINVAL, "batch is NULL");
+    if (!u_in_host || !u_out_host || !tau) return fail(PFC_EINVAL, "u_in_host, u_out_host and tau arrays are required");
+    for (int k = 0; k < b->n; ++k) {
+        if (!u_in_host[k] || !u_out_host[k]) return fail(PFC_EINVAL, "host buffer %d is NULL", k);
+        if (u_in_host[k] == u_out_host[k]) return fail(PFC_EINVAL, "u_out_host[%d] aliases u_in_host[%d]", k, k);
+        if (!isfinite(tau[k])) return fail(PFC_EINVAL, "tau[%d] is not finite", k);
+        for (int w = 0; w < 2; ++w) {
+            cudaPointerAttributes at;
+            const void* p = w ? (const void*)u_out_host[k] : u_in_host[k];
+            if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+                (void)cudaGetLastError();
+                continue;                        // plain pageable memory: allowed, the copies then block
+            }
+            if (at.type == cudaMemoryTypeDevice) return fail(PFC_EINVAL, "buffer %d is device memory", k);
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (b->hin.empty()) {
+        b->hin.assign(b->n, nullptr);
+        for (auto* v : { &b->evin, &b->evstep, &b->evres, &b->evdone }) v->assign(b->n, nullptr);
+        for (int k = 0; k < b->n; ++k) {
+            const size_t bytes = sizeof(float) * (size_t)b->P[k].nx * b->P[k].ny * b->P[k].nz;
+            PFC_CU(cudaMalloc(&b->hin[k], bytes));
+            for (auto* v : { &b->evin, &b->evstep, &b->evres, &b->evdone })
+                PFC_CU(cudaEventCreateWithFlags(&(*v)[k], cudaEventDisableTiming));
+        }
+        for (cudaStream_t& hs : b->hs) PFC_CU(cudaStreamCreateWithFlags(&hs, cudaStreamNonBlocking));
+        // first use: the copy streams start after everything already on `stream`
+        for (int k = 0; k < b->n; ++k) {
+            PFC_CU(cudaEventRecord(b->evstep[k], s));
+            PFC_CU(cudaEventRecord(b->evdone[k], s));
+        }
+    }
+    PFC_CU(cudaMemsetAsync(b->ints, 0, sizeof(unsigned) * NINTS * b->n, s));
+    PFC_CU(cudaMemsetAsync(b->scal, 0, sizeof(double) * NSCAL * b->n, s));
+    for (int k = 0; k < b->n; ++k) {
+        const long N = (long)b->P[k].nx * b->P[k].ny * b->P[k].nz;
+        PFC_CU(cudaStreamWaitEvent(b->hs[0], b->evstep[k], 0));
+        PFC_CU(cudaMemcpyAsync(b->hin[k], u_in_host[k], sizeof(float) * N, cudaMemcpyHostToDevice, b->hs[0]));
+        PFC_CU(cudaEventRecord(b->evin[k], b->hs[0]));
+        PFC_CU(cudaStreamWaitEvent(s, b->evin[k], 0));
+        PFC_CU(cudaStreamWaitEvent(s, b->evdone[k], 0));
+        Inst<float> in = b->host[k];
+        in.u = (const float*)b->hin[k];
+        in.out = (float*)b->ping[k];
+        in.vec = b->P[k].nx % 4 == 0;
+        in.tau = (float)tau[k];
+        in.trace = nullptr;
+        in.trace_cap = 0;
+        PFC_CU(launch_fused<float>(in, MODE_STEP, b->tile_y, b->max_run, s));
+        PFC_CU(cudaEventRecord(b->evstep[k], s));
+        PFC_CU(launch_add_offset<float>((float*)b->ping[k], (const float*)b->ping[k], N, in.scal + S_C, s));
+        PFC_CU(cudaEventRecord(b->evres[k], s));
+        PFC_CU(cudaStreamWaitEvent(b->hs[1], b->evres[k], 0));
+        PFC_CU(cudaMemcpyAsync(u_out_host[k], b->ping[k], sizeof(float) * N, cudaMemcpyDeviceToHost, b->hs[1]));
+        PFC_CU(cudaEventRecord(b->evdone[k], b->hs[1]));
+    }
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_batch_host_wait(pfc_batch* b, pfc_stream stream)
+{
+    if (!b) return fail(PFC_EINVAL, "batch is NULL");
+    PFC_CU(cudaStreamSynchronize((cudaStream_t)stream));
+    for (cudaStream_t hs : b->hs)
+        if (hs) PFC_CU(cudaStreamSynchronize(hs));
     return PFC_OK;
 }
 

@@ -35,7 +35,7 @@ EXPORTED = ("pfc_create", "pfc_destroy", "pfc_energy", "pfc_energy_and_grad", "p
             "pfc_hflow_field", "pfc_hflow_grad", "pfc_hflow_run", "pfc_energy_and_grad_noalloc", "pfc_b_to_a",
             "pfc_status_string", "pfc_last_error", "pfc_set_coefficient_field", "pfc_diagnostics",
             "pfc_hflow_set_coefficient_field", "pfc_hflow_set_mass_field", "pfc_surface_cells",
-            "pfc_curvature_histogram")
+            "pfc_curvature_histogram", "pfc_batch_step_host", "pfc_batch_host_wait")
 
 
 class PfcError(RuntimeError):
@@ -145,6 +145,8 @@ def load_library():
             "pfc_batch_run": ([vp, ctypes.POINTER(vp), ctypes.c_int32, dp, dp, vp], ctypes.c_int),
             "pfc_batch_step": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dp, vp, vp], ctypes.c_int),
             "pfc_batch_timing": ([vp, ctypes.c_int], ctypes.c_int),
+            "pfc_batch_step_host": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dp, vp], ctypes.c_int),
+            "pfc_batch_host_wait": ([vp, vp], ctypes.c_int),
             "pfc_batch_last_timing": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
                                       ctypes.c_int),
             "pfc_energy_and_grad_noalloc": ([P, vp, vp, dp, vp], ctypes.c_int),
@@ -398,6 +400,37 @@ class Batch:
             sp = ctypes.c_void_p(scalars.data_ptr())
         _check(self._lib.pfc_batch_step(self._h, pin, pout, taus.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                         sp, _stream(stream)))
+
+    def step_host(self, host_in, host_out, taus, wait: bool = True, stream=None):
+        """One step of every problem from and to host memory (CPU float32
+        tensors or arrays of the problems' shapes; pinned memory overlaps the
+        copies with the steps).  With wait=False the call only enqueues and
+        consecutive calls overlap; host_wait() then makes host_out final."""
+        n = len(self.probs)
+        if len(host_in) != n or len(host_out) != n:
+            raise ValueError("one input and one output buffer per problem")
+
+        def ptr(t, p, name):
+            if isinstance(t, torch.Tensor):
+                if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+                    raise TypeError(f"{name} must be a contiguous CPU float32 tensor")
+                if tuple(t.shape) != (p.nz, p.ny, p.nx):
+                    raise ValueError(f"{name} must have shape {(p.nz, p.ny, p.nx)}")
+                return t.data_ptr()
+            if t.dtype != np.float32 or not t.flags.c_contiguous or t.shape != (p.nz, p.ny, p.nx):
+                raise TypeError(f"{name} must be a C-contiguous float32 array of shape {(p.nz, p.ny, p.nx)}")
+            return t.ctypes.data
+        pin = (ctypes.c_void_p * n)(*[ptr(t, p, f"host_in[{k}]") for k, (t, p) in enumerate(zip(host_in, self.probs))])
+        pout = (ctypes.c_void_p * n)(*[ptr(t, p, f"host_out[{k}]") for k, (t, p) in enumerate(zip(host_out, self.probs))])
+        taus = np.ascontiguousarray(np.broadcast_to(np.asarray(taus, dtype=np.float64), (n,)))
+        st = _stream(stream)
+        _check(self._lib.pfc_batch_step_host(self._h, pin, pout, taus.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             st))
+        if wait:
+            self.host_wait(stream)
+
+    def host_wait(self, stream=None):
+        _check(self._lib.pfc_batch_host_wait(self._h, _stream(stream)))
 
     def timing(self, enable: bool = True):
         _check(self._lib.pfc_batch_timing(self._h, 1 if enable else 0))
