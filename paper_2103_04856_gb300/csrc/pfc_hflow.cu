@@ -265,6 +265,115 @@ __global__ void __launch_bounds__(kThreads) k_adam(const T* __restrict__ gb, T* 
     });
 }
 
+// float fields with nx % 4 == 0: the same two kernels on float4 along x (four
+// voxels per thread, one 16-byte load per field and neighbour row, the two
+// x-neighbours outside the four as scalar loads), a quarter of the load
+// instructions of the scalar forms.
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+__global__ void __launch_bounds__(kThreads) k_div4(const float* __restrict__ A, float* __restrict__ u, Flow f,
+                                                   int want_mass)
+{
+    const int nx4 = f.nx >> 2;
+    const long n = f.n, n4 = n >> 2, pls = (long)f.nx * f.ny;
+    const float sg = (float)f.sg, m0 = (float)f.m0;
+    const float* mf = (const float*)f.mf;
+    float ms = 0;
+    for (Walk w(nx4, f.ny, (long)blockIdx.x * kThreads + threadIdx.x, (long)gridDim.x * kThreads); w.i < n4;
+         w.next(nx4, f.ny)) {
+        const int x = 4 * w.x;
+        const long pl = (long)w.z * pls, row = pl + (long)w.y * f.nx, i = row + x, col = i - pl;
+        const float4 a = ld4(A + i);
+        const float am = A[row + nbr(x, -1, f.nx)], ap = A[row + nbr(x + 3, 1, f.nx)];
+        const float4 yp = ld4(A + n + pl + (long)nbr(w.y, 1, f.ny) * f.nx + x);
+        const float4 ym = ld4(A + n + pl + (long)nbr(w.y, -1, f.ny) * f.nx + x);
+        const float4 zp = ld4(A + 2 * n + (long)nbr(w.z, 1, f.nz) * pls + col);
+        const float4 zm = ld4(A + 2 * n + (long)nbr(w.z, -1, f.nz) * pls + col);
+        const float4 m = mf ? ld4(mf + i) : make_float4(m0, m0, m0, m0);
+        float4 v;
+        v.x = sg * ((a.y - am) + (yp.x - ym.x) + (zp.x - zm.x)) + m.x;
+        v.y = sg * ((a.z - a.x) + (yp.y - ym.y) + (zp.y - zm.y)) + m.y;
+        v.z = sg * ((a.w - a.y) + (yp.z - ym.z) + (zp.z - zm.z)) + m.z;
+        v.w = sg * ((ap - a.z) + (yp.w - ym.w) + (zp.w - zm.w)) + m.w;
+        st4(u + i, v);
+        ms += (v.x + v.y) + (v.z + v.w);
+    }
+    if (!want_mass) return;
+    flow_finish<float>(f, ms, 0.0f, [&](double s0, double) { f.hs[H_MASS] = s0 / (double)f.n; });
+}
+
+__global__ void __launch_bounds__(kThreads) k_adam4(const float* __restrict__ gb, float* __restrict__ A,
+                                                    float* __restrict__ m, float* __restrict__ v, Flow f, int only_grad)
+{
+    const int nx4 = f.nx >> 2;
+    const long n = f.n, n4 = n >> 2, pls = (long)f.nx * f.ny;
+    const unsigned t = f.ints[1] + 1;
+    const float b1 = (float)f.beta1, b2 = (float)f.beta2;
+    const float c1 = 1.0f / (1.0f - powf(b1, (float)t)), c2 = 1.0f / (1.0f - powf(b2, (float)t));
+    const float lr = (float)f.lr, ae = (float)f.adam_eps, sg = (float)f.sg;
+    float sabs = 0, gmax = 0;
+    for (Walk w(nx4, f.ny, (long)blockIdx.x * kThreads + threadIdx.x, (long)gridDim.x * kThreads); w.i < n4;
+         w.next(nx4, f.ny)) {
+        const int x = 4 * w.x;
+        const long pl = (long)w.z * pls, row = pl + (long)w.y * f.nx, i = row + x, col = i - pl;
+        const float4 c = ld4(gb + i);
+        const float gm = gb[row + nbr(x, -1, f.nx)], gp = gb[row + nbr(x + 3, 1, f.nx)];
+        const float4 ym = ld4(gb + pl + (long)nbr(w.y, -1, f.ny) * f.nx + x);
+        const float4 yp = ld4(gb + pl + (long)nbr(w.y, 1, f.ny) * f.nx + x);
+        const float4 zm = ld4(gb + (long)nbr(w.z, -1, f.nz) * pls + col);
+        const float4 zp = ld4(gb + (long)nbr(w.z, 1, f.nz) * pls + col);
+        float4 g[3];
+        g[0] = make_float4(sg * (gm - c.y), sg * (c.x - c.z), sg * (c.y - c.w), sg * (c.z - gp));
+        g[1] = make_float4(sg * (ym.x - yp.x), sg * (ym.y - yp.y), sg * (ym.z - yp.z), sg * (ym.w - yp.w));
+        g[2] = make_float4(sg * (zm.x - zp.x), sg * (zm.y - zp.y), sg * (zm.z - zp.z), sg * (zm.w - zp.w));
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            const long k = cc * n + i;
+            const float gg[4] = { g[cc].x, g[cc].y, g[cc].z, g[cc].w };
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float ag = fabsf(gg[j]);
+                sabs += ag;
+                gmax = fmaxf(gmax, ag);
+            }
+            if (only_grad) {
+                st4(m + k, g[cc]);
+                continue;
+            }
+            const float4 m4 = ld4(m + k), v4 = ld4(v + k), a4 = ld4(A + k);
+            const float mm[4] = { m4.x, m4.y, m4.z, m4.w }, vv[4] = { v4.x, v4.y, v4.z, v4.w };
+            const float aa[4] = { a4.x, a4.y, a4.z, a4.w };
+            float mo[4], vo[4], ao[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                mo[j] = b1 * mm[j] + (1.0f - b1) * gg[j];
+                vo[j] = b2 * vv[j] + (1.0f - b2) * gg[j] * gg[j];
+                ao[j] = aa[j] - lr * (mo[j] * c1) / (sqrtf(vo[j] * c2) + ae);
+            }
+            st4(m + k, make_float4(mo[0], mo[1], mo[2], mo[3]));
+            st4(v + k, make_float4(vo[0], vo[1], vo[2], vo[3]));
+            st4(A + k, make_float4(ao[0], ao[1], ao[2], ao[3]));
+        }
+    }
+    flow_finish<float>(f, sabs, gmax, [&](double s0, double s1) {
+        f.hs[H_GMAX] = s1;
+        f.hs[H_GABS] = s0 / (3.0 * (double)f.n);
+        if (only_grad) return;
+        f.ints[1] = t;
+        const unsigned rowi = f.ints[2];
+        if (f.trace && (int)rowi < f.trace_cap) {
+            double* r = f.trace + (size_t)rowi * 5;
+            r[0] = f.sweep_scal[S_E];
+            r[1] = s1;
+            r[2] = s0 / (3.0 * (double)f.n);
+            r[3] = f.hs[H_MASS];
+            r[4] = (double)t;
+        }
+        f.ints[2] = rowi + 1;
+    });
+}
+
 long flow_blocks(long n) { return flow_grid(n).x; }
 
 }  // namespace
@@ -440,6 +549,33 @@ static Flow flow_desc(const pfc_hflow* h)
     return f;
 }
 
+static bool al16(const void* p) { return p == nullptr || ((uintptr_t)p & 15) == 0; }
+
+// u = div A + m into `out` (float4 path when the rows allow it)
+template <typename T>
+static void launch_div(const pfc_hflow* h, const T* A, T* out, int want_mass, cudaStream_t s)
+{
+    const Flow f = flow_desc(h);
+    if (sizeof(T) == 4 && h->P.nx % 4 == 0 && al16(A) && al16(out) && al16(f.mf)) {
+        k_div4<<<flow_grid(h->N / 4), kThreads, 0, s>>>((const float*)A, (float*)out, f, want_mass);
+        return;
+    }
+    k_div<T><<<flow_grid(h->N), kThreads, 0, s>>>(A, out, f, want_mass);
+}
+
+// dG/dA and (unless only_grad) the Adam update
+template <typename T>
+static void launch_adam(const pfc_hflow* h, const T* gb, T* A, T* m, T* v, int only_grad, cudaStream_t s)
+{
+    const Flow f = flow_desc(h);
+    if (sizeof(T) == 4 && h->P.nx % 4 == 0 && al16(gb) && al16(A) && al16(m) && al16(v)) {
+        k_adam4<<<flow_grid(h->N / 4), kThreads, 0, s>>>((const float*)gb, (float*)A, (float*)m, (float*)v, f,
+                                                         only_grad);
+        return;
+    }
+    k_adam<T><<<flow_grid(h->N), kThreads, 0, s>>>(gb, A, m, v, f, only_grad);
+}
+
 // in -> k * in through the two temporaries; returns the buffer holding the result
 template <typename T>
 static cudaError_t blur3(const pfc_hflow* h, T* in, T* t1, T* t2, T** result, cudaStream_t s)
@@ -462,13 +598,12 @@ static cudaError_t field(const pfc_hflow* h, const T* A, T** ut, int want_mass, 
     T* b0 = (T*)h->buf[0];
     T* b2 = (T*)h->buf[2];
     T* b3 = (T*)h->buf[3];
-    const dim3 gr = flow_grid(h->N);
     if (h->W.R == 0) {
-        k_div<T><<<gr, kThreads, 0, s>>>(A, b0, flow_desc(h), want_mass);
+        launch_div<T>(h, A, b0, want_mass, s);
         *ut = b0;
         return cudaGetLastError();
     }
-    k_div<T><<<gr, kThreads, 0, s>>>(A, b2, flow_desc(h), want_mass);
+    launch_div<T>(h, A, b2, want_mass, s);
     launch_blur<T, 0>(b2, b3, h->P.nx, h->P.ny, h->P.nz, h->W, s);
     launch_blur<T, 1>(b3, b2, h->P.nx, h->P.ny, h->P.nz, h->W, s);
     launch_blur<T, 2>(b2, b0, h->P.nx, h->P.ny, h->P.nz, h->W, s);
@@ -505,7 +640,7 @@ static cudaError_t step(pfc_hflow* h, T* A, T* m, T* v, cudaStream_t s)
     T* gb = nullptr;
     cudaError_t e = eval<T>(h, A, &gb, s);
     if (e != cudaSuccess) return e;
-    k_adam<T><<<flow_grid(h->N), kThreads, 0, s>>>(gb, A, m, v, flow_desc(h), 0);
+    launch_adam<T>(h, gb, A, m, v, 0, s);
     return cudaGetLastError();
 }
 
@@ -532,15 +667,14 @@ extern "C" pfc_status pfc_hflow_grad(pfc_hflow* h, const void* A, void* gA, doub
     if (!dev_ptr(A) || !dev_ptr(gA)) return hfail(PFC_EINVAL, "hflow: A and gA must be device memory");
     if (A == gA) return hfail(PFC_EINVAL, "hflow: gA must not alias A");
     cudaStream_t s = (cudaStream_t)stream;
-    const Flow f = flow_desc(h);
     if (h->P.prec == PFC_FP64) {
         double* gb = nullptr;
         HCU(eval<double>(h, (const double*)A, &gb, s));
-        k_adam<double><<<flow_grid(h->N), kThreads, 0, s>>>(gb, nullptr, (double*)gA, nullptr, f, 1);
+        launch_adam<double>(h, gb, nullptr, (double*)gA, nullptr, 1, s);
     } else {
         float* gb = nullptr;
         HCU(eval<float>(h, (const float*)A, &gb, s));
-        k_adam<float><<<flow_grid(h->N), kThreads, 0, s>>>(gb, nullptr, (float*)gA, nullptr, f, 1);
+        launch_adam<float>(h, gb, nullptr, (float*)gA, nullptr, 1, s);
     }
     HCU(cudaGetLastError());
     if (G_host) {
