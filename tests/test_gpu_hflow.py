@@ -26,7 +26,8 @@ def setup(shape, prec="fp64", sigma=1.5, xi=1e-6, a=(1.0, 0.4, 0.8, 0.3, -0.2, 0
     return flow, torch.tensor(A, dtype=dt, device="cuda"), A, op, fp
 
 
-@pytest.mark.parametrize("shape,sigma", [((12, 10, 16), 1.5), ((7, 9, 11), 0.0), ((20, 24, 40), 2.0)])
+@pytest.mark.parametrize("shape,sigma", [((12, 10, 16), 1.5), ((7, 9, 11), 0.0), ((20, 24, 40), 2.0),
+                                         ((20, 24, 40), 6.0), ((9, 13, 36), 5.4)])
 def test_field_and_grad_vs_oracle(shape, sigma):
     flow, Ad, A, op, fp = setup(shape, sigma=sigma)
     ut = flow.field(Ad).cpu().numpy()
