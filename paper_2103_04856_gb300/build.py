@@ -5,6 +5,11 @@ linked into one shared library with the CUDA runtime linked statically, so the
 library does not depend on which libcudart the Python process has loaded.
 
     python -m paper_2103_04856_gb300.build [--debug]
+
+--debug builds libpfc_debug.so beside the library instead: its kernels fill
+their shared-memory staging with NaN before use, so that a read of a cell no
+load wrote shows up in the parity tests (run them with
+PFC_LIBRARY=<path of libpfc_debug.so>).
 """
 from __future__ import annotations
 
@@ -19,6 +24,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libpfc.so")
+DEBUG_LIB = os.path.join(HERE, "libpfc_debug.so")
 SOURCES = ["pfc_fused.cu", "pfc_plain.cu", "pfc_api.cu", "pfc_noalloc.cu", "pfc_hflow.cu", "pfc_diag.cu", "pfc_surface.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -40,8 +46,9 @@ def _flags(debug: bool):
     return f
 
 
-def build(debug: bool = False, verbose: bool = False, out: str = LIB) -> str:
-    tmpdir = os.path.join(HERE, "_build")
+def build(debug: bool = False, verbose: bool = False, out: str | None = None) -> str:
+    out = out or (DEBUG_LIB if debug else LIB)
+    tmpdir = os.path.join(HERE, "_build_debug" if debug else "_build")
     os.makedirs(tmpdir, exist_ok=True)
     cc = nvcc()
     srcs = [os.path.join(CSRC, s) for s in SOURCES]

@@ -10,12 +10,20 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pfc.h"
 #include "pfc_internal.h"
 
 using namespace pfc;
 
 static thread_local char g_err[512] = "";
+
+// NVTX range around an entry point (visible in profilers; no cost otherwise)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 static pfc_status fail(pfc_status s, const char* fmt, ...)
 {
@@ -294,6 +302,7 @@ extern "C" pfc_status pfc_energy(pfc_ctx* c, const void* u, double* E_host, pfc_
 
 extern "C" pfc_status pfc_energy_and_grad(pfc_ctx* c, const void* u, void* g, double* E_host, pfc_stream stream)
 {
+    NvtxRange nvtx_("pfc_energy_and_grad");
     if (!c) return fail(PFC_EINVAL, "context is NULL");
     pfc_status st = check_dev_ptr(c, u, "u");
     if (st) return st;
@@ -371,6 +380,7 @@ static cudaError_t enqueue_steps(pfc_ctx* c, void* a, void* b, int i0, int n, do
 
 extern "C" pfc_status pfc_run(pfc_ctx* c, void* u, int32_t nsteps, double tau, double* trace_host, pfc_stream stream)
 {
+    NvtxRange nvtx_("pfc_run");
     if (!c) return fail(PFC_EINVAL, "context is NULL");
     pfc_status st = check_dev_ptr(c, u, "u");
     if (st) return st;
@@ -477,6 +487,7 @@ extern "C" pfc_status pfc_set_coefficient_field(pfc_ctx* c, const void* a_field,
 
 extern "C" pfc_status pfc_diagnostics(pfc_ctx* c, const void* u, double out_host[5], pfc_stream stream)
 {
+    NvtxRange nvtx_("pfc_diagnostics");
     if (!c) return fail(PFC_EINVAL, "context is NULL");
     if (!out_host) return fail(PFC_EINVAL, "out_host is NULL");
     pfc_status st = check_dev_ptr(c, u, "u");
@@ -503,6 +514,7 @@ extern "C" pfc_status pfc_diagnostics(pfc_ctx* c, const void* u, double out_host
 extern "C" pfc_status pfc_surface_cells(pfc_ctx* c, const void* u, double level, void* cells, int64_t cap,
                                         int64_t* count_host, pfc_stream stream)
 {
+    NvtxRange nvtx_("pfc_surface_cells");
     if (!c) return fail(PFC_EINVAL, "context is NULL");
     if (!count_host) return fail(PFC_EINVAL, "count_host is NULL");
     if (!isfinite(level)) return fail(PFC_EINVAL, "level is not finite");
@@ -690,6 +702,7 @@ extern "C" void pfc_batch_destroy(pfc_batch* b)
 extern "C" pfc_status pfc_batch_run(pfc_batch* b, void* const* u, int32_t nsteps, const double* tau,
                                     double* trace_host, pfc_stream stream)
 {
+    NvtxRange nvtx_("pfc_batch_run");
     if (!b) return fail(PFC_EINVAL, "batch is NULL");
     if (!u || !tau) return fail(PFC_EINVAL, "u and tau arrays are required");
     if (nsteps < 0) return fail(PFC_EINVAL, "nsteps must be >= 0");
@@ -801,6 +814,7 @@ extern "C" pfc_status pfc_batch_run(pfc_batch* b, void* const* u, int32_t nsteps
 extern "C" pfc_status pfc_batch_step(pfc_batch* b, const void* const* u_in, void* const* u_out, const double* tau,
                                      double* scalars_dev, pfc_stream stream)
 {
+    NvtxRange nvtx_("pfc_batch_step");
     if (!b) return fail(PFC_EINVAL, "batch is NULL");
     if (!u_in || !u_out || !tau) return fail(PFC_EINVAL, "u_in, u_out and tau arrays are required");
     cudaStream_t s = (cudaStream_t)stream;
@@ -848,6 +862,7 @@ extern "C" pfc_status pfc_batch_step(pfc_batch* b, const void* const* u_in, void
 extern "C" pfc_status pfc_batch_step_host(pfc_batch* b, const void* const* u_in_host, void* const* u_out_host,
                                           const double* tau, pfc_stream stream)
 {
+    NvtxRange nvtx_("pfc_batch_step_host");
     if (!b) return fail(PFC_EINVAL, "batch is NULL");
     if (!u_in_host || !u_out_host || !tau) return fail(PFC_EINVAL, "u_in_host, u_out_host and tau arrays are required");
     for (int k = 0; k < b->n; ++k) {

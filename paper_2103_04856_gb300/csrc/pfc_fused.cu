@@ -177,6 +177,12 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
             pz = pz + 1 == nz ? 0 : pz + 1;
         };
 
+#if PFC_DEBUG
+        // debug builds: every shared value starts as NaN, so a read of a cell
+        // that no load or publish of this run wrote shows up in the results
+        for (int i = tid; i < NBUF * PLANE + 2 * 5 * NEXT; i += NT) us[i] = T(NAN);
+        __syncthreads();
+#endif
         const double cind = (MODE == MODE_STEP) ? in.scal[S_C] : 0.0;
         const T cin = (T)cind;
 

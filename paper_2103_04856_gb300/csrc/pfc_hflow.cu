@@ -18,6 +18,8 @@
 #include <stdio.h>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pfc.h"
 #include "pfc_device.cuh"
 
@@ -688,6 +690,8 @@ extern "C" pfc_status pfc_hflow_grad(pfc_hflow* h, const void* A, void* gA, doub
 extern "C" pfc_status pfc_hflow_run(pfc_hflow* h, void* A, void* m, void* v, int32_t nsteps, int32_t* t,
                                     double* trace_host, pfc_stream stream)
 {
+    nvtxRangePushA("pfc_hflow_run");
+    struct Pop { ~Pop() { nvtxRangePop(); } } pop_;
     if (!h) return hfail(PFC_EINVAL, "hflow: handle is NULL");
     if (!dev_ptr(A) || !dev_ptr(m) || !dev_ptr(v)) return hfail(PFC_EINVAL, "hflow: A, m, v must be device memory");
     if (A == m || A == v || m == v) return hfail(PFC_EINVAL, "hflow: A, m and v must be distinct");

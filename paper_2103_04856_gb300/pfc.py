@@ -21,7 +21,9 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpfc.so")
+# PFC_LIBRARY selects another build of the library (the debug build of
+# paper_2103_04856_gb300.build --debug); the default is the in-tree libpfc.so
+LIB_PATH = os.environ.get("PFC_LIBRARY") or os.path.join(_HERE, "libpfc.so")
 
 PFC_OK, PFC_EINVAL, PFC_ENOMEM, PFC_ECUDA, PFC_ENONFINITE, PFC_ETIMEOUT, PFC_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 PFC_WELL_01, PFC_WELL_PM1 = 0, 1
