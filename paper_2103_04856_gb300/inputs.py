@@ -72,7 +72,7 @@ def tanh_slab(shape, width: float, eps: float, h: float = 1.0, well: int = 0) ->
 
 # ---------------------------------------------------------------- workloads
 
-def baseline_poly_to_a(a_, b_, c_, d_=0.0, e_=0.0):
+def smaller_first_poly_to_a(a_, b_, c_, d_=0.0, e_=0.0):
     """Coefficients written with kappa1 the SMALLER curvature,
     a k1^2 + b k2^2 + c k1 k2 + d k1 + e k2, in the paper's order
     (a20, a11, a02, a10, a01, a00) with kappa1 the LARGER curvature."""
@@ -134,14 +134,14 @@ def validation_set_128():
 def tube_descent_256(n: int = 256) -> Instance:
     """256^3 FP32, p = k1^2 + 0.2 k2^2 - 0.5 k1 (k1 the smaller curvature),
     u0 = 0.25 + 0.1 N(0,1) (seed 1), eps = 1.5."""
-    return Instance(f"tube_descent_{n}", (n, n, n), 1.5, baseline_poly_to_a(1.0, 0.2, 0.0, -0.5, 0.0),
+    return Instance(f"tube_descent_{n}", (n, n, n), 1.5, smaller_first_poly_to_a(1.0, 0.2, 0.0, -0.5, 0.0),
                     init={"kind": "noise", "mean": 0.25, "std": 0.1, "seed": 1})
 
 
 def membrane_descent_512(n: int = 512) -> Instance:
     """512^3 FP32, eps = 2, p = 0.2 k1^2 + k2^2 + 0.3 k1 k2 (k1 the smaller),
     u0 = 0.3 + 0.1 N(0,1) (seed 2)."""
-    return Instance(f"membrane_descent_{n}", (n, n, n), 2.0, baseline_poly_to_a(0.2, 1.0, 0.3),
+    return Instance(f"membrane_descent_{n}", (n, n, n), 2.0, smaller_first_poly_to_a(0.2, 1.0, 0.3),
                     init={"kind": "noise", "mean": 0.3, "std": 0.1, "seed": 2})
 
 
@@ -158,7 +158,7 @@ def batch_instances(n_inst: int = 64, sizes=(64, 96, 128), seed: int = 12345):
         c_ = rng.uniform(-0.5, 0.5)
         d_, e_ = rng.uniform(-1.0, 1.0, 2)
         vf = rng.uniform(0.15, 0.45)
-        out.append(Instance(f"batch_{k}", (n, n, n), 1.5, baseline_poly_to_a(a_, b_, c_, d_, e_),
+        out.append(Instance(f"batch_{k}", (n, n, n), 1.5, smaller_first_poly_to_a(a_, b_, c_, d_, e_),
                             init={"kind": "noise", "mean": float(vf), "std": 0.1, "seed": 100 + k}))
     return out
 

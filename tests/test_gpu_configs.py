@@ -1,5 +1,5 @@
 """The full-size workloads: 256^3 adjoint checks, the 64-instance mixed batch,
-the 512^3 long run.  Judged by per-evaluation parity against the oracle (one
+the 512^3 long run.  Checked by per-evaluation parity against the oracle (one
 voxel at a time where the grid is too large for it), by central differences
 and an independent FP64 autograd reference, and by invariants that hold at
 any size (mass, finiteness, descent)."""

@@ -132,7 +132,7 @@ def test_fp64_run_32_vs_oracle(impl):
     np.testing.assert_allclose(tr[:, 2], tro[:, 2], rtol=0, atol=1e-10 * np.max(np.abs(tro[:, 3])))
     np.testing.assert_allclose(tr[:, 3:], tro[:, 3:], rtol=1e-10)
     assert abs(u.mean() - u0.mean()) < 1e-14
-    # (2) the workload's xi = 1e-6: 10-step trajectory, then 100 steps judged on
+    # (2) the workload's xi = 1e-6: 10-step trajectory, then 100 steps compared on
     # the GPU's own state (one oracle step from it), mass and descent
     p = P(inst.shape, inst.a, eps=inst.eps, impl=impl)
     uo10, tro10 = oracle.run(u0, oprob(p), 10, inst.tau)
