@@ -27,6 +27,7 @@ from . import pfc
 
 CANDIDATES = [
     {"tile_y": 16, "max_run": 0},
+    {"tile_y": 13, "max_run": 0},
     {"tile_y": 8, "max_run": 0},
     {"tile_y": 16, "max_run": 64},
     {"tile_y": 16, "max_run": 32},

@@ -103,7 +103,7 @@ static pfc_status check_problem(const pfc_problem* p)
     if (p->well != PFC_WELL_01 && p->well != PFC_WELL_PM1) return fail(PFC_EINVAL, "unknown double well %d", p->well);
     if (p->prec != PFC_FP32 && p->prec != PFC_FP64) return fail(PFC_EINVAL, "unknown precision %d", p->prec);
     if (p->impl != PFC_IMPL_FUSED && p->impl != PFC_IMPL_PLAIN) return fail(PFC_EINVAL, "unknown implementation %d", p->impl);
-    if (p->tile_y != 0 && p->tile_y != 8 && p->tile_y != 16) return fail(PFC_EINVAL, "tile_y must be 0, 8 or 16");
+    if (p->tile_y != 0 && p->tile_y != 8 && p->tile_y != 13 && p->tile_y != 16) return fail(PFC_EINVAL, "tile_y must be 0, 8, 13 or 16");
     if (p->tile_z < 0) return fail(PFC_EINVAL, "tile_z must be >= 0");
     if (!isfinite(p->mu) || !isfinite(p->theta[0]) || !isfinite(p->theta[1]) || !isfinite(p->theta[2]))
         return fail(PFC_EINVAL, "mu and theta must be finite");
@@ -120,7 +120,7 @@ static pfc_status check_problem(const pfc_problem* p)
 // so that the grid fills the GPU about twice unless the user fixed tile_z.
 static void geometry(const pfc_problem* p, int sms, int* tile_y, int* zc, int* tx, int* ty, int* cz)
 {
-    int tyv = p->tile_y ? p->tile_y : (p->prec == PFC_FP64 ? 8 : 16);
+    int tyv = p->tile_y ? p->tile_y : default_tile_y(p->ny, p->prec == PFC_FP64);
     *tile_y = tyv;
     *tx = (p->nx + 31) / 32;
     *ty = (p->ny + tyv - 1) / tyv;
@@ -646,7 +646,7 @@ extern "C" pfc_status pfc_batch_create(const pfc_problem* probs, int32_t n, pfc_
     b->host.resize(n);
     b->ping.assign(n, nullptr);
     bool ok = true;
-    b->tile_y = probs[0].tile_y ? probs[0].tile_y : 16;
+    b->tile_y = probs[0].tile_y ? probs[0].tile_y : 16;   // one height for all instances
     b->max_run = probs[0].tile_z;
     long long units = 0;
     for (int k = 0; k < n && ok; ++k) {

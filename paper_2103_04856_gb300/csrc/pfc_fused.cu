@@ -36,14 +36,20 @@ constexpr int PD = 3;       // planes in flight ahead of the plane being consume
 // halo ring whose cotangents the gather needs):
 //   warps 0 .. TY-1 : interior rows, lane = x          (these also gather)
 //   warps TY, TY+1  : the halo rows above and below the tile
-//   warps TY+2, TY+3: the left and right halo columns (TY+2 lanes each)
-// so every warp but the last two reads contiguous shared memory.
+//   then the left and right halo columns (TY+2 lanes each): one warp for
+//   both when 2 (TY+2) <= 32 (lanes 0..TY+1 left, the next TY+2 right),
+//   else one warp each
+// so every warp but the halo-column ones reads contiguous shared memory.
+// The SM's four schedulers hold the warps round-robin, and each has a
+// quarter of the register file: TY = 13 (16 warps, 4 per scheduler) may use
+// 128 registers per thread, TY = 16 (20 warps, 5 per scheduler) only 96.
 template <int TY>
 struct Tile {
     static constexpr int EX = TX + 2;             // extended (halo) columns in x
     static constexpr int EY = TY + 2;
     static constexpr int NEXT = EX * EY;
-    static constexpr int NT = (TY + 4) * 32;
+    static constexpr bool MERGED = 2 * (TY + 2) <= 32;
+    static constexpr int NT = (TY + (MERGED ? 3 : 4)) * 32;
     static constexpr int UY = TY + 4;             // u rows: y0-2 .. y0+TY+1
     static constexpr int PLANE = UY * UXP;
 };
@@ -94,7 +100,12 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
     if (warp < TY) { ey = warp + 1; ex = lane + 1; }
     else if (warp == TY) { ey = 0; ex = lane + 1; }
     else if (warp == TY + 1) { ey = TY + 1; ex = lane + 1; }
-    else {   // halo columns: lanes past the last row duplicate it and never publish
+    else if (TL::MERGED) {   // both halo columns; lanes past them duplicate the last row, never publish
+        const bool left = lane < TY + 2;
+        ex = left ? 0 : EX - 1;
+        ey = left ? lane : (lane - (TY + 2) < TY + 2 ? lane - (TY + 2) : TY + 1);
+        active = lane < 2 * (TY + 2);
+    } else {   // one halo column per warp; lanes past the last row duplicate it and never publish
         ex = warp == TY + 2 ? 0 : EX - 1;
         ey = lane < TY + 2 ? lane : TY + 1;
         active = lane < TY + 2;
@@ -482,13 +493,13 @@ cudaError_t launch_coef_field(const T* a_field, T* c_field, long n, double h, do
 template cudaError_t launch_coef_field<float>(const float*, float*, long, double, double, cudaStream_t);
 template cudaError_t launch_coef_field<double>(const double*, double*, long, double, double, cudaStream_t);
 
-int fused_threads(int tile_y) { return tile_y == 8 ? Tile<8>::NT : Tile<16>::NT; }
+int fused_threads(int tile_y) { return tile_y == 8 ? Tile<8>::NT : tile_y == 13 ? Tile<13>::NT : Tile<16>::NT; }
 
 size_t fused_smem_bytes(int elem_size, int tile_y)
 {
-    const int plane = tile_y == 8 ? Tile<8>::PLANE : Tile<16>::PLANE;
-    const int next = tile_y == 8 ? Tile<8>::NEXT : Tile<16>::NEXT;
-    const int nt = tile_y == 8 ? Tile<8>::NT : Tile<16>::NT;
+    const int plane = tile_y == 8 ? Tile<8>::PLANE : tile_y == 13 ? Tile<13>::PLANE : Tile<16>::PLANE;
+    const int next = tile_y == 8 ? Tile<8>::NEXT : tile_y == 13 ? Tile<13>::NEXT : Tile<16>::NEXT;
+    const int nt = tile_y == 8 ? Tile<8>::NT : tile_y == 13 ? Tile<13>::NT : Tile<16>::NT;
     return (size_t)elem_size * ((size_t)NBUF * plane + 2 * 5 * (size_t)next) + sizeof(float) * NPART * (size_t)nt;
 }
 
@@ -578,7 +589,9 @@ cudaError_t launch_fused(const Inst<T>& in, int mode, int tile_y, int max_run, c
 {
     if (in.C.proj) return launch_mode<T, EXT_TILE_Y, 2>(in, mode, max_run, s);
     if (needs_ext(in)) return launch_mode<T, EXT_TILE_Y, 1>(in, mode, max_run, s);
-    return tile_y == 8 ? launch_mode<T, 8>(in, mode, max_run, s) : launch_mode<T, 16>(in, mode, max_run, s);
+    if (tile_y == 8) return launch_mode<T, 8>(in, mode, max_run, s);
+    if (tile_y == 13) return launch_mode<T, 13>(in, mode, max_run, s);
+    return launch_mode<T, 16>(in, mode, max_run, s);
 }
 template cudaError_t launch_fused<float>(const Inst<float>&, int, int, int, cudaStream_t);
 template cudaError_t launch_fused<double>(const Inst<double>&, int, int, int, cudaStream_t);
@@ -587,14 +600,15 @@ template cudaError_t launch_fused<double>(const Inst<double>&, int, int, int, cu
 // travel as kernel parameters); larger batches take one launch per group.
 cudaError_t launch_fused_batch(const Inst<float>* insts, int n_inst, int tile_y, int max_run, cudaStream_t s)
 {
-    static Launch<float, BATCH_MAX> L;   // host staging; the launch copies it
+    thread_local Launch<float, BATCH_MAX> L;   // host staging (per thread); the launch copies it
     for (int g0 = 0; g0 < n_inst; g0 += BATCH_MAX) {
         const int cnt = n_inst - g0 < BATCH_MAX ? n_inst - g0 : BATCH_MAX;
         L.n = cnt;
         for (int k = 0; k < cnt; ++k) L.inst[k] = insts[g0 + k];
         plan(L, tile_y, max_run);
-        cudaError_t e = tile_y == 8 ? launch_one<float, 8, MODE_STEP, BATCH_MAX>(L, L.grid, s)
-                                    : launch_one<float, 16, MODE_STEP, BATCH_MAX>(L, L.grid, s);
+        cudaError_t e = tile_y == 8    ? launch_one<float, 8, MODE_STEP, BATCH_MAX>(L, L.grid, s)
+                        : tile_y == 13 ? launch_one<float, 13, MODE_STEP, BATCH_MAX>(L, L.grid, s)
+                                       : launch_one<float, 16, MODE_STEP, BATCH_MAX>(L, L.grid, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -614,7 +628,7 @@ template cudaError_t launch_add_offset<double>(double*, const double*, long, con
 
 cudaError_t launch_add_offset_batch(const Inst<float>* insts, int n_inst, cudaStream_t s)
 {
-    static OffsetLaunch L;
+    thread_local OffsetLaunch L;   // host staging (per thread)
     for (int g0 = 0; g0 < n_inst; g0 += BATCH_MAX) {
         const int cnt = n_inst - g0 < BATCH_MAX ? n_inst - g0 : BATCH_MAX;
         L.n = cnt;

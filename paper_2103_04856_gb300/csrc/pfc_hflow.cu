@@ -466,7 +466,7 @@ extern "C" pfc_status pfc_hflow_create(const pfc_problem* prob, const pfc_hflow_
     if (p.prec != PFC_FP32 && p.prec != PFC_FP64) return hfail(PFC_EINVAL, "hflow: unknown precision");
     if (p.well != PFC_WELL_01 && p.well != PFC_WELL_PM1) return hfail(PFC_EINVAL, "hflow: unknown double well");
     if (p.impl != PFC_IMPL_FUSED) return hfail(PFC_EUNSUPPORTED, "hflow: runs on the fused path");
-    if (p.tile_y != 0 && p.tile_y != 8 && p.tile_y != 16) return hfail(PFC_EINVAL, "hflow: tile_y must be 0, 8 or 16");
+    if (p.tile_y != 0 && p.tile_y != 8 && p.tile_y != 13 && p.tile_y != 16) return hfail(PFC_EINVAL, "hflow: tile_y must be 0, 8, 13 or 16");
     for (int i = 0; i < 6; ++i)
         if (!isfinite(p.a[i])) return hfail(PFC_EINVAL, "hflow: a coefficient is not finite");
     if (!isfinite(p.mu) || !isfinite(p.theta[0]) || !isfinite(p.theta[1]) || !isfinite(p.theta[2]))
@@ -487,7 +487,7 @@ extern "C" pfc_status pfc_hflow_create(const pfc_problem* prob, const pfc_hflow_
     h->H.blur_radius = R;
     h->N = (long)p.nx * p.ny * p.nz;
     h->esz = p.prec == PFC_FP64 ? 8 : 4;
-    h->tile_y = p.tile_y ? p.tile_y : (p.prec == PFC_FP64 ? 8 : 16);
+    h->tile_y = p.tile_y ? p.tile_y : default_tile_y(p.ny, p.prec == PFC_FP64);
     h->W.R = R;
     if (R > 0) {   // discrete Gaussian, normalised to sum 1
         double s = 0;

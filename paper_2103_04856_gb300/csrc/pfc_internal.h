@@ -91,6 +91,15 @@ template <typename T>
 Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well, double mu = 0.0,
                   const double* theta = nullptr, int proj = 0);
 
+// Automatic tile height: FP64 8 rows; FP32 the one of 16 and 13 rows that
+// pads the grid's rows least (16 on a tie: its tiles hold more rows).
+inline int default_tile_y(int ny, bool fp64)
+{
+    if (fp64) return 8;
+    const int pad16 = (ny + 15) / 16 * 16, pad13 = (ny + 12) / 13 * 13;
+    return pad13 < pad16 ? 13 : 16;
+}
+
 // The extended sweep (orientation term, c(x), projected M) runs with 8-row tiles.
 template <typename T>
 inline bool needs_ext(const Inst<T>& in) { return in.cf != nullptr || in.C.c7 != T(0) || in.C.proj != 0; }

@@ -98,7 +98,7 @@ static pfc_status run_noalloc(const pfc_problem* p, const void* u, void* g, doub
     in.u = (const T*)u;
     in.out = (T*)g;
     in.nx = p->nx; in.ny = p->ny; in.nz = p->nz;
-    const int tile_y = p->tile_y ? p->tile_y : (sizeof(T) == 8 ? 8 : 16);
+    const int tile_y = p->tile_y ? p->tile_y : default_tile_y(p->ny, sizeof(T) == 8);
     in.tiles_x = (p->nx + 31) / 32;
     in.tiles_y = (p->ny + tile_y - 1) / tile_y;
     in.zc = p->nz;
@@ -148,7 +148,7 @@ extern "C" pfc_status pfc_energy_and_grad_noalloc(const pfc_problem* prob, const
     if (p.well != PFC_WELL_01 && p.well != PFC_WELL_PM1) return na_fail(PFC_EINVAL, "noalloc: unknown double well");
     if (p.prec != PFC_FP32 && p.prec != PFC_FP64) return na_fail(PFC_EINVAL, "noalloc: unknown precision");
     if (p.impl != PFC_IMPL_FUSED) return na_fail(PFC_EUNSUPPORTED, "noalloc: only the fused path needs no allocation");
-    if (p.tile_y != 0 && p.tile_y != 8 && p.tile_y != 16) return na_fail(PFC_EINVAL, "noalloc: tile_y must be 0, 8 or 16");
+    if (p.tile_y != 0 && p.tile_y != 8 && p.tile_y != 13 && p.tile_y != 16) return na_fail(PFC_EINVAL, "noalloc: tile_y must be 0, 8, 13 or 16");
     if (p.tile_z < 0) return na_fail(PFC_EINVAL, "noalloc: tile_z must be >= 0");
     if (!is_device_ptr(u) || !is_device_ptr(g)) return na_fail(PFC_EINVAL, "noalloc: u and g must be device memory");
     if (u == g) return na_fail(PFC_EINVAL, "noalloc: g must not alias u");

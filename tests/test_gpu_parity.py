@@ -67,7 +67,7 @@ def test_fp64_energy_grad_vs_oracle(shape, impl):
         assert ctx.energy(dev(u, "fp64")) == pytest.approx(Eo, rel=1e-10, abs=1e-12)
 
 
-@pytest.mark.parametrize("tile", [(8, 3), (16, 5), (8, 64), (16, 1)])
+@pytest.mark.parametrize("tile", [(8, 3), (16, 5), (8, 64), (16, 1), (13, 0), (13, 7)])
 def test_fp64_tile_shapes(tile):
     shape = (13, 20, 44)
     a = (0.7, -0.3, 0.2, 0.5, -0.4, 0.3)
