@@ -204,15 +204,18 @@ def kernel_sources_sha():
     return h.hexdigest()[:16]
 
 
-def committed_traffic():
+def committed_traffic(tile_y, max_run):
     """DRAM bytes per launch of the fused sweep from the committed ncu summary,
-    or None if it was taken on another version of the kernel sources."""
+    or None if it was taken on another version of the kernel sources or in
+    another launch shape."""
     path = os.path.join(ROOT, "profiles", "fused_sweep_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         if d.get("kernel_sources_sha") != kernel_sources_sha():
             return None, "stale"
+        if d.get("tile_y") != tile_y or d.get("max_run") != max_run:
+            return None, f"captured with tile_y {d.get('tile_y')}, max_run {d.get('max_run')}"
         return float(d["traffic_bytes_per_launch"]), d.get("note", "")
     except Exception:
         return None, "absent"
@@ -547,14 +550,15 @@ def main():
     peaks, peak_kind = load_peaks()
     bytes_launch = 8.0 * vox                      # read u, write u' (FP32)
     hbm_achieved = bytes_launch / (ms_sweep * 1e-3) / 1e9
-    traffic, traffic_note = committed_traffic()
+    ty_used = launch["tile_y"] or 16                 # the batch's automatic height
+    traffic, traffic_note = committed_traffic(ty_used, launch["max_run"])
     alu_achieved = FLOPS_PER_VOXEL_STEP * vox / (ms_sweep * 1e-3) / 1e12
     # 211 flop per 8 B is ~2x GB300's FP32/HBM balance: the sweep is bound by
     # arithmetic issue, not by HBM; the HBM fraction is reported beside it
     roofline = {"bound": "alu", "achieved": alu_achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": alu_achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2070 MHz",
-                "kernel": "k_fused<float,16,STEP,64> (batched fused sweep)", "kernel_ms": ms_sweep,
+                "kernel": f"k_fused<float,{ty_used},STEP,64> (batched fused sweep)", "kernel_ms": ms_sweep,
                 "flops_per_voxel_step": FLOPS_PER_VOXEL_STEP, "voxels_per_launch": vox,
                 "hbm": {"achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": hbm_achieved / peaks["hbm_gbs"], "peak_kind": peak_kind,
