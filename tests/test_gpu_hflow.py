@@ -142,3 +142,31 @@ def test_paper_setting_generates_a_viable_shape():
     assert d["ratio"] < 0.75 and d["max"] > 0.1 and d["min"] < -0.1
     cells = ctx.surface_cells(ut)
     assert cells.shape[0] > 1000 and float(cells[:, 0].double().sum()) > 1.0
+
+
+@pytest.mark.parametrize("shape", [(9, 10, 11), (8, 12, 20)])
+def test_fp32_row_paths_and_misaligned_buffers(shape):
+    """FP32 flow kernels take a float4 path when rows hold a multiple of 4
+    voxels and the buffers are 16-byte aligned, else a scalar path: both
+    against FP64, and a misaligned A (offset by one element) against an
+    aligned copy of the same values."""
+    f64, _, A, op, fp = setup(shape, seed=5)
+    f32, A32, _, _, _ = setup(shape, prec="fp32", seed=5)
+    G64, g64 = f64.grad(A32.double())
+    G32, g32 = f32.grad(A32)
+    assert abs(G32 - G64) / abs(G64) < 1e-4
+    assert (torch.linalg.norm(g32.double() - g64) / torch.linalg.norm(g64)).item() < 1e-3
+    store = torch.empty(A32.numel() + 1, dtype=torch.float32, device="cuda")
+    Am = store[1:].view(A32.shape)
+    Am.copy_(A32)
+    assert Am.data_ptr() % 16 != 0
+    Gm, gm = f32.grad(Am)
+    assert Gm == pytest.approx(G32, rel=1e-5)
+    assert (torch.linalg.norm(gm - g32) / torch.linalg.norm(g32)).item() < 1e-5
+    md, vd = torch.zeros_like(Am), torch.zeros_like(Am)
+    ma, va = torch.zeros_like(A32), torch.zeros_like(A32)
+    Aa = A32.clone()
+    f32.run(Am, md, vd, 3)
+    f32.t = 0
+    f32.run(Aa, ma, va, 3)
+    assert (torch.linalg.norm(Am - Aa) / torch.linalg.norm(Aa)).item() < 1e-5
