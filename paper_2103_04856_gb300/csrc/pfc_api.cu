@@ -604,8 +604,7 @@ static void free_batch_mem(pfc_batch* b)
 {
     for (void* p : b->ping) cudaFree(p);
     cudaFree(b->partials);
-    cudaFree(b->ints);
-    cudaFree(b->scal);
+    cudaFree(b->scal);       // also holds the counters (b->ints)
     cudaFree(b->trace);
     for (cudaEvent_t e : b->ev)
         if (e) cudaEventDestroy(e);
@@ -667,10 +666,12 @@ extern "C" pfc_status pfc_batch_create(const pfc_problem* probs, int32_t n, pfc_
     // every problem may get a partial from every CTA of its launch
     const long long slots = fused_grid(units, b->max_run);
     b->total_blocks = (int)slots;
+    // the problems' scalars and counters in one block, cleared by one memset per step
     ok = ok && cudaMalloc((void**)&b->partials, sizeof(double) * NPART * (size_t)slots * n) == cudaSuccess &&
-         cudaMalloc((void**)&b->ints, sizeof(unsigned) * NINTS * (size_t)n) == cudaSuccess &&
-         cudaMalloc((void**)&b->scal, sizeof(double) * NSCAL * (size_t)n) == cudaSuccess &&
+         cudaMalloc((void**)&b->scal, sizeof(double) * NSCAL * (size_t)n + sizeof(unsigned) * NINTS * (size_t)n) ==
+             cudaSuccess &&
          cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) b->ints = reinterpret_cast<unsigned*>(b->scal + (size_t)NSCAL * n);
     if (!ok) {
         cudaError_t le = cudaGetLastError();
         free_batch_mem(b);
@@ -744,8 +745,7 @@ extern "C" pfc_status pfc_batch_run(pfc_batch* b, void* const* u, int32_t nsteps
         ev[k].trace = od[k].trace = b->trace + (size_t)k * 5 * b->trace_cap;
         ev[k].trace_cap = od[k].trace_cap = b->trace_cap;
     }
-    PFC_CU(cudaMemsetAsync(b->ints, 0, sizeof(unsigned) * NINTS * b->n, s));
-    PFC_CU(cudaMemsetAsync(b->scal, 0, sizeof(double) * NSCAL * b->n, s));
+    PFC_CU(cudaMemsetAsync(b->scal, 0, (sizeof(double) * NSCAL + sizeof(unsigned) * NINTS) * b->n, s));
     auto steps = [&](int i0, int cnt, cudaStream_t st) -> cudaError_t {
         for (int i = i0; i < i0 + cnt; ++i) {
             cudaError_t e = launch_fused_batch((i % 2) == 0 ? ev.data() : od.data(), b->n, b->tile_y, b->max_run, st);
@@ -839,8 +839,7 @@ extern "C" pfc_status pfc_batch_step(pfc_batch* b, const void* const* u_in, void
         d[k].trace_cap = 0;
     }
     if (b->timing) PFC_CU(cudaEventRecord(b->ev[0], s));
-    PFC_CU(cudaMemsetAsync(b->ints, 0, sizeof(unsigned) * NINTS * b->n, s));
-    PFC_CU(cudaMemsetAsync(b->scal, 0, sizeof(double) * NSCAL * b->n, s));
+    PFC_CU(cudaMemsetAsync(b->scal, 0, (sizeof(double) * NSCAL + sizeof(unsigned) * NINTS) * b->n, s));
     if (b->timing) PFC_CU(cudaEventRecord(b->ev[1], s));
     PFC_CU(launch_fused_batch(d.data(), b->n, b->tile_y, b->max_run, s));
     if (b->timing) PFC_CU(cudaEventRecord(b->ev[2], s));
@@ -896,8 +895,7 @@ extern "C" pfc_status pfc_batch_step_host(pfc_batch* b, const void* const* u_in_
             PFC_CU(cudaEventRecord(b->evdone[k], s));
         }
     }
-    PFC_CU(cudaMemsetAsync(b->ints, 0, sizeof(unsigned) * NINTS * b->n, s));
-    PFC_CU(cudaMemsetAsync(b->scal, 0, sizeof(double) * NSCAL * b->n, s));
+    PFC_CU(cudaMemsetAsync(b->scal, 0, (sizeof(double) * NSCAL + sizeof(unsigned) * NINTS) * b->n, s));
     for (int k = 0; k < b->n; ++k) {
         const long N = (long)b->P[k].nx * b->P[k].ny * b->P[k].nz;
         PFC_CU(cudaStreamWaitEvent(b->hs[0], b->evstep[k], 0));

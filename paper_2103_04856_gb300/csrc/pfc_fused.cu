@@ -367,6 +367,7 @@ struct OffsetLaunch {
     float* out[BATCH_MAX];
     const double* c[BATCH_MAX];
     long len[BATCH_MAX];
+    int vec[BATCH_MAX];      // 1: out is 16-byte aligned (float4 accesses, scalar tail)
 };
 __global__ void k_add_offset_batch(const __grid_constant__ OffsetLaunch L)
 {
@@ -374,8 +375,19 @@ __global__ void k_add_offset_batch(const __grid_constant__ OffsetLaunch L)
     const float off = (float)(*L.c[k]);
     float* out = L.out[k];
     const long n = L.len[k];
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        out[i] += off;
+    const long t0 = blockIdx.x * (long)blockDim.x + threadIdx.x, stride = (long)gridDim.x * blockDim.x;
+    long done = 0;
+    if (L.vec[k]) {
+        float4* o4 = reinterpret_cast<float4*>(out);
+        const long n4 = n >> 2;
+        for (long i = t0; i < n4; i += stride) {
+            float4 v = o4[i];
+            v.x += off; v.y += off; v.z += off; v.w += off;
+            o4[i] = v;
+        }
+        done = n4 << 2;
+    }
+    for (long i = done + t0; i < n; i += stride) out[i] += off;
 }
 
 // Diffuse principal curvatures (Sec. 3.1, eqs. kepsa/kepsb) per voxel.
@@ -637,6 +649,7 @@ cudaError_t launch_add_offset_batch(const Inst<float>* insts, int n_inst, cudaSt
             L.out[k] = in.out;
             L.c[k] = in.scal + S_C;
             L.len[k] = (long)in.nx * in.ny * in.nz;
+            L.vec[k] = ((uintptr_t)in.out & 15) == 0;
         }
         int bx = (152 * 8 + cnt - 1) / cnt;
         if (bx < 8) bx = 8;
