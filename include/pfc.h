@@ -29,6 +29,9 @@
  *  - Errors are returned as pfc_status; pfc_last_error() gives a message for
  *    the calling thread.  On PFC_ECUDA the CUDA error has been consumed.
  *  - A context is not thread-safe: one thread (or external locking) per context.
+ *    Different contexts may be driven from different threads on different
+ *    streams at the same time (their graph captures are thread-local, and no
+ *    call but the create and destroy functions waits for the whole device).
  */
 #ifndef PFC_H
 #define PFC_H

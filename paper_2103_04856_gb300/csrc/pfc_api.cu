@@ -196,9 +196,10 @@ extern "C" pfc_status pfc_create(const pfc_problem* prob, pfc_ctx** out)
               cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess;
     if (ok && prob->impl == PFC_IMPL_PLAIN)
         ok = cudaMalloc(&c->plain_mem, (size_t)c->esz * c->N * 21) == cudaSuccess;
-    if (ok) ok = cudaMemset(c->ints, 0, sizeof(unsigned) * NINTS) == cudaSuccess &&
-                 cudaMemset(c->scal, 0, sizeof(double) * NSCAL) == cudaSuccess &&
-                 cudaDeviceSynchronize() == cudaSuccess;
+    // cleared on the context's own stream (no device-wide wait, see ensure_trace)
+    if (ok) ok = cudaMemsetAsync(c->ints, 0, sizeof(unsigned) * NINTS, c->cap) == cudaSuccess &&
+                 cudaMemsetAsync(c->scal, 0, sizeof(double) * NSCAL, c->cap) == cudaSuccess &&
+                 cudaStreamSynchronize(c->cap) == cudaSuccess;
     if (!ok) {
         cudaError_t le = cudaGetLastError();
         free_ctx_mem(c);
@@ -350,14 +351,17 @@ extern "C" pfc_status pfc_step(pfc_ctx* c, const void* u_in, void* u_out, double
     return PFC_OK;
 }
 
-static pfc_status ensure_trace(pfc_ctx* c, int n)
+// Grows the trace buffer.  Only this call's stream is waited for (earlier
+// runs of the context ended with a synchronisation of theirs): a device-wide
+// wait would break a graph capture that another thread has in progress.
+static pfc_status ensure_trace(pfc_ctx* c, int n, cudaStream_t s)
 {
     if (n <= c->trace_cap) return PFC_OK;
     if (c->gexec) {
         cudaGraphExecDestroy(c->gexec);
         c->gexec = nullptr;
     }
-    PFC_CU(cudaDeviceSynchronize());
+    PFC_CU(cudaStreamSynchronize(s));
     cudaFree(c->trace);
     c->trace = nullptr;
     c->trace_cap = 0;
@@ -388,7 +392,7 @@ extern "C" pfc_status pfc_run(pfc_ctx* c, void* u, int32_t nsteps, double tau, d
     if (!isfinite(tau)) return fail(PFC_EINVAL, "tau is not finite");
     if (nsteps == 0) return PFC_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = ensure_trace(c, nsteps))) return st;
+    if ((st = ensure_trace(c, nsteps, s))) return st;
     PFC_CU(cudaMemsetAsync(c->ints, 0, sizeof(unsigned) * NINTS, s));
     PFC_CU(cudaMemsetAsync(c->scal, 0, sizeof(double) * NSCAL, s));
     // a CUDA graph of G steps (G even) replayed; the remainder is launched directly
@@ -724,7 +728,7 @@ extern "C" pfc_status pfc_batch_run(pfc_batch* b, void* const* u, int32_t nsteps
             cudaGraphExecDestroy(b->gexec);
             b->gexec = nullptr;
         }
-        PFC_CU(cudaDeviceSynchronize());
+        PFC_CU(cudaStreamSynchronize(s));   // not device-wide: see ensure_trace
         cudaFree(b->trace);
         b->trace = nullptr;
         b->trace_cap = 0;

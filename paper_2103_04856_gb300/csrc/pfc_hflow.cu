@@ -508,9 +508,10 @@ extern "C" pfc_status pfc_hflow_create(const pfc_problem* prob, const pfc_hflow_
          cudaMalloc((void**)&h->fints, sizeof(unsigned) * 4) == cudaSuccess &&
          cudaMalloc((void**)&h->hs, sizeof(double) * NH) == cudaSuccess &&
          cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) == cudaSuccess;
-    if (ok) ok = cudaMemset(h->sints, 0, sizeof(unsigned) * NINTS) == cudaSuccess &&
-                 cudaMemset(h->fints, 0, sizeof(unsigned) * 4) == cudaSuccess &&
-                 cudaMemset(h->hs, 0, sizeof(double) * NH) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess;
+    if (ok) ok = cudaMemsetAsync(h->sints, 0, sizeof(unsigned) * NINTS, h->cap) == cudaSuccess &&
+                 cudaMemsetAsync(h->fints, 0, sizeof(unsigned) * 4, h->cap) == cudaSuccess &&
+                 cudaMemsetAsync(h->hs, 0, sizeof(double) * NH, h->cap) == cudaSuccess &&
+                 cudaStreamSynchronize(h->cap) == cudaSuccess;
     if (!ok) {
         (void)cudaGetLastError();
         free_flow(h);
@@ -703,7 +704,9 @@ extern "C" pfc_status pfc_hflow_run(pfc_hflow* h, void* A, void* m, void* v, int
             cudaGraphExecDestroy(h->gexec);
             h->gexec = nullptr;
         }
-        HCU(cudaDeviceSynchronize());
+        // only this stream (earlier runs ended with a wait on theirs): a device-wide
+        // wait would break a graph capture that another thread has in progress
+        HCU(cudaStreamSynchronize(s));
         cudaFree(h->trace);
         h->trace = nullptr;
         h->trace_cap = 0;
