@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other_workloads lines")
     ap.add_argument("--only", default=None,
-                    choices=["alg1_flow_100", "extended_sweep_128", "alg1_spatialized", "diagnostics_512"],
+                    choices=["alg1_flow_100", "alg1_batch_100", "extended_sweep_128", "alg1_spatialized",
+                             "diagnostics_512"],
                     help="run just this one of the other workloads and print its line (for profiling)")
     return ap.parse_args()
 
@@ -337,6 +338,41 @@ def _timed(fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
+def alg1_batch_workload(pfc, I, n_inst, steps):
+    """The paper's generator in its setting (100^3, Fig. cvg_1 parameters,
+    blur 2 voxels, Adam), n_inst shapes from different white-noise A0 at
+    once (pfc_hflow_batch: one launch per kernel for all): throughput in
+    shape-iterations per second and the time of the paper's 8000-iteration
+    protocol per shape."""
+    import torch
+    pd, fd, _ = I.paper_flow_100()
+    nz, ny, nx = pd["shape"]
+    prob = pfc.Problem(nx=nx, ny=ny, nz=nz, h=pd["h"], eps=pd["eps"], xi=pd["xi"], a=pd["a"], well=pd["well"],
+                       prec="fp32")
+    fb = pfc.HFlowBatch([prob] * n_inst, [fd["m0"]] * n_inst, lr=fd["lr"], betas=(fd["beta1"], fd["beta2"]),
+                        adam_eps=fd["adam_eps"], blur_sigma=fd["blur_sigma"])
+    As = [torch.tensor(I.paper_flow_100(seed=s)[2].astype(np.float32), device="cuda") for s in range(n_inst)]
+    ms = [torch.zeros_like(a) for a in As]
+    vs = [torch.zeros_like(a) for a in As]
+    fb.run(As, ms, vs, 32, trace=False)           # warm-up: graph capture
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    fb.run(As, ms, vs, steps, trace=False)
+    e1.record()
+    e1.synchronize()
+    ms_it = e0.elapsed_time(e1) / steps
+    fb.close()
+    n = nx * ny * nz
+    peaks, kind = load_peaks()
+    state_gbs = 72.0 * n * n_inst / (ms_it * 1e-3) / 1e9
+    return {"workload": f"Alg. 1 at 100^3 (paper setting), {n_inst} shapes per batch", "instances": n_inst,
+            "ms_per_batch_iteration": ms_it, "shape_iterations_per_s": n_inst * 1e3 / ms_it,
+            "seconds_per_shape_8000_iterations": 8000 * ms_it / 1e3 / n_inst,
+            "value": n * n_inst * 1e3 / ms_it, "unit": "voxel-iterations/s",
+            "state_GBps": state_gbs, "state_frac_of_hbm": state_gbs / peaks["hbm_gbs"], "hbm_peak_kind": kind}
+
+
 def extended_sweep_workload(pfc, I, steps):
     """The Sec. 5.2 extensions on the 128^3 tanh sphere (p = k1^2 + k2^2),
     FP32 descent steps (pfc_run, graph replays): the plain sweep, with the
@@ -430,6 +466,7 @@ def main():
 
     if args.only:
         run = {"alg1_flow_100": lambda: alg1_workload(pfc, I, steps=args.steps),
+               "alg1_batch_100": lambda: alg1_batch_workload(pfc, I, 16, steps=args.steps),
                "extended_sweep_128": lambda: extended_sweep_workload(pfc, I, steps=args.steps),
                "alg1_spatialized": lambda: spatialized_flow_workload(pfc, I, steps=args.steps),
                "diagnostics_512": lambda: diagnostics_workload(pfc, I)}[args.only]
@@ -571,6 +608,7 @@ def main():
         extra = {"batch64_mixed": extra_workload(pfc, I.batch_instances(64), flush, steps=20),
                  "membrane_512": extra_workload(pfc, [I.membrane_descent_512()], flush, steps=10),
                  "alg1_flow_100": alg1_workload(pfc, I, steps=8000),
+                 "alg1_batch_100x16": alg1_batch_workload(pfc, I, 16, steps=256),
                  "extended_sweep_128": extended_sweep_workload(pfc, I, steps=64),
                  "alg1_spatialized_600x100x100": spatialized_flow_workload(pfc, I, steps=64),
                  "diagnostics_512": diagnostics_workload(pfc, I)}

@@ -237,6 +237,28 @@ pfc_status pfc_hflow_grad(pfc_hflow* flow, const void* A, void* gA, double* G_ho
 pfc_status pfc_hflow_run(pfc_hflow* flow, void* A, void* m, void* v, int32_t nsteps, int32_t* t,
                          double* trace_host, pfc_stream stream);
 
+/* Batches of the generator: up to 64 flows on grids of one size advanced
+ * together, every kernel of an iteration one launch over all of them (the
+ * paper generates many shapes, e.g. its atlas of Sec. 4.5; one 100^3 flow
+ * alone cannot fill the GPU).  probs: n_inst problems with equal nx, ny, nz,
+ * FP32, fused path, mu = 0, proj = 0 (otherwise PFC_EUNSUPPORTED or
+ * PFC_EINVAL); their coefficients, eps, h, xi and double wells may differ.
+ * m0: n_inst masses (params->m0 is ignored); the blur and Adam's settings of
+ * params are shared.  A[k], m[k], v[k]: instance k's fields as for
+ * pfc_hflow_run; *t is the common Adam step count.  trace_host (may be
+ * NULL): n_inst x nsteps rows of pfc_hflow_run's trace, instance-major.
+ * Allocates 4 fields of scratch per instance. */
+typedef struct pfc_hflow_batch pfc_hflow_batch;
+pfc_status pfc_hflow_batch_create(const pfc_problem* probs, const double* m0, int32_t n_inst,
+                                  const pfc_hflow_params* params, pfc_hflow_batch** out);
+void pfc_hflow_batch_destroy(pfc_hflow_batch* batch);
+/* ut[k] = k * (div A[k] + m0[k]) for every instance (enqueue only). */
+pfc_status pfc_hflow_batch_field(pfc_hflow_batch* batch, const void* const* A, void* const* ut, pfc_stream stream);
+/* nsteps Adam steps of every instance, in place; CUDA-graph replays of 32
+ * steps; synchronises the stream. */
+pfc_status pfc_hflow_batch_run(pfc_hflow_batch* batch, void* const* A, void* const* m, void* const* v,
+                               int32_t nsteps, int32_t* t, double* trace_host, pfc_stream stream);
+
 /* Spatialised generation parameters (Sec. 5.2) for the flow: a(x) as for
  * pfc_set_coefficient_field, and m(x) (device, N values of the problem's
  * type): u = k * (div A + m(x)), whose mean is mean(m).  Both are copied on

@@ -610,17 +610,26 @@ template cudaError_t launch_fused<double>(const Inst<double>&, int, int, int, cu
 
 // Batches of up to BATCH_MAX problems go in one launch (their descriptors
 // travel as kernel parameters); larger batches take one launch per group.
-cudaError_t launch_fused_batch(const Inst<float>* insts, int n_inst, int tile_y, int max_run, cudaStream_t s)
+// MODE_STEP (descent steps) or MODE_GRAD (energies and gradients).
+cudaError_t launch_fused_batch(const Inst<float>* insts, int n_inst, int tile_y, int max_run, cudaStream_t s,
+                               int mode)
 {
+    if (mode != MODE_STEP && mode != MODE_GRAD) return cudaErrorInvalidValue;
     thread_local Launch<float, BATCH_MAX> L;   // host staging (per thread); the launch copies it
     for (int g0 = 0; g0 < n_inst; g0 += BATCH_MAX) {
         const int cnt = n_inst - g0 < BATCH_MAX ? n_inst - g0 : BATCH_MAX;
         L.n = cnt;
         for (int k = 0; k < cnt; ++k) L.inst[k] = insts[g0 + k];
         plan(L, tile_y, max_run);
-        cudaError_t e = tile_y == 8    ? launch_one<float, 8, MODE_STEP, BATCH_MAX>(L, L.grid, s)
-                        : tile_y == 13 ? launch_one<float, 13, MODE_STEP, BATCH_MAX>(L, L.grid, s)
-                                       : launch_one<float, 16, MODE_STEP, BATCH_MAX>(L, L.grid, s);
+        cudaError_t e;
+        if (mode == MODE_STEP)
+            e = tile_y == 8    ? launch_one<float, 8, MODE_STEP, BATCH_MAX>(L, L.grid, s)
+                : tile_y == 13 ? launch_one<float, 13, MODE_STEP, BATCH_MAX>(L, L.grid, s)
+                               : launch_one<float, 16, MODE_STEP, BATCH_MAX>(L, L.grid, s);
+        else
+            e = tile_y == 8    ? launch_one<float, 8, MODE_GRAD, BATCH_MAX>(L, L.grid, s)
+                : tile_y == 13 ? launch_one<float, 13, MODE_GRAD, BATCH_MAX>(L, L.grid, s)
+                               : launch_one<float, 16, MODE_GRAD, BATCH_MAX>(L, L.grid, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

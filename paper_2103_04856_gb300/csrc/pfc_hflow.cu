@@ -72,15 +72,16 @@ template <> __device__ __forceinline__ double pow_<double>(double b, double e) {
 
 // Block totals of (sum, max) in the arithmetic type per thread, FP64 across
 // warps and blocks; the last block combines all partials in a fixed order
-// and runs `fin` with the totals (thread 0).
+// and runs `fin` with the totals (thread 0).  The blocks of one instance are
+// the grid's x dimension (a batch puts its instances along y).
 template <typename T, class Fin>
 __device__ void flow_finish(const Flow& f, T a0, T a1, Fin fin)
 {
     __shared__ double red[2 * (kThreads / 32)];
     __shared__ int last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nblocks = gridDim.x * gridDim.y * gridDim.z;
-    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int nblocks = gridDim.x;
+    const int bid = blockIdx.x;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         a0 += __shfl_xor_sync(0xffffffffu, a0, o);
@@ -128,11 +129,43 @@ inline dim3 flow_grid(long n)
 }
 
 
+// Launch descriptors: one flow (MAXI = 1) or a batch of up to BATCH_MAX
+// flows on grids of one size, instance k = blockIdx.y (blockIdx.z / zb for
+// the blur), passed by value and read from the constant bank.
+template <typename T, int MAXI>
+struct DivL {
+    Flow f[MAXI];
+    const T* A[MAXI];
+    T* u[MAXI];
+    int want_mass;
+};
+template <typename T, int MAXI>
+struct AdamL {
+    Flow f[MAXI];
+    const T* gb[MAXI];
+    T* A[MAXI];
+    T* m[MAXI];
+    T* v[MAXI];
+    int only_grad;
+};
+template <typename T, int MAXI>
+struct BlurL {
+    const T* in[MAXI];
+    T* out[MAXI];
+    int nx, ny, nz;
+    int zb;             // z blocks per instance
+    Weights w;
+};
+
 // u = div A + m0 (or + m(x)), periodic central differences (eq.
 // change_var); mass of u.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_div(const T* __restrict__ A, T* __restrict__ u, Flow f, int want_mass)
+template <typename T, int MAXI>
+__global__ void __launch_bounds__(kThreads) k_div(const __grid_constant__ DivL<T, MAXI> L)
 {
+    const Flow& f = L.f[blockIdx.y];
+    const T* __restrict__ A = L.A[blockIdx.y];
+    T* __restrict__ u = L.u[blockIdx.y];
+    const int want_mass = L.want_mass;
     const long n = f.n, pls = (long)f.nx * f.ny;
     T ms = 0;
     for (Walk w(f.nx, f.ny, (long)blockIdx.x * kThreads + threadIdx.x, (long)gridDim.x * kThreads); w.i < n;
@@ -158,17 +191,21 @@ __global__ void __launch_bounds__(kThreads) k_div(const T* __restrict__ A, T* __
 // Grid: x = tiles across x (32 wide, or kTileAx wide for AX 0), y = tiles
 // along the blurred axis (for AX 0: groups of 8 rows), z = the remaining
 // axis (looped when above the grid limit).
-template <typename T, int AX>
-__global__ void __launch_bounds__(256) k_blur(const T* __restrict__ in, T* __restrict__ out, int nx, int ny, int nz,
-                                              const __grid_constant__ Weights w)
+template <typename T, int AX, int MAXI>
+__global__ void __launch_bounds__(256) k_blur(const __grid_constant__ BlurL<T, MAXI> BL)
 {
     constexpr int L = kTileAx + 2 * kMaxRadius;
     __shared__ T s[AX == 0 ? 8 : L][AX == 0 ? L : 32];
+    const int inst = blockIdx.z / BL.zb, zo = blockIdx.z - inst * BL.zb;
+    const T* __restrict__ in = BL.in[inst];
+    T* __restrict__ out = BL.out[inst];
+    const int nx = BL.nx, ny = BL.ny, nz = BL.nz;
+    const Weights& w = BL.w;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int R = w.R;
     const long pls = (long)nx * ny;
     const int n_other = AX == 2 ? ny : nz;
-    for (int o = blockIdx.z; o < n_other; o += gridDim.z) {
+    for (int o = zo; o < n_other; o += BL.zb) {
         if (AX == 0) {
             const int x0 = blockIdx.x * kTileAx, y = blockIdx.y * 8 + ty;
             const long row = (long)o * pls + (long)y * nx;
@@ -201,23 +238,31 @@ __global__ void __launch_bounds__(256) k_blur(const T* __restrict__ in, T* __res
     }
 }
 
-template <typename T, int AX>
-static void launch_blur(const T* in, T* out, int nx, int ny, int nz, const Weights& w, cudaStream_t s)
+// One blur pass over every instance of a descriptor table (in/out filled).
+template <typename T, int AX, int MAXI>
+static void launch_blur(BlurL<T, MAXI>& BL, int n_inst, cudaStream_t s)
 {
+    const int nx = BL.nx, ny = BL.ny, nz = BL.nz;
     const int n_other = AX == 2 ? ny : nz;
-    const dim3 grid = AX == 0 ? dim3((nx + kTileAx - 1) / kTileAx, (ny + 7) / 8, n_other < 65535 ? n_other : 65535)
-                              : dim3((nx + 31) / 32, ((AX == 1 ? ny : nz) + kTileAx - 1) / kTileAx,
-                                     n_other < 65535 ? n_other : 65535);
-    k_blur<T, AX><<<grid, dim3(32, 8), 0, s>>>(in, out, nx, ny, nz, w);
+    const int cap = 65535 / n_inst;
+    BL.zb = n_other < cap ? n_other : cap;
+    const dim3 grid = AX == 0 ? dim3((nx + kTileAx - 1) / kTileAx, (ny + 7) / 8, BL.zb * n_inst)
+                              : dim3((nx + 31) / 32, ((AX == 1 ? ny : nz) + kTileAx - 1) / kTileAx, BL.zb * n_inst);
+    k_blur<T, AX, MAXI><<<grid, dim3(32, 8), 0, s>>>(BL);
 }
 
 // dG/dA from the blurred gradient gb, then Adam (Kingma and Ba) on A with
 // moments m, v; the step counter lives in f.ints[1].  `only_grad`: write
 // dG/dA to m and leave A, v alone (pfc_hflow_grad).
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_adam(const T* __restrict__ gb, T* __restrict__ A, T* __restrict__ m,
-                                                   T* __restrict__ v, Flow f, int only_grad)
+template <typename T, int MAXI>
+__global__ void __launch_bounds__(kThreads) k_adam(const __grid_constant__ AdamL<T, MAXI> L)
 {
+    const Flow& f = L.f[blockIdx.y];
+    const T* __restrict__ gb = L.gb[blockIdx.y];
+    T* __restrict__ A = L.A[blockIdx.y];
+    T* __restrict__ m = L.m[blockIdx.y];
+    T* __restrict__ v = L.v[blockIdx.y];
+    const int only_grad = L.only_grad;
     const long n = f.n, pls = (long)f.nx * f.ny;
     const unsigned t = f.ints[1] + 1;
     const T b1 = (T)f.beta1, b2 = (T)f.beta2;
@@ -274,9 +319,13 @@ __global__ void __launch_bounds__(kThreads) k_adam(const T* __restrict__ gb, T* 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
-__global__ void __launch_bounds__(kThreads) k_div4(const float* __restrict__ A, float* __restrict__ u, Flow f,
-                                                   int want_mass)
+template <int MAXI>
+__global__ void __launch_bounds__(kThreads) k_div4(const __grid_constant__ DivL<float, MAXI> L)
 {
+    const Flow& f = L.f[blockIdx.y];
+    const float* __restrict__ A = L.A[blockIdx.y];
+    float* __restrict__ u = L.u[blockIdx.y];
+    const int want_mass = L.want_mass;
     const int nx4 = f.nx >> 2;
     const long n = f.n, n4 = n >> 2, pls = (long)f.nx * f.ny;
     const float sg = (float)f.sg, m0 = (float)f.m0;
@@ -305,9 +354,15 @@ __global__ void __launch_bounds__(kThreads) k_div4(const float* __restrict__ A, 
     flow_finish<float>(f, ms, 0.0f, [&](double s0, double) { f.hs[H_MASS] = s0 / (double)f.n; });
 }
 
-__global__ void __launch_bounds__(kThreads) k_adam4(const float* __restrict__ gb, float* __restrict__ A,
-                                                    float* __restrict__ m, float* __restrict__ v, Flow f, int only_grad)
+template <int MAXI>
+__global__ void __launch_bounds__(kThreads) k_adam4(const __grid_constant__ AdamL<float, MAXI> L)
 {
+    const Flow& f = L.f[blockIdx.y];
+    const float* __restrict__ gb = L.gb[blockIdx.y];
+    float* __restrict__ A = L.A[blockIdx.y];
+    float* __restrict__ m = L.m[blockIdx.y];
+    float* __restrict__ v = L.v[blockIdx.y];
+    const int only_grad = L.only_grad;
     const int nx4 = f.nx >> 2;
     const long n = f.n, n4 = n >> 2, pls = (long)f.nx * f.ny;
     const unsigned t = f.ints[1] + 1;
@@ -554,29 +609,68 @@ static Flow flow_desc(const pfc_hflow* h)
 
 static bool al16(const void* p) { return p == nullptr || ((uintptr_t)p & 15) == 0; }
 
-// u = div A + m into `out` (float4 path when the rows allow it)
+// u = div A + m into `out` for n_inst instances of one grid size (float4
+// path when the rows and every buffer allow it)
+template <typename T, int MAXI>
+static void launch_div(DivL<T, MAXI>& L, int n_inst, long N, int nx, cudaStream_t s)
+{
+    bool v4 = sizeof(T) == 4 && nx % 4 == 0;
+    for (int k = 0; k < n_inst; ++k) v4 = v4 && al16(L.A[k]) && al16(L.u[k]) && al16(L.f[k].mf);
+    if (v4) {
+        const dim3 grid(flow_grid(N / 4).x, n_inst);
+        k_div4<MAXI><<<grid, kThreads, 0, s>>>(reinterpret_cast<const DivL<float, MAXI>&>(L));
+        return;
+    }
+    k_div<T, MAXI><<<dim3(flow_grid(N).x, n_inst), kThreads, 0, s>>>(L);
+}
+
+// dG/dA and (unless only_grad) the Adam update, n_inst instances
+template <typename T, int MAXI>
+static void launch_adam(AdamL<T, MAXI>& L, int n_inst, long N, int nx, cudaStream_t s)
+{
+    bool v4 = sizeof(T) == 4 && nx % 4 == 0;
+    for (int k = 0; k < n_inst; ++k) v4 = v4 && al16(L.gb[k]) && al16(L.A[k]) && al16(L.m[k]) && al16(L.v[k]);
+    if (v4) {
+        const dim3 grid(flow_grid(N / 4).x, n_inst);
+        k_adam4<MAXI><<<grid, kThreads, 0, s>>>(reinterpret_cast<const AdamL<float, MAXI>&>(L));
+        return;
+    }
+    k_adam<T, MAXI><<<dim3(flow_grid(N).x, n_inst), kThreads, 0, s>>>(L);
+}
+
 template <typename T>
 static void launch_div(const pfc_hflow* h, const T* A, T* out, int want_mass, cudaStream_t s)
 {
-    const Flow f = flow_desc(h);
-    if (sizeof(T) == 4 && h->P.nx % 4 == 0 && al16(A) && al16(out) && al16(f.mf)) {
-        k_div4<<<flow_grid(h->N / 4), kThreads, 0, s>>>((const float*)A, (float*)out, f, want_mass);
-        return;
-    }
-    k_div<T><<<flow_grid(h->N), kThreads, 0, s>>>(A, out, f, want_mass);
+    DivL<T, 1> L;
+    L.f[0] = flow_desc(h);
+    L.A[0] = A;
+    L.u[0] = out;
+    L.want_mass = want_mass;
+    launch_div<T, 1>(L, 1, h->N, h->P.nx, s);
 }
 
-// dG/dA and (unless only_grad) the Adam update
 template <typename T>
 static void launch_adam(const pfc_hflow* h, const T* gb, T* A, T* m, T* v, int only_grad, cudaStream_t s)
 {
-    const Flow f = flow_desc(h);
-    if (sizeof(T) == 4 && h->P.nx % 4 == 0 && al16(gb) && al16(A) && al16(m) && al16(v)) {
-        k_adam4<<<flow_grid(h->N / 4), kThreads, 0, s>>>((const float*)gb, (float*)A, (float*)m, (float*)v, f,
-                                                         only_grad);
-        return;
-    }
-    k_adam<T><<<flow_grid(h->N), kThreads, 0, s>>>(gb, A, m, v, f, only_grad);
+    AdamL<T, 1> L;
+    L.f[0] = flow_desc(h);
+    L.gb[0] = gb;
+    L.A[0] = A;
+    L.m[0] = m;
+    L.v[0] = v;
+    L.only_grad = only_grad;
+    launch_adam<T, 1>(L, 1, h->N, h->P.nx, s);
+}
+
+template <typename T, int AX>
+static void launch_blur(const T* in, T* out, int nx, int ny, int nz, const Weights& w, cudaStream_t s)
+{
+    BlurL<T, 1> BL;
+    BL.in[0] = in;
+    BL.out[0] = out;
+    BL.nx = nx; BL.ny = ny; BL.nz = nz;
+    BL.w = w;
+    launch_blur<T, AX, 1>(BL, 1, s);
 }
 
 // in -> k * in through the two temporaries; returns the buffer holding the result
@@ -793,5 +887,357 @@ extern "C" pfc_status pfc_hflow_set_mass_field(pfc_hflow* h, const void* m_field
     if (!h->mfield) HCU(cudaMalloc(&h->mfield, (size_t)h->esz * h->N));
     HCU(cudaMemcpyAsync(h->mfield, m_field, (size_t)h->esz * h->N, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
     h->mf_on = true;
+    return PFC_OK;
+}
+
+// ------------------------------------------------------------ batches of flows
+//
+// Up to BATCH_MAX flows on grids of one size (FP32, fused path) advanced
+// together: every kernel of an iteration is one launch over all instances
+// (the sweep through the batched fused kernel), so small grids such as the
+// paper's 100^3 fill the GPU.  Each instance has its own coefficients, eps,
+// h, xi, double well and mass m0; the blur and Adam's settings are shared.
+
+struct pfc_hflow_batch {
+    int n = 0;
+    int device = 0;
+    int nx = 0, ny = 0, nz = 0;
+    long N = 0;
+    int tile_y = 16;
+    std::vector<pfc_problem> P;
+    std::vector<double> m0;
+    pfc_hflow_params H{};
+    Weights W{};
+    float* bufs = nullptr;       // [n][4][N]: ut, g, two blur temporaries
+    double* spart = nullptr;     // sweep partials [n][slots][NPART]
+    unsigned* sints = nullptr;   // [n][NINTS]
+    double* sscal = nullptr;     // [n][NSCAL]
+    double* fpart = nullptr;     // flow partials [n][2 * blocks]
+    unsigned* fints = nullptr;   // [n][4]
+    double* hs = nullptr;        // [n][NH]
+    double* trace = nullptr;     // [n][cap][5]
+    int trace_cap = 0;
+    int slots = 0;
+    long fblocks = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<const void*> gkey;
+    int glen = 0;
+    double* gtrace = nullptr;
+};
+
+static void free_flow_batch(pfc_hflow_batch* b)
+{
+    cudaFree(b->bufs);
+    cudaFree(b->spart);
+    cudaFree(b->sints);
+    cudaFree(b->sscal);
+    cudaFree(b->fpart);
+    cudaFree(b->fints);
+    cudaFree(b->hs);
+    cudaFree(b->trace);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->cap) cudaStreamDestroy(b->cap);
+}
+
+extern "C" pfc_status pfc_hflow_batch_create(const pfc_problem* probs, const double* m0, int32_t n_inst,
+                                             const pfc_hflow_params* hp, pfc_hflow_batch** out)
+{
+    if (!out || !probs || !m0 || !hp) return hfail(PFC_EINVAL, "hflow batch: problems, m0, params and out are required");
+    *out = nullptr;
+    if (n_inst < 1 || n_inst > BATCH_MAX) return hfail(PFC_EINVAL, "hflow batch: between 1 and 64 instances");
+    for (int k = 0; k < n_inst; ++k) {
+        const pfc_problem& p = probs[k];
+        if (p.nx != probs[0].nx || p.ny != probs[0].ny || p.nz != probs[0].nz)
+            return hfail(PFC_EINVAL, "hflow batch: every instance must have the grid size of the first");
+        if (p.nx < 1 || p.ny < 1 || p.nz < 1 || (double)p.nx * p.ny * p.nz > 2.0e9)
+            return hfail(PFC_EINVAL, "hflow batch: grid sizes must be >= 1 and hold at most 2e9 voxels");
+        if (!(p.h > 0) || !(p.eps > 0) || !(p.xi > 0) || !isfinite(p.h) || !isfinite(p.eps) || !isfinite(p.xi))
+            return hfail(PFC_EINVAL, "hflow batch: h, eps, xi must be finite and > 0");
+        for (int i = 0; i < 6; ++i)
+            if (!isfinite(p.a[i])) return hfail(PFC_EINVAL, "hflow batch: a coefficient is not finite");
+        if (p.well != PFC_WELL_01 && p.well != PFC_WELL_PM1) return hfail(PFC_EINVAL, "hflow batch: unknown double well");
+        if (p.prec != PFC_FP32 || p.impl != PFC_IMPL_FUSED)
+            return hfail(PFC_EUNSUPPORTED, "hflow batch: FP32 on the fused path only");
+        if (p.mu != 0.0 || p.proj != 0)
+            return hfail(PFC_EUNSUPPORTED, "hflow batch: no orientation term or projected M in batches");
+        if (!isfinite(m0[k])) return hfail(PFC_EINVAL, "hflow batch: m0 must be finite");
+    }
+    if (!(hp->lr >= 0) || !(hp->beta1 >= 0 && hp->beta1 < 1) || !(hp->beta2 >= 0 && hp->beta2 < 1) ||
+        !(hp->adam_eps >= 0) || !(hp->blur_sigma >= 0))
+        return hfail(PFC_EINVAL, "hflow batch: lr >= 0, betas in [0,1), eps >= 0, sigma >= 0 required");
+    int R = 0;
+    if (hp->blur_sigma > 0) {
+        R = hp->blur_radius > 0 ? hp->blur_radius : (int)ceil(3.0 * hp->blur_sigma);
+        if (R > kMaxRadius) return hfail(PFC_EINVAL, "hflow batch: blur radius above 32 taps");
+    }
+    pfc_hflow_batch* b = new (std::nothrow) pfc_hflow_batch();
+    if (!b) return hfail(PFC_ENOMEM, "hflow batch: host allocation failed");
+    b->n = n_inst;
+    b->nx = probs[0].nx; b->ny = probs[0].ny; b->nz = probs[0].nz;
+    b->N = (long)b->nx * b->ny * b->nz;
+    b->P.assign(probs, probs + n_inst);
+    b->m0.assign(m0, m0 + n_inst);
+    b->H = *hp;
+    b->H.blur_radius = R;
+    b->W.R = R;
+    if (R > 0) {
+        double s = 0;
+        for (int j = -R; j <= R; ++j) s += exp(-(double)j * j / (2.0 * hp->blur_sigma * hp->blur_sigma));
+        for (int j = -R; j <= R; ++j) {
+            b->W.wd[j + R] = exp(-(double)j * j / (2.0 * hp->blur_sigma * hp->blur_sigma)) / s;
+            b->W.wf[j + R] = (float)b->W.wd[j + R];
+        }
+    }
+    b->tile_y = probs[0].tile_y ? probs[0].tile_y : default_tile_y(b->ny, false);
+    cudaGetDevice(&b->device);
+    const long long units = (long long)((b->nx + 31) / 32) * ((b->ny + b->tile_y - 1) / b->tile_y) * b->nz * n_inst;
+    b->slots = (int)fused_grid(units, probs[0].tile_z);
+    b->fblocks = flow_blocks(b->N);
+    const size_t n = (size_t)n_inst;
+    bool ok = cudaMalloc((void**)&b->bufs, sizeof(float) * 4 * (size_t)b->N * n) == cudaSuccess &&
+              cudaMalloc((void**)&b->spart, sizeof(double) * NPART * (size_t)b->slots * n) == cudaSuccess &&
+              cudaMalloc((void**)&b->sints, sizeof(unsigned) * NINTS * n) == cudaSuccess &&
+              cudaMalloc((void**)&b->sscal, sizeof(double) * NSCAL * n) == cudaSuccess &&
+              cudaMalloc((void**)&b->fpart, sizeof(double) * 2 * (size_t)b->fblocks * n) == cudaSuccess &&
+              cudaMalloc((void**)&b->fints, sizeof(unsigned) * 4 * n) == cudaSuccess &&
+              cudaMalloc((void**)&b->hs, sizeof(double) * NH * n) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) ok = cudaMemsetAsync(b->sints, 0, sizeof(unsigned) * NINTS * n, b->cap) == cudaSuccess &&
+                 cudaMemsetAsync(b->fints, 0, sizeof(unsigned) * 4 * n, b->cap) == cudaSuccess &&
+                 cudaMemsetAsync(b->hs, 0, sizeof(double) * NH * n, b->cap) == cudaSuccess &&
+                 cudaStreamSynchronize(b->cap) == cudaSuccess;
+    if (!ok) {
+        (void)cudaGetLastError();
+        free_flow_batch(b);
+        delete b;
+        return hfail(PFC_ENOMEM, "hflow batch: device allocation failed");
+    }
+    *out = b;
+    return PFC_OK;
+}
+
+extern "C" void pfc_hflow_batch_destroy(pfc_hflow_batch* b)
+{
+    if (!b) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    free_flow_batch(b);
+    cudaSetDevice(prev);
+    delete b;
+}
+
+static Flow flow_desc_batch(const pfc_hflow_batch* b, int k)
+{
+    Flow f;
+    f.nx = b->nx; f.ny = b->ny; f.nz = b->nz;
+    f.n = b->N;
+    f.sg = 1.0 / (2.0 * b->P[k].h);
+    f.m0 = b->m0[k];
+    f.mf = nullptr;
+    f.lr = b->H.lr; f.beta1 = b->H.beta1; f.beta2 = b->H.beta2; f.adam_eps = b->H.adam_eps;
+    f.part = b->fpart + (size_t)k * 2 * b->fblocks;
+    f.ints = b->fints + (size_t)k * 4;
+    f.hs = b->hs + (size_t)k * NH;
+    f.sweep_scal = b->sscal + (size_t)k * NSCAL;
+    f.trace = b->trace ? b->trace + (size_t)k * 5 * b->trace_cap : nullptr;
+    f.trace_cap = b->trace_cap;
+    return f;
+}
+
+static float* bbuf(const pfc_hflow_batch* b, int k, int which) { return b->bufs + ((size_t)k * 4 + which) * b->N; }
+
+// the blur over every instance: in[k] -> out[k]
+template <int AX>
+static void batch_blur(const pfc_hflow_batch* b, int from, int to, cudaStream_t s)
+{
+    BlurL<float, BATCH_MAX> BL;
+    for (int k = 0; k < b->n; ++k) {
+        BL.in[k] = bbuf(b, k, from);
+        BL.out[k] = bbuf(b, k, to);
+    }
+    BL.nx = b->nx; BL.ny = b->ny; BL.nz = b->nz;
+    BL.w = b->W;
+    launch_blur<float, AX, BATCH_MAX>(BL, b->n, s);
+}
+
+// ut[k] = k * (div A[k] + m0[k]) into buffer 0 of every instance
+static cudaError_t batch_field(const pfc_hflow_batch* b, const float* const* A, int want_mass, cudaStream_t s)
+{
+    DivL<float, BATCH_MAX> L;
+    for (int k = 0; k < b->n; ++k) {
+        L.f[k] = flow_desc_batch(b, k);
+        L.A[k] = A[k];
+        L.u[k] = bbuf(b, k, b->W.R ? 2 : 0);
+    }
+    L.want_mass = want_mass;
+    launch_div<float, BATCH_MAX>(L, b->n, b->N, b->nx, s);
+    if (b->W.R) {
+        batch_blur<0>(b, 2, 3, s);
+        batch_blur<1>(b, 3, 2, s);
+        batch_blur<2>(b, 2, 0, s);
+    }
+    return cudaGetLastError();
+}
+
+// one iteration of Alg. 1 for every instance
+static cudaError_t batch_step(const pfc_hflow_batch* b, float* const* A, float* const* m, float* const* v,
+                              cudaStream_t s)
+{
+    cudaError_t e = batch_field(b, A, 1, s);
+    if (e != cudaSuccess) return e;
+    std::vector<Inst<float>> in(b->n);
+    for (int k = 0; k < b->n; ++k) {
+        const pfc_problem& P = b->P[k];
+        Inst<float>& I = in[k];
+        I = Inst<float>{};
+        I.u = bbuf(b, k, 0);
+        I.out = bbuf(b, k, 1);
+        I.nx = b->nx; I.ny = b->ny; I.nz = b->nz;
+        I.vec = b->nx % 4 == 0;
+        I.C = make_coef<float>(P.a, P.h, P.eps, P.xi, P.well);
+        I.inv_N = 1.0 / (double)b->N;
+        I.partials = b->spart + (size_t)k * b->slots * NPART;
+        I.ints = b->sints + (size_t)k * NINTS;
+        I.scal = b->sscal + (size_t)k * NSCAL;
+    }
+    e = launch_fused_batch(in.data(), b->n, b->tile_y, b->P[0].tile_z, s, MODE_GRAD);
+    if (e != cudaSuccess) return e;
+    int gbuf = 1;
+    if (b->W.R) {   // the blur of g: 1 -> 2 -> 3 -> 2
+        batch_blur<0>(b, 1, 2, s);
+        batch_blur<1>(b, 2, 3, s);
+        batch_blur<2>(b, 3, 2, s);
+        gbuf = 2;
+    }
+    AdamL<float, BATCH_MAX> L;
+    for (int k = 0; k < b->n; ++k) {
+        L.f[k] = flow_desc_batch(b, k);
+        L.gb[k] = bbuf(b, k, gbuf);
+        L.A[k] = A[k];
+        L.m[k] = m[k];
+        L.v[k] = v[k];
+    }
+    L.only_grad = 0;
+    launch_adam<float, BATCH_MAX>(L, b->n, b->N, b->nx, s);
+    return cudaGetLastError();
+}
+
+static pfc_status check_vec_list(const void* const* p, int n, const char* name)
+{
+    if (!p) return hfail(PFC_EINVAL, "hflow batch: a pointer array is NULL");
+    for (int k = 0; k < n; ++k)
+        if (!dev_ptr(p[k])) {
+            char b_[128];
+            snprintf(b_, sizeof b_, "hflow batch: %s[%d] must be device memory", name, k);
+            return hfail(PFC_EINVAL, b_);
+        }
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_hflow_batch_field(pfc_hflow_batch* b, const void* const* A, void* const* ut,
+                                            pfc_stream stream)
+{
+    if (!b) return hfail(PFC_EINVAL, "hflow batch: handle is NULL");
+    pfc_status st;
+    if ((st = check_vec_list(A, b->n, "A")) || (st = check_vec_list(ut, b->n, "ut"))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    HCU(batch_field(b, (const float* const*)A, 0, s));
+    for (int k = 0; k < b->n; ++k)
+        HCU(cudaMemcpyAsync(ut[k], bbuf(b, k, 0), sizeof(float) * b->N, cudaMemcpyDeviceToDevice, s));
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_hflow_batch_run(pfc_hflow_batch* b, void* const* A, void* const* m, void* const* v,
+                                          int32_t nsteps, int32_t* t, double* trace_host, pfc_stream stream)
+{
+    nvtxRangePushA("pfc_hflow_batch_run");
+    struct Pop { ~Pop() { nvtxRangePop(); } } pop_;
+    if (!b) return hfail(PFC_EINVAL, "hflow batch: handle is NULL");
+    pfc_status st;
+    if ((st = check_vec_list(A, b->n, "A")) || (st = check_vec_list(m, b->n, "m")) ||
+        (st = check_vec_list(v, b->n, "v")))
+        return st;
+    for (int k = 0; k < b->n; ++k)
+        if (A[k] == m[k] || A[k] == v[k] || m[k] == v[k])
+            return hfail(PFC_EINVAL, "hflow batch: A, m and v of an instance must be distinct");
+    if (!t || *t < 0 || nsteps < 0) return hfail(PFC_EINVAL, "hflow batch: nsteps >= 0 and a step counter >= 0 required");
+    if (nsteps == 0) return PFC_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nsteps > b->trace_cap) {
+        if (b->gexec) {
+            cudaGraphExecDestroy(b->gexec);
+            b->gexec = nullptr;
+        }
+        HCU(cudaStreamSynchronize(s));   // this stream only (a device-wide wait breaks other threads' captures)
+        cudaFree(b->trace);
+        b->trace = nullptr;
+        b->trace_cap = 0;
+        HCU(cudaMalloc((void**)&b->trace, sizeof(double) * 5 * (size_t)nsteps * b->n));
+        b->trace_cap = nsteps;
+    }
+    std::vector<unsigned> ti((size_t)4 * b->n, 0u);
+    for (int k = 0; k < b->n; ++k) ti[(size_t)4 * k + 1] = (unsigned)*t;
+    HCU(cudaMemcpyAsync(b->fints, ti.data(), sizeof(unsigned) * ti.size(), cudaMemcpyHostToDevice, s));
+    HCU(cudaMemsetAsync(b->sints, 0, sizeof(unsigned) * NINTS * b->n, s));
+    float* const* Af = (float* const*)A;
+    float* const* mf = (float* const*)m;
+    float* const* vf = (float* const*)v;
+    auto enqueue = [&](int cnt, cudaStream_t st2) -> cudaError_t {
+        for (int i = 0; i < cnt; ++i) {
+            cudaError_t e = batch_step(b, Af, mf, vf, st2);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    const int G = nsteps >= 32 ? 32 : 0;
+    if (G) {
+        std::vector<const void*> key;
+        for (int k = 0; k < b->n; ++k) {
+            key.push_back(A[k]);
+            key.push_back(m[k]);
+            key.push_back(v[k]);
+        }
+        if (!(b->gexec && b->gkey == key && b->glen == G && b->gtrace == b->trace)) {
+            if (b->gexec) {
+                cudaGraphExecDestroy(b->gexec);
+                b->gexec = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            HCU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue(G, b->cap);
+            cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                (void)cudaGetLastError();
+                return hfail(PFC_ECUDA, "hflow batch: graph capture failed");
+            }
+            e = cudaGraphInstantiate(&b->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                b->gexec = nullptr;
+                (void)cudaGetLastError();
+                return hfail(PFC_ECUDA, "hflow batch: graph instantiation failed");
+            }
+            b->gkey = key;
+            b->glen = G;
+            b->gtrace = b->trace;
+        }
+        for (int k = 0; k + G <= nsteps; k += G) HCU(cudaGraphLaunch(b->gexec, s));
+    }
+    const int done = G ? (nsteps / G) * G : 0;
+    HCU(enqueue(nsteps - done, s));
+    std::vector<unsigned> back((size_t)4 * b->n);
+    HCU(cudaMemcpyAsync(back.data(), b->fints, sizeof(unsigned) * back.size(), cudaMemcpyDeviceToHost, s));
+    if (trace_host)
+        for (int k = 0; k < b->n; ++k)
+            HCU(cudaMemcpyAsync(trace_host + (size_t)k * 5 * nsteps, b->trace + (size_t)k * 5 * b->trace_cap,
+                                sizeof(double) * 5 * (size_t)nsteps, cudaMemcpyDeviceToHost, s));
+    HCU(cudaStreamSynchronize(s));
+    for (int k = 0; k < b->n; ++k)
+        if (back[(size_t)4 * k + 2] != (unsigned)nsteps) return hfail(PFC_ECUDA, "hflow batch: step count mismatch");
+    *t = (int32_t)back[1];
     return PFC_OK;
 }

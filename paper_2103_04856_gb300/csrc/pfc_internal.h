@@ -114,8 +114,10 @@ cudaError_t launch_coef_field(const T* a_field, T* c_field, long n, double h, do
 // at most fused_grid(units of the launch, max_run).
 template <typename T>
 cudaError_t launch_fused(const Inst<T>& in, int mode, int tile_y, int max_run, cudaStream_t s);
-// `insts`: host array of descriptors (copied into the launch parameters)
-cudaError_t launch_fused_batch(const Inst<float>* insts, int n_inst, int tile_y, int max_run, cudaStream_t s);
+// `insts`: host array of descriptors (copied into the launch parameters);
+// mode MODE_STEP or MODE_GRAD
+cudaError_t launch_fused_batch(const Inst<float>* insts, int n_inst, int tile_y, int max_run, cudaStream_t s,
+                               int mode = MODE_STEP);
 long long fused_grid(long long units, int max_run);
 // partial slots a single problem can need: both the requested tile height and
 // the extended sweep's

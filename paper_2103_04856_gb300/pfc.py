@@ -37,7 +37,8 @@ EXPORTED = ("pfc_create", "pfc_destroy", "pfc_energy", "pfc_energy_and_grad", "p
             "pfc_hflow_field", "pfc_hflow_grad", "pfc_hflow_run", "pfc_energy_and_grad_noalloc", "pfc_b_to_a",
             "pfc_status_string", "pfc_last_error", "pfc_set_coefficient_field", "pfc_diagnostics",
             "pfc_hflow_set_coefficient_field", "pfc_hflow_set_mass_field", "pfc_surface_cells",
-            "pfc_curvature_histogram", "pfc_batch_step_host", "pfc_batch_host_wait")
+            "pfc_curvature_histogram", "pfc_batch_step_host", "pfc_batch_host_wait", "pfc_hflow_batch_create",
+            "pfc_hflow_batch_destroy", "pfc_hflow_batch_field", "pfc_hflow_batch_run")
 
 
 class PfcError(RuntimeError):
@@ -149,6 +150,12 @@ def load_library():
             "pfc_batch_timing": ([vp, ctypes.c_int], ctypes.c_int),
             "pfc_batch_step_host": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dp, vp], ctypes.c_int),
             "pfc_batch_host_wait": ([vp, vp], ctypes.c_int),
+            "pfc_hflow_batch_create": ([P, dp, ctypes.c_int32, ctypes.POINTER(_CHFlow), ctypes.POINTER(vp)],
+                                       ctypes.c_int),
+            "pfc_hflow_batch_destroy": ([vp], None),
+            "pfc_hflow_batch_field": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp], ctypes.c_int),
+            "pfc_hflow_batch_run": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int32,
+                                     ctypes.POINTER(ctypes.c_int32), dp, vp], ctypes.c_int),
             "pfc_batch_last_timing": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
                                       ctypes.c_int),
             "pfc_energy_and_grad_noalloc": ([P, vp, vp, dp, vp], ctypes.c_int),
@@ -505,6 +512,69 @@ class HFlow:
         _check(self._lib.pfc_hflow_run(self._h, self._vec(A, "A"), self._vec(m, "m"), self._vec(v, "v"), int(nsteps),
                                        ctypes.byref(t), tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
                                        if trace else None, _stream(stream)))
+        self.t = t.value
+        return tr
+
+
+class HFlowBatch:
+    """Many flows of Alg. 1 on grids of one size (FP32), advanced together:
+    one launch per kernel of an iteration for all of them.  ``probs`` share
+    nx, ny, nz; ``m0s`` are their masses; the blur and Adam's settings are
+    shared.  Fields are lists of CUDA float32 tensors shaped (3, nz, ny, nx)."""
+
+    def __init__(self, probs, m0s, lr: float = 1e-3, betas=(0.9, 0.999), adam_eps: float = 1e-8,
+                 blur_sigma: float = 2.0, blur_radius: int = 0):
+        self.probs = list(probs)
+        self._lib = load_library()
+        arr = (_CProblem * len(self.probs))(*[p._c() for p in self.probs])
+        m0 = np.ascontiguousarray(np.broadcast_to(np.asarray(m0s, dtype=np.float64), (len(self.probs),)))
+        hp = _CHFlow(0.0, float(lr), float(betas[0]), float(betas[1]), float(adam_eps), float(blur_sigma),
+                     int(blur_radius), 0)
+        self._h = ctypes.c_void_p()
+        _check(self._lib.pfc_hflow_batch_create(arr, m0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                len(self.probs), ctypes.byref(hp), ctypes.byref(self._h)))
+        self.t = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pfc_hflow_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ptrs(self, ts, name, shape3=True):
+        if len(ts) != len(self.probs):
+            raise ValueError(f"{name}: one tensor per instance")
+        out = []
+        for k, (t, p) in enumerate(zip(ts, self.probs)):
+            want = (3, p.nz, p.ny, p.nx) if shape3 else (p.nz, p.ny, p.nx)
+            if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+                raise TypeError(f"{name}[{k}] must be a CUDA float32 tensor")
+            if tuple(t.shape) != want or not t.is_contiguous():
+                raise ValueError(f"{name}[{k}] must be contiguous with shape {want}")
+            out.append(t.data_ptr())
+        return (ctypes.c_void_p * len(out))(*out)
+
+    def field(self, As, stream=None):
+        p = self.probs[0]
+        uts = [torch.empty((p.nz, p.ny, p.nx), dtype=torch.float32, device="cuda") for _ in self.probs]
+        _check(self._lib.pfc_hflow_batch_field(self._h, self._ptrs(As, "A"), self._ptrs(uts, "ut", False),
+                                               _stream(stream)))
+        return uts
+
+    def run(self, As, ms, vs, nsteps: int, trace: bool = True, stream=None):
+        """nsteps Adam steps of every instance in place; returns the trace
+        (n, nsteps, 5) if asked."""
+        tr = np.empty((len(self.probs), max(int(nsteps), 0), 5)) if trace else None
+        t = ctypes.c_int32(self.t)
+        _check(self._lib.pfc_hflow_batch_run(self._h, self._ptrs(As, "A"), self._ptrs(ms, "m"), self._ptrs(vs, "v"),
+                                             int(nsteps), ctypes.byref(t),
+                                             tr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if trace else None,
+                                             _stream(stream)))
         self.t = t.value
         return tr
 

@@ -170,3 +170,78 @@ def test_fp32_row_paths_and_misaligned_buffers(shape):
     f32.t = 0
     f32.run(Aa, ma, va, 3)
     assert (torch.linalg.norm(Am - Aa) / torch.linalg.norm(Aa)).item() < 1e-5
+
+
+def _batch_problems(shape, wells=(0, 1, 0)):
+    nz, ny, nx = shape
+    rng = np.random.default_rng(17)
+    probs, m0s = [], []
+    for k, well in enumerate(wells):
+        a = tuple(rng.uniform(-0.5, 0.5, 6) + np.array([1.0, 0, 1.0, 0, 0, 0]))
+        probs.append(pfc.Problem(nx=nx, ny=ny, nz=nz, eps=1.5 + 0.1 * k, h=1.0 - 0.05 * k, a=a, well=well,
+                                 prec="fp32"))
+        m0s.append(0.3 if well == 0 else -0.4)
+    return probs, m0s
+
+
+@pytest.mark.parametrize("shape", [(12, 10, 16), (9, 13, 11)])
+def test_flow_batch_matches_single_flows(shape):
+    """A batch of flows (different coefficients, eps, h, wells and masses,
+    one launch per kernel for all) gives each instance's single-flow result:
+    40 steps = one 32-step graph replay plus 8 direct steps, twice."""
+    probs, m0s = _batch_problems(shape)
+    rng = np.random.default_rng(18)
+    A0 = [torch.tensor((0.04 * rng.standard_normal((3,) + shape)).astype(np.float32), device="cuda")
+          for _ in probs]
+    fb = pfc.HFlowBatch(probs, m0s, lr=1e-3, blur_sigma=1.5)
+    As = [a.clone() for a in A0]
+    ms = [torch.zeros_like(a) for a in A0]
+    vs = [torch.zeros_like(a) for a in A0]
+    trb = fb.run(As, ms, vs, 40)
+    trb2 = fb.run(As, ms, vs, 40)
+    assert fb.t == 80
+    for k, (p, m0) in enumerate(zip(probs, m0s)):
+        fl = pfc.HFlow(p, m0=m0, lr=1e-3, blur_sigma=1.5)
+        A, m, v = A0[k].clone(), torch.zeros_like(A0[k]), torch.zeros_like(A0[k])
+        tr = fl.run(A, m, v, 40)
+        tr2 = fl.run(A, m, v, 40)
+        assert (torch.linalg.norm(As[k] - A) / torch.linalg.norm(A)).item() < 1e-6
+        assert (torch.linalg.norm(vs[k] - v) / torch.linalg.norm(v)).item() < 1e-5
+        for a, b in ((trb[k], tr), (trb2[k], tr2)):
+            np.testing.assert_allclose(a[:, 0], b[:, 0], rtol=1e-5)
+            np.testing.assert_allclose(a[:, 3], m0, atol=1e-6)
+            np.testing.assert_allclose(a[:, 4], b[:, 4])
+    ut = fb.field(As)
+    for k, p in enumerate(probs):
+        fl = pfc.HFlow(p, m0=m0s[k], lr=1e-3, blur_sigma=1.5)
+        assert torch.allclose(ut[k], fl.field(As[k]), rtol=0, atol=1e-6)
+
+
+def test_flow_batch_against_oracle_and_errors():
+    shape = (8, 12, 16)
+    probs, m0s = _batch_problems(shape, wells=(1, 0))
+    rng = np.random.default_rng(19)
+    A0 = [(0.04 * rng.standard_normal((3,) + shape)).astype(np.float32).astype(np.float64) for _ in probs]
+    fb = pfc.HFlowBatch(probs, m0s, lr=1e-3, blur_sigma=1.0)
+    As = [torch.tensor(a, dtype=torch.float32, device="cuda") for a in A0]
+    ms = [torch.zeros_like(a) for a in As]
+    vs = [torch.zeros_like(a) for a in As]
+    tr = fb.run(As, ms, vs, 2)
+    for k, p in enumerate(probs):
+        op = {"a": p.a, "eps": p.eps, "h": p.h, "xi": p.xi, "well": p.well}
+        fp = {"m0": m0s[k], "blur_sigma": 1.0, "lr": 1e-3}
+        Ao, _, _, _, tro = oracle.hflow_run(A0[k], np.zeros_like(A0[k]), np.zeros_like(A0[k]), op, fp, 2)
+        np.testing.assert_allclose(tr[k][:, 0], tro[:, 0], rtol=1e-4)
+        d = As[k].double().cpu().numpy() - A0[k]
+        do = Ao - A0[k]
+        assert np.linalg.norm(d - do) / np.linalg.norm(do) < 1e-3
+    # every instance must share the grid; the extensions are not batched
+    nz, ny, nx = shape
+    bad = probs + [pfc.Problem(nx=nx + 4, ny=ny, nz=nz, eps=1.5, a=(1, 0, 1, 0, 0, 0), prec="fp32")]
+    with pytest.raises(pfc.PfcError):
+        pfc.HFlowBatch(bad, m0s + [0.3])
+    with pytest.raises(pfc.PfcError):
+        pfc.HFlowBatch([pfc.Problem(nx=nx, ny=ny, nz=nz, eps=1.5, a=(1, 0, 1, 0, 0, 0), prec="fp32", mu=1.0,
+                                    theta=(1, 0, 0))], [0.3])
+    with pytest.raises(pfc.PfcError):
+        pfc.HFlowBatch([pfc.Problem(nx=nx, ny=ny, nz=nz, eps=1.5, a=(1, 0, 1, 0, 0, 0), prec="fp64")], [0.3])
