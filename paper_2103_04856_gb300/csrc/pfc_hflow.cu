@@ -153,7 +153,9 @@ struct BlurL {
     const T* in[MAXI];
     T* out[MAXI];
     int nx, ny, nz;
-    int zb;             // z blocks per instance
+    int zb;             // z blocks per instance (tiled kernel)
+    int n;              // instances
+    int chunk, nchunks; // line pieces per thread (window kernel)
     Weights w;
 };
 
@@ -191,10 +193,13 @@ __global__ void __launch_bounds__(kThreads) k_div(const __grid_constant__ DivL<T
 // Grid: x = tiles across x (32 wide, or kTileAx wide for AX 0), y = tiles
 // along the blurred axis (for AX 0: groups of 8 rows), z = the remaining
 // axis (looped when above the grid limit).
-template <typename T, int AX, int MAXI>
+// RT > 0: the radius is RT (the paper's blurs: 3 and 6 taps per side), the
+// weights sit in registers and the tap loops unroll; RT = 0: any radius.
+// Both sum the taps in the same order.
+template <typename T, int AX, int MAXI, int RT>
 __global__ void __launch_bounds__(256) k_blur(const __grid_constant__ BlurL<T, MAXI> BL)
 {
-    constexpr int L = kTileAx + 2 * kMaxRadius;
+    constexpr int L = kTileAx + 2 * (RT ? RT : kMaxRadius);
     __shared__ T s[AX == 0 ? 8 : L][AX == 0 ? L : 32];
     const int inst = blockIdx.z / BL.zb, zo = blockIdx.z - inst * BL.zb;
     const T* __restrict__ in = BL.in[inst];
@@ -202,7 +207,16 @@ __global__ void __launch_bounds__(256) k_blur(const __grid_constant__ BlurL<T, M
     const int nx = BL.nx, ny = BL.ny, nz = BL.nz;
     const Weights& w = BL.w;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int R = w.R;
+    const int R = RT ? RT : w.R;
+    T wk[RT ? 2 * RT + 1 : 1];
+    if constexpr (RT > 0) {
+#pragma unroll
+        for (int j = 0; j <= 2 * RT; ++j) wk[j] = wget<T>(w, j);
+    }
+    auto tap = [&](int j) -> T {
+        if constexpr (RT > 0) return wk[j];
+        else return wget<T>(w, j);
+    };
     const long pls = (long)nx * ny;
     const int n_other = AX == 2 ? ny : nz;
     for (int o = zo; o < n_other; o += BL.zb) {
@@ -215,7 +229,11 @@ __global__ void __launch_bounds__(256) k_blur(const __grid_constant__ BlurL<T, M
             if (y < ny)
                 for (int k = tx; k < kTileAx && x0 + k < nx; k += 32) {
                     T acc = 0;
-                    for (int j = 0; j <= 2 * R; ++j) acc += wget<T>(w, j) * s[ty][k + j];
+#pragma unroll
+                    for (int j = 0; j <= 2 * (RT ? RT : kMaxRadius); ++j) {
+                        if (!RT && j > 2 * R) break;
+                        acc += tap(j) * s[ty][k + j];
+                    }
                     out[row + x0 + k] = acc;
                 }
         } else {
@@ -230,11 +248,74 @@ __global__ void __launch_bounds__(256) k_blur(const __grid_constant__ BlurL<T, M
             if (x < nx)
                 for (int k = ty; k < kTileAx && c0 + k < n_ax; k += 8) {
                     T acc = 0;
-                    for (int j = 0; j <= 2 * R; ++j) acc += wget<T>(w, j) * s[k + j][tx];
+#pragma unroll
+                    for (int j = 0; j <= 2 * (RT ? RT : kMaxRadius); ++j) {
+                        if (!RT && j > 2 * R) break;
+                        acc += tap(j) * s[k + j][tx];
+                    }
                     out[base + (long)(c0 + k) * stride] = acc;
                 }
         }
         __syncthreads();
+    }
+}
+
+// The y and z passes for the paper's radii (RT = 3 or 6) as a sliding
+// window in registers: a thread walks `chunk` outputs along one line (lanes
+// on consecutive x, so every load is coalesced), keeping the 2 RT + 1 inputs
+// of the current output; each step loads one new input and replaces the
+// oldest.  The tap loop is unrolled over a whole window so that slot
+// (q + j) % W is a compile-time register: no moves, no shared memory, no
+// barriers.  The taps are summed in the same order as in k_blur.
+template <typename T, int AX, int MAXI, int RT>
+__global__ void __launch_bounds__(256) k_blur_win(const __grid_constant__ BlurL<T, MAXI> BL)
+{
+    constexpr int W = 2 * RT + 1;
+    const int nx = BL.nx, ny = BL.ny, nz = BL.nz;
+    const int n_ax = AX == 1 ? ny : nz, n_oth = AX == 1 ? nz : ny;
+    const long stride = AX == 1 ? (long)nx : (long)nx * ny;
+    long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    const long total = (long)nx * BL.nchunks * n_oth * BL.n;
+    if (t >= total) return;
+    const int x = (int)(t % nx);
+    t /= nx;
+    const int ch = (int)(t % BL.nchunks);
+    t /= BL.nchunks;
+    const int o = (int)(t % n_oth);
+    const int inst = (int)(t / n_oth);
+    const long base = (AX == 1 ? (long)o * nx * ny : (long)o * nx) + x;
+    const T* __restrict__ in = BL.in[inst] + base;
+    T* __restrict__ out = BL.out[inst] + base;
+    const int c0 = ch * BL.chunk, c1 = min(n_ax, c0 + BL.chunk);
+    if (c0 >= c1) return;
+    T wk[W], win[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        wk[j] = wget<T>(BL.w, j);
+        win[j] = in[(long)nbr(c0, j - RT, n_ax) * stride];
+    }
+    int nxt = nbr(c0, RT + 1, n_ax);      // the input entering the window next
+    int c = c0;
+    for (; c + W <= c1; c += W) {
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            T acc = 0;
+#pragma unroll
+            for (int j = 0; j < W; ++j) acc += wk[j] * win[(q + j) % W];
+            out[(long)(c + q) * stride] = acc;
+            win[q] = in[(long)nxt * stride];
+            nxt = nxt + 1 == n_ax ? 0 : nxt + 1;
+        }
+    }
+    for (; c < c1; ++c) {                 // the rest, window in natural order
+        T acc = 0;
+#pragma unroll
+        for (int j = 0; j < W; ++j) acc += wk[j] * win[j];
+        out[(long)c * stride] = acc;
+#pragma unroll
+        for (int j = 0; j + 1 < W; ++j) win[j] = win[j + 1];
+        win[W - 1] = in[(long)nxt * stride];
+        nxt = nxt + 1 == n_ax ? 0 : nxt + 1;
     }
 }
 
@@ -243,12 +324,34 @@ template <typename T, int AX, int MAXI>
 static void launch_blur(BlurL<T, MAXI>& BL, int n_inst, cudaStream_t s)
 {
     const int nx = BL.nx, ny = BL.ny, nz = BL.nz;
+    BL.n = n_inst;
+    const int R = BL.w.R;
+    if (AX != 0 && (R == 3 || R == 6)) {
+        // pieces per line: enough threads to fill the GPU twice over, pieces no
+        // shorter than one window
+        const int n_ax = AX == 1 ? ny : nz, n_oth = AX == 1 ? nz : ny;
+        const long lines = (long)nx * n_oth * n_inst;
+        const long want = 152L * 2048 * 2;
+        long pieces = (want + lines - 1) / lines;
+        const long max_pieces = (n_ax + 2 * R) / (2 * R + 1);
+        if (pieces > max_pieces) pieces = max_pieces;
+        if (pieces < 1) pieces = 1;
+        BL.chunk = (int)((n_ax + pieces - 1) / pieces);
+        BL.nchunks = (n_ax + BL.chunk - 1) / BL.chunk;
+        const long total = lines * BL.nchunks;
+        const unsigned blocks = (unsigned)((total + 255) / 256);
+        if (R == 6) k_blur_win<T, AX, MAXI, 6><<<blocks, 256, 0, s>>>(BL);
+        else k_blur_win<T, AX, MAXI, 3><<<blocks, 256, 0, s>>>(BL);
+        return;
+    }
     const int n_other = AX == 2 ? ny : nz;
     const int cap = 65535 / n_inst;
     BL.zb = n_other < cap ? n_other : cap;
     const dim3 grid = AX == 0 ? dim3((nx + kTileAx - 1) / kTileAx, (ny + 7) / 8, BL.zb * n_inst)
                               : dim3((nx + 31) / 32, ((AX == 1 ? ny : nz) + kTileAx - 1) / kTileAx, BL.zb * n_inst);
-    k_blur<T, AX, MAXI><<<grid, dim3(32, 8), 0, s>>>(BL);
+    if (R == 6) k_blur<T, AX, MAXI, 6><<<grid, dim3(32, 8), 0, s>>>(BL);
+    else if (R == 3) k_blur<T, AX, MAXI, 3><<<grid, dim3(32, 8), 0, s>>>(BL);
+    else k_blur<T, AX, MAXI, 0><<<grid, dim3(32, 8), 0, s>>>(BL);
 }
 
 // dG/dA from the blurred gradient gb, then Adam (Kingma and Ba) on A with
