@@ -319,39 +319,209 @@ __global__ void __launch_bounds__(256) k_blur_win(const __grid_constant__ BlurL<
     }
 }
 
+// FP32 x pass for rows of 4 to 128 values with nx % 4 == 0 (the paper's
+// 100^3 grids): the lanes of a row hold x = 4k .. 4k+3 as one float4 each and
+// take the taps around their outputs from the neighbouring lanes' registers
+// by shuffles, wrapping inside the row (periodic).  32 / (nx/4) rows share a
+// warp; a warp covers kRowIt such groups with every load issued before the
+// arithmetic.  Taps are summed in the same order as in k_blur.
+constexpr int kRowIt = 4;
+
+__device__ __forceinline__ float f4c(const float4& q, int e)
+{
+    return e == 0 ? q.x : e == 1 ? q.y : e == 2 ? q.z : q.w;
+}
+
+template <int MAXI, int RT>
+__global__ void __launch_bounds__(256) k_blurx4(const __grid_constant__ BlurL<float, MAXI> BL)
+{
+    constexpr int NB = (RT + 3) / 4;           // float4 neighbours needed on each side
+    constexpr int E = 4 * (2 * NB + 1);        // window: x = 4(k - NB) .. 4(k + NB) + 3
+    const int n4 = BL.nx >> 2, rpw = 32 / n4;
+    const int lane = threadIdx.x & 31, r = lane / n4, k = lane - r * n4;
+    const long plane_rows = (long)BL.ny * BL.nz, rows = plane_rows * BL.n;
+    const long g = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+    if (g * kRowIt * rpw >= rows) return;      // whole warps only: the shuffles need all lanes
+    float wk[2 * RT + 1];
+#pragma unroll
+    for (int j = 0; j <= 2 * RT; ++j) wk[j] = BL.w.wf[j];
+    int src[2 * NB + 1];
+#pragma unroll
+    for (int d = 0; d <= 2 * NB; ++d) {
+        int kk = (k + d - NB) % n4;
+        if (kk < 0) kk += n4;
+        src[d] = r < rpw ? r * n4 + kk : lane;
+    }
+    float4 v[kRowIt];
+    float* op[kRowIt];
+#pragma unroll
+    for (int it = 0; it < kRowIt; ++it) {
+        const long row = (g * kRowIt + it) * rpw + r;
+        v[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+        op[it] = nullptr;
+        if (r < rpw && row < rows) {
+            const int inst = (int)(row / plane_rows);
+            const long off = (row - inst * plane_rows) * BL.nx + 4 * k;
+            v[it] = *reinterpret_cast<const float4*>(BL.in[inst] + off);
+            op[it] = BL.out[inst] + off;
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < kRowIt; ++it) {
+        float c[E];
+#pragma unroll
+        for (int d = 0; d <= 2 * NB; ++d)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int ox = 4 * (d - NB) + e;           // x offset from 4k
+                if (ox < -RT || ox > 3 + RT) continue;     // never a tap
+                const float val = f4c(v[it], e);
+                c[4 * d + e] = d == NB ? val : __shfl_sync(0xffffffffu, val, src[d]);
+            }
+        float o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float acc = 0.f;
+#pragma unroll
+            for (int j = 0; j <= 2 * RT; ++j) acc += wk[j] * c[4 * NB + e - RT + j];
+            o[e] = acc;
+        }
+        if (op[it]) *reinterpret_cast<float4*>(op[it]) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+// FP32 y and z passes with nx % 4 == 0: k_blur_win with four x-columns per
+// thread as one float4 (16-byte loads and stores, a window of 2 RT + 1
+// float4 in registers).
+template <int AX, int MAXI, int RT>
+__global__ void __launch_bounds__(256) k_blur_win4(const __grid_constant__ BlurL<float, MAXI> BL)
+{
+    constexpr int W = 2 * RT + 1;
+    const int nx = BL.nx, ny = BL.ny, nz = BL.nz, nx4 = nx >> 2;
+    const int n_ax = AX == 1 ? ny : nz, n_oth = AX == 1 ? nz : ny;
+    const long stride = AX == 1 ? (long)nx : (long)nx * ny;
+    long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    const long total = (long)nx4 * BL.nchunks * n_oth * BL.n;
+    if (t >= total) return;
+    const int x4 = (int)(t % nx4);
+    t /= nx4;
+    const int ch = (int)(t % BL.nchunks);
+    t /= BL.nchunks;
+    const int o = (int)(t % n_oth);
+    const int inst = (int)(t / n_oth);
+    const long base = (AX == 1 ? (long)o * nx * ny : (long)o * nx) + 4 * x4;
+    const float* __restrict__ in = BL.in[inst] + base;
+    float* __restrict__ out = BL.out[inst] + base;
+    const int c0 = ch * BL.chunk, c1 = min(n_ax, c0 + BL.chunk);
+    if (c0 >= c1) return;
+    auto ld = [&](int c) { return *reinterpret_cast<const float4*>(in + (long)c * stride); };
+    auto st = [&](int c, float4 q) { *reinterpret_cast<float4*>(out + (long)c * stride) = q; };
+    float wk[W];
+    float4 win[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        wk[j] = BL.w.wf[j];
+        win[j] = ld(nbr(c0, j - RT, n_ax));
+    }
+    int nxt = nbr(c0, RT + 1, n_ax);
+    int c = c0;
+    for (; c + W <= c1; c += W) {
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                const float4 s = win[(q + j) % W];
+                acc.x += wk[j] * s.x; acc.y += wk[j] * s.y; acc.z += wk[j] * s.z; acc.w += wk[j] * s.w;
+            }
+            st(c + q, acc);
+            win[q] = ld(nxt);
+            nxt = nxt + 1 == n_ax ? 0 : nxt + 1;
+        }
+    }
+    for (; c < c1; ++c) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            acc.x += wk[j] * win[j].x; acc.y += wk[j] * win[j].y; acc.z += wk[j] * win[j].z; acc.w += wk[j] * win[j].w;
+        }
+        st(c, acc);
+#pragma unroll
+        for (int j = 0; j + 1 < W; ++j) win[j] = win[j + 1];
+        win[W - 1] = ld(nxt);
+        nxt = nxt + 1 == n_ax ? 0 : nxt + 1;
+    }
+}
+
 // One blur pass over every instance of a descriptor table (in/out filled).
+// Pieces per line for the window kernels: enough threads to fill the GPU
+// about twice, no piece shorter than one window when the line holds one.
+static void blur_pieces(int n_ax, int W, long lines, long want, int* chunk, int* nchunks)
+{
+    long pieces = (want + lines - 1) / lines;
+    const long max_pieces = n_ax >= W ? n_ax / W : 1;
+    if (pieces > max_pieces) pieces = max_pieces;
+    if (pieces < 1) pieces = 1;
+    *chunk = (int)((n_ax + pieces - 1) / pieces);
+    *nchunks = (n_ax + *chunk - 1) / *chunk;
+}
+
+// FP32 with nx % 4 == 0, 16-byte aligned buffers and the paper's radii: the
+// float4 kernels (x: shuffles within a warp for rows of up to 128 values;
+// y, z: float4 windows).  Other FP32 and FP64 cases: register windows for y
+// and z at radii 3 and 6, shared-memory tiles otherwise.
 template <typename T, int AX, int MAXI>
 static void launch_blur(BlurL<T, MAXI>& BL, int n_inst, cudaStream_t s)
 {
     const int nx = BL.nx, ny = BL.ny, nz = BL.nz;
     BL.n = n_inst;
     const int R = BL.w.R;
-    if (AX != 0 && (R == 3 || R == 6)) {
-        // pieces per line: enough threads to fill the GPU twice over, pieces no
-        // shorter than one window
-        const int n_ax = AX == 1 ? ny : nz, n_oth = AX == 1 ? nz : ny;
-        const long lines = (long)nx * n_oth * n_inst;
-        const long want = 152L * 2048 * 2;
-        long pieces = (want + lines - 1) / lines;
-        const long max_pieces = (n_ax + 2 * R) / (2 * R + 1);
-        if (pieces > max_pieces) pieces = max_pieces;
-        if (pieces < 1) pieces = 1;
-        BL.chunk = (int)((n_ax + pieces - 1) / pieces);
-        BL.nchunks = (n_ax + BL.chunk - 1) / BL.chunk;
-        const long total = lines * BL.nchunks;
-        const unsigned blocks = (unsigned)((total + 255) / 256);
-        if (R == 6) k_blur_win<T, AX, MAXI, 6><<<blocks, 256, 0, s>>>(BL);
-        else k_blur_win<T, AX, MAXI, 3><<<blocks, 256, 0, s>>>(BL);
-        return;
+    const bool paper_r = R == 3 || R == 6;
+    bool vec = sizeof(T) == 4 && nx % 4 == 0 && paper_r && (AX != 0 || nx <= 128);
+    for (int k = 0; vec && k < n_inst; ++k)
+        vec = reinterpret_cast<uintptr_t>(BL.in[k]) % 16 == 0 && reinterpret_cast<uintptr_t>(BL.out[k]) % 16 == 0;
+    if constexpr (sizeof(T) == 4 && AX == 0) {
+        if (vec) {
+            const long rows = (long)ny * nz * n_inst;
+            const long per_warp = (long)(32 / (nx / 4)) * kRowIt;
+            const unsigned blocks = (unsigned)(((rows + per_warp - 1) / per_warp + 7) / 8);
+            if (R == 6) k_blurx4<MAXI, 6><<<blocks, 256, 0, s>>>(BL);
+            else k_blurx4<MAXI, 3><<<blocks, 256, 0, s>>>(BL);
+            return;
+        }
+    }
+    if constexpr (sizeof(T) == 4 && AX != 0) {
+        if (vec) {
+            const int n_ax = AX == 1 ? ny : nz, n_oth = AX == 1 ? nz : ny;
+            const long lines = (long)(nx / 4) * n_oth * n_inst;
+            blur_pieces(n_ax, 2 * R + 1, lines, 152L * 1024, &BL.chunk, &BL.nchunks);
+            const unsigned blocks = (unsigned)((lines * BL.nchunks + 255) / 256);
+            if (R == 6) k_blur_win4<AX, MAXI, 6><<<blocks, 256, 0, s>>>(BL);
+            else k_blur_win4<AX, MAXI, 3><<<blocks, 256, 0, s>>>(BL);
+            return;
+        }
+    }
+    if constexpr (AX != 0) {
+        if (paper_r) {
+            const int n_ax = AX == 1 ? ny : nz, n_oth = AX == 1 ? nz : ny;
+            const long lines = (long)nx * n_oth * n_inst;
+            blur_pieces(n_ax, 2 * R + 1, lines, 152L * 2048 * 2, &BL.chunk, &BL.nchunks);
+            const unsigned blocks = (unsigned)((lines * BL.nchunks + 255) / 256);
+            if (R == 6) k_blur_win<T, AX, MAXI, 6><<<blocks, 256, 0, s>>>(BL);
+            else k_blur_win<T, AX, MAXI, 3><<<blocks, 256, 0, s>>>(BL);
+            return;
+        }
     }
     const int n_other = AX == 2 ? ny : nz;
     const int cap = 65535 / n_inst;
     BL.zb = n_other < cap ? n_other : cap;
     const dim3 grid = AX == 0 ? dim3((nx + kTileAx - 1) / kTileAx, (ny + 7) / 8, BL.zb * n_inst)
                               : dim3((nx + 31) / 32, ((AX == 1 ? ny : nz) + kTileAx - 1) / kTileAx, BL.zb * n_inst);
-    if (R == 6) k_blur<T, AX, MAXI, 6><<<grid, dim3(32, 8), 0, s>>>(BL);
-    else if (R == 3) k_blur<T, AX, MAXI, 3><<<grid, dim3(32, 8), 0, s>>>(BL);
-    else k_blur<T, AX, MAXI, 0><<<grid, dim3(32, 8), 0, s>>>(BL);
+    if constexpr (AX == 0) {
+        if (R == 6) { k_blur<T, AX, MAXI, 6><<<grid, dim3(32, 8), 0, s>>>(BL); return; }
+        if (R == 3) { k_blur<T, AX, MAXI, 3><<<grid, dim3(32, 8), 0, s>>>(BL); return; }
+    }
+    k_blur<T, AX, MAXI, 0><<<grid, dim3(32, 8), 0, s>>>(BL);
 }
 
 // dG/dA from the blurred gradient gb, then Adam (Kingma and Ba) on A with

@@ -144,6 +144,35 @@ def test_paper_setting_generates_a_viable_shape():
     assert cells.shape[0] > 1000 and float(cells[:, 0].double().sum()) > 1.0
 
 
+@pytest.mark.parametrize("shape,sigma", [((30, 26, 12), 2.0),    # x: 10 rows of 3 float4 per warp
+                                         ((14, 40, 128), 1.0),   # x: one row of 32 float4 per warp
+                                         ((17, 9, 100), 2.0),    # the paper's row length; y shorter than a window
+                                         ((10, 28, 132), 2.0),   # x: rows above 128 values take the tiles
+                                         ((13, 27, 18), 2.0),    # nx % 4 != 0: scalar windows
+                                         ((9, 11, 20), 0.8)])    # radius 3 below a window on every axis
+def test_fp32_blur_paths_vs_oracle(shape, sigma):
+    """The FP32 blur passes (Alg. 1's Gaussian k) take float4 kernels when
+    rows hold a multiple of 4 values: shuffles across a warp along x, register
+    windows along y and z; the shapes above reach each variant, the tails of
+    the windows and the wrap of every axis.  Field and gradient against the
+    oracle in FP64.  The field is linear in A and checks the blur kernels
+    alone; the gradient's bar grows with how far rounding the field to FP32
+    moves the oracle's own dF/du (strongly blurred fields vary by a few 1e-3
+    around m0, where the FP32 energy gradient is ill-conditioned)."""
+    flow, Ad, A, op, fp = setup(shape, prec="fp32", sigma=sigma)
+    ut = flow.field(Ad).double().cpu().numpy()
+    uo = oracle.hflow_field(A, op, fp)
+    assert np.max(np.abs(ut - uo)) < 1e-6
+    G, gA = flow.grad(Ad)
+    Go, gAo = oracle.hflow_grad(A, op, fp)
+    assert G == pytest.approx(Go, rel=1e-4)
+    _, gu = oracle.energy_and_grad(uo, op)
+    _, gu32 = oracle.energy_and_grad(uo.astype(np.float32).astype(np.float64), op)
+    sens = np.linalg.norm(gu32 - gu) / np.linalg.norm(gu)
+    gA = gA.double().cpu().numpy()
+    assert np.linalg.norm(gA - gAo) / np.linalg.norm(gAo) < max(1e-3, 10 * sens)
+
+
 @pytest.mark.parametrize("shape", [(9, 10, 11), (8, 12, 20)])
 def test_fp32_row_paths_and_misaligned_buffers(shape):
     """FP32 flow kernels take a float4 path when rows hold a multiple of 4
@@ -184,8 +213,8 @@ def _batch_problems(shape, wells=(0, 1, 0)):
     return probs, m0s
 
 
-@pytest.mark.parametrize("shape", [(12, 10, 16), (9, 13, 11)])
-def test_flow_batch_matches_single_flows(shape):
+@pytest.mark.parametrize("shape,sigma", [((12, 10, 16), 1.5), ((9, 13, 11), 2.0), ((28, 13, 20), 2.0)])
+def test_flow_batch_matches_single_flows(shape, sigma):
     """A batch of flows (different coefficients, eps, h, wells and masses,
     one launch per kernel for all) gives each instance's single-flow result:
     40 steps = one 32-step graph replay plus 8 direct steps, twice."""
@@ -193,7 +222,7 @@ def test_flow_batch_matches_single_flows(shape):
     rng = np.random.default_rng(18)
     A0 = [torch.tensor((0.04 * rng.standard_normal((3,) + shape)).astype(np.float32), device="cuda")
           for _ in probs]
-    fb = pfc.HFlowBatch(probs, m0s, lr=1e-3, blur_sigma=1.5)
+    fb = pfc.HFlowBatch(probs, m0s, lr=1e-3, blur_sigma=sigma)
     As = [a.clone() for a in A0]
     ms = [torch.zeros_like(a) for a in A0]
     vs = [torch.zeros_like(a) for a in A0]
@@ -201,7 +230,7 @@ def test_flow_batch_matches_single_flows(shape):
     trb2 = fb.run(As, ms, vs, 40)
     assert fb.t == 80
     for k, (p, m0) in enumerate(zip(probs, m0s)):
-        fl = pfc.HFlow(p, m0=m0, lr=1e-3, blur_sigma=1.5)
+        fl = pfc.HFlow(p, m0=m0, lr=1e-3, blur_sigma=sigma)
         A, m, v = A0[k].clone(), torch.zeros_like(A0[k]), torch.zeros_like(A0[k])
         tr = fl.run(A, m, v, 40)
         tr2 = fl.run(A, m, v, 40)
@@ -213,7 +242,7 @@ def test_flow_batch_matches_single_flows(shape):
             np.testing.assert_allclose(a[:, 4], b[:, 4])
     ut = fb.field(As)
     for k, p in enumerate(probs):
-        fl = pfc.HFlow(p, m0=m0s[k], lr=1e-3, blur_sigma=1.5)
+        fl = pfc.HFlow(p, m0=m0s[k], lr=1e-3, blur_sigma=sigma)
         assert torch.allclose(ut[k], fl.field(As[k]), rtol=0, atol=1e-6)
 
 
