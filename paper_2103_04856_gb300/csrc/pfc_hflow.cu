@@ -591,6 +591,10 @@ __global__ void __launch_bounds__(kThreads) k_adam(const __grid_constant__ AdamL
 // instructions of the scalar forms.
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+// Streams touched once per iteration (Adam's A, m, v): evict-first loads and
+// stores, so that they do not push the stencils' reused fields out of L2.
+__device__ __forceinline__ float4 ld4s(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void st4s(float* p, float4 v) { __stcs(reinterpret_cast<float4*>(p), v); }
 
 template <int MAXI>
 __global__ void __launch_bounds__(kThreads) k_div4(const __grid_constant__ DivL<float, MAXI> L)
@@ -653,6 +657,16 @@ __global__ void __launch_bounds__(kThreads) k_adam4(const __grid_constant__ Adam
         const float4 yp = ld4(gb + pl + (long)nbr(w.y, 1, f.ny) * f.nx + x);
         const float4 zm = ld4(gb + (long)nbr(w.z, -1, f.nz) * pls + col);
         const float4 zp = ld4(gb + (long)nbr(w.z, 1, f.nz) * pls + col);
+        float4 m4[3], v4[3], a4[3];     // all state loads in flight before the arithmetic
+        if (!only_grad) {
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                const long k = cc * n + i;
+                m4[cc] = ld4s(m + k);
+                v4[cc] = ld4s(v + k);
+                a4[cc] = ld4s(A + k);
+            }
+        }
         float4 g[3];
         g[0] = make_float4(sg * (gm - c.y), sg * (c.x - c.z), sg * (c.y - c.w), sg * (c.z - gp));
         g[1] = make_float4(sg * (ym.x - yp.x), sg * (ym.y - yp.y), sg * (ym.z - yp.z), sg * (ym.w - yp.w));
@@ -671,9 +685,9 @@ __global__ void __launch_bounds__(kThreads) k_adam4(const __grid_constant__ Adam
                 st4(m + k, g[cc]);
                 continue;
             }
-            const float4 m4 = ld4(m + k), v4 = ld4(v + k), a4 = ld4(A + k);
-            const float mm[4] = { m4.x, m4.y, m4.z, m4.w }, vv[4] = { v4.x, v4.y, v4.z, v4.w };
-            const float aa[4] = { a4.x, a4.y, a4.z, a4.w };
+            const float mm[4] = { m4[cc].x, m4[cc].y, m4[cc].z, m4[cc].w };
+            const float vv[4] = { v4[cc].x, v4[cc].y, v4[cc].z, v4[cc].w };
+            const float aa[4] = { a4[cc].x, a4[cc].y, a4[cc].z, a4[cc].w };
             float mo[4], vo[4], ao[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -681,9 +695,9 @@ __global__ void __launch_bounds__(kThreads) k_adam4(const __grid_constant__ Adam
                 vo[j] = b2 * vv[j] + (1.0f - b2) * gg[j] * gg[j];
                 ao[j] = aa[j] - lr * (mo[j] * c1) / (sqrtf(vo[j] * c2) + ae);
             }
-            st4(m + k, make_float4(mo[0], mo[1], mo[2], mo[3]));
-            st4(v + k, make_float4(vo[0], vo[1], vo[2], vo[3]));
-            st4(A + k, make_float4(ao[0], ao[1], ao[2], ao[3]));
+            st4s(m + k, make_float4(mo[0], mo[1], mo[2], mo[3]));
+            st4s(v + k, make_float4(vo[0], vo[1], vo[2], vo[3]));
+            st4s(A + k, make_float4(ao[0], ao[1], ao[2], ao[3]));
         }
     }
     flow_finish<float>(f, sabs, gmax, [&](double s0, double s1) {
