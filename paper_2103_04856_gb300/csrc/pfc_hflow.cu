@@ -326,6 +326,7 @@ __global__ void __launch_bounds__(256) k_blur_win(const __grid_constant__ BlurL<
 // warp; a warp covers kRowIt such groups with every load issued before the
 // arithmetic.  Taps are summed in the same order as in k_blur.
 constexpr int kRowIt = 4;
+constexpr int kPrefetch = 3;     // extra ring slots of the float4 window
 
 __device__ __forceinline__ float f4c(const float4& q, int e)
 {
@@ -339,31 +340,32 @@ __global__ void __launch_bounds__(256) k_blurx4(const __grid_constant__ BlurL<fl
     constexpr int E = 4 * (2 * NB + 1);        // window: x = 4(k - NB) .. 4(k + NB) + 3
     const int n4 = BL.nx >> 2, rpw = 32 / n4;
     const int lane = threadIdx.x & 31, r = lane / n4, k = lane - r * n4;
-    const long plane_rows = (long)BL.ny * BL.nz, rows = plane_rows * BL.n;
-    const long g = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+    const int rows = BL.ny * BL.nz;            // of this instance (blockIdx.y)
+    const int g = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (g * kRowIt * rpw >= rows) return;      // whole warps only: the shuffles need all lanes
+    const float* __restrict__ in = BL.in[blockIdx.y];
+    float* __restrict__ out = BL.out[blockIdx.y];
     float wk[2 * RT + 1];
 #pragma unroll
     for (int j = 0; j <= 2 * RT; ++j) wk[j] = BL.w.wf[j];
     int src[2 * NB + 1];
 #pragma unroll
     for (int d = 0; d <= 2 * NB; ++d) {
-        int kk = (k + d - NB) % n4;
-        if (kk < 0) kk += n4;
+        int kk = k + d - NB;
+        while (kk < 0) kk += n4;
+        while (kk >= n4) kk -= n4;
         src[d] = r < rpw ? r * n4 + kk : lane;
     }
     float4 v[kRowIt];
-    float* op[kRowIt];
+    long off[kRowIt];
 #pragma unroll
     for (int it = 0; it < kRowIt; ++it) {
-        const long row = (g * kRowIt + it) * rpw + r;
+        const int row = (g * kRowIt + it) * rpw + r;
         v[it] = make_float4(0.f, 0.f, 0.f, 0.f);
-        op[it] = nullptr;
+        off[it] = -1;
         if (r < rpw && row < rows) {
-            const int inst = (int)(row / plane_rows);
-            const long off = (row - inst * plane_rows) * BL.nx + 4 * k;
-            v[it] = *reinterpret_cast<const float4*>(BL.in[inst] + off);
-            op[it] = BL.out[inst] + off;
+            off[it] = (long)row * BL.nx + 4 * k;
+            v[it] = *reinterpret_cast<const float4*>(in + off[it]);
         }
     }
 #pragma unroll
@@ -386,52 +388,50 @@ __global__ void __launch_bounds__(256) k_blurx4(const __grid_constant__ BlurL<fl
             for (int j = 0; j <= 2 * RT; ++j) acc += wk[j] * c[4 * NB + e - RT + j];
             o[e] = acc;
         }
-        if (op[it]) *reinterpret_cast<float4*>(op[it]) = make_float4(o[0], o[1], o[2], o[3]);
+        if (off[it] >= 0) *reinterpret_cast<float4*>(out + off[it]) = make_float4(o[0], o[1], o[2], o[3]);
     }
 }
 
 // FP32 y and z passes with nx % 4 == 0: k_blur_win with four x-columns per
-// thread as one float4 (16-byte loads and stores, a window of 2 RT + 1
-// float4 in registers).
-template <int AX, int MAXI, int RT>
+// thread as one float4 (16-byte loads and stores) and a ring of 2 RT + 1 + D
+// float4 in registers: the input loaded after output q is first needed D + 1
+// outputs later, so D + 1 loads per thread are in flight.  Instance =
+// blockIdx.y; all index arithmetic in 32 bits (the launch checks the sizes).
+template <int AX, int MAXI, int RT, int D>
 __global__ void __launch_bounds__(256) k_blur_win4(const __grid_constant__ BlurL<float, MAXI> BL)
 {
-    constexpr int W = 2 * RT + 1;
+    constexpr int W = 2 * RT + 1, S = W + D;
     const int nx = BL.nx, ny = BL.ny, nz = BL.nz, nx4 = nx >> 2;
     const int n_ax = AX == 1 ? ny : nz, n_oth = AX == 1 ? nz : ny;
     const long stride = AX == 1 ? (long)nx : (long)nx * ny;
-    long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    const long total = (long)nx4 * BL.nchunks * n_oth * BL.n;
-    if (t >= total) return;
-    const int x4 = (int)(t % nx4);
-    t /= nx4;
-    const int ch = (int)(t % BL.nchunks);
-    t /= BL.nchunks;
-    const int o = (int)(t % n_oth);
-    const int inst = (int)(t / n_oth);
+    unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (unsigned)(nx4 * BL.nchunks * n_oth)) return;
+    const int x4 = (int)(t % (unsigned)nx4);
+    t /= (unsigned)nx4;
+    const int ch = (int)(t % (unsigned)BL.nchunks);
+    const int o = (int)(t / (unsigned)BL.nchunks);
     const long base = (AX == 1 ? (long)o * nx * ny : (long)o * nx) + 4 * x4;
-    const float* __restrict__ in = BL.in[inst] + base;
-    float* __restrict__ out = BL.out[inst] + base;
+    const float* __restrict__ in = BL.in[blockIdx.y] + base;
+    float* __restrict__ out = BL.out[blockIdx.y] + base;
     const int c0 = ch * BL.chunk, c1 = min(n_ax, c0 + BL.chunk);
     if (c0 >= c1) return;
     auto ld = [&](int c) { return *reinterpret_cast<const float4*>(in + (long)c * stride); };
     auto st = [&](int c, float4 q) { *reinterpret_cast<float4*>(out + (long)c * stride) = q; };
     float wk[W];
-    float4 win[W];
+    float4 win[S];                        // slot s: input c - RT + s (rotating by whole rings)
 #pragma unroll
-    for (int j = 0; j < W; ++j) {
-        wk[j] = BL.w.wf[j];
-        win[j] = ld(nbr(c0, j - RT, n_ax));
-    }
-    int nxt = nbr(c0, RT + 1, n_ax);
+    for (int j = 0; j < W; ++j) wk[j] = BL.w.wf[j];
+#pragma unroll
+    for (int s = 0; s < S; ++s) win[s] = ld(nbr(c0, s - RT, n_ax));
+    int nxt = nbr(c0, S - RT, n_ax);      // the input entering the ring next
     int c = c0;
-    for (; c + W <= c1; c += W) {
+    for (; c + S <= c1; c += S) {
 #pragma unroll
-        for (int q = 0; q < W; ++q) {
+        for (int q = 0; q < S; ++q) {
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int j = 0; j < W; ++j) {
-                const float4 s = win[(q + j) % W];
+                const float4 s = win[(q + j) % S];
                 acc.x += wk[j] * s.x; acc.y += wk[j] * s.y; acc.z += wk[j] * s.z; acc.w += wk[j] * s.w;
             }
             st(c + q, acc);
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(256) k_blur_win4(const __grid_constant__ BlurL
             nxt = nxt + 1 == n_ax ? 0 : nxt + 1;
         }
     }
-    for (; c < c1; ++c) {
+    for (; c < c1; ++c) {                 // the rest, ring in natural order
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < W; ++j) {
@@ -447,13 +447,19 @@ __global__ void __launch_bounds__(256) k_blur_win4(const __grid_constant__ BlurL
         }
         st(c, acc);
 #pragma unroll
-        for (int j = 0; j + 1 < W; ++j) win[j] = win[j + 1];
-        win[W - 1] = ld(nxt);
+        for (int s = 0; s + 1 < S; ++s) win[s] = win[s + 1];
+        win[S - 1] = ld(nxt);
         nxt = nxt + 1 == n_ax ? 0 : nxt + 1;
     }
 }
 
-// One blur pass over every instance of a descriptor table (in/out filled).
+template <int MAXI>
+static void k_blurx4_launch(const BlurL<float, MAXI>& BL, int R, dim3 grid, cudaStream_t s)
+{
+    if (R == 6) k_blurx4<MAXI, 6><<<grid, 256, 0, s>>>(BL);
+    else k_blurx4<MAXI, 3><<<grid, 256, 0, s>>>(BL);
+}
+
 // Pieces per line for the window kernels: enough threads to fill the GPU
 // about twice, no piece shorter than one window when the line holds one.
 static void blur_pieces(int n_ax, int W, long lines, long want, int* chunk, int* nchunks)
@@ -477,27 +483,26 @@ static void launch_blur(BlurL<T, MAXI>& BL, int n_inst, cudaStream_t s)
     BL.n = n_inst;
     const int R = BL.w.R;
     const bool paper_r = R == 3 || R == 6;
-    bool vec = sizeof(T) == 4 && nx % 4 == 0 && paper_r && (AX != 0 || nx <= 128);
+    bool vec = sizeof(T) == 4 && nx % 4 == 0 && paper_r && (AX != 0 || nx <= 128) &&
+               (long)nx * ny * nz < (1L << 31);     // 32-bit indexing inside the instance
     for (int k = 0; vec && k < n_inst; ++k)
         vec = reinterpret_cast<uintptr_t>(BL.in[k]) % 16 == 0 && reinterpret_cast<uintptr_t>(BL.out[k]) % 16 == 0;
     if constexpr (sizeof(T) == 4 && AX == 0) {
         if (vec) {
-            const long rows = (long)ny * nz * n_inst;
             const long per_warp = (long)(32 / (nx / 4)) * kRowIt;
-            const unsigned blocks = (unsigned)(((rows + per_warp - 1) / per_warp + 7) / 8);
-            if (R == 6) k_blurx4<MAXI, 6><<<blocks, 256, 0, s>>>(BL);
-            else k_blurx4<MAXI, 3><<<blocks, 256, 0, s>>>(BL);
+            const long warps = ((long)ny * nz + per_warp - 1) / per_warp;
+            k_blurx4_launch<MAXI>(BL, R, dim3((unsigned)((warps + 7) / 8), n_inst), s);
             return;
         }
     }
     if constexpr (sizeof(T) == 4 && AX != 0) {
         if (vec) {
             const int n_ax = AX == 1 ? ny : nz, n_oth = AX == 1 ? nz : ny;
-            const long lines = (long)(nx / 4) * n_oth * n_inst;
-            blur_pieces(n_ax, 2 * R + 1, lines, 152L * 1024, &BL.chunk, &BL.nchunks);
-            const unsigned blocks = (unsigned)((lines * BL.nchunks + 255) / 256);
-            if (R == 6) k_blur_win4<AX, MAXI, 6><<<blocks, 256, 0, s>>>(BL);
-            else k_blur_win4<AX, MAXI, 3><<<blocks, 256, 0, s>>>(BL);
+            const long lines = (long)(nx / 4) * n_oth;
+            blur_pieces(n_ax, 2 * R + 1, lines * n_inst, 152L * 1024, &BL.chunk, &BL.nchunks);
+            const dim3 grid((unsigned)((lines * BL.nchunks + 255) / 256), n_inst);
+            if (R == 6) k_blur_win4<AX, MAXI, 6, kPrefetch><<<grid, 256, 0, s>>>(BL);
+            else k_blur_win4<AX, MAXI, 3, kPrefetch><<<grid, 256, 0, s>>>(BL);
             return;
         }
     }
