@@ -128,6 +128,17 @@ inline dim3 flow_grid(long n)
     return dim3((unsigned)(b < kFlowBlocks ? b : kFlowBlocks));
 }
 
+// Blocks per instance when n_inst instances share a launch (instances along
+// grid y): about two waves in all, so that each block strides over enough
+// work to pay for its closing reduction (a fence and a ticket per block).
+inline unsigned inst_blocks(long n, int n_inst)
+{
+    const unsigned b = flow_grid(n).x;
+    if (n_inst <= 1) return b;
+    const unsigned cap = (unsigned)((2 * kFlowBlocks + n_inst - 1) / n_inst);
+    return b < cap ? b : cap;
+}
+
 
 // Launch descriptors: one flow (MAXI = 1) or a batch of up to BATCH_MAX
 // flows on grids of one size, instance k = blockIdx.y (blockIdx.z / zb for
@@ -636,6 +647,102 @@ __global__ void __launch_bounds__(kThreads) k_div4(const __grid_constant__ DivL<
     flow_finish<float>(f, ms, 0.0f, [&](double s0, double) { f.hs[H_MASS] = s0 / (double)f.n; });
 }
 
+// div A + m followed by the x pass of the blur in one kernel, for FP32 rows
+// of 4 to 128 values with nx % 4 == 0 (the paper's 100^3 grids): the lanes
+// of a row hold x = 4k .. 4k+3 as one float4, take A_x at x - 1 and x + 4
+// from their neighbours by shuffles, form the row of div A + m in registers
+// and blur it along x as k_blurx4 does (same arithmetic, same tap order as
+// k_div4 followed by k_blurx4).  The mass is the mean of div A + m before
+// the blur, summed as k_div4 sums it.  Instance = blockIdx.y; blocks stride
+// over groups of rows.
+constexpr int kDivRowIt = 2;
+
+template <int MAXI, int RT>
+__global__ void __launch_bounds__(kThreads)
+k_div_blurx4(const __grid_constant__ DivL<float, MAXI> L, const __grid_constant__ Weights w)
+{
+    constexpr int NB = (RT + 3) / 4;           // float4 neighbours needed on each side (>= 1)
+    constexpr int E = 4 * (2 * NB + 1);
+    const Flow& f = L.f[blockIdx.y];
+    const float* __restrict__ A = L.A[blockIdx.y];
+    float* __restrict__ u = L.u[blockIdx.y];
+    const int nx = f.nx, ny = f.ny, nz = f.nz, n4 = nx >> 2, rpw = 32 / n4;
+    const long n = f.n, pls = (long)nx * ny;
+    const int lane = threadIdx.x & 31, r = lane / n4, k = lane - r * n4;
+    const int rows = ny * nz;
+    const float sg = (float)f.sg, m0 = (float)f.m0;
+    const float* mf = (const float*)f.mf;
+    float wk[2 * RT + 1];
+#pragma unroll
+    for (int j = 0; j <= 2 * RT; ++j) wk[j] = w.wf[j];
+    int src[2 * NB + 1];
+#pragma unroll
+    for (int d = 0; d <= 2 * NB; ++d) {
+        int kk = k + d - NB;
+        while (kk < 0) kk += n4;
+        while (kk >= n4) kk -= n4;
+        src[d] = r < rpw ? r * n4 + kk : lane;
+    }
+    float ms = 0.f;
+    constexpr int wpb = kThreads / 32;
+    for (int g = blockIdx.x * wpb + (threadIdx.x >> 5); g * kDivRowIt * rpw < rows; g += gridDim.x * wpb) {
+        float4 ax[kDivRowIt], yp[kDivRowIt], ym[kDivRowIt], zp[kDivRowIt], zm[kDivRowIt], mm[kDivRowIt];
+        long off[kDivRowIt];
+#pragma unroll
+        for (int it = 0; it < kDivRowIt; ++it) {
+            const int row = (g * kDivRowIt + it) * rpw + r;
+            const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+            ax[it] = yp[it] = ym[it] = zp[it] = zm[it] = zero;
+            mm[it] = make_float4(m0, m0, m0, m0);
+            off[it] = -1;
+            if (r < rpw && row < rows) {
+                const int z = row / ny, y = row - z * ny, x = 4 * k;
+                const long pl = (long)z * pls, i = pl + (long)y * nx + x, col = i - pl;
+                off[it] = i;
+                ax[it] = ld4(A + i);
+                yp[it] = ld4(A + n + pl + (long)nbr(y, 1, ny) * nx + x);
+                ym[it] = ld4(A + n + pl + (long)nbr(y, -1, ny) * nx + x);
+                zp[it] = ld4(A + 2 * n + (long)nbr(z, 1, nz) * pls + col);
+                zm[it] = ld4(A + 2 * n + (long)nbr(z, -1, nz) * pls + col);
+                if (mf) mm[it] = ld4(mf + i);
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < kDivRowIt; ++it) {
+            const float am = __shfl_sync(0xffffffffu, ax[it].w, src[NB - 1]);
+            const float ap = __shfl_sync(0xffffffffu, ax[it].x, src[NB + 1]);
+            const float4 a = ax[it], p = yp[it], q = ym[it], zu = zp[it], zd = zm[it], m = mm[it];
+            float4 v;
+            v.x = sg * ((a.y - am) + (p.x - q.x) + (zu.x - zd.x)) + m.x;
+            v.y = sg * ((a.z - a.x) + (p.y - q.y) + (zu.y - zd.y)) + m.y;
+            v.z = sg * ((a.w - a.y) + (p.z - q.z) + (zu.z - zd.z)) + m.z;
+            v.w = sg * ((ap - a.z) + (p.w - q.w) + (zu.w - zd.w)) + m.w;
+            if (off[it] >= 0) ms += (v.x + v.y) + (v.z + v.w);
+            float c[E];
+#pragma unroll
+            for (int d = 0; d <= 2 * NB; ++d)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int ox = 4 * (d - NB) + e;
+                    if (ox < -RT || ox > 3 + RT) continue;
+                    const float val = f4c(v, e);
+                    c[4 * d + e] = d == NB ? val : __shfl_sync(0xffffffffu, val, src[d]);
+                }
+            float o[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                float acc = 0.f;
+#pragma unroll
+                for (int j = 0; j <= 2 * RT; ++j) acc += wk[j] * c[4 * NB + e - RT + j];
+                o[e] = acc;
+            }
+            if (off[it] >= 0) st4(u + off[it], make_float4(o[0], o[1], o[2], o[3]));
+        }
+    }
+    if (!L.want_mass) return;
+    flow_finish<float>(f, ms, 0.0f, [&](double s0, double) { f.hs[H_MASS] = s0 / (double)f.n; });
+}
+
 template <int MAXI>
 __global__ void __launch_bounds__(kThreads) k_adam4(const __grid_constant__ AdamL<float, MAXI> L)
 {
@@ -909,11 +1016,36 @@ static void launch_div(DivL<T, MAXI>& L, int n_inst, long N, int nx, cudaStream_
     bool v4 = sizeof(T) == 4 && nx % 4 == 0;
     for (int k = 0; k < n_inst; ++k) v4 = v4 && al16(L.A[k]) && al16(L.u[k]) && al16(L.f[k].mf);
     if (v4) {
-        const dim3 grid(flow_grid(N / 4).x, n_inst);
+        const dim3 grid(inst_blocks(N / 4, n_inst), n_inst);
         k_div4<MAXI><<<grid, kThreads, 0, s>>>(reinterpret_cast<const DivL<float, MAXI>&>(L));
         return;
     }
-    k_div<T, MAXI><<<dim3(flow_grid(N).x, n_inst), kThreads, 0, s>>>(L);
+    k_div<T, MAXI><<<dim3(inst_blocks(N, n_inst), n_inst), kThreads, 0, s>>>(L);
+}
+
+// div A + m and the blur's x pass in one kernel into L.u; false (nothing
+// launched) unless FP32, nx % 4 == 0, nx <= 128, radius 3 or 6 and aligned
+// buffers
+template <typename T, int MAXI>
+static bool launch_div_blurx(DivL<T, MAXI>& L, int n_inst, long N, int nx, int ny, int nz, const Weights& w,
+                             cudaStream_t s)
+{
+    if constexpr (sizeof(T) != 4) {
+        return false;
+    } else {
+        if (nx % 4 != 0 || nx > 128 || !(w.R == 3 || w.R == 6) || N >= (1L << 31)) return false;
+        for (int k = 0; k < n_inst; ++k)
+            if (!al16(L.A[k]) || !al16(L.u[k]) || !al16(L.f[k].mf)) return false;
+        const long per_warp = (long)(32 / (nx / 4)) * kDivRowIt;
+        const long warps = ((long)ny * nz + per_warp - 1) / per_warp;
+        long blocks = (warps + kThreads / 32 - 1) / (kThreads / 32);
+        if (blocks > (long)inst_blocks(N, n_inst)) blocks = inst_blocks(N, n_inst);   // <= partials capacity
+        const dim3 grid((unsigned)blocks, n_inst);
+        const DivL<float, MAXI>& Lf = reinterpret_cast<const DivL<float, MAXI>&>(L);
+        if (w.R == 6) k_div_blurx4<MAXI, 6><<<grid, kThreads, 0, s>>>(Lf, w);
+        else k_div_blurx4<MAXI, 3><<<grid, kThreads, 0, s>>>(Lf, w);
+        return true;
+    }
 }
 
 // dG/dA and (unless only_grad) the Adam update, n_inst instances
@@ -923,11 +1055,11 @@ static void launch_adam(AdamL<T, MAXI>& L, int n_inst, long N, int nx, cudaStrea
     bool v4 = sizeof(T) == 4 && nx % 4 == 0;
     for (int k = 0; k < n_inst; ++k) v4 = v4 && al16(L.gb[k]) && al16(L.A[k]) && al16(L.m[k]) && al16(L.v[k]);
     if (v4) {
-        const dim3 grid(flow_grid(N / 4).x, n_inst);
+        const dim3 grid(inst_blocks(N / 4, n_inst), n_inst);
         k_adam4<MAXI><<<grid, kThreads, 0, s>>>(reinterpret_cast<const AdamL<float, MAXI>&>(L));
         return;
     }
-    k_adam<T, MAXI><<<dim3(flow_grid(N).x, n_inst), kThreads, 0, s>>>(L);
+    k_adam<T, MAXI><<<dim3(inst_blocks(N, n_inst), n_inst), kThreads, 0, s>>>(L);
 }
 
 template <typename T>
@@ -992,8 +1124,15 @@ static cudaError_t field(const pfc_hflow* h, const T* A, T** ut, int want_mass, 
         *ut = b0;
         return cudaGetLastError();
     }
-    launch_div<T>(h, A, b2, want_mass, s);
-    launch_blur<T, 0>(b2, b3, h->P.nx, h->P.ny, h->P.nz, h->W, s);
+    DivL<T, 1> L;
+    L.f[0] = flow_desc(h);
+    L.A[0] = A;
+    L.u[0] = b3;
+    L.want_mass = want_mass;
+    if (!launch_div_blurx<T, 1>(L, 1, h->N, h->P.nx, h->P.ny, h->P.nz, h->W, s)) {
+        launch_div<T>(h, A, b2, want_mass, s);
+        launch_blur<T, 0>(b2, b3, h->P.nx, h->P.ny, h->P.nz, h->W, s);
+    }
     launch_blur<T, 1>(b3, b2, h->P.nx, h->P.ny, h->P.nz, h->W, s);
     launch_blur<T, 2>(b2, b0, h->P.nx, h->P.ny, h->P.nz, h->W, s);
     *ut = b0;
@@ -1362,9 +1501,15 @@ static cudaError_t batch_field(const pfc_hflow_batch* b, const float* const* A, 
     for (int k = 0; k < b->n; ++k) {
         L.f[k] = flow_desc_batch(b, k);
         L.A[k] = A[k];
-        L.u[k] = bbuf(b, k, b->W.R ? 2 : 0);
+        L.u[k] = bbuf(b, k, b->W.R ? 3 : 0);
     }
     L.want_mass = want_mass;
+    if (b->W.R && launch_div_blurx<float, BATCH_MAX>(L, b->n, b->N, b->nx, b->ny, b->nz, b->W, s)) {
+        batch_blur<1>(b, 3, 2, s);
+        batch_blur<2>(b, 2, 0, s);
+        return cudaGetLastError();
+    }
+    for (int k = 0; k < b->n; ++k) L.u[k] = bbuf(b, k, b->W.R ? 2 : 0);
     launch_div<float, BATCH_MAX>(L, b->n, b->N, b->nx, s);
     if (b->W.R) {
         batch_blur<0>(b, 2, 3, s);

@@ -186,6 +186,34 @@ def test_flow_with_spatialised_parameters_vs_oracle():
     assert abs(flow.field(Ad).cpu().numpy().mean()) < 1e-13
 
 
+@pytest.mark.parametrize("sigma", [1.0, 2.0])
+def test_flow_with_mass_field_fp32(sigma):
+    """FP32 u = k * (div A + m(x)) (Sec. 5.2) on rows of 24 values, which take
+    the kernel that forms div A + m and blurs it along x in one pass (radii 3
+    and 6, the latter wider than the 4-voxel y and z axes): field, its mean
+    and the trace's mass column against the oracle."""
+    af, mf = I.spatialized_fields(4)
+    shape = af.shape[1:]
+    nz, ny, nx = shape
+    a = (1.0, 0.4, 0.8, 0.3, -0.2, 0.1)
+    p = pfc.Problem(nx=nx, ny=ny, nz=nz, eps=1.5, h=1.0, xi=1e-6, a=a, well=1, prec="fp32")
+    flow = pfc.HFlow(p, m0=0.0, lr=1e-3, blur_sigma=sigma)
+    flow.set_mass_field(dev(mf, "fp32"))
+    rng = np.random.default_rng(15)
+    A = (0.05 * rng.standard_normal((3,) + shape)).astype(np.float32).astype(np.float64)
+    Ad = dev(A, "fp32")
+    op = {"a": a, "eps": 1.5, "h": 1.0, "xi": 1e-6, "well": 1}
+    fp = {"m0": 0.0, "lr": 1e-3, "blur_sigma": sigma, "m_field": mf.astype(np.float32).astype(np.float64)}
+    ut = flow.field(Ad).double().cpu().numpy()
+    uo = oracle.hflow_field(A, op, fp)
+    assert np.max(np.abs(ut - uo)) < 1e-6
+    assert abs(ut.mean() - uo.mean()) < 1e-6
+    md, vd = torch.zeros_like(Ad), torch.zeros_like(Ad)
+    tr = flow.run(Ad, md, vd, 5)
+    _, _, _, _, tro = oracle.hflow_run(A, np.zeros_like(A), np.zeros_like(A), op, fp, 5)
+    np.testing.assert_allclose(tr[:, 3], tro[:, 3], rtol=0, atol=1e-6)
+
+
 # ------------------------------------------------------------ diagnostics
 
 @pytest.mark.parametrize("shape", [(7, 9, 11), (40, 33, 64), (1, 4, 8)])
