@@ -274,3 +274,53 @@ def test_flow_batch_against_oracle_and_errors():
                                     theta=(1, 0, 0))], [0.3])
     with pytest.raises(pfc.PfcError):
         pfc.HFlowBatch([pfc.Problem(nx=nx, ny=ny, nz=nz, eps=1.5, a=(1, 0, 1, 0, 0, 0), prec="fp64")], [0.3])
+
+
+def test_flow_batch_64_instances_misaligned_and_limits():
+    """The largest batch (64 flows, every descriptor slot in use) against single
+    flows at both ends and in the middle (the batch runs another instantiation
+    of the sweep, and Adam's m / sqrt(v) turns last-bit differences of
+    near-zero gradients into visible ones: 1e-5); an A that is not 16-byte aligned
+    sends the whole batch to the scalar div / Adam kernels, which must agree
+    with the float4 ones; 65 flows and an empty batch are rejected."""
+    shape = (9, 12, 16)
+    nz, ny, nx = shape
+    rng = np.random.default_rng(23)
+    probs, m0s = [], []
+    for k in range(64):
+        a = tuple(rng.uniform(-0.3, 0.3, 6) + np.array([1.0, 0, 1.0, 0, 0, 0]))
+        probs.append(pfc.Problem(nx=nx, ny=ny, nz=nz, eps=1.5, a=a, well=k % 2, prec="fp32"))
+        m0s.append(0.3 if k % 2 == 0 else -0.4)
+    A0 = [torch.tensor((0.04 * rng.standard_normal((3,) + shape)).astype(np.float32), device="cuda") for _ in probs]
+    fb = pfc.HFlowBatch(probs, m0s, lr=1e-3, blur_sigma=2.0)
+    As = [a.clone() for a in A0]
+    ms = [torch.zeros_like(a) for a in A0]
+    vs = [torch.zeros_like(a) for a in A0]
+    tr = fb.run(As, ms, vs, 6)
+    assert tr.shape == (64, 6, 5) and np.all(np.isfinite(tr))
+    for k in (0, 31, 63):
+        fl = pfc.HFlow(probs[k], m0=m0s[k], lr=1e-3, blur_sigma=2.0)
+        A, m, v = A0[k].clone(), torch.zeros_like(A0[k]), torch.zeros_like(A0[k])
+        trs = fl.run(A, m, v, 6)
+        assert (torch.linalg.norm(As[k] - A) / torch.linalg.norm(A)).item() < 1e-5
+        np.testing.assert_allclose(tr[k][:, 0], trs[:, 0], rtol=1e-5)
+        np.testing.assert_allclose(tr[k][:, 3], m0s[k], atol=1e-6)
+    # instance 5's A (and moments) one element off a 16-byte boundary
+    stores = [torch.empty(A0[5].numel() + 1, dtype=torch.float32, device="cuda") for _ in range(3)]
+    Am, mm, vm = (s[1:].view(A0[5].shape) for s in stores)
+    Am.copy_(A0[5]); mm.zero_(); vm.zero_()
+    assert Am.data_ptr() % 16 != 0
+    fb2 = pfc.HFlowBatch(probs, m0s, lr=1e-3, blur_sigma=2.0)
+    Bs = [a.clone() for a in A0]
+    Bs[5] = Am
+    mb = [torch.zeros_like(a) for a in A0]
+    vb = [torch.zeros_like(a) for a in A0]
+    mb[5], vb[5] = mm, vm
+    tr2 = fb2.run(Bs, mb, vb, 6)
+    for k in (0, 5, 63):
+        assert (torch.linalg.norm(Bs[k] - As[k]) / torch.linalg.norm(As[k])).item() < 1e-5
+        np.testing.assert_allclose(tr2[k][:, 0], tr[k][:, 0], rtol=1e-5)
+    with pytest.raises(pfc.PfcError):
+        pfc.HFlowBatch(probs + probs[:1], m0s + m0s[:1])
+    with pytest.raises(pfc.PfcError):
+        pfc.HFlowBatch([], [])
