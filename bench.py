@@ -205,10 +205,10 @@ def kernel_sources_sha():
     return h.hexdigest()[:16]
 
 
-def committed_traffic(tile_y, max_run):
-    """DRAM bytes per launch of the fused sweep from the committed ncu summary,
-    or None if it was taken on another version of the kernel sources or in
-    another launch shape."""
+def committed_profile(tile_y, max_run):
+    """The fused sweep's figures from the committed ncu summary (DRAM bytes and
+    instructions per launch), or None if they were taken on another version of
+    the kernel sources or in another launch shape."""
     path = os.path.join(ROOT, "profiles", "fused_sweep_traffic.json")
     try:
         with open(path) as f:
@@ -217,9 +217,15 @@ def committed_traffic(tile_y, max_run):
             return None, "stale"
         if d.get("tile_y") != tile_y or d.get("max_run") != max_run:
             return None, f"captured with tile_y {d.get('tile_y')}, max_run {d.get('max_run')}"
-        return float(d["traffic_bytes_per_launch"]), d.get("note", "")
+        return d, d.get("note", "")
     except Exception:
         return None, "absent"
+
+
+def committed_traffic(tile_y, max_run):
+    """DRAM bytes per launch of the fused sweep from the committed ncu summary."""
+    d, note = committed_profile(tile_y, max_run)
+    return (float(d["traffic_bytes_per_launch"]) if d else None), note
 
 
 def cpu_baseline_oracle():
@@ -446,6 +452,8 @@ def diagnostics_workload(pfc, I):
 FLOPS_PER_VOXEL_STEP = 211
 # FP32 peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz maximum SM clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+# instruction issue peak: 152 SMs x 4 schedulers x 1 warp instruction per clock x 2070 MHz
+ISSUE_PEAK_TWIPS = 152 * 4 * 2070e6 / 1e12
 
 
 # ------------------------------------------------------------ our arm
@@ -588,7 +596,8 @@ def main():
     bytes_launch = 8.0 * vox                      # read u, write u' (FP32)
     hbm_achieved = bytes_launch / (ms_sweep * 1e-3) / 1e9
     ty_used = launch["tile_y"] or 16                 # the batch's automatic height
-    traffic, traffic_note = committed_traffic(ty_used, launch["max_run"])
+    prof, traffic_note = committed_profile(ty_used, launch["max_run"])
+    traffic = float(prof["traffic_bytes_per_launch"]) if prof else None
     alu_achieved = FLOPS_PER_VOXEL_STEP * vox / (ms_sweep * 1e-3) / 1e12
     # 211 flop per 8 B is ~2x GB300's FP32/HBM balance: the sweep is bound by
     # arithmetic issue, not by HBM; the HBM fraction is reported beside it
@@ -602,6 +611,15 @@ def main():
                         "algorithmic_bytes_per_launch": bytes_launch}}
     if traffic is None:
         roofline["traffic_note"] = traffic_note
+    if prof and prof.get("warp_instructions_per_launch"):
+        # what actually bounds the sweep: instruction issue (one warp
+        # instruction per scheduler per clock), from the committed count of
+        # this kernel's instructions and its live duration
+        wi = float(prof["warp_instructions_per_launch"])
+        issue_achieved = wi / (ms_sweep * 1e-3) / 1e12
+        roofline["issue"] = {"achieved": issue_achieved, "peak": ISSUE_PEAK_TWIPS, "unit": "T warp-instr/s",
+                             "frac": issue_achieved / ISSUE_PEAK_TWIPS, "warp_instructions_per_launch": wi,
+                             "peak_kind": "derived: 152 SM x 4 schedulers x 1 warp instruction x 2070 MHz"}
 
     extra = None
     if not args.no_extra:
