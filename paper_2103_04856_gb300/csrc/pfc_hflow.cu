@@ -231,6 +231,12 @@ __global__ void __launch_bounds__(256) k_blur(const __grid_constant__ BlurL<T, M
     const long pls = (long)nx * ny;
     const int n_other = AX == 2 ? ny : nz;
     for (int o = zo; o < n_other; o += BL.zb) {
+#if PFC_DEBUG
+        // debug builds: the tile starts as NaN, so an output that reads a cell
+        // this pass did not load shows up in the results
+        for (int i = ty * 32 + tx; i < (int)(sizeof(s) / sizeof(T)); i += 256) (&s[0][0])[i] = T(NAN);
+        __syncthreads();
+#endif
         if (AX == 0) {
             const int x0 = blockIdx.x * kTileAx, y = blockIdx.y * 8 + ty;
             const long row = (long)o * pls + (long)y * nx;
