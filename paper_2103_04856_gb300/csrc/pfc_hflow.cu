@@ -477,12 +477,12 @@ static void k_blurx4_launch(const BlurL<float, MAXI>& BL, int R, dim3 grid, cuda
     else k_blurx4<MAXI, 3><<<grid, 256, 0, s>>>(BL);
 }
 
-// Pieces per line for the window kernels: enough threads to fill the GPU
-// about twice, no piece shorter than one window when the line holds one.
-static void blur_pieces(int n_ax, int W, long lines, long want, int* chunk, int* nchunks)
+// Pieces per line for the window kernels: enough threads to fill the GPU,
+// no piece shorter than min_chunk outputs when the line holds that many.
+static void blur_pieces(int n_ax, int min_chunk, long lines, long want, int* chunk, int* nchunks)
 {
     long pieces = (want + lines - 1) / lines;
-    const long max_pieces = n_ax >= W ? n_ax / W : 1;
+    const long max_pieces = n_ax >= min_chunk ? n_ax / min_chunk : 1;
     if (pieces > max_pieces) pieces = max_pieces;
     if (pieces < 1) pieces = 1;
     *chunk = (int)((n_ax + pieces - 1) / pieces);
@@ -516,7 +516,10 @@ static void launch_blur(BlurL<T, MAXI>& BL, int n_inst, cudaStream_t s)
         if (vec) {
             const int n_ax = AX == 1 ? ny : nz, n_oth = AX == 1 ? nz : ny;
             const long lines = (long)(nx / 4) * n_oth;
-            blur_pieces(n_ax, 2 * R + 1, lines * n_inst, 152L * 1024, &BL.chunk, &BL.nchunks);
+            // pieces as short as 4 outputs when there are few lines (one flow:
+            // the GPU would otherwise sit half idle); the taps are summed in
+            // the same order whatever the pieces
+            blur_pieces(n_ax, 4, lines * n_inst, 152L * 1024, &BL.chunk, &BL.nchunks);
             const dim3 grid((unsigned)((lines * BL.nchunks + 255) / 256), n_inst);
             if (R == 6) k_blur_win4<AX, MAXI, 6, kPrefetch><<<grid, 256, 0, s>>>(BL);
             else k_blur_win4<AX, MAXI, 3, kPrefetch><<<grid, 256, 0, s>>>(BL);

@@ -324,3 +324,22 @@ def test_flow_batch_64_instances_misaligned_and_limits():
         pfc.HFlowBatch(probs + probs[:1], m0s + m0s[:1])
     with pytest.raises(pfc.PfcError):
         pfc.HFlowBatch([], [])
+
+
+def test_flow_batch_field_bit_identical_to_single_at_paper_size():
+    """At the paper's 100^3 (blur radius 6) a batch of 16 splits the y and z
+    blur lines into long pieces (the unrolled register ring) and a single flow
+    into short ones (the ring's tail loop); div + x pass, windows and taps are
+    the same arithmetic in the same order, so the fields agree bit for bit."""
+    from paper_2103_04856_gb300 import inputs as I
+    pd, fd, _ = I.paper_flow_100()
+    nz, ny, nx = pd["shape"]
+    prob = pfc.Problem(nx=nx, ny=ny, nz=nz, h=pd["h"], eps=pd["eps"], xi=pd["xi"], a=pd["a"], well=pd["well"],
+                       prec="fp32")
+    n = 16
+    fb = pfc.HFlowBatch([prob] * n, [fd["m0"]] * n, lr=fd["lr"], blur_sigma=fd["blur_sigma"])
+    As = [torch.tensor(I.paper_flow_100(seed=s)[2].astype(np.float32), device="cuda") for s in range(n)]
+    ub = fb.field(As)
+    fl = pfc.HFlow(prob, m0=fd["m0"], lr=fd["lr"], blur_sigma=fd["blur_sigma"])
+    for k in (0, 7, 15):
+        assert torch.equal(ub[k], fl.field(As[k]))
