@@ -207,20 +207,27 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
     const T Tr = Mxx + Myy + Mzz;
     const T off = fma_(Mxy, Mxy, fma_(Mxz, Mxz, Myz * Myz));
     const T S = fma_(Mxx, Mxx, fma_(Myy, Myy, fma_(Mzz, Mzz, T(2) * off)));
-    // D = 2S - T^2 with the rounding error of T^2 put back (two-product)
     const T t2 = Tr * Tr;
-    const T t2e = fma_(Tr, Tr, -t2);
-    T D = fma_(T(2), S, -t2) - t2e;
     const T a3 = fma_(C.c3, Tr, C.c5 * q);              // c3 T + c5 q
-    if (sizeof(T) == 4) {
-        const T scale = fma_(T(2), S, t2);
-        if (a3 != T(0) && scale > T(65536) * fmax(fabs(D), C.xi)) D = (T)refine();
+    T r = T(0), rs = T(0), Pp = T(0);
+    // For p symmetric in kappa1, kappa2 (c3 = c5 = 0, a problem-wide, warp-
+    // uniform flag) a3 is exactly 0 and r enters only through a3 r, c3 r and
+    // c5 r: they stay exact zeros with r = P' = 0, so D, P and sqrt(P) are
+    // skipped with the same result bits.  (Not with a per-voxel c(x).)
+    if (ORIENT || PROJ || !C.sym) {
+        // D = 2S - T^2 with the rounding error of T^2 put back (two-product)
+        const T t2e = fma_(Tr, Tr, -t2);
+        T D = fma_(T(2), S, -t2) - t2e;
+        if (sizeof(T) == 4) {
+            const T scale = fma_(T(2), S, t2);
+            if (a3 != T(0) && scale > T(65536) * fmax(fabs(D), C.xi)) D = (T)refine();
+        }
+        T P;
+        softplus_(D, C, P, Pp);
+        // float: one reciprocal square root gives both sqrt(P) and 1/(2 sqrt(P))
+        rs = (sizeof(T) == 4 && P > T(0)) ? rsqrt_(P) : T(0);
+        r = sizeof(T) == 4 ? P * rs : sqrt_(P);
     }
-    T P, Pp;
-    softplus_(D, C, P, Pp);
-    // float: one reciprocal square root gives both sqrt(P) and 1/(2 sqrt(P))
-    const T rs = (sizeof(T) == 4 && P > T(0)) ? rsqrt_(P) : T(0);
-    const T r = sizeof(T) == 4 ? P * rs : sqrt_(P);
     T e = fma_(C.c1, S, fma_(C.c2, t2, fma_(a3, r, fma_(C.c4 * q, Tr, C.c6 * g2))));
     T tg = T(0);
     if (ORIENT) {

@@ -473,6 +473,7 @@ Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well, 
     C.th1 = (T)(theta ? theta[1] : 0.0);
     C.th2 = (T)(theta ? theta[2] : 0.0);
     C.proj = proj ? 1 : 0;
+    C.sym = (C.c3 == T(0) && C.c5 == T(0)) ? 1 : 0;
     return C;
 }
 template Coef<float> make_coef<float>(const double*, double, double, double, int, double, const double*, int);

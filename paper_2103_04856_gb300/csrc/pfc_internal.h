@@ -44,6 +44,9 @@ struct Coef {
     // orientation term of Sec. 5.2, eps mu (theta . grad u)^2: c7 = eps mu h^3
     T c7, th0, th1, th2;
     int proj;   // 1: tangent-projected M = -eps P Hess u P instead of eq. Meps
+    // 1: c3 = c5 = 0 in the arithmetic type (p symmetric in kappa1, kappa2), so
+    // the weight c3 T + c5 q of the sqrt(D+) terms is exactly zero
+    int sym;
 };
 
 // Coefficient fields: c(x) = (c1..c6)(a(x)) as 6 component planes of N

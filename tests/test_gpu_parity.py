@@ -400,3 +400,28 @@ def test_errors_are_reported():
     # the context still works after the errors
     Eo = oracle.energy(u.cpu().numpy(), oprob(p))
     assert ctx.energy(u) == pytest.approx(Eo, rel=1e-10)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_symmetric_polynomial_skip_matches_full_path(prec):
+    """p symmetric in kappa1, kappa2 (a20 = a02, a10 = a01: c3 = c5 = 0) gives
+    the sqrt(D+) terms of eq. Feps the weight c3 T + c5 q = 0 exactly, and
+    the plain sweep skips them.  The extended sweep (taken here by an
+    orientation weight mu = 1e-30, which adds ~1e-32 per voxel) evaluates
+    them: energy and gradient agree, and a step of either matches."""
+    shape = (12, 20, 40)
+    a = (1.0, 0.3, 1.0, 0.2, 0.2, 0.1)
+    u = I.noise(shape, 0.3, 0.1, 3)
+    if prec == "fp32":
+        u = u.astype(np.float32).astype(np.float64)
+    ud = dev(u, prec)
+    p0 = P(shape, a, prec=prec)
+    p1 = P(shape, a, prec=prec, mu=1e-30, theta=(1.0, 0.0, 0.0))
+    E0, g0 = pfc.Context(p0).energy_and_grad(ud)
+    E1, g1 = pfc.Context(p1).energy_and_grad(ud)
+    tol = 1e-6 if prec == "fp32" else 1e-13
+    assert E0 == pytest.approx(E1, rel=tol)
+    assert (torch.linalg.norm(g0 - g1) / torch.linalg.norm(g1)).item() < tol
+    Eo, go = oracle.energy_and_grad(u, oprob(p0))
+    assert E0 == pytest.approx(Eo, rel=1e-4 if prec == "fp32" else 1e-10)
+    assert rel_max(g0.double().cpu().numpy(), go) < (1e-3 if prec == "fp32" else 1e-10)
