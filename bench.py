@@ -657,6 +657,9 @@ def main():
             "config": {"workload": "validation_128: 4 x 128^3 (tanh sphere R=32, z-cylinder r=20; eps=2, h=1; "
                                    "p=k1^2+k2^2 and p=k1k2), one batched fused step each",
                        "voxels_per_step": vox, "l2": f"flushed ({args.flush_mb} MB write) before every timed step",
+                       "symmetric_p": "both polynomials are symmetric in k1, k2: the sqrt(D+) terms have weight "
+                                      "exactly 0 and are not evaluated (same result bits); 185 flop per "
+                                      "voxel-step counted; other_workloads hold asymmetric p",
                        "parallelism": f"replicas x{ws}"},
             "wall_ms_per_step_incl_flush": 1e3 * wall / args.steps,
             "rel_energy_err_fp32_vs_fp64": rel_err, "mass_drift": mass_err,
