@@ -199,7 +199,7 @@ def job_value(voxels_per_rank, world_size, ms_per_step_max):
 
 def kernel_sources_sha():
     h = hashlib.sha256()
-    for f in ("pfc_fused.cu", "pfc_device.cuh", "pfc_internal.h"):
+    for f in ("pfc_fused.cu", "pfc_fused_kernel.cuh", "pfc_fused_sym.cu", "pfc_device.cuh", "pfc_internal.h"):
         with open(os.path.join(ROOT, "paper_2103_04856_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -614,13 +614,15 @@ def main():
     prof, traffic_note = committed_profile(ty_used, launch["max_run"])
     traffic = float(prof["traffic_bytes_per_launch"]) if prof else None
     flops_launch = workload_flops(insts)
+    all_sym = all(i.a[0] == i.a[2] and i.a[3] == i.a[4] for i in insts)
     alu_achieved = flops_launch / (ms_sweep * 1e-3) / 1e12
     # 211 flop per 8 B is ~2x GB300's FP32/HBM balance: the sweep is bound by
     # arithmetic issue, not by HBM; the HBM fraction is reported beside it
     roofline = {"bound": "alu", "achieved": alu_achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": alu_achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2070 MHz",
-                "kernel": f"k_fused<float,{ty_used},STEP,64> (batched fused sweep)", "kernel_ms": ms_sweep,
+                "kernel": f"k_fused<float,{ty_used},STEP,64{',SYM' if all_sym else ''}> (batched fused sweep)",
+                "kernel_ms": ms_sweep,
                 "flops_per_voxel_step": flops_launch / vox, "voxels_per_launch": vox,
                 "hbm": {"achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": hbm_achieved / peaks["hbm_gbs"], "peak_kind": peak_kind,

@@ -153,10 +153,17 @@ struct NoRefine {
 // PROJ replaces eq. Meps by the tangent-projected M = P K P, K = -eps Hess u,
 // P = I - G G^T / rho (no double-well term): with k = K G and
 // s = G.k, M = K - (G m^T + m G^T)/rho, m = k - (s / 2rho) G.
-template <typename T, bool GRAD, bool ORIENT = false, bool PROJ = false, class Refine = NoRefine>
+//
+// SKIPD (p symmetric in kappa1, kappa2: c3 = c5 = 0 for every voxel the
+// caller evaluates): a3 = c3 T + c5 q is exactly 0 and r enters only through
+// a3 r, c3 r and c5 r, which stay exact zeros with r = r' = 0; D, P and
+// sqrt(P) are then not computed, with the same result bits.
+template <typename T, bool GRAD, bool ORIENT = false, bool PROJ = false, bool SKIPD = false,
+          class Refine = NoRefine>
 __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz, T hxx, T hyy,
                                         T hzz, T hxy, T hxz, T hyz, Cot<T>& ct, const Refine& refine = Refine())
 {
+    static_assert(!(SKIPD && (ORIENT || PROJ)), "the symmetric shortcut is for the plain energy only");
     const T Gx = dx * C.sg, Gy = dy * C.sg, Gz = dz * C.sg;
     const T g2 = fma_(Gx, Gx, fma_(Gy, Gy, Gz * Gz));
     const T rho = g2 + C.xi2;
@@ -210,11 +217,7 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
     const T t2 = Tr * Tr;
     const T a3 = fma_(C.c3, Tr, C.c5 * q);              // c3 T + c5 q
     T r = T(0), rs = T(0), Pp = T(0);
-    // For p symmetric in kappa1, kappa2 (c3 = c5 = 0, a problem-wide, warp-
-    // uniform flag) a3 is exactly 0 and r enters only through a3 r, c3 r and
-    // c5 r: they stay exact zeros with r = P' = 0, so D, P and sqrt(P) are
-    // skipped with the same result bits.  (Not with a per-voxel c(x).)
-    if (ORIENT || PROJ || !C.sym) {
+    if constexpr (!SKIPD) {
         // D = 2S - T^2 with the rounding error of T^2 put back (two-product)
         const T t2e = fma_(Tr, Tr, -t2);
         T D = fma_(T(2), S, -t2) - t2e;

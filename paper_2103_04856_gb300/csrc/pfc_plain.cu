@@ -45,13 +45,14 @@ __global__ void k_plain_deriv(const T* __restrict__ u, PlainBufs<T> b, int nx, i
     }
 }
 
-template <typename T>
+// SYM: c3 = c5 = 0, the sqrt(D+) terms (weight zero) are not evaluated
+template <typename T, bool SYM>
 __global__ void k_plain_local(const T* __restrict__ u, PlainBufs<T> b, long n, Coef<T> C)
 {
     PFC_GRID_STRIDE(i, n)
     {
         Cot<T> ct;
-        b.e[i] = voxel_eval<T, true>(C, u[i], b.d[0][i], b.d[1][i], b.d[2][i], b.d[3][i], b.d[4][i],
+        b.e[i] = voxel_eval<T, true, false, false, SYM>(C, u[i], b.d[0][i], b.d[1][i], b.d[2][i], b.d[3][i], b.d[4][i],
                                      b.d[5][i], b.d[6][i], b.d[7][i], b.d[8][i], ct);
         b.ct[0][i] = ct.u;
         b.ct[1][i] = ct.dx;
@@ -147,7 +148,8 @@ cudaError_t launch_plain(const T* u, T* out, const PlainBufs<T>& b_in, int nx, i
     in.inv_N = inv_N;
     if (nb != nblocks) return cudaErrorInvalidValue;
     k_plain_deriv<T><<<nb, 256, 0, s>>>(u, b, nx, ny, nz);
-    k_plain_local<T><<<nb, 256, 0, s>>>(u, b, n, C);
+    if (C.sym) k_plain_local<T, true><<<nb, 256, 0, s>>>(u, b, n, C);
+    else k_plain_local<T, false><<<nb, 256, 0, s>>>(u, b, n, C);
     if (mode != MODE_ENERGY) k_plain_adjoint<T><<<nb, 256, 0, s>>>(b, nx, ny, nz);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
