@@ -500,7 +500,8 @@ def main():
     launch = {"tile_y": args.tile_y, "max_run": max(args.max_run, 0), "source": "command line"}
     if not args.no_autotune and args.tile_y == 0 and args.max_run < 0:
         from paper_2103_04856_gb300 import autotune
-        best = autotune.tune([i.shape for i in insts], cache=None)
+        best = autotune.tune([i.shape for i in insts], cache=None,
+                             symmetric=all(i.a[0] == i.a[2] and i.a[3] == i.a[4] for i in insts))
         launch = {"tile_y": best["tile_y"], "max_run": best["max_run"], "source": "autotuned",
                   "tried": [{k: r[k] for k in ("tile_y", "max_run", "sweep_ms")} for r in best["tried"]]}
     probs = [pfc.Problem.from_shape(i.shape, eps=i.eps, a=i.a, prec="fp32", tile_y=launch["tile_y"],

@@ -6,8 +6,10 @@ trade halo recomputation, registers and balance against each other, and the
 best choice depends on the grid sizes.  `tune` times every candidate with
 CUDA events on synthetic noise fields of the requested shapes (L2 flushed
 between steps, medians of repeated steps) through the library's own batched
-step, and caches the winner in a JSON file keyed by GPU name, precision and
-the multiset of shapes.
+step, and caches the winner in a JSON file keyed by GPU name, precision, the
+multiset of shapes and whether the polynomials are symmetric in kappa1,
+kappa2 (those problems run another instantiation of the sweep, without the
+sqrt(D+) terms, whose best tile can differ).
 
     from paper_2103_04856_gb300 import autotune
     best = autotune.tune([(128, 128, 128)] * 4)        # {'tile_y': 16, 'max_run': 0, ...}
@@ -36,10 +38,10 @@ CANDIDATES = [
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache.json")
 
 
-def cache_key(shapes, prec: str = "fp32") -> str:
+def cache_key(shapes, prec: str = "fp32", symmetric: bool = False) -> str:
     dev = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
     shp = ",".join("x".join(str(int(d)) for d in s) for s in sorted(tuple(s) for s in shapes))
-    return f"{dev}|{prec}|{shp}"
+    return f"{dev}|{prec}|{shp}" + ("|sym" if symmetric else "")
 
 
 def _load(path):
@@ -57,9 +59,17 @@ def _store(path, data):
     os.replace(tmp, path)
 
 
-def time_candidate(shapes, cand, steps: int = 30, warmup: int = 5, flush_mb: int = 256, eps: float = 1.5):
+# polynomials (paper order) the candidates are timed with: a general one, and
+# one symmetric in kappa1, kappa2 (a20 = a02, a10 = a01)
+A_GENERAL = (1.0, 0.3, 0.6, 0.1, -0.1, 0.0)
+A_SYMMETRIC = (1.0, 0.3, 1.0, 0.1, 0.1, 0.0)
+
+
+def time_candidate(shapes, cand, steps: int = 30, warmup: int = 5, flush_mb: int = 256, eps: float = 1.5,
+                   symmetric: bool = False):
     """Median device time (ms) of one batched fused sweep over noise fields."""
-    probs = [pfc.Problem.from_shape(s, eps=eps, a=(1.0, 0.3, 0.6, 0.1, -0.1, 0.0), prec="fp32",
+    a = A_SYMMETRIC if symmetric else A_GENERAL
+    probs = [pfc.Problem.from_shape(s, eps=eps, a=a, prec="fp32",
                                     tile_y=cand["tile_y"], tile_z=cand["max_run"]) for s in shapes]
     A = [torch.tensor(inputs.noise(s, 0.3, 0.1, 1000 + k).astype(np.float32), device="cuda")
          for k, s in enumerate(shapes)]
@@ -80,20 +90,28 @@ def time_candidate(shapes, cand, steps: int = 30, warmup: int = 5, flush_mb: int
 
 
 def tune(shapes, prec: str = "fp32", cache: str | None = DEFAULT_CACHE, force: bool = False,
-         candidates=None, steps: int = 30):
-    """Best launch shape for these problem shapes (each (nz, ny, nx)); cached."""
+         candidates=None, steps: int = 30, symmetric: bool = False, rounds: int = 3):
+    """Best launch shape for these problem shapes (each (nz, ny, nx)); cached.
+    ``symmetric``: the problems' polynomials are all symmetric in kappa1,
+    kappa2.  Candidates are timed in ``rounds`` interleaved rounds (so that
+    a drift of the clock or of a neighbour's load does not favour the ones
+    timed first); each one's time is the median over all its steps."""
     if prec != "fp32":
         raise ValueError("the batched sweep is FP32; FP64 uses the library defaults")
-    key = cache_key(shapes, prec)
+    key = cache_key(shapes, prec, symmetric)
     data = _load(cache) if cache else {}
     if not force and key in data:
         return data[key]
-    results = []
-    for cand in candidates or CANDIDATES:
-        ms = time_candidate(shapes, cand, steps=steps)
-        results.append({**cand, "sweep_ms": ms})
+    cands = list(candidates or CANDIDATES)
+    times = [[] for _ in cands]
+    per_round = max(1, steps // max(rounds, 1))
+    for _ in range(max(rounds, 1)):
+        for j, cand in enumerate(cands):
+            times[j].append(time_candidate(shapes, cand, steps=per_round, symmetric=symmetric))
+    results = [{**cand, "sweep_ms": float(np.median(t))} for cand, t in zip(cands, times)]
     best = min(results, key=lambda r: r["sweep_ms"])
     entry = {"tile_y": best["tile_y"], "max_run": best["max_run"], "sweep_ms": best["sweep_ms"],
+             "symmetric": bool(symmetric),
              "voxels": int(sum(int(np.prod(s)) for s in shapes)), "tried": results,
              "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
     if cache:

@@ -19,7 +19,8 @@ def test_picks_fastest_and_caches(tmp_path, monkeypatch):
     cache = str(tmp_path / "cache.json")
     best = autotune.tune([(64, 64, 64), (32, 32, 32)], cache=cache)
     assert (best["tile_y"], best["max_run"]) == (16, 64)
-    assert len(calls) == len(autotune.CANDIDATES)
+    assert len(calls) == 3 * len(autotune.CANDIDATES)           # three interleaved rounds
+    assert calls[:len(autotune.CANDIDATES)] == calls[len(autotune.CANDIDATES):2 * len(autotune.CANDIDATES)]
     stored = json.load(open(cache))
     assert list(stored.values())[0]["tile_y"] == 16
     # second call: from the cache, no timing; the key ignores shape order
@@ -28,7 +29,28 @@ def test_picks_fastest_and_caches(tmp_path, monkeypatch):
     assert calls == [] and again["max_run"] == 64
     # force re-times
     autotune.tune([(32, 32, 32), (64, 64, 64)], cache=cache, force=True)
-    assert len(calls) == len(autotune.CANDIDATES)
+    assert len(calls) == 3 * len(autotune.CANDIDATES)
+
+
+def test_symmetric_problems_are_tuned_and_cached_apart(tmp_path, monkeypatch):
+    """Polynomials symmetric in kappa1, kappa2 run another instantiation of
+    the sweep: they are timed with a symmetric polynomial and cached under
+    their own key."""
+    from paper_2103_04856_gb300 import autotune
+    seen = []
+
+    def timer(shapes, cand, steps=30, symmetric=False, **kw):
+        seen.append(symmetric)
+        return {True: {16: 0.10, 13: 0.11}, False: {16: 0.17, 13: 0.16}}[symmetric].get(cand["tile_y"], 1.0) + \
+            0.01 * cand["max_run"]
+
+    monkeypatch.setattr(autotune, "time_candidate", timer)
+    cache = str(tmp_path / "cache.json")
+    sym = autotune.tune([(64, 64, 64)], cache=cache, symmetric=True)
+    gen = autotune.tune([(64, 64, 64)], cache=cache)
+    assert (sym["tile_y"], gen["tile_y"]) == (16, 13)
+    assert sym["symmetric"] and not gen["symmetric"]
+    assert set(seen) == {True, False} and len(json.load(open(cache))) == 2
 
 
 def test_rejects_fp64():
