@@ -7,11 +7,14 @@
 //   sweep  : k * u -> E, g = dF/du                    (the fused kernel)
 //   blur   : g -> k * g     (the blur is symmetric and periodic: self-adjoint)
 //   adam   : dG/dA_c = -(k*g)(j+e_c) + (k*g)(j-e_c), over 2h; moments; A update
-// The div, blur and Adam kernels are memory-bound (grid-stride loops over
-// the voxels, or shared-memory tiles for the blur; FP32 sums per thread and
-// FP64 only across warps and blocks: FP64 runs at a small fraction of the
-// FP32 rate on this GPU); the
-// sweep is the issue-bound kernel of pfc_fused.cu.
+// The div, blur and Adam kernels are memory-bound: grid-stride loops over the
+// voxels (FP32 sums per thread, FP64 only across warps and blocks: FP64 runs
+// at a small fraction of the FP32 rate on this GPU); for FP32 rows of up to
+// 128 values div and the x pass of the blur share one kernel (shuffles across
+// a warp), the y and z passes are register windows along each line, and other
+// radii or precisions take shared-memory tiles.  The sweep is the issue-bound
+// kernel of pfc_fused_kernel.cuh.  A batch runs every kernel once for up to
+// 64 flows on grids of one size (instances along grid y).
 #include <cuda_runtime.h>
 
 #include <math.h>
