@@ -185,6 +185,24 @@ pfc_status pfc_batch_run(pfc_batch* batch, void* const* u, int32_t nsteps, const
  * receives n_inst rows of the 5 scalars of pfc_step. */
 pfc_status pfc_batch_step(pfc_batch* batch, const void* const* u_in, void* const* u_out, const double* tau,
                           double* scalars_dev, pfc_stream stream);
+/* Chained steps in the fused form of the mass projection (the update of the
+ * descent step with u <- u - tau (g - mean g) written, as for pfc_run, as
+ * v = (u + c) - tau g with the offset c = m - mean(v) applied one step
+ * later).  Each call is one fused launch over all instances: it reads
+ * u_in[k], adds the offset c_k left by the previous call of the chain as it
+ * loads (none when first != 0, which opens the chain and takes the mean of
+ * u_in[k] as the mass m_k to keep), stores v in u_out[k] and leaves the new
+ * c_k on the device.  After any number of calls the projected field of
+ * instance k is u_out[k] + c_k; pfc_batch_lazy_finish(u_out) adds c_k in
+ * place (one launch) and closes the chain.  Results equal a sequence of
+ * pfc_batch_step calls up to FP32 rounding (the offset enters the loads, not
+ * the stencil differences).  u_out[k] must not alias u_in[k]; enqueue only;
+ * PFC_EINVAL for first == 0 without an open chain.  pfc_batch_step,
+ * pfc_batch_run and pfc_batch_step_host close an open chain (they reset the
+ * offsets). */
+pfc_status pfc_batch_step_lazy(pfc_batch* batch, const void* const* u_in, void* const* u_out, const double* tau,
+                               int32_t first, pfc_stream stream);
+pfc_status pfc_batch_lazy_finish(pfc_batch* batch, void* const* u, pfc_stream stream);
 /* pfc_batch_step from and to HOST memory: u_in_host[k] is copied to the
  * device, stepped, and the result copied to u_out_host[k] (host arrays of
  * the instances' sizes, float; page-locked memory lets the copies overlap,

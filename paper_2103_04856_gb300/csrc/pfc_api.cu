@@ -597,6 +597,7 @@ struct pfc_batch {
     cudaStream_t cap = nullptr;
     cudaEvent_t ev[4] = { nullptr, nullptr, nullptr, nullptr };
     bool timing = false;
+    int lazy = 0;   // a chain of pfc_batch_step_lazy is open (offsets pending in scal)
     // pfc_batch_step_host: device staging and the copy pipeline
     std::vector<void*> hin;
     cudaStream_t hs[2] = { nullptr, nullptr };    // host-to-device, device-to-host
@@ -749,6 +750,7 @@ extern "C" pfc_status pfc_batch_run(pfc_batch* b, void* const* u, int32_t nsteps
         ev[k].trace = od[k].trace = b->trace + (size_t)k * 5 * b->trace_cap;
         ev[k].trace_cap = od[k].trace_cap = b->trace_cap;
     }
+    b->lazy = 0;
     PFC_CU(cudaMemsetAsync(b->scal, 0, (sizeof(double) * NSCAL + sizeof(unsigned) * NINTS) * b->n, s));
     auto steps = [&](int i0, int cnt, cudaStream_t st) -> cudaError_t {
         for (int i = i0; i < i0 + cnt; ++i) {
@@ -842,6 +844,7 @@ extern "C" pfc_status pfc_batch_step(pfc_batch* b, const void* const* u_in, void
         d[k].trace = nullptr;
         d[k].trace_cap = 0;
     }
+    b->lazy = 0;   // the scalars are reset: an open chain of lazy steps ends here
     if (b->timing) PFC_CU(cudaEventRecord(b->ev[0], s));
     PFC_CU(cudaMemsetAsync(b->scal, 0, (sizeof(double) * NSCAL + sizeof(unsigned) * NINTS) * b->n, s));
     if (b->timing) PFC_CU(cudaEventRecord(b->ev[1], s));
@@ -852,6 +855,73 @@ extern "C" pfc_status pfc_batch_step(pfc_batch* b, const void* const* u_in, void
         PFC_CU(cudaMemcpy2DAsync(scalars_dev, 5 * sizeof(double), b->scal, NSCAL * sizeof(double), 5 * sizeof(double),
                                  b->n, cudaMemcpyDeviceToDevice, s));
     if (b->timing) PFC_CU(cudaEventRecord(b->ev[3], s));
+    return PFC_OK;
+}
+
+// Chained steps in the fused form of the mass projection: the step stores
+// v = (u_in + c) - tau g with the pending offset c of the previous chained
+// step added as the sweep loads u_in, and leaves the new offset
+// c' = target - mean(v) (FP64, from the CTAs' partials) in the instance's
+// scalar slot for the next step; pfc_batch_lazy_finish adds it.  The target
+// mass is the mean of the first step's input.
+extern "C" pfc_status pfc_batch_step_lazy(pfc_batch* b, const void* const* u_in, void* const* u_out,
+                                          const double* tau, int32_t first, pfc_stream stream)
+{
+    NvtxRange nvtx_("pfc_batch_step_lazy");
+    if (!b) return fail(PFC_EINVAL, "batch is NULL");
+    if (!u_in || !u_out || !tau) return fail(PFC_EINVAL, "u_in, u_out and tau arrays are required");
+    if (!first && !b->lazy) return fail(PFC_EINVAL, "no chain of lazy steps is open: start one with first = 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<Inst<float>> d(b->host);
+    for (int k = 0; k < b->n; ++k) {
+        for (int w = 0; w < 2; ++w) {
+            const void* p = w ? (const void*)u_out[k] : u_in[k];
+            cudaPointerAttributes at;
+            if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess ||
+                (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+                (void)cudaGetLastError();
+                return fail(PFC_EINVAL, "%s[%d] is not device memory", w ? "u_out" : "u_in", k);
+            }
+        }
+        if (u_in[k] == u_out[k]) return fail(PFC_EINVAL, "u_out[%d] aliases u_in[%d]", k, k);
+        if (!isfinite(tau[k])) return fail(PFC_EINVAL, "tau[%d] is not finite", k);
+        d[k].u = (const float*)u_in[k];
+        d[k].out = (float*)u_out[k];
+        d[k].vec = (b->P[k].nx % 4 == 0) && ((uintptr_t)u_in[k]) % 16 == 0;
+        d[k].tau = (float)tau[k];
+        d[k].trace = nullptr;
+        d[k].trace_cap = 0;
+    }
+    if (b->timing) PFC_CU(cudaEventRecord(b->ev[0], s));
+    if (first) PFC_CU(cudaMemsetAsync(b->scal, 0, (sizeof(double) * NSCAL + sizeof(unsigned) * NINTS) * b->n, s));
+    if (b->timing) PFC_CU(cudaEventRecord(b->ev[1], s));
+    PFC_CU(launch_fused_batch(d.data(), b->n, b->tile_y, b->max_run, s));
+    if (b->timing) {
+        PFC_CU(cudaEventRecord(b->ev[2], s));
+        PFC_CU(cudaEventRecord(b->ev[3], s));
+    }
+    b->lazy = 1;
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_batch_lazy_finish(pfc_batch* b, void* const* u, pfc_stream stream)
+{
+    NvtxRange nvtx_("pfc_batch_lazy_finish");
+    if (!b) return fail(PFC_EINVAL, "batch is NULL");
+    if (!u) return fail(PFC_EINVAL, "u array is required");
+    if (!b->lazy) return fail(PFC_EINVAL, "no chain of lazy steps is open");
+    std::vector<Inst<float>> d(b->host);
+    for (int k = 0; k < b->n; ++k) {
+        cudaPointerAttributes at;
+        if (!u[k] || cudaPointerGetAttributes(&at, u[k]) != cudaSuccess ||
+            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            (void)cudaGetLastError();
+            return fail(PFC_EINVAL, "u[%d] is not device memory", k);
+        }
+        d[k].out = (float*)u[k];
+    }
+    PFC_CU(launch_add_offset_batch(d.data(), b->n, (cudaStream_t)stream));
+    b->lazy = 0;
     return PFC_OK;
 }
 
@@ -899,6 +969,7 @@ extern "C" pfc_status pfc_batch_step_host(pfc_batch* b, const void* const* u_in_
             PFC_CU(cudaEventRecord(b->evdone[k], s));
         }
     }
+    b->lazy = 0;
     PFC_CU(cudaMemsetAsync(b->scal, 0, (sizeof(double) * NSCAL + sizeof(unsigned) * NINTS) * b->n, s));
     for (int k = 0; k < b->n; ++k) {
         const long N = (long)b->P[k].nx * b->P[k].ny * b->P[k].nz;

@@ -38,7 +38,8 @@ EXPORTED = ("pfc_create", "pfc_destroy", "pfc_energy", "pfc_energy_and_grad", "p
             "pfc_status_string", "pfc_last_error", "pfc_set_coefficient_field", "pfc_diagnostics",
             "pfc_hflow_set_coefficient_field", "pfc_hflow_set_mass_field", "pfc_surface_cells",
             "pfc_curvature_histogram", "pfc_batch_step_host", "pfc_batch_host_wait", "pfc_hflow_batch_create",
-            "pfc_hflow_batch_destroy", "pfc_hflow_batch_field", "pfc_hflow_batch_run")
+            "pfc_hflow_batch_destroy", "pfc_hflow_batch_field", "pfc_hflow_batch_run", "pfc_batch_step_lazy",
+            "pfc_batch_lazy_finish")
 
 
 class PfcError(RuntimeError):
@@ -149,6 +150,8 @@ def load_library():
             "pfc_batch_step": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dp, vp, vp], ctypes.c_int),
             "pfc_batch_timing": ([vp, ctypes.c_int], ctypes.c_int),
             "pfc_batch_step_host": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dp, vp], ctypes.c_int),
+            "pfc_batch_step_lazy": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dp, ctypes.c_int32, vp], ctypes.c_int),
+            "pfc_batch_lazy_finish": ([vp, ctypes.POINTER(vp), vp], ctypes.c_int),
             "pfc_batch_host_wait": ([vp, vp], ctypes.c_int),
             "pfc_hflow_batch_create": ([P, dp, ctypes.c_int32, ctypes.POINTER(_CHFlow), ctypes.POINTER(vp)],
                                        ctypes.c_int),
@@ -409,6 +412,29 @@ class Batch:
             sp = ctypes.c_void_p(scalars.data_ptr())
         _check(self._lib.pfc_batch_step(self._h, pin, pout, taus.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                         sp, _stream(stream)))
+
+    def step_lazy(self, fields_in, fields_out, taus, first: bool, stream=None):
+        """One chained step in the fused form of the mass projection (enqueue
+        only): the stored result plus the pending per-problem offset is the
+        projected field; ``first`` opens the chain; ``lazy_finish`` adds the
+        offsets and closes it."""
+        n = len(self.probs)
+        if len(fields_in) != n or len(fields_out) != n:
+            raise ValueError("one input and one output field per problem")
+        pin = (ctypes.c_void_p * n)(*[_field(f, p, f"u_in[{k}]").value for k, (f, p) in enumerate(zip(fields_in, self.probs))])
+        pout = (ctypes.c_void_p * n)(*[_field(f, p, f"u_out[{k}]").value for k, (f, p) in enumerate(zip(fields_out, self.probs))])
+        taus = np.ascontiguousarray(np.broadcast_to(np.asarray(taus, dtype=np.float64), (n,)))
+        _check(self._lib.pfc_batch_step_lazy(self._h, pin, pout, taus.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             1 if first else 0, _stream(stream)))
+
+    def lazy_finish(self, fields, stream=None):
+        """Adds the pending offsets of a chain of ``step_lazy`` calls to the
+        fields (its last outputs) and closes the chain (enqueue only)."""
+        n = len(self.probs)
+        if len(fields) != n:
+            raise ValueError("one field per problem")
+        pu = (ctypes.c_void_p * n)(*[_field(f, p, f"u[{k}]").value for k, (f, p) in enumerate(zip(fields, self.probs))])
+        _check(self._lib.pfc_batch_lazy_finish(self._h, pu, _stream(stream)))
 
     def step_host(self, host_in, host_out, taus, wait: bool = True, stream=None):
         """One step of every problem from and to host memory (CPU float32

@@ -425,3 +425,57 @@ def test_symmetric_polynomial_skip_matches_full_path(prec):
     Eo, go = oracle.energy_and_grad(u, oprob(p0))
     assert E0 == pytest.approx(Eo, rel=1e-4 if prec == "fp32" else 1e-10)
     assert rel_max(g0.double().cpu().numpy(), go) < (1e-3 if prec == "fp32" else 1e-10)
+
+
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_lazy_step_chain_matches_exact_steps(symmetric):
+    """Chained steps in the fused form of the mass projection (the offset
+    c = m - mean(v) carried into the next step's loads and added once at the
+    end) and the same number of exact steps (offset added after each), both
+    FP32, against FP64 exact steps: the chain is no further from FP64 than the
+    exact FP32 steps are (they round differently: the offset enters the loads,
+    not the stencil differences), and the mass is kept.  A symmetric batch
+    runs the SYM sweep, a mixed one the general sweep."""
+    shapes = [(16, 20, 24), (12, 12, 32)]
+    a_sym, a_gen = (1.0, 0.3, 1.0, 0.1, 0.1, 0.0), (1.0, 0.3, 0.6, 0.1, -0.1, 0.0)
+    avals = [a_sym if (symmetric or k == 0) else a_gen for k in range(len(shapes))]
+    probs = [P(s, a, prec="fp32") for s, a in zip(shapes, avals)]
+    u0 = [I.noise(s, 0.3, 0.1, 40 + k).astype(np.float32) for k, s in enumerate(shapes)]
+    taus = [2e-3, 1e-3]
+    K = 12
+    ref = []
+    for s, a, u, tau in zip(shapes, avals, u0, taus):
+        ctx = pfc.Context(P(s, a, prec="fp64"))
+        x, y = torch.tensor(u.astype(np.float64), device="cuda"), None
+        y = torch.empty_like(x)
+        for k in range(K):
+            ctx.step(x, y, tau)
+            x, y = y, x
+        ref.append(x.clone())
+    b = pfc.Batch(probs)
+    A = [torch.tensor(x, device="cuda") for x in u0]
+    B = [torch.empty_like(x) for x in A]
+    for k in range(K):
+        b.step(A, B, taus)
+        A, B = B, A
+    exact = [x.clone() for x in A]
+    A = [torch.tensor(x, device="cuda") for x in u0]
+    B = [torch.empty_like(x) for x in A]
+    for k in range(K):
+        b.step_lazy(A, B, taus, first=(k == 0))
+        A, B = B, A
+    b.lazy_finish(A)
+    torch.cuda.synchronize()
+    for x, e, r, u in zip(A, exact, ref, u0):
+        err_lazy = (torch.linalg.norm(x.double() - r) / torch.linalg.norm(r)).item()
+        err_exact = (torch.linalg.norm(e.double() - r) / torch.linalg.norm(r)).item()
+        assert err_lazy < 1e-3 and err_lazy < 2.0 * err_exact + 1e-6, (err_lazy, err_exact)
+        assert abs(x.double().mean().item() - u.astype(np.float64).mean()) < 1e-6
+    # a chain must be opened, and an exact step closes it
+    with pytest.raises(pfc.PfcError):
+        b.step_lazy(A, B, taus, first=False)
+    b.step_lazy(A, B, taus, first=True)
+    b.step(B, A, taus)
+    with pytest.raises(pfc.PfcError):
+        b.lazy_finish(A)
+    b.close()
