@@ -67,3 +67,19 @@ def test_real_tune_small(tmp_path):
     assert {"tile_y", "max_run", "sweep_ms"} <= set(best)
     assert best["sweep_ms"] > 0 and len(best["tried"]) == len(autotune.CANDIDATES)
     assert min(r["sweep_ms"] for r in best["tried"]) == best["sweep_ms"]
+
+
+def test_bench_counts_algorithmic_flops_per_polynomial():
+    """The roofline's algorithmic flops: 211 per voxel-step in general, 185
+    for polynomials symmetric in kappa1, kappa2 (a20 = a02, a10 = a01), whose
+    sqrt(D+) terms have weight zero and are not evaluated; a workload counts
+    each problem by its own polynomial."""
+    import numpy as np
+    import bench
+    from paper_2103_04856_gb300 import inputs as I
+    assert bench.flops_per_voxel_step((1.0, 0.0, 1.0, 0.0, 0.0, 0.0)) == 185
+    assert bench.flops_per_voxel_step((0.0, 1.0, 0.0, 0.0, 0.0, 0.0)) == 185
+    assert bench.flops_per_voxel_step((1.0, 0.3, 0.2, 0.0, 0.0, 0.0)) == 211
+    assert bench.flops_per_voxel_step((1.0, 0.0, 1.0, 0.1, -0.1, 0.0)) == 211
+    val = I.validation_set_128()
+    assert bench.workload_flops(val) == 185.0 * sum(int(np.prod(i.shape)) for i in val)
