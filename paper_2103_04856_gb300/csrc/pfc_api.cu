@@ -817,14 +817,12 @@ extern "C" pfc_status pfc_batch_run(pfc_batch* b, void* const* u, int32_t nsteps
     return PFC_OK;
 }
 
-extern "C" pfc_status pfc_batch_step(pfc_batch* b, const void* const* u_in, void* const* u_out, const double* tau,
-                                     double* scalars_dev, pfc_stream stream)
+// The launch descriptors of one step of every instance from u_in to u_out
+// (device fields, not aliased, finite step sizes).
+static pfc_status step_descriptors(const pfc_batch* b, const void* const* u_in, void* const* u_out,
+                                   const double* tau, std::vector<Inst<float>>& d)
 {
-    NvtxRange nvtx_("pfc_batch_step");
-    if (!b) return fail(PFC_EINVAL, "batch is NULL");
-    if (!u_in || !u_out || !tau) return fail(PFC_EINVAL, "u_in, u_out and tau arrays are required");
-    cudaStream_t s = (cudaStream_t)stream;
-    std::vector<Inst<float>> d(b->host);
+    d = b->host;
     for (int k = 0; k < b->n; ++k) {
         for (int w = 0; w < 2; ++w) {
             const void* p = w ? (const void*)u_out[k] : u_in[k];
@@ -844,6 +842,18 @@ extern "C" pfc_status pfc_batch_step(pfc_batch* b, const void* const* u_in, void
         d[k].trace = nullptr;
         d[k].trace_cap = 0;
     }
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_batch_step(pfc_batch* b, const void* const* u_in, void* const* u_out, const double* tau,
+                                     double* scalars_dev, pfc_stream stream)
+{
+    NvtxRange nvtx_("pfc_batch_step");
+    if (!b) return fail(PFC_EINVAL, "batch is NULL");
+    if (!u_in || !u_out || !tau) return fail(PFC_EINVAL, "u_in, u_out and tau arrays are required");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<Inst<float>> d;
+    if (pfc_status st = step_descriptors(b, u_in, u_out, tau, d); st != PFC_OK) return st;
     b->lazy = 0;   // the scalars are reset: an open chain of lazy steps ends here
     if (b->timing) PFC_CU(cudaEventRecord(b->ev[0], s));
     PFC_CU(cudaMemsetAsync(b->scal, 0, (sizeof(double) * NSCAL + sizeof(unsigned) * NINTS) * b->n, s));
@@ -872,26 +882,8 @@ extern "C" pfc_status pfc_batch_step_lazy(pfc_batch* b, const void* const* u_in,
     if (!u_in || !u_out || !tau) return fail(PFC_EINVAL, "u_in, u_out and tau arrays are required");
     if (!first && !b->lazy) return fail(PFC_EINVAL, "no chain of lazy steps is open: start one with first = 1");
     cudaStream_t s = (cudaStream_t)stream;
-    std::vector<Inst<float>> d(b->host);
-    for (int k = 0; k < b->n; ++k) {
-        for (int w = 0; w < 2; ++w) {
-            const void* p = w ? (const void*)u_out[k] : u_in[k];
-            cudaPointerAttributes at;
-            if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess ||
-                (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
-                (void)cudaGetLastError();
-                return fail(PFC_EINVAL, "%s[%d] is not device memory", w ? "u_out" : "u_in", k);
-            }
-        }
-        if (u_in[k] == u_out[k]) return fail(PFC_EINVAL, "u_out[%d] aliases u_in[%d]", k, k);
-        if (!isfinite(tau[k])) return fail(PFC_EINVAL, "tau[%d] is not finite", k);
-        d[k].u = (const float*)u_in[k];
-        d[k].out = (float*)u_out[k];
-        d[k].vec = (b->P[k].nx % 4 == 0) && ((uintptr_t)u_in[k]) % 16 == 0;
-        d[k].tau = (float)tau[k];
-        d[k].trace = nullptr;
-        d[k].trace_cap = 0;
-    }
+    std::vector<Inst<float>> d;
+    if (pfc_status st = step_descriptors(b, u_in, u_out, tau, d); st != PFC_OK) return st;
     if (b->timing) PFC_CU(cudaEventRecord(b->ev[0], s));
     if (first) PFC_CU(cudaMemsetAsync(b->scal, 0, (sizeof(double) * NSCAL + sizeof(unsigned) * NINTS) * b->n, s));
     if (b->timing) PFC_CU(cudaEventRecord(b->ev[1], s));
