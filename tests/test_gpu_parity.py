@@ -479,3 +479,32 @@ def test_lazy_step_chain_matches_exact_steps(symmetric):
     with pytest.raises(pfc.PfcError):
         b.lazy_finish(A)
     b.close()
+
+
+def test_validation_128_chained_steps_as_benchmarked():
+    """The benchmark's timed step at full size: the four 128^3 validation
+    problems in one batch (the SYM sweep, 32 x 16 tiles), 10 chained steps
+    with the projection in fused form against 10 exact steps: the smooth
+    tanh fields keep the two within FP32 rounding, and the mass is kept."""
+    insts = I.validation_set_128()
+    probs = [pfc.Problem.from_shape(i.shape, eps=i.eps, a=i.a, prec="fp32", tile_y=16, tile_z=0) for i in insts]
+    u0 = [i.field().astype(np.float32) for i in insts]
+    taus = [i.tau for i in insts]
+    b = pfc.Batch(probs)
+    A = [torch.tensor(x, device="cuda") for x in u0]
+    B = [torch.empty_like(x) for x in A]
+    for k in range(10):
+        b.step(A, B, taus)
+        A, B = B, A
+    exact = [x.clone() for x in A]
+    A = [torch.tensor(x, device="cuda") for x in u0]
+    B = [torch.empty_like(x) for x in A]
+    for k in range(10):
+        b.step_lazy(A, B, taus, first=(k == 0))
+        A, B = B, A
+    b.lazy_finish(A)
+    torch.cuda.synchronize()
+    for x, e, u in zip(A, exact, u0):
+        assert (torch.linalg.norm(x - e) / torch.linalg.norm(e)).item() < 1e-6
+        assert abs(x.double().mean().item() - u.astype(np.float64).mean()) < 1e-6
+    b.close()
