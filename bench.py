@@ -245,31 +245,250 @@ def cpu_baseline_oracle():
             "sample": f"{reps} FP64 oracle step(s) of the 128^3 tanh sphere (2,097,152 voxels each), single thread"}
 
 
-def extra_workload(pfc, insts, flush, steps):
-    """Steady-state batched FP32 steps of another workload (L2 flushed before
-    each): voxel-steps/s and the sweep's share of HBM and FP32 peaks."""
+def problem_of(pfc, inst, prec="fp32", **kw):
+    return pfc.Problem.from_shape(inst.shape, eps=inst.eps, a=inst.a, h=inst.h, xi=inst.xi, well=inst.well,
+                                  prec=prec, **kw)
+
+
+def accuracy(pfc, insts, fields):
+    """FP32 fused against FP64 fused on the same FP32 states (the FP64 path
+    equals the oracle to 1e-10 in the tests): the worst relative energy
+    error and relative gradient 2-norm error over the instances."""
     import torch
-    probs = [pfc.Problem.from_shape(i.shape, eps=i.eps, a=i.a, prec="fp32") for i in insts]
-    A = [torch.tensor(i.field().astype(np.float32), device="cuda") for i in insts]
-    B = [torch.empty_like(a) for a in A]
-    vox = sum(a.numel() for a in A)
-    b = pfc.Batch(probs)
-    b.timing(True)
-    st, sw = [], []
-    for k in range(steps + 3):
+    e_err = g_err = 0.0
+    for inst, f in zip(insts, fields):
+        if isinstance(f, torch.Tensor):
+            u32 = f.to(device="cuda", dtype=torch.float32).contiguous()
+        else:
+            u32 = torch.tensor(np.asarray(f, dtype=np.float32), device="cuda")
+        c32, c64 = pfc.Context(problem_of(pfc, inst, "fp32")), pfc.Context(problem_of(pfc, inst, "fp64"))
+        E32, g32 = c32.energy_and_grad(u32)
+        E64, g64 = c64.energy_and_grad(u32.double())
+        e_err = max(e_err, abs(E32 - E64) / abs(E64))
+        g_err = max(g_err, float(torch.linalg.norm(g32.double() - g64) / torch.linalg.norm(g64)))
+        c32.close()
+        c64.close()
+        del g32, g64, u32
+    return {"rel_energy_err": e_err, "rel_grad_norm_err": g_err}
+
+
+def lazy_chain(batch, A, B, taus, flush, steps, warmup):
+    """`warmup` untimed, then `steps` timed chained steps (pfc_batch_step_lazy)
+    with the L2 flushed before each, and the launch that adds the last
+    offset, timed and spread over the steps.  Returns (ms per step, ms per
+    sweep, the projected fields)."""
+    import torch
+    cur, nxt = A, B
+    for k in range(warmup):
         flush.zero_()
-        b.step(A, B, [i.tau for i in insts])
-        x, y = b.last_timing()
-        if k >= 3:
-            st.append(x)
-            sw.append(y)
-        A, B = B, A
+        batch.step_lazy(cur, nxt, taus, first=(k == 0))
+        cur, nxt = nxt, cur
+    if warmup:
+        batch.lazy_finish(cur)
+    st, sw = [], []
+    for k in range(steps):
+        flush.zero_()
+        batch.step_lazy(cur, nxt, taus, first=(k == 0))
+        a, b = batch.last_timing()
+        st.append(a)
+        sw.append(b)
+        cur, nxt = nxt, cur
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    batch.lazy_finish(cur)
+    ev1.record()
+    torch.cuda.synchronize()
+    return float(np.mean(st)) + ev0.elapsed_time(ev1) / steps, float(np.mean(sw)), cur
+
+
+def alu_roofline(flops, ms, peak, peak_kind, kernel):
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_kind": peak_kind, "kernel": kernel, "kernel_ms": ms}
+
+
+def cpu_oracle_rate(inst, edge, seconds):
+    """The FP64 oracle (single thread) on an edge^3 crop of the workload's
+    field, repeated for about `seconds`: voxel-steps/s."""
+    import oracle
+    u = inst.field()[:edge, :edge, :edge].astype(np.float32).astype(np.float64).copy()
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.step(u, inst.problem(), inst.tau)
+        reps += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    return reps * u.size / (time.perf_counter() - t0), reps
+
+
+def membrane_block(pfc, I, flush, steps, peak, peak_kind, with_cpu):
+    """The largest single-GPU workload, 512^3 FP32 with the membrane-favouring
+    (asymmetric) polynomial: chained steps of the general sweep, its roofline,
+    end to end through host buffers, accuracy at the first and last state,
+    and the oracle on a crop of the same field."""
+    import torch
+    inst = I.membrane_descent_512()
+    host = inst.field().astype(np.float32)
+    vox = host.size
+    A = [torch.tensor(host, device="cuda")]
+    B = [torch.empty_like(A[0])]
+    acc0 = accuracy(pfc, [inst], A)
+    b = pfc.Batch([problem_of(pfc, inst)])
+    b.timing(True)
+    ms, msw, cur = lazy_chain(b, A, B, [inst.tau], flush, steps, 3)
+    acc1 = accuracy(pfc, [inst], cur)
+    del A, B, cur
+    peaks, hk = load_peaks()
+    roof = alu_roofline(workload_flops([inst]), msw, peak, peak_kind, "k_fused<float,16,STEP,64> (general sweep)")
+    hbm = 8.0 * vox / (msw * 1e-3) / 1e9
+    roof["traffic"] = None
+    roof["traffic_note"] = "no ncu capture of this launch (512^3 is above the capture size rule)"
+    roof["hbm"] = {"achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm / peaks["hbm_gbs"],
+                   "peak_kind": hk, "algorithmic_bytes_per_launch": 8.0 * vox}
+    pin_in = torch.from_numpy(host).pin_memory()
+    pin_out = torch.empty_like(pin_in).pin_memory()
+    for _ in range(2):
+        b.step_host([pin_in], [pin_out], [inst.tau])
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    n_e2e = 5
+    for _ in range(n_e2e):
+        b.step_host([pin_in], [pin_out], [inst.tau], wait=False)
+    b.host_wait()
+    e2e = {"value": vox * n_e2e / (time.perf_counter() - t1), "unit": UNIT, "h2d_bytes_per_step": host.nbytes,
+           "d2h_bytes_per_step": host.nbytes}
     b.close()
-    ms, msw = float(np.mean(st)), float(np.mean(sw))
-    return {"workload": f"{len(insts)} problem(s), {vox} voxels", "value": vox / (ms * 1e-3), "unit": UNIT,
-            "ms_per_step": ms, "sweep_ms": msw,
-            "alu_frac": workload_flops(insts) / (msw * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
-            "hbm_gbs": 8.0 * vox / (msw * 1e-3) / 1e9}
+    out = {"workload": "membrane_512: 512^3 FP32, eps=2, p=0.2k1^2+k2^2+0.3k1k2 (k1 the smaller), noise u0",
+           "value": vox / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "sweep_ms": msw, "roofline": roof,
+           "e2e": e2e, "accuracy_fp32_vs_fp64": {"initial": acc0, "final": acc1, "steps_between": steps + 3}}
+    if with_cpu:
+        rate, reps = cpu_oracle_rate(inst, 96, 5.0)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"{reps} FP64 oracle step(s) of a 96^3 crop of the 512^3 field, single thread"}
+    return out
+
+
+def descent_32_block(pfc, I):
+    """The 32^3 plain FP64 workload: 100 mass-projected steps of 1e-3 from
+    noise (pfc_run, one CUDA graph), fused and plain FP64 paths."""
+    import torch
+    inst = I.willmore_descent_32()
+    u0 = torch.tensor(inst.field(), device="cuda")
+    out = {"workload": "willmore_descent_32: 32^3 FP64, eps=1.5, p=k1^2+k2^2, 100 steps of 1e-3"}
+    for impl in ("fused", "plain"):
+        ctx = pfc.Context(problem_of(pfc, inst, "fp64", impl=impl))
+        x = u0.clone()
+        ctx.run(x, 100, inst.tau, trace=False)           # graph capture
+        x.copy_(u0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        tr = ctx.run(x, 100, inst.tau)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[impl] = {"ms_per_run": ms, "value": u0.numel() * 100 / (ms * 1e-3), "unit": UNIT,
+                     "energy_first_last": [float(tr[0, 0]), float(tr[-1, 0])]}
+        ctx.close()
+    out["note"] = "32,768 voxels per step: launch-bound (the run includes its trace copy and synchronisation)"
+    return out
+
+
+def tube_256_block(pfc, I, steps, peak, peak_kind):
+    """The 256^3 FP32 tube-favouring workload (asymmetric p): `steps`
+    mass-projected steps (pfc_run: the projection in fused form, 64-step CUDA
+    graphs), accuracy at the first and last state."""
+    import torch
+    inst = I.tube_descent_256()
+    u0 = torch.tensor(inst.field().astype(np.float32), device="cuda")
+    ctx = pfc.Context(problem_of(pfc, inst))
+    x = u0.clone()
+    ctx.run(x, 64, inst.tau, trace=False)                # graph capture
+    x.copy_(u0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    tr = ctx.run(x, steps, inst.tau)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ctx.close()
+    n = u0.numel()
+    return {"workload": "tube_descent_256: 256^3 FP32, eps=1.5, p=k1^2+0.2k2^2-0.5k1 (k1 the smaller), "
+                        f"{steps} steps of 1e-3",
+            "value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "roofline_incl_run_overheads": alu_roofline(workload_flops([inst]), ms, peak, peak_kind,
+                                                        "pfc_run step (general sweep + graph)"),
+            "energy_first_last": [float(tr[0, 0]), float(tr[-1, 0])], "mass_drift": float(abs(tr[-1, 1] - tr[0, 1])),
+            "accuracy_fp32_vs_fp64": {"initial": accuracy(pfc, [inst], [u0]), "final": accuracy(pfc, [inst], [x])}}
+
+
+def batch64_block(pfc, I, steps, ws, rank):
+    """The 64 mixed-size instances (random asymmetric p), partitioned across
+    the ranks by voxels, `steps` steps each (pfc_batch_run: one launch per
+    step over a rank's instances, 64-step graphs); traces gathered on rank 0.
+    Random polynomials can make a descent blow up: per-instance finiteness is
+    reported."""
+    import torch
+    from paper_2103_04856_gb300 import slab
+    insts = I.batch_instances(64)
+    sizes = [int(np.prod(i.shape)) for i in insts]
+    parts = slab.partition_instances(sizes, ws)
+    mine = parts[rank]
+    my = [insts[k] for k in mine]
+    b = pfc.Batch([problem_of(pfc, i) for i in my])
+    init = [torch.tensor(i.field().astype(np.float32), device="cuda") for i in my]
+    fields = [x.clone() for x in init]
+    b.run(fields, 64, [i.tau for i in my], trace=False, allow_nonfinite=True)    # graph capture
+    for f, x in zip(fields, init):
+        f.copy_(x)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0.record()
+    tr, finite = b.run(fields, steps, [i.tau for i in my], allow_nonfinite=True)
+    e1.record()
+    e1.synchronize()
+    ms = max_over_ranks([e0.elapsed_time(e1)])[0]
+    b.close()
+    traces = slab.gather_traces({k: tr[j] for j, k in enumerate(mine)}, len(insts))
+    vox = sum(sizes)
+    out = {"workload": f"batch64_mixed: 64 instances of 64^3/96^3/128^3 ({vox} voxels), random p, {steps} steps",
+           "value": vox * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "ranks": ws,
+           "partition": "by voxels, largest first (paper_2103_04856_gb300.slab.partition_instances)"}
+    if traces is not None:
+        out["finite_instances"] = int(sum(bool(np.all(np.isfinite(t))) for t in traces))
+    return out
+
+
+def slab_block(pfc, I, steps, ws, rank):
+    """The 512^3 membrane workload split in z across the ranks (one slab per
+    rank; with one rank the halo wraps locally): per step a halo exchange of
+    two planes per side, the slab's fused sweep, an all-gather of the sums
+    and their combine (paper_2103_04856_gb300.slab.SlabDescent)."""
+    import torch
+    from paper_2103_04856_gb300 import slab
+    inst = I.membrane_descent_512()
+    z0, nzl = slab.split_z(inst.shape[0], ws)[rank]
+    host = inst.field()[z0:z0 + nzl].astype(np.float32)
+    drv = slab.SlabDescent(problem_of(pfc, inst), torch.tensor(host, device="cuda"), z0)
+    drv.run(3, inst.tau)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        drv.step(inst.tau)
+    e1.record()
+    e1.synchronize()
+    ms = max_over_ranks([e0.elapsed_time(e1) / steps])[0]
+    n = int(np.prod(inst.shape))
+    return {"workload": f"membrane_512 split in {ws} z-slab(s), FP32, {steps} chained steps",
+            "value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "ranks": ws,
+            "halo_bytes_per_rank_per_step": 2 * 2 * inst.shape[1] * inst.shape[2] * 4}
 
 
 def alg1_workload(pfc, I, steps):
@@ -504,8 +723,7 @@ def main():
                              symmetric=all(i.a[0] == i.a[2] and i.a[3] == i.a[4] for i in insts))
         launch = {"tile_y": best["tile_y"], "max_run": best["max_run"], "source": "autotuned",
                   "tried": [{k: r[k] for k in ("tile_y", "max_run", "sweep_ms")} for r in best["tried"]]}
-    probs = [pfc.Problem.from_shape(i.shape, eps=i.eps, a=i.a, prec="fp32", tile_y=launch["tile_y"],
-                                    tile_z=launch["max_run"]) for i in insts]
+    probs = [problem_of(pfc, i, "fp32", tile_y=launch["tile_y"], tile_z=launch["max_run"]) for i in insts]
     host = [i.field().astype(np.float32) for i in insts]
     taus = [i.tau for i in insts]
     A = [torch.tensor(h, device="cuda") for h in host]
@@ -517,12 +735,7 @@ def main():
 
     # accuracy on the initial state: FP32 fused vs FP64 fused (the FP64 path
     # equals the oracle to 1e-10 in the tests)
-    rel_err = 0.0
-    for p, h, inst in zip(probs, host, insts):
-        e32 = pfc.Context(p).energy(torch.tensor(h, device="cuda"))
-        p64 = pfc.Problem.from_shape(inst.shape, eps=inst.eps, a=inst.a, prec="fp64")
-        e64 = pfc.Context(p64).energy(torch.tensor(h.astype(np.float64), device="cuda"))
-        rel_err = max(rel_err, abs(e32 - e64) / abs(e64))
+    acc_initial = accuracy(pfc, insts, host)
 
     # one step = one batched fused launch, the mass projection in its fused
     # form: each step's FP64 offset c = m - mean(u') is added by the next
@@ -545,7 +758,10 @@ def main():
         gpu_uuid = None
     clocks = ClockSampler(gpu_uuid)
     clocks.start()
-    time.sleep(0.3)
+    # the FP32 issue peak of this GPU now, measured in-process with FMA
+    # chains (pfc_measure_fp32_peak): the arithmetic roofline's denominator
+    fp32_peak = pfc.measure_fp32_peak()
+    time.sleep(0.2)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -583,32 +799,39 @@ def main():
     torch.cuda.synchronize()
     ms_step_mat = max_over_ranks([float(np.mean(mat_ms))])[0]
 
-    # mass is kept exactly by every step
+    # mass is kept by every step; accuracy again on the last state
     mass_err = max(abs(c.double().mean().item() - h.astype(np.float64).mean()) for c, h in zip(cur, host))
+    acc_final = accuracy(pfc, insts, cur)
 
-    # FP64 plain (unfused) GPU path on the same workload
-    fp64 = None
-    if args.fp64_steps > 0:
-        ctxs = [pfc.Context(pfc.Problem.from_shape(i.shape, eps=i.eps, a=i.a, prec="fp64", impl="plain"))
-                for i in insts]
+    # the FP64 paths on the same workload: plain (5 unfused passes through
+    # HBM) and fused (the same sweep in FP64), exact steps one at a time
+    def fp64_rate(impl, nsteps):
+        ctxs = [pfc.Context(problem_of(pfc, i, "fp64", impl=impl)) for i in insts]
         ua = [torch.tensor(h.astype(np.float64), device="cuda") for h in host]
         ub = [torch.empty_like(x) for x in ua]
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         tot = 0.0
-        for k in range(args.fp64_steps + 2):
+        for k in range(nsteps + 2):
             flush.zero_()
-            ev0.record()
+            e0.record()
             for c, x, y, tau in zip(ctxs, ua, ub, taus):
                 c.step(x, y, tau)
-            ev1.record()
-            ev1.synchronize()
+            e1.record()
+            e1.synchronize()
             if k >= 2:
-                tot += ev0.elapsed_time(ev1)
+                tot += e0.elapsed_time(e1)
             ua, ub = ub, ua
-        ms64 = tot / args.fp64_steps
-        fp64 = {"value": vox / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64, "dtype": "f64",
-                "impl": "plain: 5 unfused passes storing grad u, Hess u and cotangents in HBM"}
-        del ctxs, ua, ub
+        for c in ctxs:
+            c.close()
+        ms64 = tot / nsteps
+        return {"value": vox / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64, "dtype": "f64"}
+
+    fp64 = fp64f = None
+    if args.fp64_steps > 0:
+        fp64 = fp64_rate("plain", args.fp64_steps)
+        fp64["impl"] = "plain: 5 unfused passes storing grad u, Hess u and cotangents in HBM"
+        fp64f = fp64_rate("fused", args.fp64_steps)
+        fp64f["impl"] = "fused: the same single sweep in FP64, plus the projection launch"
 
     # end to end through the C ABI with host buffers (pfc_batch_step_host):
     # every step copies its four fields in from pinned host memory, steps them
@@ -630,6 +853,8 @@ def main():
            "d2h_bytes_per_step": e2e_bytes}
 
     peaks, peak_kind = load_peaks()
+    fp32_kind = ("measured in-process: pfc_measure_fp32_peak (FMA chains on every SM, best of 3, CUDA events) "
+                 "just before the timed steps")
     bytes_launch = 8.0 * vox                      # read u, write u' (FP32)
     hbm_achieved = bytes_launch / (ms_sweep * 1e-3) / 1e9
     ty_used = launch["tile_y"] or 16                 # the batch's automatic height
@@ -637,18 +862,16 @@ def main():
     traffic = float(prof["traffic_bytes_per_launch"]) if prof else None
     flops_launch = workload_flops(insts)
     all_sym = all(i.a[0] == i.a[2] and i.a[3] == i.a[4] for i in insts)
-    alu_achieved = flops_launch / (ms_sweep * 1e-3) / 1e12
-    # 211 flop per 8 B is ~2x GB300's FP32/HBM balance: the sweep is bound by
-    # arithmetic issue, not by HBM; the HBM fraction is reported beside it
-    roofline = {"bound": "alu", "achieved": alu_achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": alu_achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2070 MHz",
-                "kernel": f"k_fused<float,{ty_used},STEP,64{',SYM' if all_sym else ''}> (batched fused sweep)",
-                "kernel_ms": ms_sweep,
-                "flops_per_voxel_step": flops_launch / vox, "voxels_per_launch": vox,
-                "hbm": {"achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                        "frac": hbm_achieved / peaks["hbm_gbs"], "peak_kind": peak_kind,
-                        "algorithmic_bytes_per_launch": bytes_launch}}
+    # 185-211 flop per 8 B is ~2x GB300's FP32/HBM balance: the sweep is bound
+    # by arithmetic issue, not by HBM; the HBM fraction is reported beside it
+    roofline = alu_roofline(flops_launch, ms_sweep, fp32_peak, fp32_kind,
+                            f"k_fused<float,{ty_used},STEP,64{',SYM' if all_sym else ''}> (batched fused sweep)")
+    roofline.update({"traffic": traffic, "derived_peak": FP32_PEAK_TFLOPS,
+                     "derived_peak_kind": "152 SM x 128 FP32 lanes x 2 flop x 2070 MHz",
+                     "flops_per_voxel_step": flops_launch / vox, "voxels_per_launch": vox,
+                     "hbm": {"achieved": hbm_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                             "frac": hbm_achieved / peaks["hbm_gbs"], "peak_kind": peak_kind,
+                             "algorithmic_bytes_per_launch": bytes_launch}})
     if traffic is None:
         roofline["traffic_note"] = traffic_note
     if prof and prof.get("warp_instructions_per_launch"):
@@ -663,8 +886,12 @@ def main():
 
     extra = None
     if not args.no_extra:
-        extra = {"batch64_mixed": extra_workload(pfc, I.batch_instances(64), flush, steps=20),
-                 "membrane_512": extra_workload(pfc, [I.membrane_descent_512()], flush, steps=10),
+        extra = {"membrane_512": membrane_block(pfc, I, flush, 10, fp32_peak, fp32_kind,
+                                                with_cpu=(rank == 0 and ws == 1 and not args.no_cpu_baseline)),
+                 "batch64_mixed": batch64_block(pfc, I, 500, ws, rank),
+                 "tube_256_2000_steps": tube_256_block(pfc, I, 2000, fp32_peak, fp32_kind),
+                 "willmore_32_fp64_100_steps": descent_32_block(pfc, I),
+                 "membrane_512_zslabs": slab_block(pfc, I, 20, ws, rank),
                  "alg1_flow_100": alg1_workload(pfc, I, steps=8000),
                  "alg1_batch_100x16": alg1_batch_workload(pfc, I, 16, steps=256),
                  "extended_sweep_128": extended_sweep_workload(pfc, I, steps=64),
@@ -690,9 +917,13 @@ def main():
                        "parallelism": f"replicas x{ws}"},
             "wall_ms_per_step_incl_flush": 1e3 * wall / args.steps,
             "ms_per_step_materialized": ms_step_mat,
-            "rel_energy_err_fp32_vs_fp64": rel_err, "mass_drift": mass_err,
-            "fp64_plain": fp64,
+            "accuracy_fp32_vs_fp64": {"initial": acc_initial, "final": acc_final,
+                                      "steps_between": args.warmup + 2 * args.steps},
+            "rel_energy_err_fp32_vs_fp64": max(acc_initial["rel_energy_err"], acc_final["rel_energy_err"]),
+            "mass_drift": mass_err,
+            "fp64_plain": fp64, "fp64_fused": fp64f,
             "speedup_vs_fp64_plain": (value / ws) / fp64["value"] if fp64 else None,
+            "speedup_vs_fp64_fused": (value / ws) / fp64f["value"] if fp64f else None,
             "launch": launch, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "other_workloads": extra,
             "gpu_launches": args.steps + 1, "clocks": clocks.summary()}
     if rank == 0:

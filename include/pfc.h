@@ -84,8 +84,18 @@ typedef struct {
      * replaces eq. Meps in the energy, its gradient and the curvatures; 0:
      * eq. Meps.  Fused path only; runs the extended sweep. */
     int32_t proj;
-    int32_t reserved;       /* must be 0 */
+    /* PFC_FLAG_* bits; 0 for the default behaviour. */
+    uint32_t flags;
 } pfc_problem;
+
+/* FP32 only: D = 2||M||^2 - (Tr M)^2 is the difference of two numbers of
+ * size ||M||^2, so its FP32 rounding error is about 2^-22 (2||M||^2 + (Tr
+ * M)^2).  Where that error is more than 2^-6 of max(|D|, xi) and the sqrt(D+)
+ * terms carry weight (c3 Tr M + c5 |grad u| != 0), the sweep recomputes D in
+ * FP64 from the exact stencil inputs (Sec. 3.1 invariants).  This flag turns
+ * that refinement off (for measuring what it changes); it has no effect on
+ * FP64 problems or on polynomials symmetric in kappa1, kappa2. */
+#define PFC_FLAG_NO_DISCRIMINANT_REFINEMENT 1u
 
 typedef struct pfc_ctx pfc_ctx;
 
@@ -164,6 +174,59 @@ pfc_status pfc_curvature_histogram(pfc_ctx* ctx, const void* cells, int64_t n, i
  * have the type and layout of u. */
 pfc_status pfc_curvatures(pfc_ctx* ctx, const void* u, void* k1, void* k2, pfc_stream stream);
 
+/* ---- One periodic grid split in z across processes (one per GPU).  The
+ * stencils of the sweep reach two planes (a voxel's cotangents need its
+ * neighbours, whose stencils need theirs: Sec. 4.1 periodic finite
+ * differences), so a slab of planes [z0, z0 + nz_local) is evaluated
+ * exactly from its own planes plus the two planes below and the two above
+ * it, with the periodic wrap of the whole grid.  Per step:
+ *   1. fill the slab's halo from its neighbours (the caller's transport:
+ *      NCCL send/recv, cudaMemcpyPeerAsync, a local copy for one slab);
+ *   2. pfc_slab_sweep: the fused sweep over the slab, writing g or the
+ *      stored step v = (u + c) - tau g and the slab's FP64 sums;
+ *   3. gather every slab's sums (all-gather, rank order) and pfc_slab_finish:
+ *      every slab combines them in the same order into the same scalars,
+ *      including the offset c = m - mean(v) of the mass projection in its
+ *      fused form (as pfc_run applies it), which the next STEP sweep adds to
+ *      u as it loads.
+ * pfc_slab_apply_offset adds the pending c to u and closes the chain. */
+typedef struct pfc_slab pfc_slab;
+enum { PFC_SLAB_ENERGY = 0, PFC_SLAB_GRAD = 1, PFC_SLAB_STEP = 2 };
+#define PFC_SLAB_NSUMS 8     /* doubles per slab in a row of sums (6 used, 2 spare) */
+/* prob: the WHOLE grid (nx, ny, nz global), fused path, FP32 or FP64 (mu and
+ * proj allowed; no coefficient field).  This slab holds planes
+ * [z0, z0 + nz_local), nz_local >= 2, inside [0, nz).  Allocates the slab's
+ * FP64 partials and scalars (not its fields). */
+pfc_status pfc_slab_create(const pfc_problem* prob, int32_t z0, int32_t nz_local, pfc_slab** out);
+void pfc_slab_destroy(pfc_slab* slab);
+/* One sweep over the slab.  u: the slab's nz_local planes (device, layout of
+ * pfc_energy_and_grad with nz = nz_local).  halo: 4 planes of nx*ny values
+ * (device, caller-owned): global planes z0-2, z0-1, z0+nz_local,
+ * z0+nz_local+1 (mod nz) of the field u belongs to, e.g. the neighbouring
+ * slabs' stored fields after a STEP; read, never written.  mode:
+ *   PFC_SLAB_ENERGY  out unused (may be NULL);
+ *   PFC_SLAB_GRAD    out = g = dE/du on the slab's planes;
+ *   PFC_SLAB_STEP    out = (u + c) - tau g, c the pending offset (0 after
+ *                    create and after pfc_slab_apply_offset).
+ * ENERGY and GRAD evaluate u as given (apply a pending offset first).
+ * sums_dev (device, PFC_SLAB_NSUMS doubles) receives this slab's FP64 sums
+ * (energy, sum of u + c, sum of g, sum of |g|, max |g|, sum of out).  out
+ * must not alias u or halo.  Enqueue only. */
+pfc_status pfc_slab_sweep(pfc_slab* slab, const void* u, const void* halo, void* out, int32_t mode, double tau,
+                          double* sums_dev, pfc_stream stream);
+/* Combines nslabs rows of sums (device, nslabs x PFC_SLAB_NSUMS doubles, in
+ * rank order: row r from slab r) of the last sweep, one thread in a fixed
+ * order, into the slab's scalars; scalars_dev (device, may be NULL) receives
+ * E, mean(u + c) (STEP only), lambda = mean g, max|g|, mean|g| of the whole
+ * grid, as pfc_step's.  After a STEP the new offset c is left for the next
+ * STEP sweep; the mass kept is that of the first STEP's input after create
+ * or apply_offset.  Enqueue only. */
+pfc_status pfc_slab_finish(pfc_slab* slab, const double* sums_all_dev, int32_t nslabs, double* scalars_dev,
+                           pfc_stream stream);
+/* u += c (the pending offset; u: the slab's last stored field), and the
+ * chain is closed.  Enqueue only. */
+pfc_status pfc_slab_apply_offset(pfc_slab* slab, void* u, pfc_stream stream);
+
 /* Many independent problems (any sizes, each with its own coefficients and
  * step size), advanced together: every step is ONE kernel launch over the
  * tiles of all instances, and the step loop is captured in a CUDA graph.
@@ -197,7 +260,8 @@ pfc_status pfc_batch_step(pfc_batch* batch, const void* const* u_in, void* const
  * place (one launch) and closes the chain.  Results equal a sequence of
  * pfc_batch_step calls up to FP32 rounding (the offset enters the loads, not
  * the stencil differences).  u_out[k] must not alias u_in[k]; enqueue only;
- * PFC_EINVAL for first == 0 without an open chain.  pfc_batch_step,
+ * PFC_EINVAL for first == 0 without an open chain, and for first != 0 while
+ * a chain is open (its pending offsets would be lost).  pfc_batch_step,
  * pfc_batch_run and pfc_batch_step_host close an open chain (they reset the
  * offsets). */
 pfc_status pfc_batch_step_lazy(pfc_batch* batch, const void* const* u_in, void* const* u_out, const double* tau,
@@ -291,9 +355,11 @@ pfc_status pfc_hflow_set_mass_field(pfc_hflow* flow, const void* m_field, pfc_st
  * the allocator's implicit device-wide synchronisation).  The paper has no
  * counterpart: this is an interface convenience.
  *  - prob: the problem (impl must be PFC_IMPL_FUSED); u, g: caller-owned
- *    device fields as for pfc_energy_and_grad; E_host may be NULL (then the
- *    call only enqueues work).
- *  - Scratch: a static device array in the library (49,256 bytes, held by
+ *    fields of the current device as for pfc_energy_and_grad (PFC_EINVAL for
+ *    host memory, another device's memory, or g == u); E_host may be NULL:
+ *    then the call only enqueues work, and the scratch stays in use until the
+ *    stream has run it.  PFC_ENONFINITE if E_host receives a non-finite energy.
+ *  - Scratch: a static device array in the library (49,232 bytes, held by
  *    every GPU that loads the library until the process exits) with room for
  *    1024 CTAs of FP64 partial sums; a problem that would need more CTAs
  *    (only possible with a small tile_z) returns PFC_EINVAL.
@@ -304,6 +370,14 @@ pfc_status pfc_hflow_set_mass_field(pfc_hflow* flow, const void* m_field, pfc_st
  *    them, e.g. on one stream. */
 pfc_status pfc_energy_and_grad_noalloc(const pfc_problem* prob, const void* u, void* g, double* E_host,
                                        pfc_stream stream);
+
+/* FP32 FMA throughput of the current device in TFLOP/s (2 flops per FMA):
+ * independent FMA chains on every SM, the best of three launches timed with
+ * CUDA events on `stream` after one warm-up (about 20 ms each at the GB300's
+ * maximum clock).  The denominator of the fused sweep's arithmetic roofline;
+ * the paper has no counterpart.  Allocates nothing (two events); changes no
+ * device setting; synchronises the stream. */
+pfc_status pfc_measure_fp32_peak(double* tflops_host, pfc_stream stream);
 
 /* eq. redundant: b = (h2, H0, k1, alpha, kappa1_0, beta, kappa2_0) expanded
  * into a = (a20, a11, a02, a10, a01, a00).  Host only. */

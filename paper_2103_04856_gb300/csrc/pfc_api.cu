@@ -83,12 +83,9 @@ struct pfc_ctx {
     cudaStream_t cap = nullptr;
 };
 
-static int sm_count(int dev)
-{
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
-    return n;
-}
+
+// 1 unless the problem turns the FP32 discriminant refinement off
+static int refine_of(const pfc_problem& p) { return (p.flags & PFC_FLAG_NO_DISCRIMINANT_REFINEMENT) ? 0 : 1; }
 
 static pfc_status check_problem(const pfc_problem* p)
 {
@@ -110,7 +107,7 @@ static pfc_status check_problem(const pfc_problem* p)
     if (p->mu != 0.0 && p->impl != PFC_IMPL_FUSED)
         return fail(PFC_EUNSUPPORTED, "the orientation term (mu != 0) runs on the fused path only");
     if (p->proj != 0 && p->proj != 1) return fail(PFC_EINVAL, "proj must be 0 or 1");
-    if (p->reserved != 0) return fail(PFC_EINVAL, "reserved must be 0");
+    if (p->flags & ~PFC_FLAG_NO_DISCRIMINANT_REFINEMENT) return fail(PFC_EINVAL, "unknown flags 0x%x", p->flags);
     if (p->proj && p->impl != PFC_IMPL_FUSED)
         return fail(PFC_EUNSUPPORTED, "the projected M runs on the fused path only");
     return PFC_OK;
@@ -134,6 +131,21 @@ static void geometry(const pfc_problem* p, int sms, int* tile_y, int* zc, int* t
     *cz = (p->nz + z - 1) / z;
 }
 
+// ptr is device (or managed) memory of `device`, and `device` is current:
+// the kernels run on the current device and must not touch another GPU's
+// memory
+static bool on_device(const void* ptr, int device)
+{
+    cudaPointerAttributes at;
+    int cur = -1;
+    if (!ptr || cudaGetDevice(&cur) != cudaSuccess || cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == device &&
+           cur == device;
+}
+
 static pfc_status check_dev_ptr(const pfc_ctx* c, const void* ptr, const char* name)
 {
     if (!ptr) return fail(PFC_EINVAL, "%s is NULL", name);
@@ -146,6 +158,11 @@ static pfc_status check_dev_ptr(const pfc_ctx* c, const void* ptr, const char* n
     if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
         return fail(PFC_EINVAL, "%s is not device memory", name);
     if (at.device != c->device) return fail(PFC_EINVAL, "%s is on device %d, context on %d", name, at.device, c->device);
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != c->device) {
+        (void)cudaGetLastError();
+        return fail(PFC_EINVAL, "the context's device %d is not the current device", c->device);
+    }
     return PFC_OK;
 }
 
@@ -185,7 +202,7 @@ extern "C" pfc_status pfc_create(const pfc_problem* prob, pfc_ctx** out)
         (void)cudaGetLastError();
         return fail(PFC_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     }
-    geometry(prob, sm_count(c->device), &c->tile_y, &c->zc, &c->tiles_x, &c->tiles_y, &c->chunks_z);
+    geometry(prob, device_sms(), &c->tile_y, &c->zc, &c->tiles_x, &c->tiles_y, &c->chunks_z);
     c->nblocks = (int)fused_slots(prob->nx, prob->ny, prob->nz, c->tile_y, prob->tile_z);
     c->plain_nblocks = plain_blocks(c->N);
     const int nparts = c->nblocks > c->plain_nblocks ? c->nblocks : c->plain_nblocks;
@@ -236,7 +253,7 @@ static Inst<T> make_inst(const pfc_ctx* c, const void* u, void* out, double tau)
     in.vec = (P.nx % vecw == 0) && (((uintptr_t)u) % 16 == 0);
     in.first_block = 0;
     in.nblocks = c->nblocks;
-    in.C = make_coef<T>(P.a, P.h, P.eps, P.xi, P.well, P.mu, P.theta, P.proj);
+    in.C = make_coef<T>(P.a, P.h, P.eps, P.xi, P.well, P.mu, P.theta, P.proj, refine_of(P));
     in.cf = c->cf_on ? (const T*)c->cfield : nullptr;
     in.tau = (T)tau;
     in.inv_N = 1.0 / (double)c->N;
@@ -267,11 +284,11 @@ static cudaError_t enqueue(pfc_ctx* c, int mode, const void* u, void* out, doubl
     if (c->P.impl == PFC_IMPL_PLAIN) {
         if (c->P.prec == PFC_FP64)
             return launch_plain<double>((const double*)u, (double*)out, plain_bufs<double>(c), c->P.nx, c->P.ny,
-                                        c->P.nz, make_coef<double>(c->P.a, c->P.h, c->P.eps, c->P.xi, c->P.well, c->P.mu, c->P.theta, c->P.proj),
+                                        c->P.nz, make_coef<double>(c->P.a, c->P.h, c->P.eps, c->P.xi, c->P.well, c->P.mu, c->P.theta, c->P.proj, refine_of(c->P)),
                                         mode, tau, 1.0 / (double)c->N, c->partials, c->plain_nblocks, c->ints,
                                         c->scal, c->trace, c->trace_cap, s);
         return launch_plain<float>((const float*)u, (float*)out, plain_bufs<float>(c), c->P.nx, c->P.ny, c->P.nz,
-                                   make_coef<float>(c->P.a, c->P.h, c->P.eps, c->P.xi, c->P.well, c->P.mu, c->P.theta, c->P.proj), mode,
+                                   make_coef<float>(c->P.a, c->P.h, c->P.eps, c->P.xi, c->P.well, c->P.mu, c->P.theta, c->P.proj, refine_of(c->P)), mode,
                                    (float)tau, 1.0 / (double)c->N, c->partials, c->plain_nblocks, c->ints, c->scal,
                                    c->trace, c->trace_cap, s);
     }
@@ -573,6 +590,163 @@ extern "C" pfc_status pfc_curvature_histogram(pfc_ctx* c, const void* cells, int
     return PFC_OK;
 }
 
+// ------------------------------------------------------------ z-slab
+
+// One z-slab of a periodic grid split across processes (one per GPU): the
+// slab's planes, a caller-owned halo of the two planes beyond each end
+// (filled from the neighbouring slabs before every sweep), and the scalars
+// combined from every slab's FP64 sums.
+struct pfc_slab {
+    pfc_problem P;          // the whole grid
+    int z0 = 0, nzl = 0;    // global index of the first plane, planes held
+    int device = 0;
+    int tile_y = 16;
+    long long N = 0;        // voxels of the whole grid
+    int nblocks = 0;        // partial slots of one sweep
+    double* mem = nullptr;  // partials, then scalars, then counters
+    double* partials = nullptr;
+    double* scal = nullptr;
+    unsigned* ints = nullptr;
+    int last_mode = -1;     // mode of the last sweep: what pfc_slab_finish combines
+};
+
+extern "C" pfc_status pfc_slab_create(const pfc_problem* prob, int32_t z0, int32_t nz_local, pfc_slab** out)
+{
+    if (!out) return fail(PFC_EINVAL, "out is NULL");
+    *out = nullptr;
+    pfc_status st = check_problem(prob);
+    if (st) return st;
+    if (prob->impl != PFC_IMPL_FUSED) return fail(PFC_EUNSUPPORTED, "z-slabs run on the fused path only");
+    if (nz_local < 2 || z0 < 0 || (long long)z0 + nz_local > prob->nz)
+        return fail(PFC_EINVAL, "slab [%d, %d + %d) must hold >= 2 planes inside 0..nz = %d", z0, z0, nz_local, prob->nz);
+    pfc_slab* sl = new (std::nothrow) pfc_slab();
+    if (!sl) return fail(PFC_ENOMEM, "host allocation failed");
+    sl->P = *prob;
+    sl->z0 = z0;
+    sl->nzl = nz_local;
+    sl->N = (long long)prob->nx * prob->ny * prob->nz;
+    if (cudaGetDevice(&sl->device) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete sl;
+        return fail(PFC_ECUDA, "cudaGetDevice failed");
+    }
+    pfc_problem local = *prob;
+    local.nz = nz_local;
+    int zc, tx, ty, cz;
+    geometry(&local, device_sms(), &sl->tile_y, &zc, &tx, &ty, &cz);
+    sl->nblocks = (int)fused_slots(prob->nx, prob->ny, nz_local, sl->tile_y, prob->tile_z);
+    const size_t bytes = sizeof(double) * ((size_t)NPART * sl->nblocks + NSCAL) + sizeof(unsigned) * NINTS;
+    if (cudaMalloc((void**)&sl->mem, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete sl;
+        return fail(PFC_ENOMEM, "device allocation of %zu bytes failed", bytes);
+    }
+    sl->partials = sl->mem;
+    sl->scal = sl->mem + (size_t)NPART * sl->nblocks;
+    sl->ints = reinterpret_cast<unsigned*>(sl->scal + NSCAL);
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMemsetAsync(sl->scal, 0, sizeof(double) * NSCAL + sizeof(unsigned) * NINTS, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        if (s) cudaStreamDestroy(s);
+        cudaFree(sl->mem);
+        delete sl;
+        return fail(PFC_ECUDA, "clearing the slab's scalars failed: %s", cudaGetErrorString(e));
+    }
+    cudaStreamDestroy(s);
+    *out = sl;
+    return PFC_OK;
+}
+
+extern "C" void pfc_slab_destroy(pfc_slab* sl)
+{
+    if (!sl) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(sl->device);
+    cudaDeviceSynchronize();
+    cudaFree(sl->mem);
+    cudaSetDevice(prev);
+    delete sl;
+}
+
+template <typename T>
+static Inst<T> slab_inst(const pfc_slab* sl, const void* u, const void* halo, void* out, double tau, double* sums)
+{
+    Inst<T> in{};
+    const pfc_problem& P = sl->P;
+    in.u = (const T*)u;
+    in.out = (T*)out;
+    in.nx = P.nx; in.ny = P.ny; in.nz = sl->nzl;
+    in.vec = (P.nx % (16 / (int)sizeof(T)) == 0) && ((uintptr_t)u) % 16 == 0 && ((uintptr_t)halo) % 16 == 0;
+    in.nblocks = sl->nblocks;
+    in.C = make_coef<T>(P.a, P.h, P.eps, P.xi, P.well, P.mu, P.theta, P.proj, refine_of(P));
+    in.tau = (T)tau;
+    in.inv_N = 1.0 / (double)sl->N;
+    in.partials = sl->partials;
+    in.ints = sl->ints;
+    in.scal = sl->scal;
+    in.halo = (const T*)halo;
+    in.sums_out = sums;
+    return in;
+}
+
+extern "C" pfc_status pfc_slab_sweep(pfc_slab* sl, const void* u, const void* halo, void* out, int32_t mode,
+                                     double tau, double* sums_dev, pfc_stream stream)
+{
+    NvtxRange nvtx_("pfc_slab_sweep");
+    if (!sl) return fail(PFC_EINVAL, "slab is NULL");
+    if (mode != MODE_ENERGY && mode != MODE_GRAD && mode != MODE_STEP) return fail(PFC_EINVAL, "unknown mode %d", mode);
+    if (!on_device(u, sl->device) || !on_device(halo, sl->device) || !on_device(sums_dev, sl->device))
+        return fail(PFC_EINVAL, "u, halo and sums_dev must be device memory of the slab's (current) device");
+    if (mode != MODE_ENERGY) {
+        if (!on_device(out, sl->device)) return fail(PFC_EINVAL, "out must be device memory of the slab's device");
+        if (out == u || out == halo) return fail(PFC_EINVAL, "out must not alias u or halo");
+    }
+    if (!isfinite(tau)) return fail(PFC_EINVAL, "tau is not finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (sl->P.prec == PFC_FP64)
+        PFC_CU(launch_fused<double>(slab_inst<double>(sl, u, halo, out, tau, sums_dev), mode, sl->tile_y,
+                                    sl->P.tile_z, s));
+    else
+        PFC_CU(launch_fused<float>(slab_inst<float>(sl, u, halo, out, tau, sums_dev), mode, sl->tile_y,
+                                   sl->P.tile_z, s));
+    sl->last_mode = mode;
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_slab_finish(pfc_slab* sl, const double* sums_all_dev, int32_t nslabs, double* scalars_dev,
+                                      pfc_stream stream)
+{
+    NvtxRange nvtx_("pfc_slab_finish");
+    if (!sl) return fail(PFC_EINVAL, "slab is NULL");
+    if (sl->last_mode < 0) return fail(PFC_EINVAL, "no sweep to finish");
+    if (nslabs < 1) return fail(PFC_EINVAL, "nslabs must be >= 1");
+    if (!on_device(sums_all_dev, sl->device)) return fail(PFC_EINVAL, "sums_all_dev must be device memory of the slab's device");
+    if (scalars_dev && !on_device(scalars_dev, sl->device))
+        return fail(PFC_EINVAL, "scalars_dev must be device memory of the slab's device");
+    PFC_CU(launch_slab_finish(sums_all_dev, nslabs, 1.0 / (double)sl->N, sl->last_mode, sl->scal, sl->ints,
+                              scalars_dev, (cudaStream_t)stream));
+    return PFC_OK;
+}
+
+extern "C" pfc_status pfc_slab_apply_offset(pfc_slab* sl, void* u, pfc_stream stream)
+{
+    if (!sl) return fail(PFC_EINVAL, "slab is NULL");
+    if (!on_device(u, sl->device)) return fail(PFC_EINVAL, "u must be device memory of the slab's (current) device");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long n = (long)sl->P.nx * sl->P.ny * sl->nzl;
+    if (sl->P.prec == PFC_FP64)
+        PFC_CU(launch_add_offset<double>((double*)u, (const double*)u, n, sl->scal + S_C, s));
+    else
+        PFC_CU(launch_add_offset<float>((float*)u, (const float*)u, n, sl->scal + S_C, s));
+    // the chain is closed: no pending offset, and the next step takes its input's mass as the target
+    PFC_CU(cudaMemsetAsync(sl->scal + S_C, 0, sizeof(double), s));
+    PFC_CU(cudaMemsetAsync(sl->ints + I_COUNTER, 0, sizeof(unsigned), s));
+    return PFC_OK;
+}
+
 // ------------------------------------------------------------ batch
 
 struct pfc_batch {
@@ -646,7 +820,7 @@ extern "C" pfc_status pfc_batch_create(const pfc_problem* probs, int32_t n, pfc_
         (void)cudaGetLastError();
         return fail(PFC_ECUDA, "cudaGetDevice failed");
     }
-    const int sms = sm_count(b->device);
+    const int sms = device_sms();
     b->host.resize(n);
     b->ping.assign(n, nullptr);
     bool ok = true;
@@ -664,7 +838,7 @@ extern "C" pfc_status pfc_batch_create(const pfc_problem* probs, int32_t n, pfc_
         in.zc = zc;
         in.tiles_x = tx; in.tiles_y = tyn; in.chunks_z = cz;
         units += (long long)tx * tyn * p.nz;
-        in.C = make_coef<float>(p.a, p.h, p.eps, p.xi, p.well);
+        in.C = make_coef<float>(p.a, p.h, p.eps, p.xi, p.well, 0.0, nullptr, 0, refine_of(p));
         in.inv_N = 1.0 / ((double)p.nx * p.ny * p.nz);
         ok = cudaMalloc(&b->ping[k], sizeof(float) * (size_t)p.nx * p.ny * p.nz) == cudaSuccess;
     }
@@ -714,12 +888,7 @@ extern "C" pfc_status pfc_batch_run(pfc_batch* b, void* const* u, int32_t nsteps
     if (nsteps < 0) return fail(PFC_EINVAL, "nsteps must be >= 0");
     for (int k = 0; k < b->n; ++k) {
         if (!u[k]) return fail(PFC_EINVAL, "u[%d] is NULL", k);
-        cudaPointerAttributes at;
-        if (cudaPointerGetAttributes(&at, u[k]) != cudaSuccess ||
-            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
-            (void)cudaGetLastError();
-            return fail(PFC_EINVAL, "u[%d] is not device memory", k);
-        }
+        if (!on_device(u[k], b->device)) return fail(PFC_EINVAL, "u[%d] is not device memory of the batch's device", k);
         if (!isfinite(tau[k])) return fail(PFC_EINVAL, "tau[%d] is not finite", k);
     }
     if (nsteps == 0) return PFC_OK;
@@ -826,12 +995,8 @@ static pfc_status step_descriptors(const pfc_batch* b, const void* const* u_in, 
     for (int k = 0; k < b->n; ++k) {
         for (int w = 0; w < 2; ++w) {
             const void* p = w ? (const void*)u_out[k] : u_in[k];
-            cudaPointerAttributes at;
-            if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess ||
-                (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
-                (void)cudaGetLastError();
-                return fail(PFC_EINVAL, "%s[%d] is not device memory", w ? "u_out" : "u_in", k);
-            }
+            if (!on_device(p, b->device))
+                return fail(PFC_EINVAL, "%s[%d] is not device memory of the batch's device", w ? "u_out" : "u_in", k);
         }
         if (u_in[k] == u_out[k]) return fail(PFC_EINVAL, "u_out[%d] aliases u_in[%d]", k, k);
         if (!isfinite(tau[k])) return fail(PFC_EINVAL, "tau[%d] is not finite", k);
@@ -881,6 +1046,8 @@ extern "C" pfc_status pfc_batch_step_lazy(pfc_batch* b, const void* const* u_in,
     if (!b) return fail(PFC_EINVAL, "batch is NULL");
     if (!u_in || !u_out || !tau) return fail(PFC_EINVAL, "u_in, u_out and tau arrays are required");
     if (!first && !b->lazy) return fail(PFC_EINVAL, "no chain of lazy steps is open: start one with first = 1");
+    // opening a chain resets the offsets: the open chain's last output would lose its projection
+    if (first && b->lazy) return fail(PFC_EINVAL, "a chain of lazy steps is open: close it with pfc_batch_lazy_finish");
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<Inst<float>> d;
     if (pfc_status st = step_descriptors(b, u_in, u_out, tau, d); st != PFC_OK) return st;
@@ -904,12 +1071,7 @@ extern "C" pfc_status pfc_batch_lazy_finish(pfc_batch* b, void* const* u, pfc_st
     if (!b->lazy) return fail(PFC_EINVAL, "no chain of lazy steps is open");
     std::vector<Inst<float>> d(b->host);
     for (int k = 0; k < b->n; ++k) {
-        cudaPointerAttributes at;
-        if (!u[k] || cudaPointerGetAttributes(&at, u[k]) != cudaSuccess ||
-            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
-            (void)cudaGetLastError();
-            return fail(PFC_EINVAL, "u[%d] is not device memory", k);
-        }
+        if (!on_device(u[k], b->device)) return fail(PFC_EINVAL, "u[%d] is not device memory of the batch's device", k);
         d[k].out = (float*)u[k];
     }
     PFC_CU(launch_add_offset_batch(d.data(), b->n, (cudaStream_t)stream));

@@ -223,7 +223,7 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
         T D = fma_(T(2), S, -t2) - t2e;
         if (sizeof(T) == 4) {
             const T scale = fma_(T(2), S, t2);
-            if (a3 != T(0) && scale > T(65536) * fmax(fabs(D), C.xi)) D = (T)refine();
+            if (a3 != T(0) && C.refine && scale > T(65536) * fmax(fabs(D), C.xi)) D = (T)refine();
         }
         T P;
         softplus_(D, C, P, Pp);
@@ -409,9 +409,46 @@ __device__ __forceinline__ void block_reduce_parts(double v[NPART], double* red)
     }
 }
 
+// The problem's scalars from its FP64 totals s[NPART] (sums over every voxel,
+// except s[P_GMAX], a max): energy, mean of the gradient (the multiplier),
+// max and mean |g|; after a step also the mass, the target mass (set by the
+// first step of a run), the offset c = target - mean(v) that the next step's
+// loads add, and a trace row.  One thread.
+__device__ __forceinline__ void set_scalars(const double s[NPART], double inv_N, int mode, double* sc, unsigned* ints,
+                                            double* trace, int trace_cap)
+{
+    const double E = s[P_E];
+    bool bad = !isfinite(E);
+    if (mode == MODE_ENERGY) {
+        sc[S_E] = E;
+    } else {
+        const double lam = s[P_G] * inv_N;
+        sc[S_E] = E;
+        sc[S_LAMBDA] = lam;
+        sc[S_GMAX] = s[P_GMAX];
+        sc[S_GMEAN] = s[P_AG] * inv_N;
+        bad = bad || !isfinite(lam);
+        if (mode == MODE_STEP) {
+            const double mass = s[P_U] * inv_N;
+            const unsigned cnt = ints[I_COUNTER];
+            if (cnt == 0) sc[S_TARGET] = mass;   // conserve the mass of the first field
+            sc[S_MASS] = mass;
+            sc[S_C] = sc[S_TARGET] - s[P_OUT] * inv_N;
+            bad = bad || !isfinite(mass) || !isfinite(sc[S_C]);
+            if (trace && (int)cnt < trace_cap) {
+                double* row = trace + (size_t)cnt * 5;
+                row[0] = E; row[1] = mass; row[2] = lam; row[3] = s[P_GMAX]; row[4] = sc[S_GMEAN];
+            }
+            ints[I_COUNTER] = cnt + 1;
+        }
+    }
+    if (bad) ints[I_NONFINITE] = 1;
+}
+
 // Publish one CTA's totals `tot` (shared, NPART doubles) as partial `slot`
 // of a problem; the last CTA to arrive (atomic ticket, no waiting) combines
-// all partials of the problem in a fixed order and writes its scalars.
+// all partials of the problem in a fixed order and writes its scalars (or,
+// for a z-slab, its totals to in.sums_out).
 template <typename T>
 __device__ void finish_problem(const Inst<T>& in, int slot, int mode, const double* tot)
 {
@@ -440,33 +477,12 @@ __device__ void finish_problem(const Inst<T>& in, int slot, int mode, const doub
 #pragma unroll
     for (int i = 0; i < NPART; ++i) s[i] = (i == P_GMAX) ? warp_max(s[i]) : warp_sum(s[i]);
     if (lane != 0) return;
-    double* sc = in.scal;
-    const double E = s[P_E];
-    bool bad = !isfinite(E);
-    if (mode == MODE_ENERGY) {
-        sc[S_E] = E;
+    if (in.sums_out) {
+#pragma unroll
+        for (int i = 0; i < NPART; ++i) in.sums_out[i] = s[i];
     } else {
-        const double lam = s[P_G] * in.inv_N;
-        sc[S_E] = E;
-        sc[S_LAMBDA] = lam;
-        sc[S_GMAX] = s[P_GMAX];
-        sc[S_GMEAN] = s[P_AG] * in.inv_N;
-        bad = bad || !isfinite(lam);
-        if (mode == MODE_STEP) {
-            const double mass = s[P_U] * in.inv_N;
-            const unsigned cnt = in.ints[I_COUNTER];
-            if (cnt == 0) sc[S_TARGET] = mass;   // conserve the mass of the first field
-            sc[S_MASS] = mass;
-            sc[S_C] = sc[S_TARGET] - s[P_OUT] * in.inv_N;
-            bad = bad || !isfinite(mass) || !isfinite(sc[S_C]);
-            if (in.trace && (int)cnt < in.trace_cap) {
-                double* row = in.trace + (size_t)cnt * 5;
-                row[0] = E; row[1] = mass; row[2] = lam; row[3] = s[P_GMAX]; row[4] = sc[S_GMEAN];
-            }
-            in.ints[I_COUNTER] = cnt + 1;
-        }
+        set_scalars(s, in.inv_N, mode, in.scal, in.ints, in.trace, in.trace_cap);
     }
-    if (bad) in.ints[I_NONFINITE] = 1;
     __threadfence();
     in.ints[I_TICKET] = 0;   // ready for the next launch on this problem
 }

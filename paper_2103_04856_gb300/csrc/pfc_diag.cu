@@ -14,7 +14,6 @@ namespace {
 
 constexpr int kDX = 32, kDY = 8;
 constexpr int kDiagThreads = kDX * kDY;
-constexpr int kDiagTarget = 152 * 8 * 4;   // blocks to aim for: about 4 waves of 8 per SM
 
 __device__ __forceinline__ double fmax_(double a, double b) { return a > b ? a : b; }
 __device__ __forceinline__ double fmin_(double a, double b) { return a < b ? a : b; }
@@ -139,7 +138,8 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const T* __restrict__ u, 
 static dim3 diag_grid(int nx, int ny, int nz, int* zc)
 {
     const long tiles = (long)((nx + kDX - 1) / kDX) * ((ny + kDY - 1) / kDY);
-    long chunks = (kDiagTarget + tiles - 1) / tiles;
+    const long target = 32L * device_sms();   // blocks to aim for: about 4 waves of 8 per SM
+    long chunks = (target + tiles - 1) / tiles;
     if (chunks > nz) chunks = nz;
     if (chunks < 1) chunks = 1;
     *zc = (int)((nz + chunks - 1) / chunks);

@@ -1,5 +1,7 @@
 // pfc_fused.cu -- launches of the fused forward + adjoint stencil sweep
 // (pfc_fused_kernel.cuh) and the small kernels around it.
+#include <atomic>
+
 #include "pfc_fused_kernel.cuh"
 
 namespace pfc {
@@ -41,6 +43,37 @@ __global__ void k_add_offset_batch(const __grid_constant__ OffsetLaunch L)
         done = n4 << 2;
     }
     for (long i = done + t0; i < n; i += stride) out[i] += off;
+}
+
+// The scalars of a z-slab step from every slab's FP64 sums, combined by one
+// thread in rank order (so every slab given the same rows computes the same
+// offset c, bit for bit).
+__global__ void k_slab_finish(const double* __restrict__ rows, int nslabs, double inv_N, int mode, double* scal,
+                              unsigned* ints, double* out5)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s[NPART];
+    for (int i = 0; i < NPART; ++i) s[i] = 0.0;
+    for (int r = 0; r < nslabs; ++r)
+        for (int i = 0; i < NPART; ++i) {
+            const double x = rows[(size_t)r * SLAB_NSUMS + i];
+            s[i] = i == P_GMAX ? fmax(s[i], x) : s[i] + x;
+        }
+    set_scalars(s, inv_N, mode, scal, ints, nullptr, 0);
+    if (out5) {
+        out5[0] = scal[S_E];
+        out5[1] = scal[S_MASS];
+        out5[2] = scal[S_LAMBDA];
+        out5[3] = scal[S_GMAX];
+        out5[4] = scal[S_GMEAN];
+    }
+}
+
+cudaError_t launch_slab_finish(const double* rows, int nslabs, double inv_N, int mode, double* scal, unsigned* ints,
+                               double* out5, cudaStream_t s)
+{
+    k_slab_finish<<<1, 32, 0, s>>>(rows, nslabs, inv_N, mode, scal, ints, out5);
+    return cudaGetLastError();
 }
 
 // Diffuse principal curvatures (Sec. 3.1, eqs. kepsa/kepsb) per voxel.
@@ -98,7 +131,7 @@ __global__ void k_curvatures(const T* __restrict__ u, T* __restrict__ k1, T* __r
 
 template <typename T>
 Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well, double mu, const double* theta,
-                  int proj)
+                  int proj, int refine)
 {
     const double h3 = h * h * h;
     Coef<T> C;
@@ -127,10 +160,11 @@ Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well, 
     C.th2 = (T)(theta ? theta[2] : 0.0);
     C.proj = proj ? 1 : 0;
     C.sym = (C.c3 == T(0) && C.c5 == T(0)) ? 1 : 0;
+    C.refine = refine ? 1 : 0;
     return C;
 }
-template Coef<float> make_coef<float>(const double*, double, double, double, int, double, const double*, int);
-template Coef<double> make_coef<double>(const double*, double, double, double, int, double, const double*, int);
+template Coef<float> make_coef<float>(const double*, double, double, double, int, double, const double*, int, int);
+template Coef<double> make_coef<double>(const double*, double, double, double, int, double, const double*, int, int);
 
 // c(x) from a(x): the coefficients of eq. Feps (times h^3) per voxel, in FP64
 // then rounded to the arithmetic type, exactly as make_coef does for a constant a.
@@ -169,20 +203,30 @@ size_t fused_smem_bytes(int elem_size, int tile_y)
     return (size_t)elem_size * ((size_t)NBUF * plane + 2 * 5 * (size_t)next) + sizeof(float) * NPART * (size_t)nt;
 }
 
-static int sm_count_current()
+int device_sms()
 {
-    int dev = 0, n = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+    static std::atomic<int> cache[64];   // 0: not queried yet
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
         (void)cudaGetLastError();
-        n = 152;
+        dev = -1;
     }
+    if (dev >= 0 && dev < 64) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int n = 0;
+    if (dev < 0 || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        (void)cudaGetLastError();
+        return 1;   // no device to ask: the launch that follows reports the error
+    }
+    if (dev < 64) cache[dev].store(n, std::memory_order_relaxed);
     return n;
 }
 
 long long fused_grid(long long units, int max_run)
 {
-    long long G = sm_count_current();                   // one CTA per SM
+    long long G = device_sms();                   // one CTA per SM
     if (max_run > 0 && (units + max_run - 1) / max_run > G) G = (units + max_run - 1) / max_run;
     return G < units ? G : units;
 }
@@ -286,7 +330,7 @@ cudaError_t launch_add_offset(T* out, const T* in, long n, const double* c, cuda
 {
     if (n <= 0) return cudaSuccess;
     long blocks = (n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > 16L * device_sms()) blocks = 16L * device_sms();
     k_add_offset<T><<<(int)blocks, 256, 0, s>>>(out, in, n, c);
     return cudaGetLastError();
 }
@@ -306,7 +350,7 @@ cudaError_t launch_add_offset_batch(const Inst<float>* insts, int n_inst, cudaSt
             L.len[k] = (long)in.nx * in.ny * in.nz;
             L.vec[k] = ((uintptr_t)in.out & 15) == 0;
         }
-        int bx = (152 * 8 + cnt - 1) / cnt;
+        int bx = (8 * device_sms() + cnt - 1) / cnt;
         if (bx < 8) bx = 8;
         k_add_offset_batch<<<dim3(bx, cnt), 256, 0, s>>>(L);
         cudaError_t e = cudaGetLastError();
@@ -321,7 +365,7 @@ cudaError_t launch_curvatures(const T* u, T* k1, T* k2, int nx, int ny, int nz, 
 {
     const long n = (long)nx * ny * nz;
     long blocks = (n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > 16L * device_sms()) blocks = 16L * device_sms();
     k_curvatures<T><<<(int)blocks, 256, 0, s>>>(u, k1, k2, nx, ny, nz, C, (T)eps);
     return cudaGetLastError();
 }

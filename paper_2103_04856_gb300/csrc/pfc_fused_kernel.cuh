@@ -184,7 +184,9 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
             if (!loader) return;                   // warp-uniform: only loading warps copy, commit and wait
             if (p <= plast) {
                 T* dst = us + (p & (NBUF - 1)) * PLANE;
-                const T* src = in.u + (size_t)pz * plane_g;
+                // a z-slab takes the planes beyond its ends from its halo buffer
+                const T* src = (in.halo && (p < 0 || p >= nz)) ? in.halo + (size_t)(p < 0 ? p + 2 : p - nz + 2) * plane_g
+                                                              : in.u + (size_t)pz * plane_g;
                 if (in.vec) {
                     if (ld_off >= 0) cp_async16(dst + ld_dst, src + ld_off);
                 } else {

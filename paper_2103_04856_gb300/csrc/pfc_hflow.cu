@@ -121,14 +121,14 @@ __device__ void flow_finish(const Flow& f, T a0, T a1, Fin fin)
     f.ints[0] = 0;
 }
 
-// Launch of the pointwise kernels: a 1-D grid of at most kFlowBlocks blocks
+// Launch of the pointwise kernels: a 1-D grid of at most 8 blocks per SM
 // striding over the flattened voxel index; each thread carries its (x, y, z)
 // and advances it by the stride's own (sx, sy, sz) with two carries.
-constexpr int kFlowBlocks = 152 * 8;
+inline long flow_blocks() { return 8L * device_sms(); }
 inline dim3 flow_grid(long n)
 {
-    const long b = (n + kThreads - 1) / kThreads;
-    return dim3((unsigned)(b < kFlowBlocks ? b : kFlowBlocks));
+    const long b = (n + kThreads - 1) / kThreads, cap = flow_blocks();
+    return dim3((unsigned)(b < cap ? b : cap));
 }
 
 // Blocks per instance when n_inst instances share a launch (instances along
@@ -138,7 +138,7 @@ inline unsigned inst_blocks(long n, int n_inst)
 {
     const unsigned b = flow_grid(n).x;
     if (n_inst <= 1) return b;
-    const unsigned cap = (unsigned)((2 * kFlowBlocks + n_inst - 1) / n_inst);
+    const unsigned cap = (unsigned)((2 * flow_blocks() + n_inst - 1) / n_inst);
     return b < cap ? b : cap;
 }
 
@@ -522,7 +522,7 @@ static void launch_blur(BlurL<T, MAXI>& BL, int n_inst, cudaStream_t s)
             // pieces as short as 4 outputs when there are few lines (one flow:
             // the GPU would otherwise sit half idle); the taps are summed in
             // the same order whatever the pieces
-            blur_pieces(n_ax, 4, lines * n_inst, 152L * 1024, &BL.chunk, &BL.nchunks);
+            blur_pieces(n_ax, 4, lines * n_inst, 1024L * device_sms(), &BL.chunk, &BL.nchunks);
             const dim3 grid((unsigned)((lines * BL.nchunks + 255) / 256), n_inst);
             if (R == 6) k_blur_win4<AX, MAXI, 6, kPrefetch><<<grid, 256, 0, s>>>(BL);
             else k_blur_win4<AX, MAXI, 3, kPrefetch><<<grid, 256, 0, s>>>(BL);
@@ -533,7 +533,7 @@ static void launch_blur(BlurL<T, MAXI>& BL, int n_inst, cudaStream_t s)
         if (paper_r) {
             const int n_ax = AX == 1 ? ny : nz, n_oth = AX == 1 ? nz : ny;
             const long lines = (long)nx * n_oth * n_inst;
-            blur_pieces(n_ax, 2 * R + 1, lines, 152L * 2048 * 2, &BL.chunk, &BL.nchunks);
+            blur_pieces(n_ax, 2 * R + 1, lines, 4096L * device_sms(), &BL.chunk, &BL.nchunks);
             const unsigned blocks = (unsigned)((lines * BL.nchunks + 255) / 256);
             if (R == 6) k_blur_win<T, AX, MAXI, 6><<<blocks, 256, 0, s>>>(BL);
             else k_blur_win<T, AX, MAXI, 3><<<blocks, 256, 0, s>>>(BL);
@@ -895,14 +895,27 @@ static pfc_status hfail(pfc_status s, const char* msg)
         }                                                                      \
     } while (0)
 
-static bool dev_ptr(const void* p)
+static bool is_current(int device)
 {
-    cudaPointerAttributes at;
-    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
         (void)cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return cur == device;
+}
+
+// p is device (or managed) memory of the current device, where the flow's
+// kernels run
+static bool dev_ptr(const void* p)
+{
+    cudaPointerAttributes at;
+    int cur = -1;
+    if (!p || cudaGetDevice(&cur) != cudaSuccess || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == cur;
 }
 
 static void free_flow(pfc_hflow* h)
@@ -937,7 +950,8 @@ extern "C" pfc_status pfc_hflow_create(const pfc_problem* prob, const pfc_hflow_
         if (!isfinite(p.a[i])) return hfail(PFC_EINVAL, "hflow: a coefficient is not finite");
     if (!isfinite(p.mu) || !isfinite(p.theta[0]) || !isfinite(p.theta[1]) || !isfinite(p.theta[2]))
         return hfail(PFC_EINVAL, "hflow: mu and theta must be finite");
-    if ((p.proj != 0 && p.proj != 1) || p.reserved != 0) return hfail(PFC_EINVAL, "hflow: proj 0 or 1, reserved 0");
+    if ((p.proj != 0 && p.proj != 1) || (p.flags & ~PFC_FLAG_NO_DISCRIMINANT_REFINEMENT))
+        return hfail(PFC_EINVAL, "hflow: proj 0 or 1, unknown flags");
     if (!isfinite(hp->m0) || !(hp->lr >= 0) || !(hp->beta1 >= 0 && hp->beta1 < 1) || !(hp->beta2 >= 0 && hp->beta2 < 1) ||
         !(hp->adam_eps >= 0) || !(hp->blur_sigma >= 0))
         return hfail(PFC_EINVAL, "hflow: m0 finite, lr >= 0, betas in [0,1), eps >= 0, sigma >= 0 required");
@@ -1163,7 +1177,8 @@ static cudaError_t eval(pfc_hflow* h, const T* A, T** gb, cudaStream_t s)
     in.out = (T*)h->buf[1];
     in.nx = h->P.nx; in.ny = h->P.ny; in.nz = h->P.nz;
     in.vec = (h->P.nx % (16 / (int)sizeof(T)) == 0);
-    in.C = make_coef<T>(h->P.a, h->P.h, h->P.eps, h->P.xi, h->P.well, h->P.mu, h->P.theta, h->P.proj);
+    in.C = make_coef<T>(h->P.a, h->P.h, h->P.eps, h->P.xi, h->P.well, h->P.mu, h->P.theta, h->P.proj,
+                          (h->P.flags & PFC_FLAG_NO_DISCRIMINANT_REFINEMENT) ? 0 : 1);
     in.cf = h->cf_on ? (const T*)h->cfield : nullptr;
     in.inv_N = 1.0 / (double)h->N;
     in.partials = h->spart;
@@ -1187,6 +1202,7 @@ static cudaError_t step(pfc_hflow* h, T* A, T* m, T* v, cudaStream_t s)
 extern "C" pfc_status pfc_hflow_field(pfc_hflow* h, const void* A, void* ut, pfc_stream stream)
 {
     if (!h) return hfail(PFC_EINVAL, "hflow: handle is NULL");
+    if (!is_current(h->device)) return hfail(PFC_EINVAL, "hflow: the flow's device is not the current device");
     if (!dev_ptr(A) || !dev_ptr(ut)) return hfail(PFC_EINVAL, "hflow: A and ut must be device memory");
     cudaStream_t s = (cudaStream_t)stream;
     if (h->P.prec == PFC_FP64) {
@@ -1204,6 +1220,7 @@ extern "C" pfc_status pfc_hflow_field(pfc_hflow* h, const void* A, void* ut, pfc
 extern "C" pfc_status pfc_hflow_grad(pfc_hflow* h, const void* A, void* gA, double* G_host, pfc_stream stream)
 {
     if (!h) return hfail(PFC_EINVAL, "hflow: handle is NULL");
+    if (!is_current(h->device)) return hfail(PFC_EINVAL, "hflow: the flow's device is not the current device");
     if (!dev_ptr(A) || !dev_ptr(gA)) return hfail(PFC_EINVAL, "hflow: A and gA must be device memory");
     if (A == gA) return hfail(PFC_EINVAL, "hflow: gA must not alias A");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1231,6 +1248,7 @@ extern "C" pfc_status pfc_hflow_run(pfc_hflow* h, void* A, void* m, void* v, int
     nvtxRangePushA("pfc_hflow_run");
     struct Pop { ~Pop() { nvtxRangePop(); } } pop_;
     if (!h) return hfail(PFC_EINVAL, "hflow: handle is NULL");
+    if (!is_current(h->device)) return hfail(PFC_EINVAL, "hflow: the flow's device is not the current device");
     if (!dev_ptr(A) || !dev_ptr(m) || !dev_ptr(v)) return hfail(PFC_EINVAL, "hflow: A, m, v must be device memory");
     if (A == m || A == v || m == v) return hfail(PFC_EINVAL, "hflow: A, m and v must be distinct");
     if (!t || *t < 0 || nsteps < 0) return hfail(PFC_EINVAL, "hflow: nsteps >= 0 and a step counter >= 0 required");
@@ -1304,6 +1322,7 @@ extern "C" pfc_status pfc_hflow_run(pfc_hflow* h, void* A, void* m, void* v, int
 extern "C" pfc_status pfc_hflow_set_coefficient_field(pfc_hflow* h, const void* a_field, pfc_stream stream)
 {
     if (!h) return hfail(PFC_EINVAL, "hflow: handle is NULL");
+    if (!is_current(h->device)) return hfail(PFC_EINVAL, "hflow: the flow's device is not the current device");
     if (!a_field) {
         h->cf_on = false;
         return PFC_OK;
@@ -1322,6 +1341,7 @@ extern "C" pfc_status pfc_hflow_set_coefficient_field(pfc_hflow* h, const void* 
 extern "C" pfc_status pfc_hflow_set_mass_field(pfc_hflow* h, const void* m_field, pfc_stream stream)
 {
     if (!h) return hfail(PFC_EINVAL, "hflow: handle is NULL");
+    if (!is_current(h->device)) return hfail(PFC_EINVAL, "hflow: the flow's device is not the current device");
     if (!m_field) {
         h->mf_on = false;
         return PFC_OK;
@@ -1546,7 +1566,8 @@ static cudaError_t batch_step(const pfc_hflow_batch* b, float* const* A, float* 
         I.out = bbuf(b, k, 1);
         I.nx = b->nx; I.ny = b->ny; I.nz = b->nz;
         I.vec = b->nx % 4 == 0;
-        I.C = make_coef<float>(P.a, P.h, P.eps, P.xi, P.well);
+        I.C = make_coef<float>(P.a, P.h, P.eps, P.xi, P.well, 0.0, nullptr, 0,
+                               (P.flags & PFC_FLAG_NO_DISCRIMINANT_REFINEMENT) ? 0 : 1);
         I.inv_N = 1.0 / (double)b->N;
         I.partials = b->spart + (size_t)k * b->slots * NPART;
         I.ints = b->sints + (size_t)k * NINTS;
@@ -1590,6 +1611,7 @@ extern "C" pfc_status pfc_hflow_batch_field(pfc_hflow_batch* b, const void* cons
                                             pfc_stream stream)
 {
     if (!b) return hfail(PFC_EINVAL, "hflow batch: handle is NULL");
+    if (!is_current(b->device)) return hfail(PFC_EINVAL, "hflow batch: the batch's device is not the current device");
     pfc_status st;
     if ((st = check_vec_list(A, b->n, "A")) || (st = check_vec_list(ut, b->n, "ut"))) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1605,6 +1627,7 @@ extern "C" pfc_status pfc_hflow_batch_run(pfc_hflow_batch* b, void* const* A, vo
     nvtxRangePushA("pfc_hflow_batch_run");
     struct Pop { ~Pop() { nvtxRangePop(); } } pop_;
     if (!b) return hfail(PFC_EINVAL, "hflow batch: handle is NULL");
+    if (!is_current(b->device)) return hfail(PFC_EINVAL, "hflow batch: the batch's device is not the current device");
     pfc_status st;
     if ((st = check_vec_list(A, b->n, "A")) || (st = check_vec_list(m, b->n, "m")) ||
         (st = check_vec_list(v, b->n, "v")))

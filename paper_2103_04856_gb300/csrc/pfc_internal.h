@@ -47,6 +47,9 @@ struct Coef {
     // 1: c3 = c5 = 0 in the arithmetic type (p symmetric in kappa1, kappa2), so
     // the weight c3 T + c5 q of the sqrt(D+) terms is exactly zero
     int sym;
+    // 1: FP32 voxels whose D = 2S - T^2 may have lost its accuracy to
+    // cancellation recompute it in FP64 (voxel_eval); 0: never
+    int refine;
 };
 
 // Coefficient fields: c(x) = (c1..c6)(a(x)) as 6 component planes of N
@@ -74,6 +77,13 @@ struct Inst {
     double* scal;        // [NSCAL]
     double* trace;       // [trace_cap][5] or null
     int trace_cap;
+    // z-slab of a larger periodic grid: null, or 4 planes of nx*ny values
+    // (the two planes below the slab, then the two above) read instead of
+    // wrapping around z
+    const T* halo;
+    // null, or NPART doubles receiving this launch's FP64 sums for the
+    // problem (the scalars are then set by a later combine over all slabs)
+    double* sums_out;
 };
 
 // Problems of one fused launch, passed by value as a kernel parameter (the
@@ -92,7 +102,7 @@ struct Launch {
 
 template <typename T>
 Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well, double mu = 0.0,
-                  const double* theta = nullptr, int proj = 0);
+                  const double* theta = nullptr, int proj = 0, int refine = 1);
 
 // Automatic tile height: FP64 8 rows; FP32 the one of 16 and 13 rows that
 // pads the grid's rows least (16 on a tie: its tiles hold more rows).
@@ -110,6 +120,10 @@ constexpr int EXT_TILE_Y = 8;
 // c(x) from a(x) (both [6][n], the arithmetic type; a in the paper's order)
 template <typename T>
 cudaError_t launch_coef_field(const T* a_field, T* c_field, long n, double h, double eps, cudaStream_t s);
+
+// Streaming multiprocessors of the current device (queried once per device
+// ordinal and cached; launch grids are sized in multiples of it).
+int device_sms();
 
 // fused kernels (pfc_fused.cu)
 // max_run > 0 caps the planes one CTA processes per problem (more CTAs);
@@ -129,6 +143,12 @@ template <typename T>
 cudaError_t launch_add_offset(T* out, const T* in, long n, const double* c, cudaStream_t s);
 // out += scal[S_C] for every problem of a batch (host descriptors), in place
 cudaError_t launch_add_offset_batch(const Inst<float>* insts, int n_inst, cudaStream_t s);
+// z-slabs: combine nslabs rows of FP64 sums (stride PFC_SLAB_NSUMS = 8,
+// written by the slabs' sweeps) in rank order into the scalars of one slab;
+// out5 (may be null) receives E, mass, lambda, max|g|, mean|g|
+constexpr int SLAB_NSUMS = 8;
+cudaError_t launch_slab_finish(const double* rows, int nslabs, double inv_N, int mode, double* scal, unsigned* ints,
+                               double* out5, cudaStream_t s);
 template <typename T>
 cudaError_t launch_curvatures(const T* u, T* k1, T* k2, int nx, int ny, int nz, const Coef<T>& C,
                               double eps, cudaStream_t s);

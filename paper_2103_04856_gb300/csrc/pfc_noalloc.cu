@@ -28,7 +28,8 @@ constexpr int kMaxCtas = 1024;
 constexpr size_t kPartBytes = sizeof(double) * NPART * (size_t)kMaxCtas;
 constexpr size_t kScalBytes = sizeof(double) * NSCAL;
 constexpr size_t kIntsBytes = sizeof(unsigned) * NINTS;
-constexpr size_t kScratchBytes = kPartBytes + kScalBytes + kIntsBytes;   // 49,256 bytes
+constexpr size_t kScratchBytes = kPartBytes + kScalBytes + kIntsBytes;
+static_assert(kScratchBytes == 49232, "the scratch size stated in include/pfc.h");
 
 constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices] = {};   // device address of the array, per device
@@ -80,14 +81,17 @@ static void* scratch_on_current_device(pfc_status* st)
     return g_scratch_addr[dev];
 }
 
-static bool is_device_ptr(const void* p)
+// p is device (or managed) memory of the current device: the kernels run on
+// the current device and must not touch another GPU's memory
+static bool is_current_device_ptr(const void* p)
 {
     cudaPointerAttributes at;
-    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    int dev = -1;
+    if (!p || cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         (void)cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 template <typename T>
@@ -104,7 +108,8 @@ static pfc_status run_noalloc(const pfc_problem* p, const void* u, void* g, doub
     in.zc = p->nz;
     in.chunks_z = 1;
     in.vec = (p->nx % (16 / (int)sizeof(T)) == 0) && ((uintptr_t)u) % 16 == 0;
-    in.C = make_coef<T>(p->a, p->h, p->eps, p->xi, p->well, p->mu, p->theta, p->proj);
+    in.C = make_coef<T>(p->a, p->h, p->eps, p->xi, p->well, p->mu, p->theta, p->proj,
+                      (p->flags & PFC_FLAG_NO_DISCRIMINANT_REFINEMENT) ? 0 : 1);
     in.cf = nullptr;
     in.tau = T(0);
     in.inv_N = 1.0 / ((double)p->nx * p->ny * p->nz);
@@ -144,13 +149,15 @@ extern "C" pfc_status pfc_energy_and_grad_noalloc(const pfc_problem* prob, const
         if (!isfinite(p.a[i])) return na_fail(PFC_EINVAL, "noalloc: a coefficient is not finite");
     if (!isfinite(p.mu) || !isfinite(p.theta[0]) || !isfinite(p.theta[1]) || !isfinite(p.theta[2]))
         return na_fail(PFC_EINVAL, "noalloc: mu and theta must be finite");
-    if ((p.proj != 0 && p.proj != 1) || p.reserved != 0) return na_fail(PFC_EINVAL, "noalloc: proj 0 or 1, reserved 0");
+    if ((p.proj != 0 && p.proj != 1) || (p.flags & ~PFC_FLAG_NO_DISCRIMINANT_REFINEMENT))
+        return na_fail(PFC_EINVAL, "noalloc: proj 0 or 1, unknown flags");
     if (p.well != PFC_WELL_01 && p.well != PFC_WELL_PM1) return na_fail(PFC_EINVAL, "noalloc: unknown double well");
     if (p.prec != PFC_FP32 && p.prec != PFC_FP64) return na_fail(PFC_EINVAL, "noalloc: unknown precision");
     if (p.impl != PFC_IMPL_FUSED) return na_fail(PFC_EUNSUPPORTED, "noalloc: only the fused path needs no allocation");
     if (p.tile_y != 0 && p.tile_y != 8 && p.tile_y != 13 && p.tile_y != 16) return na_fail(PFC_EINVAL, "noalloc: tile_y must be 0, 8, 13 or 16");
     if (p.tile_z < 0) return na_fail(PFC_EINVAL, "noalloc: tile_z must be >= 0");
-    if (!is_device_ptr(u) || !is_device_ptr(g)) return na_fail(PFC_EINVAL, "noalloc: u and g must be device memory");
+    if (!is_current_device_ptr(u) || !is_current_device_ptr(g))
+        return na_fail(PFC_EINVAL, "noalloc: u and g must be device memory of the current device");
     if (u == g) return na_fail(PFC_EINVAL, "noalloc: g must not alias u");
     pfc_status st;
     unsigned char* base = (unsigned char*)scratch_on_current_device(&st);

@@ -125,8 +125,8 @@ __global__ void k_plain_update(const T* __restrict__ u, const T* __restrict__ g,
 
 int plain_blocks(long n)
 {
-    long b = (n + 255) / 256;
-    return (int)(b < 152 * 8 ? b : 152 * 8);
+    const long b = (n + 255) / 256, cap = 8L * device_sms();
+    return (int)(b < cap ? b : cap);
 }
 
 template <typename T>

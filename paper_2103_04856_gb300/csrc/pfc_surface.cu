@@ -300,7 +300,7 @@ cudaError_t launch_curvature_histogram(const T* cells, long long n, int nbins, d
     cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(double) * (size_t)nbins * nbins, s);
     if (e != cudaSuccess || n <= 0) return e;
     long long b = (n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > 16LL * device_sms()) b = 16LL * device_sms();
     k_curv_hist<T><<<(unsigned)b, 256, 0, s>>>(cells, n, nbins, lo, nbins / (hi - lo), hist);
     return cudaGetLastError();
 }

@@ -29,6 +29,7 @@ PFC_OK, PFC_EINVAL, PFC_ENOMEM, PFC_ECUDA, PFC_ENONFINITE, PFC_ETIMEOUT, PFC_EUN
 PFC_WELL_01, PFC_WELL_PM1 = 0, 1
 PFC_FP32, PFC_FP64 = 0, 1
 PFC_IMPL_FUSED, PFC_IMPL_PLAIN = 0, 1
+FLAG_NO_DISCRIMINANT_REFINEMENT = 1
 
 # every symbol include/pfc.h declares
 EXPORTED = ("pfc_create", "pfc_destroy", "pfc_energy", "pfc_energy_and_grad", "pfc_step", "pfc_run",
@@ -39,7 +40,10 @@ EXPORTED = ("pfc_create", "pfc_destroy", "pfc_energy", "pfc_energy_and_grad", "p
             "pfc_hflow_set_coefficient_field", "pfc_hflow_set_mass_field", "pfc_surface_cells",
             "pfc_curvature_histogram", "pfc_batch_step_host", "pfc_batch_host_wait", "pfc_hflow_batch_create",
             "pfc_hflow_batch_destroy", "pfc_hflow_batch_field", "pfc_hflow_batch_run", "pfc_batch_step_lazy",
-            "pfc_batch_lazy_finish")
+            "pfc_batch_lazy_finish", "pfc_slab_create", "pfc_slab_destroy", "pfc_slab_sweep", "pfc_slab_finish",
+            "pfc_slab_apply_offset", "pfc_measure_fp32_peak")
+SLAB_ENERGY, SLAB_GRAD, SLAB_STEP = 0, 1, 2
+SLAB_NSUMS = 8
 
 
 class PfcError(RuntimeError):
@@ -66,7 +70,7 @@ class _CProblem(ctypes.Structure):
         ("a", ctypes.c_double * 6),
         ("tile_y", ctypes.c_int32), ("tile_z", ctypes.c_int32),
         ("mu", ctypes.c_double), ("theta", ctypes.c_double * 3),
-        ("proj", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("proj", ctypes.c_int32), ("flags", ctypes.c_uint32),
     ]
 
 
@@ -76,7 +80,9 @@ class Problem:
     kappa1 >= kappa2.  ``prec`` is "fp32" or "fp64", ``impl`` "fused" or "plain".
     ``mu``, ``theta`` (x, y, z): the orientation term eps mu (theta . grad u)^2
     of Sec. 5.2 (mu = 0: none).  ``proj`` = 1: the tangent-projected
-    M = -eps P Hess u P instead of eq. Meps."""
+    M = -eps P Hess u P instead of eq. Meps.  ``flags``: PFC_FLAG_* bits
+    (FLAG_NO_DISCRIMINANT_REFINEMENT turns the FP32 path's FP64
+    re-evaluation of D off)."""
     nx: int
     ny: int
     nz: int
@@ -92,6 +98,7 @@ class Problem:
     mu: float = 0.0
     theta: tuple = (0.0, 0.0, 0.0)
     proj: int = 0
+    flags: int = 0
 
     @classmethod
     def from_shape(cls, shape, **kw):
@@ -117,7 +124,7 @@ class Problem:
                          float(self.h), float(self.eps), float(self.xi),
                          (ctypes.c_double * 6)(*[float(x) for x in self.a]),
                          int(self.tile_y), int(self.tile_z), float(self.mu),
-                         (ctypes.c_double * 3)(*[float(x) for x in self.theta]), int(self.proj), 0)
+                         (ctypes.c_double * 3)(*[float(x) for x in self.theta]), int(self.proj), int(self.flags))
 
 
 _lib = None
@@ -177,6 +184,12 @@ def load_library():
                                   ctypes.c_int),
             "pfc_curvature_histogram": ([vp, vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_double, vp,
                                          vp], ctypes.c_int),
+            "pfc_slab_create": ([P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(vp)], ctypes.c_int),
+            "pfc_slab_destroy": ([vp], None),
+            "pfc_slab_sweep": ([vp, vp, vp, vp, ctypes.c_int32, ctypes.c_double, vp, vp], ctypes.c_int),
+            "pfc_slab_finish": ([vp, vp, ctypes.c_int32, vp, vp], ctypes.c_int),
+            "pfc_slab_apply_offset": ([vp, vp, vp], ctypes.c_int),
+            "pfc_measure_fp32_peak": ([dp, vp], ctypes.c_int),
             "pfc_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "pfc_last_error": ([], ctypes.c_char_p),
         }
@@ -255,6 +268,13 @@ def energy_and_grad_noalloc(prob: Problem, u: torch.Tensor, g: torch.Tensor, str
                                                       _field(g, prob, "g"), ctypes.byref(E) if sync else None,
                                                       _stream(stream)))
     return E.value if sync else None
+
+
+def measure_fp32_peak(stream=None) -> float:
+    """FP32 FMA throughput of the current GPU in TFLOP/s (pfc_measure_fp32_peak)."""
+    t = ctypes.c_double()
+    _check(load_library().pfc_measure_fp32_peak(ctypes.byref(t), _stream(stream)))
+    return t.value
 
 
 class Context:
@@ -475,6 +495,72 @@ class Batch:
         a, b = ctypes.c_float(), ctypes.c_float()
         _check(self._lib.pfc_batch_last_timing(self._h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+
+class Slab:
+    """One z-slab [z0, z0 + nz_local) of a periodic grid split across
+    processes (pfc_slab_*): ``prob`` describes the WHOLE grid.  Fields of the
+    slab are CUDA tensors (nz_local, ny, nx); its halo is (4, ny, nx): the two
+    planes below the slab, then the two above (periodic), filled by the
+    caller before every sweep (see paper_2103_04856_gb300.slab)."""
+
+    def __init__(self, prob: Problem, z0: int, nz_local: int):
+        self.prob = prob
+        self.z0, self.nzl = int(z0), int(nz_local)
+        self._lib = load_library()
+        self._h = ctypes.c_void_p()
+        _check(self._lib.pfc_slab_create(ctypes.byref(prob._c()), self.z0, self.nzl, ctypes.byref(self._h)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pfc_slab_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (self.nzl, self.prob.ny, self.prob.nx)
+
+    def new_field(self):
+        return torch.empty(self.shape, dtype=self.prob.dtype, device="cuda")
+
+    def new_halo(self):
+        return torch.empty((4, self.prob.ny, self.prob.nx), dtype=self.prob.dtype, device="cuda")
+
+    def _t(self, t, shape, name, dtype=None):
+        dtype = dtype or self.prob.dtype
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype:
+            raise TypeError(f"{name} must be a CUDA {dtype} tensor")
+        if tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous with shape {tuple(shape)}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def sweep(self, u, halo, out, mode: int, tau: float, sums_row, stream=None):
+        """The fused sweep over the slab (enqueue only); sums_row: CUDA float64
+        tensor of SLAB_NSUMS values receiving the slab's sums."""
+        op = None if (mode == SLAB_ENERGY and out is None) else self._t(out, self.shape, "out")
+        _check(self._lib.pfc_slab_sweep(self._h, self._t(u, self.shape, "u"),
+                                        self._t(halo, (4, self.prob.ny, self.prob.nx), "halo"), op, int(mode),
+                                        float(tau), self._t(sums_row, (SLAB_NSUMS,), "sums_row", torch.float64),
+                                        _stream(stream)))
+
+    def finish(self, sums_all, scalars=None, stream=None):
+        """Combine every slab's sums (CUDA float64, (nslabs, SLAB_NSUMS), rank
+        order) into the scalars; ``scalars``: optional CUDA float64 tensor of 5."""
+        if sums_all.dim() != 2 or sums_all.shape[1] != SLAB_NSUMS:
+            raise ValueError("sums_all must be shaped (nslabs, SLAB_NSUMS)")
+        sp = None if scalars is None else self._t(scalars, (5,), "scalars", torch.float64)
+        _check(self._lib.pfc_slab_finish(self._h, self._t(sums_all, tuple(sums_all.shape), "sums_all", torch.float64),
+                                         int(sums_all.shape[0]), sp, _stream(stream)))
+
+    def apply_offset(self, u, stream=None):
+        """u += the pending offset of the mass projection; closes the chain."""
+        _check(self._lib.pfc_slab_apply_offset(self._h, self._t(u, self.shape, "u"), _stream(stream)))
 
 
 class HFlow:

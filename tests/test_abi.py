@@ -81,7 +81,7 @@ def test_create_rejects_bad_problems_without_touching_the_gpu(lib):
     from paper_2103_04856_gb300 import pfc
     h = ctypes.c_void_p()
     bad = [dict(eps=0.0), dict(nx=0), dict(xi=-1.0), dict(tile_y=12), dict(h=float("nan")),
-           dict(mu=float("inf")), dict(theta=(0.0, float("nan"), 1.0))]
+           dict(mu=float("inf")), dict(theta=(0.0, float("nan"), 1.0)), dict(flags=2)]
     for kw in bad:
         base = dict(nx=8, ny=8, nz=8, eps=1.5, a=(1, 0, 1, 0, 0, 0))
         base.update(kw)
@@ -97,6 +97,23 @@ def test_create_rejects_bad_problems_without_touching_the_gpu(lib):
     # the orientation term is a fused-path feature
     p = pfc.Problem(nx=8, ny=8, nz=8, eps=1.5, a=(1, 0, 1, 0, 0, 0), impl="plain", mu=1.0, theta=(0, 0, 1))
     assert lib.pfc_create(ctypes.byref(p._c()), ctypes.byref(h)) == pfc.PFC_EUNSUPPORTED
+
+
+def test_noalloc_rejects_host_memory_without_launching(lib):
+    """The no-allocation entry point checks its fields before it touches the
+    GPU: host memory (or, on a machine without a GPU, any pointer) is refused
+    with a message, and nothing is launched."""
+    from paper_2103_04856_gb300 import pfc
+    p = pfc.Problem(nx=8, ny=8, nz=8, eps=1.5, a=(1, 0, 1, 0, 0, 0))
+    u = np.zeros(512, dtype=np.float32)
+    g = np.zeros(512, dtype=np.float32)
+    rc = lib.pfc_energy_and_grad_noalloc(ctypes.byref(p._c()), ctypes.c_void_p(u.ctypes.data),
+                                         ctypes.c_void_p(g.ctypes.data), None, None)
+    assert rc == pfc.PFC_EINVAL
+    assert b"device memory" in lib.pfc_last_error()
+    c = p._c()
+    c.flags = 4
+    assert lib.pfc_energy_and_grad_noalloc(ctypes.byref(c), None, None, None, None) == pfc.PFC_EINVAL
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):

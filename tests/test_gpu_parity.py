@@ -471,10 +471,13 @@ def test_lazy_step_chain_matches_exact_steps(symmetric):
         err_exact = (torch.linalg.norm(e.double() - r) / torch.linalg.norm(r)).item()
         assert err_lazy < 1e-3 and err_lazy < 2.0 * err_exact + 1e-6, (err_lazy, err_exact)
         assert abs(x.double().mean().item() - u.astype(np.float64).mean()) < 1e-6
-    # a chain must be opened, and an exact step closes it
+    # a chain must be opened, may not be reopened while open (its pending
+    # offsets would be lost), and an exact step closes it
     with pytest.raises(pfc.PfcError):
         b.step_lazy(A, B, taus, first=False)
     b.step_lazy(A, B, taus, first=True)
+    with pytest.raises(pfc.PfcError):
+        b.step_lazy(B, A, taus, first=True)
     b.step(B, A, taus)
     with pytest.raises(pfc.PfcError):
         b.lazy_finish(A)

@@ -59,3 +59,20 @@ def test_noalloc_rejects_bad_input():
     rc = lib.pfc_energy_and_grad_noalloc(ctypes.byref(p._c()), ctypes.c_void_p(host.ctypes.data),
                                          ctypes.c_void_p(g.data_ptr()), None, None)
     assert rc == pfc.PFC_EINVAL
+    # g aliasing u is refused before anything is launched
+    p = pfc.Problem.from_shape(shape, eps=1.5, a=(1, 0, 1, 0, 0, 0), prec="fp32")
+    rc = lib.pfc_energy_and_grad_noalloc(ctypes.byref(p._c()), ctypes.c_void_p(u.data_ptr()),
+                                         ctypes.c_void_p(u.data_ptr()), None, None)
+    assert rc == pfc.PFC_EINVAL and b"alias" in lib.pfc_last_error()
+    # a non-finite field gives a non-finite energy, reported as such
+    bad = torch.full(shape, float("nan"), device="cuda")
+    E = ctypes.c_double()
+    rc = lib.pfc_energy_and_grad_noalloc(ctypes.byref(p._c()), ctypes.c_void_p(bad.data_ptr()),
+                                         ctypes.c_void_p(g.data_ptr()), ctypes.byref(E), None)
+    assert rc == pfc.PFC_ENONFINITE
+    # and the next call is correct again (the counters were left at zero)
+    ok = torch.tensor(I.noise(shape, 0.3, 0.1, 3), dtype=torch.float32, device="cuda")
+    E_ref, g_ref = pfc.Context(p).energy_and_grad(ok)
+    rc = lib.pfc_energy_and_grad_noalloc(ctypes.byref(p._c()), ctypes.c_void_p(ok.data_ptr()),
+                                         ctypes.c_void_p(g.data_ptr()), ctypes.byref(E), None)
+    assert rc == pfc.PFC_OK and abs(E.value - E_ref) <= 1e-4 * abs(E_ref)
