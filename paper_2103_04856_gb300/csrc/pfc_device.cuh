@@ -215,15 +215,16 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
     const T off = fma_(Mxy, Mxy, fma_(Mxz, Mxz, Myz * Myz));
     const T S = fma_(Mxx, Mxx, fma_(Myy, Myy, fma_(Mzz, Mzz, T(2) * off)));
     const T t2 = Tr * Tr;
-    const T a3 = fma_(C.c3, Tr, C.c5 * q);              // c3 T + c5 q
+    T a3 = T(0);                                        // c3 T + c5 q
     T r = T(0), rs = T(0), Pp = T(0);
     if constexpr (!SKIPD) {
+        a3 = fma_(C.c3, Tr, C.c5 * q);
         // D = 2S - T^2 with the rounding error of T^2 put back (two-product)
         const T t2e = fma_(Tr, Tr, -t2);
         T D = fma_(T(2), S, -t2) - t2e;
         if (sizeof(T) == 4) {
             const T scale = fma_(T(2), S, t2);
-            if (a3 != T(0) && C.refine && scale > T(65536) * fmax(fabs(D), C.xi)) D = (T)refine();
+            if (a3 != T(0) && scale > C.rthr * fmax(fabs(D), C.xi)) D = (T)refine();
         }
         T P;
         softplus_(D, C, P, Pp);
@@ -231,7 +232,9 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
         rs = (sizeof(T) == 4 && P > T(0)) ? rsqrt_(P) : T(0);
         r = sizeof(T) == 4 ? P * rs : sqrt_(P);
     }
-    T e = fma_(C.c1, S, fma_(C.c2, t2, fma_(a3, r, fma_(C.c4 * q, Tr, C.c6 * g2))));
+    // SKIPD: the a3 r term is an exact zero (written out: the compiler may not drop a3 * 0)
+    T e = SKIPD ? fma_(C.c1, S, fma_(C.c2, t2, fma_(C.c4 * q, Tr, C.c6 * g2)))
+                : fma_(C.c1, S, fma_(C.c2, t2, fma_(a3, r, fma_(C.c4 * q, Tr, C.c6 * g2))));
     T tg = T(0);
     if (ORIENT) {
         tg = fma_(C.th0, Gx, fma_(C.th1, Gy, C.th2 * Gz));
@@ -241,12 +244,20 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
 
     // local reverse mode: e(S, T, r(D(S,T)), q(G), |G|^2), M(Hess, w(u), G)
     // dr/dD, 0 where r = 0
-    const T rp = sizeof(T) == 4 ? T(0.5) * Pp * rs : (r > T(0) ? T(0.5) * Pp / r : T(0));
-    const T k = a3 * rp;                                     // de/dD
-    const T dS = fma_(T(2), k, C.c1);
-    const T dT = fma_(T(2) * C.c2, Tr, fma_(C.c3, r, fma_(C.c4, q, -T(2) * Tr * k)));
-    const T dq = fma_(C.c4, Tr, C.c5 * r);
-    const T s2 = T(2) * dS;
+    T dT, dq, s2;   // de/dT, de/dq, 2 de/dS
+    if constexpr (SKIPD) {
+        // r = r' = 0: the same values as below with k = 0 and r = 0
+        dT = fma_(C.c2x2, Tr, C.c4 * q);
+        dq = C.c4 * Tr;
+        s2 = C.c1x2;
+    } else {
+        const T rp = sizeof(T) == 4 ? T(0.5) * Pp * rs : (r > T(0) ? T(0.5) * Pp / r : T(0));
+        const T k = a3 * rp;                                 // de/dD
+        const T dS = fma_(T(2), k, C.c1);
+        dT = fma_(C.c2x2, Tr, fma_(C.c3, r, fma_(C.c4, q, -T(2) * Tr * k)));
+        dq = fma_(C.c4, Tr, C.c5 * r);
+        s2 = T(2) * dS;
+    }
     // Lambda = de/dM = 2 dS M + dT I
     const T Lxx = fma_(s2, Mxx, dT), Lyy = fma_(s2, Myy, dT), Lzz = fma_(s2, Mzz, dT);
     const T Lxy = s2 * Mxy, Lxz = s2 * Mxz, Lyz = s2 * Myz;
@@ -274,7 +285,7 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
         const T BGz = fma_(Lxz, pkx, fma_(Lyz, pky, Lzz * pkz)) + fma_(Kxz, plx, fma_(Kyz, ply, Kzz * plz));
         const T GBG = T(2) * fma_(LGx, kx, fma_(LGy, ky, fma_(LGz, kz, -si * GLG)));
         const T al = -T(2) * irho;
-        const T be = fma_(T(2) * GBG * irho, irho, fma_(dq, iq, T(2) * C.c6));
+        const T be = fma_(T(2) * GBG * irho, irho, fma_(dq, iq, C.c6x2));
         ct.u = T(0);
         ct.dx = C.sg * fma_(al, BGx, be * Gx);
         ct.dy = C.sg * fma_(al, BGy, be * Gy);
@@ -288,15 +299,14 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
         ct.hxx = C.kd * Pxx;
         ct.hyy = C.kd * Pyy;
         ct.hzz = C.kd * Pzz;
-        const T ko2p = T(2) * C.ko;
-        ct.hxy = ko2p * Pxy;
-        ct.hxz = ko2p * Pxz;
-        ct.hyz = ko2p * Pyz;
+        ct.hxy = C.ko2 * Pxy;
+        ct.hxz = C.ko2 * Pxz;
+        ct.hyz = C.ko2 * Pyz;
         return e;
     }
     ct.u = wpp * C.inv_eps * GLG * irho;
     const T al = T(2) * wr;
-    const T be = fma_(-al * GLG, irho, fma_(dq, iq, T(2) * C.c6));
+    const T be = fma_(-al * GLG, irho, fma_(dq, iq, C.c6x2));
     ct.dx = C.sg * fma_(al, LGx, be * Gx);
     ct.dy = C.sg * fma_(al, LGy, be * Gy);
     ct.dz = C.sg * fma_(al, LGz, be * Gz);
@@ -309,10 +319,9 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
     ct.hxx = C.kd * Lxx;
     ct.hyy = C.kd * Lyy;
     ct.hzz = C.kd * Lzz;
-    const T ko2 = T(2) * C.ko;                                // Hess_cd feeds M_cd and M_dc
-    ct.hxy = ko2 * Lxy;
-    ct.hxz = ko2 * Lxz;
-    ct.hyz = ko2 * Lyz;
+    ct.hxy = C.ko2 * Lxy;                                     // Hess_cd feeds M_cd and M_dc
+    ct.hxz = C.ko2 * Lxz;
+    ct.hyz = C.ko2 * Lyz;
     return e;
 }
 

@@ -3,9 +3,9 @@
 // energy  h^3 sum (eps/2 |grad u|^2 + W(u)/eps)  (the diffuse area) and the
 // extremes of u.  grad u is the periodic central difference, without xi.
 //
-// One pass that marches in z (HBM-bound: u is read once); per-thread sums
-// in the arithmetic type, FP64 across warps and blocks, combined in a fixed
-// order by the last block to finish (ticket).
+// One pass that marches in z (HBM-bound: u is read once, 4 or 8 B/voxel);
+// per-thread sums in the arithmetic type, FP64 across warps and blocks,
+// combined in a fixed order by the last block to finish (ticket).
 #include "pfc_device.cuh"
 
 namespace pfc {
@@ -18,57 +18,35 @@ constexpr int kDiagThreads = kDX * kDY;
 __device__ __forceinline__ double fmax_(double a, double b) { return a > b ? a : b; }
 __device__ __forceinline__ double fmin_(double a, double b) { return a < b ? a : b; }
 
-// Block (32 x 8 threads) = one (x, y) tile; blockIdx.z = a chunk of zc
-// planes that every thread marches through, keeping u(z-1), u(z), u(z+1) of
-// its column in registers: one new load per voxel from HBM, the four x/y
-// neighbours from L1/L2, and no index arithmetic beyond a pointer step.
+// The per-voxel terms: |eps/2 |G|^2 - W/eps| and eps/2 |G|^2 + W/eps.
 template <typename T>
-__global__ void __launch_bounds__(kDiagThreads) k_diag(const T* __restrict__ u, int nx, int ny, int nz, int zc, T sg,
-                                                      T half_eps, T inv_eps, int well, double h3, double* part,
-                                                      unsigned* ticket, double* out)
+__device__ __forceinline__ void diag_terms(T gx, T gy, T gz, T u0, T half_eps, T inv_eps, int well, T& d, T& c)
 {
-    const long pls = (long)nx * ny;
-    const int x = blockIdx.x * kDX + threadIdx.x, y = blockIdx.y * kDY + threadIdx.y;
-    const int z0 = blockIdx.z * zc, z1 = min(nz, z0 + zc);
-    T sd = 0, sc = 0;
-    T umax = -INFINITY, umin = INFINITY;
-    if (x < nx && y < ny && z0 < z1) {
-        const int xm = nbr(x, -1, nx) - x, xp = nbr(x, 1, nx) - x;
-        const long ym = (long)(nbr(y, -1, ny) - y) * nx, yp = (long)(nbr(y, 1, ny) - y) * nx;
-        const T* col = u + (long)y * nx + x;
-        T um = col[(long)nbr(z0, -1, nz) * pls];
-        T u0 = col[(long)z0 * pls];
-        const T* c = col + (long)z0 * pls;
-#pragma unroll 4
-        for (int z = z0; z < z1; ++z, c += pls) {
-            const T up = col[(long)(z + 1 == nz ? 0 : z + 1) * pls];
-            const T gx = sg * (c[xp] - c[xm]);
-            const T gy = sg * (c[yp] - c[ym]);
-            const T gz = sg * (up - um);
-            const T kin = half_eps * fma_(gx, gx, fma_(gy, gy, gz * gz));
-            T W;
-            if (well == 0) {
-                const T t = u0 - u0 * u0;   // u (1 - u)
-                W = t * t;
-            } else {
-                const T t = T(1) - u0 * u0;
-                W = T(0.25) * t * t;
-            }
-            const T pot = W * inv_eps;
-            const T d = kin - pot;
-            sd += d < T(0) ? -d : d;
-            sc += kin + pot;
-            umax = u0 > umax ? u0 : umax;
-            umin = u0 < umin ? u0 : umin;
-            um = u0;
-            u0 = up;
-        }
+    const T kin = half_eps * fma_(gx, gx, fma_(gy, gy, gz * gz));
+    T W;
+    if (well == 0) {
+        const T q = u0 - u0 * u0;   // u (1 - u)
+        W = q * q;
+    } else {
+        const T q = T(1) - u0 * u0;
+        W = T(0.25) * q * q;
     }
-    // FP64 beyond the thread: warp shuffles, then one value per warp
-    double v[4] = { (double)sd, (double)sc, (double)umax, (double)umin };
+    const T pot = W * inv_eps;
+    const T e = kin - pot;
+    d = e < T(0) ? -e : e;
+    c = kin + pot;
+}
+
+// FP64 beyond the thread: warp shuffles, one value per warp, one partial per
+// block; the last block to arrive (ticket, no waiting) combines the partials
+// in block order and writes the five results.  Called by every thread.
+__device__ void diag_finish(double sd, double sc, double umax, double umin, int nblocks, int bid, double h3,
+                            double* part, unsigned* ticket, double* out)
+{
+    double v[4] = { sd, sc, umax, umin };
     __shared__ double red[kDiagThreads / 32][4];
     __shared__ int last;
-    const int tid = threadIdx.y * kDX + threadIdx.x;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int lane = tid & 31, wid = tid >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -80,8 +58,6 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const T* __restrict__ u, 
     if (lane == 0)
         for (int k = 0; k < 4; ++k) red[wid][k] = v[k];
     __syncthreads();
-    const int nblocks = gridDim.x * gridDim.y * gridDim.z;
-    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     if (tid == 0) {
         double s0 = 0, s1 = 0, mx = -INFINITY, mn = INFINITY;
         for (int w = 0; w < kDiagThreads / 32; ++w) {
@@ -133,12 +109,134 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const T* __restrict__ u, 
     *ticket = 0;
 }
 
+// Any element type and row length.  Block (32 x 8 threads) = one (x, y)
+// tile; blockIdx.z = a chunk of zc planes that every thread marches through,
+// keeping u(z-1), u(z), u(z+1) of its column in registers: one new load per
+// voxel from HBM, the four x/y neighbours from L1/L2.
+template <typename T>
+__global__ void __launch_bounds__(kDiagThreads) k_diag(const T* __restrict__ u, int nx, int ny, int nz, int zc, T sg,
+                                                      T half_eps, T inv_eps, int well, double h3, double* part,
+                                                      unsigned* ticket, double* out)
+{
+    const long pls = (long)nx * ny;
+    const int x = blockIdx.x * kDX + threadIdx.x, y = blockIdx.y * kDY + threadIdx.y;
+    const int z0 = blockIdx.z * zc, z1 = min(nz, z0 + zc);
+    T sd = 0, sc = 0;
+    T umax = -INFINITY, umin = INFINITY;
+    if (x < nx && y < ny && z0 < z1) {
+        const int xm = nbr(x, -1, nx) - x, xp = nbr(x, 1, nx) - x;
+        const long ym = (long)(nbr(y, -1, ny) - y) * nx, yp = (long)(nbr(y, 1, ny) - y) * nx;
+        const T* col = u + (long)y * nx + x;
+        T um = col[(long)nbr(z0, -1, nz) * pls];
+        T u0 = col[(long)z0 * pls];
+        const T* c = col + (long)z0 * pls;
+#pragma unroll 4
+        for (int z = z0; z < z1; ++z, c += pls) {
+            const T up = col[(long)(z + 1 == nz ? 0 : z + 1) * pls];
+            T d, s;
+            diag_terms<T>(sg * (c[xp] - c[xm]), sg * (c[yp] - c[ym]), sg * (up - um), u0, half_eps, inv_eps, well,
+                          d, s);
+            sd += d;
+            sc += s;
+            umax = u0 > umax ? u0 : umax;
+            umin = u0 < umin ? u0 : umin;
+            um = u0;
+            u0 = up;
+        }
+    }
+    const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    diag_finish((double)sd, (double)sc, (double)umax, (double)umin, nblocks, bid, h3, part, ticket, out);
+}
+
+// FP32 rows of a multiple of 4 voxels on a 16-byte aligned field: each
+// thread owns 4 consecutive x voxels (one float4), a warp 128 voxels of a
+// row, a block (32 x 8 threads) a tile of 128 x 8 columns.  Persistent grid:
+// block b walks the work items b, b + gridDim.x, ... (a tile over a chunk of
+// zc planes).  Each thread marches its 4 columns up z, issuing the loads of
+// kB planes together (its own float4 from HBM, the y neighbours' float4 from
+// L1/L2); the x neighbours are in its own float4 or its lanes' (shuffles),
+// and the tile's two edge columns are loaded by the edge lanes.  A quarter
+// of the load instructions of one voxel per thread, kB loads in flight.
+constexpr int kB = 4;
+
+__global__ void __launch_bounds__(kDiagThreads) k_diag4(const float* __restrict__ u, int nx, int ny, int nz, int zc,
+                                                       int tiles_x, int tiles_y, int chunks, float sg, float half_eps,
+                                                       float inv_eps, int well, double h3, double* part,
+                                                       unsigned* ticket, double* out)
+{
+    const long pls = (long)nx * ny;
+    const int lx = threadIdx.x;
+    float sd = 0.f, sc = 0.f, umax = -INFINITY, umin = INFINITY;
+    const int items = tiles_x * tiles_y * chunks;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int ch = it % chunks, t = it / chunks;
+        const int x4 = (t % tiles_x) * (4 * kDX) + 4 * lx, y = (t / tiles_x) * kDY + threadIdx.y;
+        const int z0 = ch * zc, z1 = min(nz, z0 + zc);
+        // lanes past a ragged edge work on a valid (clamped) column and count nothing
+        const bool live = x4 < nx && y < ny;
+        const int xq = min(x4, nx - 4), yl = min(y, ny - 1);
+        // whether lane -1 / +1 holds the voxel left of x4 / right of x4 + 3
+        const bool sh_l = lx > 0, sh_r = lx < kDX - 1 && x4 + 4 < nx;
+        const long ym = (long)(nbr(yl, -1, ny) - yl) * nx, yp = (long)(nbr(yl, 1, ny) - yl) * nx;
+        const int xl = nbr(xq, -1, nx) - xq, xr = nbr(xq, 4, nx) - xq;
+        const float* col = u + (long)yl * nx + xq;
+        float4 um = *reinterpret_cast<const float4*>(col + (long)nbr(z0, -1, nz) * pls);
+        float4 u0 = *reinterpret_cast<const float4*>(col + (long)z0 * pls);
+        for (int zb = z0; zb < z1; zb += kB) {
+            const int n = min(kB, z1 - zb);   // uniform across the block: the shuffles see full warps
+            float4 up[kB], vp[kB], vm[kB];
+            float el[kB], er[kB];
+#pragma unroll
+            for (int k = 0; k < kB; ++k) {
+                if (k < n) {
+                    const int z = zb + k;
+                    const float* c = col + (long)z * pls;
+                    up[k] = *reinterpret_cast<const float4*>(col + (long)(z + 1 == nz ? 0 : z + 1) * pls);
+                    vp[k] = *reinterpret_cast<const float4*>(c + yp);
+                    vm[k] = *reinterpret_cast<const float4*>(c + ym);
+                    el[k] = sh_l ? 0.f : c[xl];
+                    er[k] = sh_r ? 0.f : c[xr];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kB; ++k) {
+                if (k < n) {
+                    const float left = __shfl_up_sync(0xffffffffu, u0.w, 1);
+                    const float right = __shfl_down_sync(0xffffffffu, u0.x, 1);
+                    const float l = sh_l ? left : el[k], r = sh_r ? right : er[k];
+                    float d0, c0, d1, c1, d2, c2, d3, c3;
+                    diag_terms<float>(sg * (u0.y - l), sg * (vp[k].x - vm[k].x), sg * (up[k].x - um.x), u0.x,
+                                      half_eps, inv_eps, well, d0, c0);
+                    diag_terms<float>(sg * (u0.z - u0.x), sg * (vp[k].y - vm[k].y), sg * (up[k].y - um.y), u0.y,
+                                      half_eps, inv_eps, well, d1, c1);
+                    diag_terms<float>(sg * (u0.w - u0.y), sg * (vp[k].z - vm[k].z), sg * (up[k].z - um.z), u0.z,
+                                      half_eps, inv_eps, well, d2, c2);
+                    diag_terms<float>(sg * (r - u0.z), sg * (vp[k].w - vm[k].w), sg * (up[k].w - um.w), u0.w,
+                                      half_eps, inv_eps, well, d3, c3);
+                    if (live) {
+                        sd += (d0 + d1) + (d2 + d3);
+                        sc += (c0 + c1) + (c2 + c3);
+                        umax = fmaxf(umax, fmaxf(fmaxf(u0.x, u0.y), fmaxf(u0.z, u0.w)));
+                        umin = fminf(umin, fminf(fminf(u0.x, u0.y), fminf(u0.z, u0.w)));
+                    }
+                    um = u0;
+                    u0 = up[k];
+                }
+            }
+        }
+    }
+    diag_finish((double)sd, (double)sc, (double)umax, (double)umin, gridDim.x, blockIdx.x, h3, part, ticket, out);
+}
+
 }  // namespace
 
+// The scalar kernel's grid: (x, y) tiles times z chunks, about 4 waves of 8
+// blocks per SM.
 static dim3 diag_grid(int nx, int ny, int nz, int* zc)
 {
     const long tiles = (long)((nx + kDX - 1) / kDX) * ((ny + kDY - 1) / kDY);
-    const long target = 32L * device_sms();   // blocks to aim for: about 4 waves of 8 per SM
+    const long target = 32L * device_sms();
     long chunks = (target + tiles - 1) / tiles;
     if (chunks > nz) chunks = nz;
     if (chunks < 1) chunks = 1;
@@ -147,17 +245,61 @@ static dim3 diag_grid(int nx, int ny, int nz, int* zc)
     return dim3((nx + kDX - 1) / kDX, (ny + kDY - 1) / kDY, (unsigned)chunks);
 }
 
+// The float4 kernel: work items of up to 32 planes (more, shorter items when
+// the grid is small, so that each block walks several), one resident wave
+// of blocks.
+struct Diag4Geom {
+    int tiles_x, tiles_y, chunks, zc, blocks;
+};
+static int diag4_blocks_per_sm()
+{
+    static int cached = 0;
+    if (!cached) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_diag4, kDiagThreads, 0) != cudaSuccess || n < 1) {
+            (void)cudaGetLastError();
+            n = 2;
+        }
+        cached = n;
+    }
+    return cached;
+}
+static Diag4Geom diag4_geom(int nx, int ny, int nz)
+{
+    Diag4Geom g;
+    g.tiles_x = (nx + 4 * kDX - 1) / (4 * kDX);
+    g.tiles_y = (ny + kDY - 1) / kDY;
+    const long tiles = (long)g.tiles_x * g.tiles_y;
+    const long wave = (long)diag4_blocks_per_sm() * device_sms();
+    long chunks = (nz + 31) / 32;
+    if (tiles * chunks < 8 * wave) chunks = (8 * wave + tiles - 1) / tiles;
+    if (chunks > nz) chunks = nz;
+    g.zc = (int)((nz + chunks - 1) / chunks);
+    g.chunks = (nz + g.zc - 1) / g.zc;
+    const long items = tiles * g.chunks;
+    g.blocks = (int)(items < wave ? items : wave);
+    return g;
+}
+
 long diag_blocks(int nx, int ny, int nz)
 {
     int zc;
     const dim3 g = diag_grid(nx, ny, nz, &zc);
-    return (long)g.x * g.y * g.z;
+    const long a = (long)g.x * g.y * g.z, b = diag4_geom(nx, ny, nz).blocks;
+    return a > b ? a : b;
 }
 
 template <typename T>
 cudaError_t launch_diagnostics(const T* u, int nx, int ny, int nz, double h, double eps, int well, double* part,
                                unsigned* ticket, double* out, cudaStream_t s)
 {
+    if (sizeof(T) == 4 && nx % 4 == 0 && ((uintptr_t)u) % 16 == 0) {
+        const Diag4Geom g = diag4_geom(nx, ny, nz);
+        k_diag4<<<g.blocks, dim3(kDX, kDY), 0, s>>>((const float*)u, nx, ny, nz, g.zc, g.tiles_x, g.tiles_y,
+                                                    g.chunks, (float)(1.0 / (2.0 * h)), (float)(0.5 * eps),
+                                                    (float)(1.0 / eps), well, h * h * h, part, ticket, out);
+        return cudaGetLastError();
+    }
     int zc;
     const dim3 g = diag_grid(nx, ny, nz, &zc);
     k_diag<T><<<g, dim3(kDX, kDY), 0, s>>>(u, nx, ny, nz, zc, (T)(1.0 / (2.0 * h)), (T)(0.5 * eps), (T)(1.0 / eps),

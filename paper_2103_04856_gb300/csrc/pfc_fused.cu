@@ -141,8 +141,12 @@ Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well, 
     C.c4 = (T)((a[3] + a[4]) / 2.0 * h3);
     C.c5 = (T)((a[3] - a[4]) / 2.0 * h3);
     C.c6 = (T)(a[5] * eps * h3);
+    C.c1x2 = T(2) * C.c1;
+    C.c2x2 = T(2) * C.c2;
+    C.c6x2 = T(2) * C.c6;
     C.kd = (T)(-eps / (h * h));
     C.ko = (T)(-eps / (4.0 * h * h));
+    C.ko2 = T(2) * C.ko;
     C.sg = (T)(1.0 / (2.0 * h));
     C.inv_eps = (T)(1.0 / eps);
     C.xi = (T)xi;
@@ -160,7 +164,8 @@ Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well, 
     C.th2 = (T)(theta ? theta[2] : 0.0);
     C.proj = proj ? 1 : 0;
     C.sym = (C.c3 == T(0) && C.c5 == T(0)) ? 1 : 0;
-    C.refine = refine ? 1 : 0;
+    // the refinement test is scale > rthr max(|D|, xi): 2^16 = 2^22 / 2^6, or never
+    C.rthr = refine ? T(65536) : T(INFINITY);
     return C;
 }
 template Coef<float> make_coef<float>(const double*, double, double, double, int, double, const double*, int, int);
@@ -239,31 +244,6 @@ long long fused_slots(int nx, int ny, int nz, int tile_y, int max_run)
     return a > b ? a : b;
 }
 
-// Split the launch's work units evenly over G CTAs and record, per problem,
-// the first CTA that holds a partial of it and how many do.
-template <typename T, int MAXI>
-static void plan(Launch<T, MAXI>& L, int tile_y, int max_run)
-{
-    long long W = 0;
-    for (int k = 0; k < L.n; ++k) {
-        Inst<T>& in = L.inst[k];
-        in.tiles_x = (in.nx + TX - 1) / TX;
-        in.tiles_y = (in.ny + tile_y - 1) / tile_y;
-        in.unit_base = W;
-        W += (long long)in.tiles_x * in.tiles_y * in.nz;
-    }
-    const long long G = fused_grid(W, max_run);
-    L.units = W;
-    L.grid = (int)G;
-    for (int k = 0; k < L.n; ++k) {
-        Inst<T>& in = L.inst[k];
-        const long long a = in.unit_base, b = a + (long long)in.tiles_x * in.tiles_y * in.nz - 1;
-        const int c0 = (int)(((a + 1) * G - 1) / W), c1 = (int)(((b + 1) * G - 1) / W);
-        in.first_block = c0;
-        in.nblocks = c1 - c0 + 1;
-    }
-}
-
 template <typename T, int TY, int EXT = 0>
 static cudaError_t launch_mode(const Inst<T>& in, int mode, int max_run, cudaStream_t s)
 {
@@ -285,6 +265,7 @@ static cudaError_t launch_mode(const Inst<T>& in, int mode, int max_run, cudaStr
 template <typename T>
 cudaError_t launch_fused(const Inst<T>& in, int mode, int tile_y, int max_run, cudaStream_t s)
 {
+    if (in.halo) return launch_fused_halo<T>(in, mode, tile_y, max_run, s);
     if (in.C.proj) return launch_mode<T, EXT_TILE_Y, 2>(in, mode, max_run, s);
     if (needs_ext(in)) return launch_mode<T, EXT_TILE_Y, 1>(in, mode, max_run, s);
     if (tile_y == 8) return launch_mode<T, 8>(in, mode, max_run, s);

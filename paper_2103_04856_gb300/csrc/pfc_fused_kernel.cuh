@@ -88,7 +88,10 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // SYM: every problem of the launch has c3 = c5 = 0 (FP32, EXT = 0 only): the
 // sqrt(D+) terms, whose weight is exactly zero then, are not compiled in.
-template <typename T, int TY, int MODE, int MAXI, int EXT = 0, bool SYM = false>
+// HALO: the problem is a z-slab whose planes beyond its ends come from
+// in.halo (instantiated only for slab launches, in pfc_fused_slab.cu: the
+// check costs the other launches registers they do not have).
+template <typename T, int TY, int MODE, int MAXI, int EXT = 0, bool SYM = false, bool HALO = false>
 __global__ void __launch_bounds__(Tile<TY>::NT, 1)
 k_fused(const __grid_constant__ Launch<T, MAXI> L)
 {
@@ -185,8 +188,8 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
             if (p <= plast) {
                 T* dst = us + (p & (NBUF - 1)) * PLANE;
                 // a z-slab takes the planes beyond its ends from its halo buffer
-                const T* src = (in.halo && (p < 0 || p >= nz)) ? in.halo + (size_t)(p < 0 ? p + 2 : p - nz + 2) * plane_g
-                                                              : in.u + (size_t)pz * plane_g;
+                const T* src = (HALO && (p < 0 || p >= nz)) ? in.halo + (size_t)(p < 0 ? p + 2 : p - nz + 2) * plane_g
+                                                           : in.u + (size_t)pz * plane_g;
                 if (in.vec) {
                     if (ld_off >= 0) cp_async16(dst + ld_dst, src + ld_off);
                 } else {
@@ -275,6 +278,7 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
                 if (cfp) {
                     Cv.c1 = ccn[0]; Cv.c2 = ccn[1]; Cv.c3 = ccn[2];
                     Cv.c4 = ccn[3]; Cv.c5 = ccn[4]; Cv.c6 = ccn[5];
+                    Cv.c1x2 = T(2) * ccn[0]; Cv.c2x2 = T(2) * ccn[1]; Cv.c6x2 = T(2) * ccn[5];
                 }
                 load_c(m + 1);
             }
@@ -367,20 +371,50 @@ size_t fused_smem_bytes(int elem_size, int tile_y);
 
 // One launch of k_fused (sets the dynamic shared-memory limit once per
 // instantiation; idempotent, so a race between threads is harmless).
-template <typename T, int TY, int MODE, int MAXI, int EXT = 0, bool SYM = false>
+template <typename T, int TY, int MODE, int MAXI, int EXT = 0, bool SYM = false, bool HALO = false>
 static cudaError_t launch_kernel(const Launch<T, MAXI>& L, int blocks, cudaStream_t s)
 {
     const size_t smem = fused_smem_bytes(sizeof(T), TY);
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<T, TY, MODE, MAXI, EXT, SYM>,
+        cudaError_t e = cudaFuncSetAttribute(k_fused<T, TY, MODE, MAXI, EXT, SYM, HALO>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    k_fused<T, TY, MODE, MAXI, EXT, SYM><<<blocks, Tile<TY>::NT, smem, s>>>(L);
+    k_fused<T, TY, MODE, MAXI, EXT, SYM, HALO><<<blocks, Tile<TY>::NT, smem, s>>>(L);
     return cudaGetLastError();
 }
+
+// Split the launch's work units evenly over G CTAs and record, per problem,
+// the first CTA that holds a partial of it and how many do.
+template <typename T, int MAXI>
+static void plan(Launch<T, MAXI>& L, int tile_y, int max_run)
+{
+    long long W = 0;
+    for (int k = 0; k < L.n; ++k) {
+        Inst<T>& in = L.inst[k];
+        in.tiles_x = (in.nx + TX - 1) / TX;
+        in.tiles_y = (in.ny + tile_y - 1) / tile_y;
+        in.unit_base = W;
+        W += (long long)in.tiles_x * in.tiles_y * in.nz;
+    }
+    const long long G = fused_grid(W, max_run);
+    L.units = W;
+    L.grid = (int)G;
+    for (int k = 0; k < L.n; ++k) {
+        Inst<T>& in = L.inst[k];
+        const long long a = in.unit_base, b = a + (long long)in.tiles_x * in.tiles_y * in.nz - 1;
+        const int c0 = (int)(((a + 1) * G - 1) / W), c1 = (int)(((b + 1) * G - 1) / W);
+        in.first_block = c0;
+        in.nblocks = c1 - c0 + 1;
+    }
+}
+
+// The sweep of a z-slab (in.halo set): every tile height and extension, the
+// general instantiation (pfc_fused_slab.cu).
+template <typename T>
+cudaError_t launch_fused_halo(const Inst<T>& in, int mode, int tile_y, int max_run, cudaStream_t s);
 
 // The FP32 sweep for launches whose problems all have c3 = c5 = 0 (pfc_fused_sym.cu).
 template <int MAXI>

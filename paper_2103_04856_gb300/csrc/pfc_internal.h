@@ -34,8 +34,10 @@ struct CoefD {
 template <typename T>
 struct Coef {
     T c1, c2, c3, c4, c5, c6;
+    T c1x2, c2x2, c6x2;   // 2 c1, 2 c2, 2 c6 (exact doublings, formed once on the host)
     T kd;       // -eps / h^2     : d M_cc / d (u+ - 2u + u-)
     T ko;       // -eps / (4 h^2) : d M_cd / d (4-point mixed difference)
+    T ko2;      // 2 ko: Hess_cd feeds both M_cd and M_dc
     T sg;       // 1 / (2h)       : d G_c / d (u+ - u-)
     T inv_eps;  // 1 / eps
     T xi, xi2, inv_xi;
@@ -47,9 +49,10 @@ struct Coef {
     // 1: c3 = c5 = 0 in the arithmetic type (p symmetric in kappa1, kappa2), so
     // the weight c3 T + c5 q of the sqrt(D+) terms is exactly zero
     int sym;
-    // 1: FP32 voxels whose D = 2S - T^2 may have lost its accuracy to
-    // cancellation recompute it in FP64 (voxel_eval); 0: never
-    int refine;
+    // FP32 voxels whose D = 2S - T^2 may have lost its accuracy to
+    // cancellation recompute it in FP64 where 2S + T^2 > rthr max(|D|, xi)
+    // (voxel_eval): rthr = 2^16, or infinity to never refine
+    T rthr;
 };
 
 // Coefficient fields: c(x) = (c1..c6)(a(x)) as 6 component planes of N

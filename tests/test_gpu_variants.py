@@ -216,7 +216,7 @@ def test_flow_with_mass_field_fp32(sigma):
 
 # ------------------------------------------------------------ diagnostics
 
-@pytest.mark.parametrize("shape", [(7, 9, 11), (40, 33, 64), (1, 4, 8)])
+@pytest.mark.parametrize("shape", [(7, 9, 11), (40, 33, 64), (1, 4, 8), (20, 17, 45), (6, 5, 33), (37, 8, 32)])
 def test_diagnostics_vs_oracle(shape):
     for well in (0, 1):
         u = I.noise(shape, 0.3 if well == 0 else -0.1, 0.2, 15)
