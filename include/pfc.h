@@ -91,8 +91,9 @@ typedef struct {
 /* FP32 only: D = 2||M||^2 - (Tr M)^2 is the difference of two numbers of
  * size ||M||^2, so its FP32 rounding error is about 2^-22 (2||M||^2 + (Tr
  * M)^2).  Where that error is more than 2^-6 of max(|D|, xi) and the sqrt(D+)
- * terms carry weight (c3 Tr M + c5 |grad u| != 0), the sweep recomputes D in
- * FP64 from the exact stencil inputs (Sec. 3.1 invariants).  This flag turns
+ * terms carry weight (c3 Tr M + c5 |grad u| != 0), the sweep recomputes D from
+ * the exact stencil inputs in double-float arithmetic (pairs of floats, about
+ * 44 bits; FP64 for the projected M) (Sec. 3.1 invariants).  This flag turns
  * that refinement off (for measuring what it changes); it has no effect on
  * FP64 problems or on polynomials symmetric in kappa1, kappa2. */
 #define PFC_FLAG_NO_DISCRIMINANT_REFINEMENT 1u
@@ -237,7 +238,10 @@ void pfc_batch_destroy(pfc_batch* batch);
 /* u[k]: device field of instance k, advanced in place by nsteps steps of
  * size tau[k] (host array).  trace_host (may be NULL): n_inst x nsteps x 5
  * doubles, instance-major.  Synchronises.  PFC_ENONFINITE if any instance
- * produced a non-finite scalar (the others are still advanced). */
+ * produced a non-finite scalar; the others are still advanced, while such an
+ * instance is retired for the rest of the call (it is not evaluated again:
+ * its field is filled with NaN and its later trace rows are NaN).  The same
+ * holds within a chain of pfc_batch_step_lazy calls. */
 pfc_status pfc_batch_run(pfc_batch* batch, void* const* u, int32_t nsteps, const double* tau,
                          double* trace_host, pfc_stream stream);
 

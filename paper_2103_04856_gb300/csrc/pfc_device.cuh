@@ -57,45 +57,96 @@ struct Cot {
     T hxy, hxz, hyz;        // 4-point mixed differences
 };
 
-// rho^2 D = 2||rho M||^2 - (Tr rho M)^2 in FP64 from raw stencil values that
-// are exact in FP64 (differences of float inputs), for the float path's
-// refinement; rho M = rho kd Hess + w G G^T needs no division.
-__device__ __forceinline__ double discriminant_rho2_fp64(const CoefD& R, int well, double u0, double dx, double dy,
-                                                         double dz, double hxx, double hyy, double hzz, double hxy,
-                                                         double hxz, double hyz, double* rho_out)
+// ------------------------------------------------------------ double-float
+
+// An unevaluated sum hi + lo of two floats (|lo| <= ulp(hi) / 2): about 44
+// significant bits from FP32 operations, far cheaper on this GPU than FP64
+// (whose pipe runs at 1/64 of the FP32 rate).  The error-free transformations
+// are Knuth's two-sum and the product error from one FMA; the _rn intrinsics
+// keep the compiler from contracting or reordering them.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_two_sum(float a, float b)
 {
-    const double Gx = dx * R.sg, Gy = dy * R.sg, Gz = dz * R.sg;
-    const double rho = fma(Gx, Gx, fma(Gy, Gy, fma(Gz, Gz, R.xi2)));
-    const double w = (well == 0 ? 2.0 * (u0 - u0 * u0) * (1.0 - 2.0 * u0) : u0 * u0 * u0 - u0) * R.inv_eps;
-    const double ak = rho * R.kd, bk = rho * R.ko;
-    const double wx = w * Gx, wy = w * Gy, wz = w * Gz;
-    const double Mxx = fma(ak, hxx, wx * Gx), Myy = fma(ak, hyy, wy * Gy), Mzz = fma(ak, hzz, wz * Gz);
-    const double Mxy = fma(bk, hxy, wx * Gy), Mxz = fma(bk, hxz, wx * Gz), Myz = fma(bk, hyz, wy * Gz);
-    const double Tr = Mxx + Myy + Mzz;
-    const double S = Mxx * Mxx + Myy * Myy + Mzz * Mzz + 2.0 * (Mxy * Mxy + Mxz * Mxz + Myz * Myz);
-    *rho_out = rho;
-    return 2.0 * S - Tr * Tr;
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return { s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)) };
+}
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b)   // |a| >= |b| or a == 0
+{
+    const float s = __fadd_rn(a, b);
+    return { s, __fsub_rn(b, __fsub_rn(s, a)) };
+}
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    const DF s = df_two_sum(a.hi, b.hi), t = df_two_sum(a.lo, b.lo);
+    const DF r = df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return df_fast_two_sum(r.hi, __fadd_rn(t.lo, r.lo));
+}
+__device__ __forceinline__ DF df_neg(DF a) { return { -a.hi, -a.lo }; }
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ DF df_mul(DF a, DF b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.hi, -p)));
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ DF df_scale2(DF a) { return { __fmul_rn(2.0f, a.hi), __fmul_rn(2.0f, a.lo) }; }   // exact
+__device__ __forceinline__ DF df_div(DF a, DF b)
+{
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const DF r = df_sub(a, df_mul(DF{ q1, 0.0f }, b));
+    return df_fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
 }
 
-// D for the voxel whose 19 stencil inputs sit in three u planes (pm, p0, pp
-// point at the voxel; `pitch` is the row pitch).  Kept out of line: it runs
-// for few voxels and must not add registers to the float hot path.
+// D of eq. Meps's M in double-float from the 19 raw stencil values of the
+// voxel (exact floats in three u planes: pm, p0, pp point at the voxel,
+// `pitch` is the row pitch) plus the offset c the loads add: differences
+// of the inputs are exact (two-sum), every later operation keeps about 44
+// bits, so the cancellation in 2S - T^2 no longer loses the result.  Kept out
+// of line: it runs for few voxels and must not add registers to the float
+// hot path.
 template <typename T>
-__device__ __noinline__ T discriminant_fp64_at(const CoefD& R, int well, const T* pm, const T* p0, const T* pp,
-                                               int pitch, double c)
+__device__ __noinline__ T discriminant_df_at(const CoefD& R, int well, const T* pm, const T* p0, const T* pp, int pitch,
+                                             double c)
 {
-    auto d = [](T v) { return (double)v; };
-    const double u0 = d(p0[0]);
-    double rho;
-    const double Dr2 = discriminant_rho2_fp64(
-        R, well, u0 + c, d(p0[1]) - d(p0[-1]), d(p0[pitch]) - d(p0[-pitch]), d(pp[0]) - d(pm[0]),
-        (d(p0[1]) + d(p0[-1])) - 2.0 * u0, (d(p0[pitch]) + d(p0[-pitch])) - 2.0 * u0, (d(pp[0]) + d(pm[0])) - 2.0 * u0,
-        (d(p0[pitch + 1]) - d(p0[pitch - 1])) - (d(p0[-pitch + 1]) - d(p0[-pitch - 1])),
-        (d(pp[1]) - d(pp[-1])) - (d(pm[1]) - d(pm[-1])), (d(pp[pitch]) - d(pp[-pitch])) - (d(pm[pitch]) - d(pm[-pitch])),
-        &rho);
-    // the cancellation is resolved; the division keeps float's relative accuracy
-    const T r = (T)rho;
-    return (T)Dr2 / (r * r);
+    const float ch = (float)c;
+    const DF cdf = { ch, (float)(c - (double)ch) };
+    const float uc = (float)p0[0];
+    const DF u0 = df_add(DF{ uc, 0.0f }, cdf);
+    auto f = [](T v) { return (float)v; };
+    auto diff = [&](const T* p, int o) { return df_two_sum(f(p[o]), -f(p[-o])); };                  // u(+) - u(-)
+    auto lap = [&](const T* p, int o) { return df_sub(df_two_sum(f(p[o]), f(p[-o])), DF{ 2.0f * uc, 0.0f }); };
+    const DF kd = { R.kd_h, R.kd_l }, ko = { R.ko_h, R.ko_l }, sg = { R.sg_h, R.sg_l };
+    const DF Gx = df_mul(diff(p0, 1), sg), Gy = df_mul(diff(p0, pitch), sg);
+    const DF Gz = df_mul(df_two_sum(f(pp[0]), -f(pm[0])), sg);
+    const DF hxx = lap(p0, 1), hyy = lap(p0, pitch);
+    const DF hzz = df_sub(df_two_sum(f(pp[0]), f(pm[0])), DF{ 2.0f * uc, 0.0f });
+    const DF hxy = df_sub(df_two_sum(f(p0[pitch + 1]), -f(p0[pitch - 1])), df_two_sum(f(p0[-pitch + 1]), -f(p0[-pitch - 1])));
+    const DF hxz = df_sub(df_two_sum(f(pp[1]), -f(pp[-1])), df_two_sum(f(pm[1]), -f(pm[-1])));
+    const DF hyz = df_sub(df_two_sum(f(pp[pitch]), -f(pp[-pitch])), df_two_sum(f(pm[pitch]), -f(pm[-pitch])));
+    const DF rho = df_add(df_add(df_mul(Gx, Gx), df_mul(Gy, Gy)), df_add(df_mul(Gz, Gz), DF{ R.xi2_h, R.xi2_l }));
+    DF w;   // W'(u) / eps
+    const DF one = { 1.0f, 0.0f };
+    if (well == 0) {
+        const DF t = df_sub(u0, df_mul(u0, u0));                       // u (1 - u)
+        w = df_mul(df_scale2(t), df_sub(one, df_scale2(u0)));
+    } else {
+        w = df_sub(df_mul(df_mul(u0, u0), u0), u0);
+    }
+    const DF wr = df_div(df_mul(w, DF{ R.ie_h, R.ie_l }), rho);        // (W'/eps) / rho
+    const DF wx = df_mul(wr, Gx), wy = df_mul(wr, Gy), wz = df_mul(wr, Gz);
+    const DF Mxx = df_add(df_mul(kd, hxx), df_mul(wx, Gx)), Myy = df_add(df_mul(kd, hyy), df_mul(wy, Gy));
+    const DF Mzz = df_add(df_mul(kd, hzz), df_mul(wz, Gz));
+    const DF Mxy = df_add(df_mul(ko, hxy), df_mul(wx, Gy)), Mxz = df_add(df_mul(ko, hxz), df_mul(wx, Gz));
+    const DF Myz = df_add(df_mul(ko, hyz), df_mul(wy, Gz));
+    const DF Tr = df_add(df_add(Mxx, Myy), Mzz);
+    const DF dg = df_add(df_add(df_mul(Mxx, Mxx), df_mul(Myy, Myy)), df_mul(Mzz, Mzz));
+    const DF od = df_add(df_add(df_mul(Mxy, Mxy), df_mul(Mxz, Mxz)), df_mul(Myz, Myz));
+    const DF S = df_add(dg, df_scale2(od));
+    const DF D = df_sub(df_scale2(S), df_mul(Tr, Tr));
+    return (T)__fadd_rn(D.hi, D.lo);
 }
 
 // rho^4 D of the tangent-projected M, in FP64 from the exact raw stencil
@@ -130,8 +181,18 @@ __device__ __noinline__ T discriminant_fp64_proj_at(const CoefD& R, const T* pm,
     return (T)((2.0 * S - Tr * Tr) / (r2 * r2));
 }
 
+// No refinement available (the plain path evaluates voxels from stored
+// derivatives): D keeps its FP32 value.
 struct NoRefine {
     __device__ __forceinline__ float operator()() const { return 0.0f; }
+};
+template <class R>
+struct refines {
+    static constexpr bool value = true;
+};
+template <>
+struct refines<NoRefine> {
+    static constexpr bool value = false;
 };
 
 // Forward (eq. Meps, Sec. 3.1 invariants, eq. Feps) and, if GRAD, local
@@ -143,9 +204,10 @@ struct NoRefine {
 // error is about 2^-22 (2S + T^2).  Only the sqrt(D+) terms, of weight
 // a3 = c3 T + c5 q (zero for polynomials symmetric in kappa1, kappa2), see
 // that error, and it matters only where it is more than 2^-6 of max(|D|, xi):
-// there `refine()` recomputes D in FP64 from the exact float inputs (about
-// one voxel in 10^4 on noise fields; the kernel's CTAs wait for the slowest
-// warp at every plane, so the test is kept tight).
+// there `refine()` recomputes D from the exact float inputs in double-float
+// (eq. Meps) or FP64 (the projected form) arithmetic (about one voxel in 10^4
+// on noise fields, many more on fields that are blowing up; the kernel's CTAs
+// wait for the slowest warp at every plane, so the test is kept tight).
 //
 // ORIENT adds the orientation term of Sec. 5.2, c7 (theta . G)^2, and its
 // cotangent 2 c7 (theta . G) theta on G.
@@ -222,7 +284,7 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
         // D = 2S - T^2 with the rounding error of T^2 put back (two-product)
         const T t2e = fma_(Tr, Tr, -t2);
         T D = fma_(T(2), S, -t2) - t2e;
-        if (sizeof(T) == 4) {
+        if (sizeof(T) == 4 && refines<Refine>::value) {
             const T scale = fma_(T(2), S, t2);
             if (a3 != T(0) && scale > C.rthr * fmax(fabs(D), C.xi)) D = (T)refine();
         }
@@ -422,10 +484,19 @@ __device__ __forceinline__ void block_reduce_parts(double v[NPART], double* red)
 // except s[P_GMAX], a max): energy, mean of the gradient (the multiplier),
 // max and mean |g|; after a step also the mass, the target mass (set by the
 // first step of a run), the offset c = target - mean(v) that the next step's
-// loads add, and a trace row.  One thread.
+// loads add, and a trace row.  `retire` (batch steps): an instance already
+// flagged non-finite was not evaluated; it only records a NaN trace row.
+// One thread.
 __device__ __forceinline__ void set_scalars(const double s[NPART], double inv_N, int mode, double* sc, unsigned* ints,
-                                            double* trace, int trace_cap)
+                                            double* trace, int trace_cap, bool retire = false)
 {
+    if (retire && mode == MODE_STEP && ints[I_NONFINITE]) {
+        const unsigned cnt = ints[I_COUNTER];
+        if (trace && (int)cnt < trace_cap)
+            for (int i = 0; i < 5; ++i) trace[(size_t)cnt * 5 + i] = NAN;
+        ints[I_COUNTER] = cnt + 1;
+        return;
+    }
     const double E = s[P_E];
     bool bad = !isfinite(E);
     if (mode == MODE_ENERGY) {
@@ -459,7 +530,7 @@ __device__ __forceinline__ void set_scalars(const double s[NPART], double inv_N,
 // all partials of the problem in a fixed order and writes its scalars (or,
 // for a z-slab, its totals to in.sums_out).
 template <typename T>
-__device__ void finish_problem(const Inst<T>& in, int slot, int mode, const double* tot)
+__device__ void finish_problem(const Inst<T>& in, int slot, int mode, const double* tot, bool retire = false)
 {
     __shared__ int am_last;
     if (threadIdx.x == 0) {
@@ -490,7 +561,7 @@ __device__ void finish_problem(const Inst<T>& in, int slot, int mode, const doub
 #pragma unroll
         for (int i = 0; i < NPART; ++i) in.sums_out[i] = s[i];
     } else {
-        set_scalars(s, in.inv_N, mode, in.scal, in.ints, in.trace, in.trace_cap);
+        set_scalars(s, in.inv_N, mode, in.scal, in.ints, in.trace, in.trace_cap, retire);
     }
     __threadfence();
     in.ints[I_TICKET] = 0;   // ready for the next launch on this problem

@@ -158,6 +158,15 @@ Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well, 
     C.R.sg = 1.0 / (2.0 * h);
     C.R.inv_eps = 1.0 / eps;
     C.R.xi2 = xi * xi;
+    auto split = [](double v, float& hi, float& lo) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    };
+    split(C.R.kd, C.R.kd_h, C.R.kd_l);
+    split(C.R.ko, C.R.ko_h, C.R.ko_l);
+    split(C.R.sg, C.R.sg_h, C.R.sg_l);
+    split(C.R.inv_eps, C.R.ie_h, C.R.ie_l);
+    split(C.R.xi2, C.R.xi2_h, C.R.xi2_l);
     C.c7 = (T)(eps * mu * h3);
     C.th0 = (T)(theta ? theta[0] : 0.0);
     C.th1 = (T)(theta ? theta[1] : 0.0);

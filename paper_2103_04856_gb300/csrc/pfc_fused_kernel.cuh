@@ -138,7 +138,7 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
         const T v[NPART] = { se, su, sg, sag, gmax, sout };
         block_sums<NT>(v, scr, tot);
         const Inst<T>& pin = L.inst[cur];
-        finish_problem(pin, (int)blockIdx.x - pin.first_block, MODE, tot);
+        finish_problem(pin, (int)blockIdx.x - pin.first_block, MODE, tot, MAXI > 1);
         se = su = sg = sag = gmax = sout = 0;
     };
 
@@ -174,6 +174,19 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
         const int gx = x0 + ex - 1, gy = y0 + ey - 1;
         const bool interior = warp < TY && gx < nx && gy < ny;
         const bool loader = !in.vec || warp < LOADWARPS;
+        // batch steps: an instance whose scalars became non-finite in an
+        // earlier step of the chain is retired (the flag is written only by
+        // the finish of a launch, after every CTA has read it): its runs
+        // write NaN and add nothing to its sums
+        if constexpr (MAXI > 1 && MODE == MODE_STEP) {
+            if (__ldcg(&in.ints[I_NONFINITE])) {
+                if (interior) {
+                    T* o = in.out + (size_t)z0 * plane_g + (size_t)gy * nx + gx;
+                    for (int z = z0; z < zend; ++z, o += plane_g) *o = T(NAN);
+                }
+                continue;
+            }
+        }
 
         // ---- loads: every u plane of the tile, periodic in x, y and z
         int ld_off = -1, ld_dst = 0;
@@ -307,10 +320,11 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
                 if constexpr (EXT) return Cv;
                 else return in.C;
             }();
-            // FP64 re-evaluation of D from the exact float inputs (float path only)
+            // re-evaluation of D from the exact float inputs (float path only):
+            // double-float for eq. Meps, FP64 for the projected form
             auto refine = [&]() -> T {
                 if constexpr (EXT == 2) return discriminant_fp64_proj_at<T>(in.C.R, pm, p0, pp, UXP);
-                else return discriminant_fp64_at<T>(in.C.R, in.C.well, pm, p0, pp, UXP, cind);
+                else return discriminant_df_at<T>(in.C.R, in.C.well, pm, p0, pp, UXP, cind);
             };
             if constexpr (MODE == MODE_ENERGY) {
                 const T e = voxel_eval<T, false, EXT != 0, EXT == 2, SYM>(CC, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ctv, refine);

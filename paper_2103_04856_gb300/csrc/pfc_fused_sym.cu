@@ -1,8 +1,8 @@
 // pfc_fused_sym.cu -- the fused sweep for launches whose problems all have
 // c3 = c5 = 0 (polynomials symmetric in kappa1, kappa2): FP32, no extensions.
 // The sqrt(D+) terms of eq. Feps have weight c3 T + c5 q = 0 there; this
-// instantiation does not compile them in (nor the FP64 refinement of D that
-// serves them), with the same result bits as the general sweep.
+// instantiation does not compile them in (nor the refinement of D that serves
+// them), with the same result bits as the general sweep.
 #include "pfc_fused_kernel.cuh"
 
 namespace pfc {

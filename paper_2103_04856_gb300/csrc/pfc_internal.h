@@ -22,11 +22,13 @@ enum Part { P_E = 0, P_U, P_G, P_AG, P_GMAX, P_OUT, NPART };
 enum Scal { S_E = 0, S_MASS, S_LAMBDA, S_GMAX, S_GMEAN, S_C, S_TARGET, NSCAL = 8 };
 enum Ints { I_TICKET = 0, I_COUNTER, I_NONFINITE, NINTS = 4 };
 
-// The same scale factors in FP64, for re-evaluating the discriminant
-// D = 2||M||^2 - (Tr M)^2 of a float voxel where FP32 cancellation would
-// matter (see voxel_eval).
+// The same scale factors in FP64, and as float pairs hi + lo (about 44
+// significant bits), for re-evaluating the discriminant D = 2||M||^2 -
+// (Tr M)^2 of a float voxel where FP32 cancellation would matter (see
+// voxel_eval): eq. Meps in double-float arithmetic, the projected form in FP64.
 struct CoefD {
     double kd, ko, sg, inv_eps, xi2;
+    float kd_h, kd_l, ko_h, ko_l, sg_h, sg_l, ie_h, ie_l, xi2_h, xi2_l;
 };
 
 // Coefficients of eq. Feps (times h^3, so that summing the per-voxel density
