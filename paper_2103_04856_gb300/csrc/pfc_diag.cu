@@ -18,23 +18,19 @@ constexpr int kDiagThreads = kDX * kDY;
 __device__ __forceinline__ double fmax_(double a, double b) { return a > b ? a : b; }
 __device__ __forceinline__ double fmin_(double a, double b) { return a < b ? a : b; }
 
-// The per-voxel terms: |eps/2 |G|^2 - W/eps| and eps/2 |G|^2 + W/eps.
+// The per-voxel terms |eps/2 |G|^2 - W/eps| and eps/2 |G|^2 + W/eps from
+// the raw differences d = u(+) - u(-) (G = d / 2h): kin = ks |d|^2 with
+// ks = eps / (8 h^2), and W/eps = q wq q with q = u (1 - u), wq = 1/eps
+// (wells 0/1) or q = 1 - u^2, wq = 1/(4 eps) (wells -1/1).
 template <typename T>
-__device__ __forceinline__ void diag_terms(T gx, T gy, T gz, T u0, T half_eps, T inv_eps, int well, T& d, T& c)
+__device__ __forceinline__ void diag_terms(T dx, T dy, T dz, T u0, T ks, T wq, int well, T& d, T& c)
 {
-    const T kin = half_eps * fma_(gx, gx, fma_(gy, gy, gz * gz));
-    T W;
-    if (well == 0) {
-        const T q = u0 - u0 * u0;   // u (1 - u)
-        W = q * q;
-    } else {
-        const T q = T(1) - u0 * u0;
-        W = T(0.25) * q * q;
-    }
-    const T pot = W * inv_eps;
-    const T e = kin - pot;
+    const T kin = ks * fma_(dx, dx, fma_(dy, dy, dz * dz));
+    const T q = well == 0 ? fma_(-u0, u0, u0) : fma_(-u0, u0, T(1));
+    const T qw = q * wq;
+    const T e = fma_(-qw, q, kin);
     d = e < T(0) ? -e : e;
-    c = kin + pot;
+    c = fma_(qw, q, kin);
 }
 
 // FP64 beyond the thread: warp shuffles, one value per warp, one partial per
@@ -114,9 +110,9 @@ __device__ void diag_finish(double sd, double sc, double umax, double umin, int 
 // keeping u(z-1), u(z), u(z+1) of its column in registers: one new load per
 // voxel from HBM, the four x/y neighbours from L1/L2.
 template <typename T>
-__global__ void __launch_bounds__(kDiagThreads) k_diag(const T* __restrict__ u, int nx, int ny, int nz, int zc, T sg,
-                                                      T half_eps, T inv_eps, int well, double h3, double* part,
-                                                      unsigned* ticket, double* out)
+__global__ void __launch_bounds__(kDiagThreads) k_diag(const T* __restrict__ u, int nx, int ny, int nz, int zc, T ks,
+                                                      T wq, int well, double h3, double* part, unsigned* ticket,
+                                                      double* out)
 {
     const long pls = (long)nx * ny;
     const int x = blockIdx.x * kDX + threadIdx.x, y = blockIdx.y * kDY + threadIdx.y;
@@ -134,8 +130,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const T* __restrict__ u, 
         for (int z = z0; z < z1; ++z, c += pls) {
             const T up = col[(long)(z + 1 == nz ? 0 : z + 1) * pls];
             T d, s;
-            diag_terms<T>(sg * (c[xp] - c[xm]), sg * (c[yp] - c[ym]), sg * (up - um), u0, half_eps, inv_eps, well,
-                          d, s);
+            diag_terms<T>(c[xp] - c[xm], c[yp] - c[ym], up - um, u0, ks, wq, well, d, s);
             sd += d;
             sc += s;
             umax = u0 > umax ? u0 : umax;
@@ -161,9 +156,9 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const T* __restrict__ u, 
 constexpr int kB = 4;
 
 __global__ void __launch_bounds__(kDiagThreads) k_diag4(const float* __restrict__ u, int nx, int ny, int nz, int zc,
-                                                       int tiles_x, int tiles_y, int chunks, float sg, float half_eps,
-                                                       float inv_eps, int well, double h3, double* part,
-                                                       unsigned* ticket, double* out)
+                                                       int tiles_x, int tiles_y, int chunks, float ks, float wq,
+                                                       int well, double h3, double* part, unsigned* ticket,
+                                                       double* out)
 {
     const long pls = (long)nx * ny;
     const int lx = threadIdx.x;
@@ -206,14 +201,10 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag4(const float* __restrict_
                     const float right = __shfl_down_sync(0xffffffffu, u0.x, 1);
                     const float l = sh_l ? left : el[k], r = sh_r ? right : er[k];
                     float d0, c0, d1, c1, d2, c2, d3, c3;
-                    diag_terms<float>(sg * (u0.y - l), sg * (vp[k].x - vm[k].x), sg * (up[k].x - um.x), u0.x,
-                                      half_eps, inv_eps, well, d0, c0);
-                    diag_terms<float>(sg * (u0.z - u0.x), sg * (vp[k].y - vm[k].y), sg * (up[k].y - um.y), u0.y,
-                                      half_eps, inv_eps, well, d1, c1);
-                    diag_terms<float>(sg * (u0.w - u0.y), sg * (vp[k].z - vm[k].z), sg * (up[k].z - um.z), u0.z,
-                                      half_eps, inv_eps, well, d2, c2);
-                    diag_terms<float>(sg * (r - u0.z), sg * (vp[k].w - vm[k].w), sg * (up[k].w - um.w), u0.w,
-                                      half_eps, inv_eps, well, d3, c3);
+                    diag_terms<float>(u0.y - l, vp[k].x - vm[k].x, up[k].x - um.x, u0.x, ks, wq, well, d0, c0);
+                    diag_terms<float>(u0.z - u0.x, vp[k].y - vm[k].y, up[k].y - um.y, u0.y, ks, wq, well, d1, c1);
+                    diag_terms<float>(u0.w - u0.y, vp[k].z - vm[k].z, up[k].z - um.z, u0.z, ks, wq, well, d2, c2);
+                    diag_terms<float>(r - u0.z, vp[k].w - vm[k].w, up[k].w - um.w, u0.w, ks, wq, well, d3, c3);
                     if (live) {
                         sd += (d0 + d1) + (d2 + d3);
                         sc += (c0 + c1) + (c2 + c3);
@@ -293,17 +284,16 @@ template <typename T>
 cudaError_t launch_diagnostics(const T* u, int nx, int ny, int nz, double h, double eps, int well, double* part,
                                unsigned* ticket, double* out, cudaStream_t s)
 {
+    const double ks = eps / (8.0 * h * h), wq = well == 0 ? 1.0 / eps : 0.25 / eps;
     if (sizeof(T) == 4 && nx % 4 == 0 && ((uintptr_t)u) % 16 == 0) {
         const Diag4Geom g = diag4_geom(nx, ny, nz);
         k_diag4<<<g.blocks, dim3(kDX, kDY), 0, s>>>((const float*)u, nx, ny, nz, g.zc, g.tiles_x, g.tiles_y,
-                                                    g.chunks, (float)(1.0 / (2.0 * h)), (float)(0.5 * eps),
-                                                    (float)(1.0 / eps), well, h * h * h, part, ticket, out);
+                                                    g.chunks, (float)ks, (float)wq, well, h * h * h, part, ticket, out);
         return cudaGetLastError();
     }
     int zc;
     const dim3 g = diag_grid(nx, ny, nz, &zc);
-    k_diag<T><<<g, dim3(kDX, kDY), 0, s>>>(u, nx, ny, nz, zc, (T)(1.0 / (2.0 * h)), (T)(0.5 * eps), (T)(1.0 / eps),
-                                          well, h * h * h, part, ticket, out);
+    k_diag<T><<<g, dim3(kDX, kDY), 0, s>>>(u, nx, ny, nz, zc, (T)ks, (T)wq, well, h * h * h, part, ticket, out);
     return cudaGetLastError();
 }
 template cudaError_t launch_diagnostics<float>(const float*, int, int, int, double, double, int, double*, unsigned*,
