@@ -25,7 +25,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libpfc.so")
 DEBUG_LIB = os.path.join(HERE, "libpfc_debug.so")
-SOURCES = ["pfc_fused.cu", "pfc_fused_sym.cu", "pfc_fused_slab.cu", "pfc_plain.cu", "pfc_api.cu", "pfc_noalloc.cu", "pfc_hflow.cu", "pfc_diag.cu", "pfc_surface.cu", "pfc_peak.cu"]
+SOURCES = ["pfc_fused.cu", "pfc_fused_sym.cu", "pfc_fused_slab.cu", "pfc_fused_uni.cu", "pfc_plain.cu", "pfc_api.cu", "pfc_noalloc.cu", "pfc_hflow.cu", "pfc_diag.cu", "pfc_surface.cu", "pfc_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

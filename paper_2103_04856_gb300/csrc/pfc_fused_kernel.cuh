@@ -91,7 +91,11 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // HALO: the problem is a z-slab whose planes beyond its ends come from
 // in.halo (instantiated only for slab launches, in pfc_fused_slab.cu: the
 // check costs the other launches registers they do not have).
-template <typename T, int TY, int MODE, int MAXI, int EXT = 0, bool SYM = false, bool HALO = false>
+// UNI (batched launches, EXT = 0): every problem of the launch has the
+// coefficients L.C0 and the step size L.tau0; per-voxel arithmetic takes them
+// as constant-bank operands, where in.C at the run-time problem index costs a
+// load per use (pfc_fused_uni.cu).
+template <typename T, int TY, int MODE, int MAXI, int EXT = 0, bool SYM = false, bool HALO = false, bool UNI = false>
 __global__ void __launch_bounds__(Tile<TY>::NT, 1)
 k_fused(const __grid_constant__ Launch<T, MAXI> L)
 {
@@ -266,7 +270,7 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
                 if (interior) *optr = g;
             } else {
                 const T u0 = us[(kz & (NBUF - 1)) * PLANE + uc] + cin;
-                const T v = fma_(-in.tau, g, u0);
+                const T v = fma_(UNI ? -L.tau0 : -in.tau, g, u0);
                 if (interior) *optr = v;
                 su += interior ? u0 : T(0);
                 sout += interior ? v : T(0);
@@ -318,13 +322,14 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
             Cot<T> ctv;
             const Coef<T>& CC = [&]() -> const Coef<T>& {
                 if constexpr (EXT) return Cv;
+                else if constexpr (UNI) return L.C0;
                 else return in.C;
             }();
             // re-evaluation of D from the exact float inputs (float path only):
             // double-float for eq. Meps, FP64 for the projected form
             auto refine = [&]() -> T {
                 if constexpr (EXT == 2) return discriminant_fp64_proj_at<T>(in.C.R, pm, p0, pp, UXP);
-                else return discriminant_df_at<T>(in.C.R, in.C.well, pm, p0, pp, UXP, cind);
+                else return discriminant_df_at<T>(CC.R, CC.well, pm, p0, pp, UXP, cind);
             };
             if constexpr (MODE == MODE_ENERGY) {
                 const T e = voxel_eval<T, false, EXT != 0, EXT == 2, SYM>(CC, u0 + cin, dx, dy, dz, hxx, hyy, hzz, hxy, hxz, hyz, ctv, refine);
@@ -385,20 +390,24 @@ size_t fused_smem_bytes(int elem_size, int tile_y);
 
 // One launch of k_fused (sets the dynamic shared-memory limit once per
 // instantiation; idempotent, so a race between threads is harmless).
-template <typename T, int TY, int MODE, int MAXI, int EXT = 0, bool SYM = false, bool HALO = false>
+template <typename T, int TY, int MODE, int MAXI, int EXT = 0, bool SYM = false, bool HALO = false, bool UNI = false>
 static cudaError_t launch_kernel(const Launch<T, MAXI>& L, int blocks, cudaStream_t s)
 {
     const size_t smem = fused_smem_bytes(sizeof(T), TY);
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused<T, TY, MODE, MAXI, EXT, SYM, HALO>,
+        cudaError_t e = cudaFuncSetAttribute(k_fused<T, TY, MODE, MAXI, EXT, SYM, HALO, UNI>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    k_fused<T, TY, MODE, MAXI, EXT, SYM, HALO><<<blocks, Tile<TY>::NT, smem, s>>>(L);
+    k_fused<T, TY, MODE, MAXI, EXT, SYM, HALO, UNI><<<blocks, Tile<TY>::NT, smem, s>>>(L);
     return cudaGetLastError();
 }
+
+// Batched launches whose problems share L.C0 and L.tau0 (pfc_fused_uni.cu);
+// sym: the SYM instantiation.
+cudaError_t launch_fused_uni(const Launch<float, BATCH_MAX>& L, int tile_y, int mode, bool sym, cudaStream_t s);
 
 // Split the launch's work units evenly over G CTAs and record, per problem,
 // the first CTA that holds a partial of it and how many do.

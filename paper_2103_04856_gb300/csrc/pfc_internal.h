@@ -102,6 +102,11 @@ struct Launch {
     int n;
     int grid;            // G
     long long units;     // W
+    // launches whose problems share one coefficient set and step size
+    // (k_fused<..., UNI = true>) read them here, at a fixed offset of the
+    // constant bank, instead of from inst[k] at a run-time index
+    Coef<T> C0;
+    T tau0;
     Inst<T> inst[MAXI];
 };
 
