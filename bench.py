@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the other_workloads lines")
     ap.add_argument("--only", default=None,
                     choices=["alg1_flow_100", "alg1_batch_100", "extended_sweep_128", "alg1_spatialized",
-                             "diagnostics_512"],
+                             "diagnostics_512", "batch64_mixed"],
                     help="run just this one of the other workloads and print its line (for profiling)")
     return ap.parse_args()
 
@@ -456,9 +456,19 @@ def batch64_block(pfc, I, steps, ws, rank):
     traces = slab.gather_traces({k: tr[j] for j, k in enumerate(mine)}, len(insts))
     vox = sum(sizes)
     out = {"workload": f"batch64_mixed: 64 instances of 64^3/96^3/128^3 ({vox} voxels), random p, {steps} steps",
-           "value": vox * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "ranks": ws,
-           "partition": "by voxels, largest first (paper_2103_04856_gb300.slab.partition_instances)"}
+           "unit": UNIT, "ms_per_step": ms / steps, "ranks": ws,
+           "partition": "by voxels, largest first (paper_2103_04856_gb300.slab.partition_instances)",
+           "value_all_instances": vox * steps / (ms * 1e-3)}
     if traces is not None:
+        # an instance whose scalars turned non-finite is retired (its later
+        # steps only store NaN): count the voxel-steps evaluated, up to and
+        # including each instance's first non-finite step
+        evaluated = 0
+        for t, n in zip(traces, sizes):
+            bad = np.flatnonzero(~np.all(np.isfinite(t), axis=1))
+            evaluated += n * (steps if bad.size == 0 else int(bad[0]) + 1)
+        out["value"] = evaluated / (ms * 1e-3)
+        out["voxel_steps_evaluated"] = evaluated
         out["finite_instances"] = int(sum(bool(np.all(np.isfinite(t))) for t in traces))
     return out
 
@@ -711,7 +721,8 @@ def main():
                "alg1_batch_100": lambda: alg1_batch_workload(pfc, I, 16, steps=args.steps),
                "extended_sweep_128": lambda: extended_sweep_workload(pfc, I, steps=args.steps),
                "alg1_spatialized": lambda: spatialized_flow_workload(pfc, I, steps=args.steps),
-               "diagnostics_512": lambda: diagnostics_workload(pfc, I)}[args.only]
+               "diagnostics_512": lambda: diagnostics_workload(pfc, I),
+               "batch64_mixed": lambda: batch64_block(pfc, I, 500, ws, rank)}[args.only]
         print(json.dumps({"only": args.only, **run()}), flush=True)
         return 0
 

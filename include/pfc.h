@@ -93,7 +93,8 @@ typedef struct {
  * M)^2).  Where that error is more than 2^-6 of max(|D|, xi) and the sqrt(D+)
  * terms carry weight (c3 Tr M + c5 |grad u| != 0), the sweep recomputes D from
  * the exact stencil inputs in double-float arithmetic (pairs of floats, about
- * 44 bits; FP64 for the projected M) (Sec. 3.1 invariants).  This flag turns
+ * 44 bits; FP64 for the projected M) (Sec. 3.1 invariants); a non-finite D
+ * (invariants that overflowed FP32) is left as it is.  This flag turns
  * that refinement off (for measuring what it changes); it has no effect on
  * FP64 problems or on polynomials symmetric in kappa1, kappa2. */
 #define PFC_FLAG_NO_DISCRIMINANT_REFINEMENT 1u
@@ -240,8 +241,11 @@ void pfc_batch_destroy(pfc_batch* batch);
  * doubles, instance-major.  Synchronises.  PFC_ENONFINITE if any instance
  * produced a non-finite scalar; the others are still advanced, while such an
  * instance is retired for the rest of the call (it is not evaluated again:
- * its field is filled with NaN and its later trace rows are NaN).  The same
- * holds within a chain of pfc_batch_step_lazy calls. */
+ * its field is filled with NaN and its later trace rows are NaN).  The steps
+ * run in chunks of 16 launches; after each chunk the host reads the
+ * instances' flags and the retired ones leave the launches, so that the
+ * others' work is spread over all SMs again.  Retirement also holds within a
+ * chain of pfc_batch_step_lazy calls (without leaving the launches). */
 pfc_status pfc_batch_run(pfc_batch* batch, void* const* u, int32_t nsteps, const double* tau,
                          double* trace_host, pfc_stream stream);
 

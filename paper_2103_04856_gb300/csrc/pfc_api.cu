@@ -921,47 +921,95 @@ extern "C" pfc_status pfc_batch_run(pfc_batch* b, void* const* u, int32_t nsteps
     }
     b->lazy = 0;
     PFC_CU(cudaMemsetAsync(b->scal, 0, (sizeof(double) * NSCAL + sizeof(unsigned) * NINTS) * b->n, s));
+    // The loop runs in chunks of G steps.  After each chunk the host reads
+    // the instances' flags, and the instances whose scalars became non-finite
+    // leave the launches: the persistent schedule splits a launch's units
+    // evenly over the CTAs, so a retired instance left in it (its runs only
+    // store NaN) would leave its CTAs idle while the others work.  A dropped
+    // instance's two field buffers are filled with NaN, its later trace rows
+    // too.  A chunk runs from a CUDA graph of G launches when one was
+    // captured for the same instances; otherwise it is launched directly and
+    // the graph is captured while the GPU runs it, for the chunks after.
+    std::vector<int> live;
+    for (int k = 0; k < b->n; ++k) live.push_back(k);
+    std::vector<int> dropped_at(b->n, -1);
+    std::vector<Inst<float>> evl(ev), odl(od);
     auto steps = [&](int i0, int cnt, cudaStream_t st) -> cudaError_t {
+        if (live.empty()) return cudaSuccess;
         for (int i = i0; i < i0 + cnt; ++i) {
-            cudaError_t e = launch_fused_batch((i % 2) == 0 ? ev.data() : od.data(), b->n, b->tile_y, b->max_run, st);
+            cudaError_t e = launch_fused_batch((i % 2) == 0 ? evl.data() : odl.data(), (int)live.size(), b->tile_y,
+                                               b->max_run, st);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
     };
-    const int G = nsteps >= 64 ? 64 : (nsteps & ~1);
+    constexpr int kChunk = 16;
+    const int G = nsteps >= kChunk ? kChunk : (nsteps & ~1);
+    std::vector<unsigned> ints((size_t)NINTS * b->n);
+    int done = 0;
     if (G >= 2) {
-        // the descriptors are kernel parameters: the graph depends on the fields and steps
-        std::vector<void*> key(u, u + b->n);
-        std::vector<double> tkey(tau, tau + b->n);
-        if (!(b->gexec && b->g_len == G && b->g_trace == b->trace && b->g_u == key && b->g_tau == tkey)) {
-            if (b->gexec) {
-                cudaGraphExecDestroy(b->gexec);
-                b->gexec = nullptr;
+        const std::vector<double> tkey(tau, tau + b->n);
+        while (!live.empty() && done + G <= nsteps) {
+            // the descriptors are kernel parameters: a graph holds the
+            // fields, the step sizes and the instances still advanced
+            std::vector<void*> key(u, u + b->n);
+            for (int k = 0; k < b->n; ++k)
+                if (dropped_at[k] >= 0) key[k] = nullptr;
+            if (b->gexec && b->g_len == G && b->g_trace == b->trace && b->g_u == key && b->g_tau == tkey) {
+                PFC_CU(cudaGraphLaunch(b->gexec, s));
+            } else {
+                PFC_CU(steps(done, G, s));
+                if (b->gexec) {
+                    cudaGraphExecDestroy(b->gexec);
+                    b->gexec = nullptr;
+                }
+                cudaGraph_t graph = nullptr;
+                PFC_CU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+                cudaError_t e = steps(0, G, b->cap);
+                cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+                if (e != cudaSuccess || e2 != cudaSuccess) {
+                    if (graph) cudaGraphDestroy(graph);
+                    (void)cudaGetLastError();
+                    return fail(PFC_ECUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+                }
+                e = cudaGraphInstantiate(&b->gexec, graph, 0);
+                cudaGraphDestroy(graph);
+                if (e != cudaSuccess) {
+                    b->gexec = nullptr;
+                    (void)cudaGetLastError();
+                    return fail(PFC_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+                }
+                b->g_len = G;
+                b->g_trace = b->trace;
+                b->g_u = key;
+                b->g_tau = tkey;
             }
-            cudaGraph_t graph = nullptr;
-            PFC_CU(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = steps(0, G, b->cap);
-            cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
-            if (e != cudaSuccess || e2 != cudaSuccess) {
-                if (graph) cudaGraphDestroy(graph);
-                (void)cudaGetLastError();
-                return fail(PFC_ECUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+            done += G;
+            if (done >= nsteps) break;
+            PFC_CU(cudaMemcpyAsync(ints.data(), b->ints, sizeof(unsigned) * ints.size(), cudaMemcpyDeviceToHost, s));
+            PFC_CU(cudaStreamSynchronize(s));
+            std::vector<int> keep;
+            for (int k : live) {
+                if (ints[(size_t)k * NINTS + I_NONFINITE] == 0) {
+                    keep.push_back(k);
+                    continue;
+                }
+                dropped_at[k] = done;
+                const size_t bytes = sizeof(float) * (size_t)b->P[k].nx * b->P[k].ny * b->P[k].nz;
+                PFC_CU(cudaMemsetAsync(u[k], 0xff, bytes, s));   // all-ones words: NaN
+                PFC_CU(cudaMemsetAsync(b->ping[k], 0xff, bytes, s));
             }
-            e = cudaGraphInstantiate(&b->gexec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (e != cudaSuccess) {
-                b->gexec = nullptr;
-                (void)cudaGetLastError();
-                return fail(PFC_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+            if (keep.size() != live.size()) {
+                live.swap(keep);
+                evl.clear();
+                odl.clear();
+                for (int k : live) {
+                    evl.push_back(ev[k]);
+                    odl.push_back(od[k]);
+                }
             }
-            b->g_len = G;
-            b->g_trace = b->trace;
-            b->g_u = key;
-            b->g_tau = tkey;
         }
-        for (int k = 0; k + G <= nsteps; k += G) PFC_CU(cudaGraphLaunch(b->gexec, s));
     }
-    const int done = G >= 2 ? (nsteps / G) * G : 0;
     PFC_CU(steps(done, nsteps - done, s));
     const bool in_ping = (nsteps % 2) == 1;
     for (int k = 0; k < b->n; ++k) {
@@ -969,17 +1017,22 @@ extern "C" pfc_status pfc_batch_run(pfc_batch* b, void* const* u, int32_t nsteps
         PFC_CU(launch_add_offset<float>((float*)u[k], (const float*)(in_ping ? b->ping[k] : u[k]), N,
                                         b->scal + (size_t)k * NSCAL + S_C, s));
     }
-    std::vector<unsigned> ints((size_t)NINTS * b->n);
     PFC_CU(cudaMemcpyAsync(ints.data(), b->ints, sizeof(unsigned) * ints.size(), cudaMemcpyDeviceToHost, s));
     if (trace_host)
         for (int k = 0; k < b->n; ++k)
             PFC_CU(cudaMemcpyAsync(trace_host + (size_t)k * 5 * nsteps, b->trace + (size_t)k * 5 * b->trace_cap,
                                    sizeof(double) * 5 * (size_t)nsteps, cudaMemcpyDeviceToHost, s));
     PFC_CU(cudaStreamSynchronize(s));
+    if (trace_host)
+        for (int k = 0; k < b->n; ++k)
+            if (dropped_at[k] >= 0)
+                for (size_t i = (size_t)dropped_at[k] * 5; i < (size_t)nsteps * 5; ++i)
+                    trace_host[(size_t)k * 5 * nsteps + i] = NAN;
     int bad = 0;
     for (int k = 0; k < b->n; ++k) {
-        if (ints[(size_t)k * NINTS + I_COUNTER] != (unsigned)nsteps)
-            return fail(PFC_ECUDA, "instance %d: step counter %u != %d", k, ints[(size_t)k * NINTS + I_COUNTER], nsteps);
+        const unsigned want = dropped_at[k] >= 0 ? (unsigned)dropped_at[k] : (unsigned)nsteps;
+        if (ints[(size_t)k * NINTS + I_COUNTER] != want)
+            return fail(PFC_ECUDA, "instance %d: step counter %u != %u", k, ints[(size_t)k * NINTS + I_COUNTER], want);
         bad += ints[(size_t)k * NINTS + I_NONFINITE] != 0;
     }
     if (bad) return fail(PFC_ENONFINITE, "%d instance(s) produced non-finite scalars", bad);

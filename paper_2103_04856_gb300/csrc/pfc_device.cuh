@@ -21,6 +21,13 @@ __device__ __forceinline__ float  sqrt_(float x)  { return sqrtf(x); }
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 __device__ __forceinline__ float  fma_(float a, float b, float c)    { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+// max that returns NaN when either operand is NaN (fmaxf drops a NaN operand)
+__device__ __forceinline__ float fmax_nan_(float a, float b) {
+    float r;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ double fmax_nan_(double a, double b) { return (a != a || b != b) ? a + b : fmax(a, b); }
 
 // Smooth positive part P(D) = xi log(1 + exp(D/xi)) of Sec. 4.1 and its
 // derivative P'(D) = logistic(D/xi).
@@ -286,7 +293,9 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
         T D = fma_(T(2), S, -t2) - t2e;
         if (sizeof(T) == 4 && refines<Refine>::value) {
             const T scale = fma_(T(2), S, t2);
-            if (a3 != T(0) && scale > C.rthr * fmax(fabs(D), C.xi)) D = (T)refine();
+            // a non-finite D comes from invariants that overflowed FP32, which the
+            // refinement cannot recover: the NaN-propagating max keeps it out
+            if (a3 != T(0) && scale > C.rthr * fmax_nan_(fabs(D), C.xi)) D = (T)refine();
         }
         T P;
         softplus_(D, C, P, Pp);

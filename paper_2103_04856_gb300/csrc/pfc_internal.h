@@ -52,8 +52,9 @@ struct Coef {
     // the weight c3 T + c5 q of the sqrt(D+) terms is exactly zero
     int sym;
     // FP32 voxels whose D = 2S - T^2 may have lost its accuracy to
-    // cancellation recompute it in FP64 where 2S + T^2 > rthr max(|D|, xi)
-    // (voxel_eval): rthr = 2^16, or infinity to never refine
+    // cancellation recompute it (double-float; FP64 for the projected M)
+    // where 2S + T^2 > rthr max(|D|, xi) and D is finite (voxel_eval):
+    // rthr = 2^16, or infinity to never refine
     T rthr;
 };
 
