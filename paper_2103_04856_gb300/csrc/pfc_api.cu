@@ -113,11 +113,34 @@ static pfc_status check_problem(const pfc_problem* p)
     return PFC_OK;
 }
 
+// Automatic tile height of problems sharing one launch shape (one problem,
+// or all instances of a batch): FP64 8 rows; FP32 the one of 16 and 13 rows
+// with the smaller cost, the rows padded to whole tiles (summed over the
+// problems' x-z planes) times the measured cost of a row.  In the symmetric
+// sweep a 13-row tile's row costs 3.5 % more (four 128^3 problems: 104.3 us
+// at 16 rows, 109.5 us at 13, padded to 130 rows); the general 16-row sweep
+// (20 warps at 96 registers) spills, and there the 16-row tile's row costs
+// 4 % more (a 256^3 problem: 274.2 us at 16 rows, 267.3 us at 13, padded to
+// 260 rows).
+static int auto_tile_y(const pfc_problem* p, int n)
+{
+    if (p[0].prec == PFC_FP64) return 8;
+    bool general = false;
+    double rows16 = 0.0, rows13 = 0.0;
+    for (int k = 0; k < n; ++k) {
+        const double plane = (double)p[k].nx * p[k].nz;
+        rows16 += plane * ((p[k].ny + 15) / 16 * 16);
+        rows13 += plane * ((p[k].ny + 12) / 13 * 13);
+        general = general || !make_coef<float>(p[k].a, p[k].h, p[k].eps, p[k].xi, p[k].well).sym;
+    }
+    return rows13 * (general ? 1.0 : 1.035) < rows16 * (general ? 1.04 : 1.0) ? 13 : 16;
+}
+
 // Launch geometry of one problem: 32 x tile_y columns per CTA, z chunks chosen
 // so that the grid fills the GPU about twice unless the user fixed tile_z.
 static void geometry(const pfc_problem* p, int sms, int* tile_y, int* zc, int* tx, int* ty, int* cz)
 {
-    int tyv = p->tile_y ? p->tile_y : default_tile_y(p->ny, p->prec == PFC_FP64);
+    int tyv = p->tile_y ? p->tile_y : auto_tile_y(p, 1);
     *tile_y = tyv;
     *tx = (p->nx + 31) / 32;
     *ty = (p->ny + tyv - 1) / tyv;
@@ -824,7 +847,7 @@ extern "C" pfc_status pfc_batch_create(const pfc_problem* probs, int32_t n, pfc_
     b->host.resize(n);
     b->ping.assign(n, nullptr);
     bool ok = true;
-    b->tile_y = probs[0].tile_y ? probs[0].tile_y : 16;   // one height for all instances
+    b->tile_y = probs[0].tile_y ? probs[0].tile_y : auto_tile_y(probs, n);   // one height for all instances
     b->max_run = probs[0].tile_z;
     long long units = 0;
     for (int k = 0; k < n && ok; ++k) {
