@@ -667,11 +667,31 @@ def diagnostics_workload(pfc, I):
     ctx = pfc.Context(pfc.Problem.from_shape(inst.shape, eps=inst.eps, a=inst.a, prec="fp32"))
     res = {}
     ms = _timed(lambda: res.update(ctx.diagnostics(u)), 10)
+    # the kernel alone: back-to-back launches writing to device memory
+    # (pfc_diagnostics_dev), CUDA events on the launching stream; the 537 MB
+    # field is 4x the L2
+    out = torch.empty(5, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        ctx.diagnostics_dev(u, out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 20
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(n):
+        ctx.diagnostics_dev(u, out)
+    e1.record()
+    e1.synchronize()
+    ms_k = e0.elapsed_time(e1) / n
     ctx.close()
     peaks, kind = load_peaks()
     gbs = 4.0 * u.numel() / (ms * 1e-3) / 1e9
-    return {"workload": "viability diagnostics of a 512^3 FP32 noise field", "ms_per_call_incl_sync": ms,
-            "GBps_of_4B_per_voxel": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"], "hbm_peak_kind": kind,
+    gbs_k = 4.0 * u.numel() / (ms_k * 1e-3) / 1e9
+    return {"workload": "viability diagnostics of a 512^3 FP32 noise field", "kernel": "k_diag_rows<2,4,well>",
+            "ms_per_launch": ms_k, "GBps_of_4B_per_voxel": gbs_k, "frac_of_hbm": gbs_k / peaks["hbm_gbs"],
+            "hbm_peak_kind": kind, "ms_per_call_incl_sync": ms, "GBps_incl_sync": gbs,
+            "same_values": bool(np.allclose(out.cpu().numpy(), [res[k] for k in ("discrepancy", "cahn_hilliard",
+                                                                                 "ratio", "max", "min")],
+                                            rtol=0, atol=0)),
             "ratio": res["ratio"]}
 
 

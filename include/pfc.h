@@ -150,6 +150,11 @@ pfc_status pfc_set_coefficient_field(pfc_ctx* ctx, const void* a_field, pfc_stre
  * viable when the ratio is below 0.75 and max u > 0.1 > -0.1 > min u (wells
  * -1 and 1).  Synchronises the stream. */
 pfc_status pfc_diagnostics(pfc_ctx* ctx, const void* u, double out_host[5], pfc_stream stream);
+/* The same five values written to out_dev (device memory, 5 doubles):
+ * enqueue only, one launch (for pipelines and CUDA graphs).  Calls of
+ * pfc_diagnostics and pfc_diagnostics_dev on one context share its scratch:
+ * issue them on one stream. */
+pfc_status pfc_diagnostics_dev(pfc_ctx* ctx, const void* u, double* out_dev, pfc_stream stream);
 
 /* Cells of the curvature diagram (Sec. 4.1, eq. curva_diagram): the surface
  * {u = level} (0 for the paper's wells -1/1, 0.5 for wells 0/1) triangulated

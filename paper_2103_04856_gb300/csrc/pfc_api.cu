@@ -529,6 +529,27 @@ extern "C" pfc_status pfc_set_coefficient_field(pfc_ctx* c, const void* a_field,
     return PFC_OK;
 }
 
+// One diagnostics launch writing its five values to out (device; null: the
+// context's own five doubles).
+static pfc_status diagnostics_launch(pfc_ctx* c, const void* u, double* out, cudaStream_t s)
+{
+    if (!c->dpart) {
+        PFC_CU(cudaMalloc((void**)&c->dpart, sizeof(double) * 4 * (size_t)diag_blocks(c->P.nx, c->P.ny, c->P.nz)));
+        PFC_CU(cudaMalloc((void**)&c->dticket, sizeof(unsigned)));
+        PFC_CU(cudaMalloc((void**)&c->dout, sizeof(double) * 5));
+        PFC_CU(cudaMemset(c->dticket, 0, sizeof(unsigned)));
+    }
+    const pfc_problem& P = c->P;
+    if (!out) out = c->dout;
+    if (P.prec == PFC_FP64)
+        PFC_CU(launch_diagnostics<double>((const double*)u, P.nx, P.ny, P.nz, P.h, P.eps, P.well, c->dpart,
+                                          c->dticket, out, s));
+    else
+        PFC_CU(launch_diagnostics<float>((const float*)u, P.nx, P.ny, P.nz, P.h, P.eps, P.well, c->dpart,
+                                         c->dticket, out, s));
+    return PFC_OK;
+}
+
 extern "C" pfc_status pfc_diagnostics(pfc_ctx* c, const void* u, double out_host[5], pfc_stream stream)
 {
     NvtxRange nvtx_("pfc_diagnostics");
@@ -536,23 +557,22 @@ extern "C" pfc_status pfc_diagnostics(pfc_ctx* c, const void* u, double out_host
     if (!out_host) return fail(PFC_EINVAL, "out_host is NULL");
     pfc_status st = check_dev_ptr(c, u, "u");
     if (st) return st;
-    if (!c->dpart) {
-        PFC_CU(cudaMalloc((void**)&c->dpart, sizeof(double) * 4 * (size_t)diag_blocks(c->P.nx, c->P.ny, c->P.nz)));
-        PFC_CU(cudaMalloc((void**)&c->dticket, sizeof(unsigned)));
-        PFC_CU(cudaMalloc((void**)&c->dout, sizeof(double) * 5));
-        PFC_CU(cudaMemset(c->dticket, 0, sizeof(unsigned)));
-    }
     cudaStream_t s = (cudaStream_t)stream;
-    const pfc_problem& P = c->P;
-    if (P.prec == PFC_FP64)
-        PFC_CU(launch_diagnostics<double>((const double*)u, P.nx, P.ny, P.nz, P.h, P.eps, P.well, c->dpart,
-                                          c->dticket, c->dout, s));
-    else
-        PFC_CU(launch_diagnostics<float>((const float*)u, P.nx, P.ny, P.nz, P.h, P.eps, P.well, c->dpart,
-                                         c->dticket, c->dout, s));
+    if ((st = diagnostics_launch(c, u, nullptr, s))) return st;
     PFC_CU(cudaMemcpyAsync(out_host, c->dout, sizeof(double) * 5, cudaMemcpyDeviceToHost, s));
     PFC_CU(cudaStreamSynchronize(s));
     return PFC_OK;
+}
+
+extern "C" pfc_status pfc_diagnostics_dev(pfc_ctx* c, const void* u, double* out_dev, pfc_stream stream)
+{
+    NvtxRange nvtx_("pfc_diagnostics_dev");
+    if (!c) return fail(PFC_EINVAL, "context is NULL");
+    pfc_status st = check_dev_ptr(c, u, "u");
+    if (st) return st;
+    if (!out_dev || !on_device(out_dev, c->device))
+        return fail(PFC_EINVAL, "out_dev is not device memory of the context's device");
+    return diagnostics_launch(c, u, out_dev, (cudaStream_t)stream);
 }
 
 extern "C" pfc_status pfc_surface_cells(pfc_ctx* c, const void* u, double level, void* cells, int64_t cap,

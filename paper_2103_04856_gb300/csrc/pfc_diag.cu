@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const T* __restrict__ u, 
     diag_finish((double)sd, (double)sc, (double)umax, (double)umin, nblocks, bid, h3, part, ticket, out);
 }
 
-// FP32 rows of a multiple of 4 voxels on a 16-byte aligned field: each
+// FP32 rows of a multiple of 4 voxels on a 16-byte aligned field of 2^31
+// voxels or more (64-bit offsets; smaller grids take k_diag_rows): each
 // thread owns 4 consecutive x voxels (one float4), a warp 128 voxels of a
 // row, a block (32 x 8 threads) a tile of 128 x 8 columns.  Persistent grid:
 // block b walks the work items b, b + gridDim.x, ... (a tile over a chunk of
@@ -220,6 +221,134 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag4(const float* __restrict_
     diag_finish((double)sd, (double)sc, (double)umax, (double)umin, gridDim.x, blockIdx.x, h3, part, ticket, out);
 }
 
+// The FP32 kernel for grids of fewer than 2^31 voxels (rows of a multiple of
+// 4 voxels, 16-byte aligned field).  Each thread owns one float4 of x
+// columns in R consecutive rows, a block (32 x 8 threads) a tile of 128 x 8R
+// columns; persistent grid over work items (a tile over a chunk of zc
+// planes).  The thread marches up z keeping u(z-1) and u(z) of its rows in
+// registers and issues the loads of KB planes together: its rows' float4 at
+// z+1 (from HBM), the rows below and above its own at z (L1/L2), one voxel
+// beyond a warp's edge for the edge lanes; the x neighbours inside the warp
+// come by shuffles, the y neighbours between its rows from its own
+// registers.  Per load one address instruction (32-bit plane offsets, one
+// base pointer per row).  The per-voxel terms are scaled by 1/ks (ks = eps /
+// 8h^2), the sums by ks at the end, and the double well is a template
+// parameter: about 14 arithmetic instructions per voxel.
+template <int WELL>
+__device__ __forceinline__ void diag_terms_k(float dx, float dy, float dz, float u0, float wk, float& d, float& c)
+{
+    const float g2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float q = WELL == 0 ? fmaf(-u0, u0, u0) : fmaf(-u0, u0, 1.f);
+    const float qw = q * wk;
+    const float e = fmaf(-qw, q, g2);
+    d = fabsf(e);
+    c = fmaf(qw, q, g2);
+}
+
+template <int R, int KB, int WELL>
+__global__ void __launch_bounds__(kDiagThreads) k_diag_rows(const float* __restrict__ u, int nx, int ny, int nz,
+                                                            int zc, int tiles_x, int chunks, float wk, float ks,
+                                                            double h3, double* part, unsigned* ticket, double* out)
+{
+    static_assert(R >= 1 && R <= 4, "one to four rows per thread");
+    const int pls = nx * ny;   // fewer than 2^31 voxels in all
+    const int lx = threadIdx.x;
+    float sd = 0.f, sc = 0.f, umax = -INFINITY, umin = INFINITY;
+    const int items = tiles_x * ((ny + kDY * R - 1) / (kDY * R)) * chunks;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int ch = it % chunks, t = it / chunks;
+        const int x4 = (t % tiles_x) * (4 * kDX) + 4 * lx, yb = (t / tiles_x) * (kDY * R) + R * threadIdx.y;
+        const int z0 = ch * zc, z1 = min(nz, z0 + zc);
+        // lanes and rows past a ragged edge count nothing.  A lane past the
+        // row's end works on the columns x4 modulo nx, so that the lane
+        // before it finds its right neighbour there; a row past the edge
+        // reads the upper neighbour of the row before it instead, which that
+        // row then takes as its own
+        const int xq = x4 < nx ? x4 : x4 % nx, y0 = min(yb, ny - 1);
+        bool live[R];
+        int yr[R];
+        yr[0] = y0;
+        live[0] = x4 < nx && yb < ny;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            yr[r] = yb + r < ny ? yb + r : nbr(yr[r - 1], 1, ny);
+            live[r] = x4 < nx && yb + r < ny;
+        }
+        const float* prow[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) prow[r] = u + yr[r] * nx + xq;
+        const float* pym = u + nbr(y0, -1, ny) * nx + xq;
+        const float* pyp = u + nbr(yr[R - 1], 1, ny) * nx + xq;
+        // x neighbours: lane - 1 holds the voxel left of x4, lane + 1 the one
+        // right of x4 + 3 (periodic, through the wrapped columns); lanes 0
+        // and 31 load the one beyond the warp's edge
+        const bool need = lx == 0 || lx == kDX - 1;
+        const int eoff = lx == 0 ? nbr(xq, -1, nx) - xq : nbr(xq + 3, 1, nx) - xq;
+        float4 m[R], c[R];
+        int zo = z0 * pls;
+        {
+            const int om = nbr(z0, -1, nz) * pls;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                m[r] = *reinterpret_cast<const float4*>(prow[r] + om);
+                c[r] = *reinterpret_cast<const float4*>(prow[r] + zo);
+            }
+        }
+        for (int zb = z0; zb < z1; zb += KB) {
+            const int n = min(KB, z1 - zb);   // uniform across the block: the shuffles see full warps
+            float4 up[KB][R], lo[KB], hi[KB];
+            float ev[KB][R];
+#pragma unroll
+            for (int k = 0; k < KB; ++k) {
+                if (k < n) {
+                    const int o = zo + k * pls, on = zb + k + 1 == nz ? 0 : o + pls;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        up[k][r] = *reinterpret_cast<const float4*>(prow[r] + on);
+                        ev[k][r] = need ? prow[r][o + eoff] : 0.f;
+                    }
+                    lo[k] = *reinterpret_cast<const float4*>(pym + o);
+                    hi[k] = *reinterpret_cast<const float4*>(pyp + o);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < KB; ++k) {
+                if (k < n) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float4 a = c[r];
+                        const float4 b = r == 0 ? lo[k] : c[r > 0 ? r - 1 : 0];        // the row below
+                        const float4 t4 = r == R - 1 ? hi[k] : c[r + 1 < R ? r + 1 : r];   // the row above
+                        const float left = __shfl_up_sync(0xffffffffu, a.w, 1);
+                        const float right = __shfl_down_sync(0xffffffffu, a.x, 1);
+                        const float l = lx == 0 ? ev[k][r] : left;
+                        const float rr = lx == kDX - 1 ? ev[k][r] : right;
+                        float d0, c0, d1, c1, d2, c2, d3, c3;
+                        diag_terms_k<WELL>(a.y - l, t4.x - b.x, up[k][r].x - m[r].x, a.x, wk, d0, c0);
+                        diag_terms_k<WELL>(a.z - a.x, t4.y - b.y, up[k][r].y - m[r].y, a.y, wk, d1, c1);
+                        diag_terms_k<WELL>(a.w - a.y, t4.z - b.z, up[k][r].z - m[r].z, a.z, wk, d2, c2);
+                        diag_terms_k<WELL>(rr - a.z, t4.w - b.w, up[k][r].w - m[r].w, a.w, wk, d3, c3);
+                        if (live[r]) {
+                            sd += (d0 + d1) + (d2 + d3);
+                            sc += (c0 + c1) + (c2 + c3);
+                            umax = fmaxf(umax, fmaxf(fmaxf(a.x, a.y), fmaxf(a.z, a.w)));
+                            umin = fminf(umin, fminf(fminf(a.x, a.y), fminf(a.z, a.w)));
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        m[r] = c[r];
+                        c[r] = up[k][r];
+                    }
+                }
+            }
+            zo += n * pls;
+        }
+    }
+    diag_finish((double)sd * ks, (double)sc * ks, (double)umax, (double)umin, gridDim.x, blockIdx.x, h3, part,
+                ticket, out);
+}
+
 }  // namespace
 
 // The scalar kernel's grid: (x, y) tiles times z chunks, about 4 waves of 8
@@ -272,12 +401,62 @@ static Diag4Geom diag4_geom(int nx, int ny, int nz)
     return g;
 }
 
+// The row kernel: two rows per thread, four planes of loads issued together
+// (k_diag_rows<kRows, kPlanes, well>: 121 registers, two blocks per SM);
+// grids of fewer than 2^31 voxels.  Measured on a 512^3 field: 131 us
+// (4.1 TB/s); one row and four planes 255 us (spills at three blocks per
+// SM), two rows and two planes 170 us, four rows and two planes 135 us.
+// Staging the planes in a shared-memory ring with cp.async (no registers
+// held by loads) hid the latency but issued 20 % more instructions: 144 us.
+// Packed FP32 (FFMA2) pairs of voxels: 135-172 us (the pairs of x
+// differences need register moves).
+constexpr int kRows = 2, kPlanes = 4;
+template <int WELL>
+static int diag_rows_blocks_per_sm()
+{
+    static int cached = 0;
+    if (!cached) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_diag_rows<kRows, kPlanes, WELL>, kDiagThreads, 0) !=
+                cudaSuccess ||
+            n < 1) {
+            (void)cudaGetLastError();
+            n = 2;
+        }
+        cached = n;
+    }
+    return cached;
+}
+static bool diag_rows_fits(int nx, int ny, int nz) { return (long long)nx * ny * nz < (1LL << 31); }
+static Diag4Geom diag_rows_geom(int nx, int ny, int nz, int well)
+{
+    Diag4Geom g;
+    g.tiles_x = (nx + 4 * kDX - 1) / (4 * kDX);
+    g.tiles_y = (ny + kDY * kRows - 1) / (kDY * kRows);
+    const long tiles = (long)g.tiles_x * g.tiles_y;
+    const long wave = (long)(well == 0 ? diag_rows_blocks_per_sm<0>() : diag_rows_blocks_per_sm<1>()) * device_sms();
+    long chunks = (nz + 31) / 32;
+    if (tiles * chunks < 8 * wave) chunks = (8 * wave + tiles - 1) / tiles;
+    if (chunks > nz) chunks = nz;
+    g.zc = (int)((nz + chunks - 1) / chunks);
+    g.chunks = (nz + g.zc - 1) / g.zc;
+    const long items = tiles * g.chunks;
+    g.blocks = (int)(items < wave ? items : wave);
+    return g;
+}
+
 long diag_blocks(int nx, int ny, int nz)
 {
     int zc;
     const dim3 g = diag_grid(nx, ny, nz, &zc);
-    const long a = (long)g.x * g.y * g.z, b = diag4_geom(nx, ny, nz).blocks;
-    return a > b ? a : b;
+    long a = (long)g.x * g.y * g.z;
+    const long b = diag4_geom(nx, ny, nz).blocks;
+    if (b > a) a = b;
+    for (int well = 0; well < 2; ++well) {
+        const long c = diag_rows_geom(nx, ny, nz, well).blocks;
+        if (c > a) a = c;
+    }
+    return a;
 }
 
 template <typename T>
@@ -285,6 +464,17 @@ cudaError_t launch_diagnostics(const T* u, int nx, int ny, int nz, double h, dou
                                unsigned* ticket, double* out, cudaStream_t s)
 {
     const double ks = eps / (8.0 * h * h), wq = well == 0 ? 1.0 / eps : 0.25 / eps;
+    if (sizeof(T) == 4 && nx % 4 == 0 && ((uintptr_t)u) % 16 == 0 && diag_rows_fits(nx, ny, nz)) {
+        const Diag4Geom g = diag_rows_geom(nx, ny, nz, well);
+        const float wk = (float)(wq / ks);
+        if (well == 0)
+            k_diag_rows<kRows, kPlanes, 0><<<g.blocks, dim3(kDX, kDY), 0, s>>>(
+                (const float*)u, nx, ny, nz, g.zc, g.tiles_x, g.chunks, wk, (float)ks, h * h * h, part, ticket, out);
+        else
+            k_diag_rows<kRows, kPlanes, 1><<<g.blocks, dim3(kDX, kDY), 0, s>>>(
+                (const float*)u, nx, ny, nz, g.zc, g.tiles_x, g.chunks, wk, (float)ks, h * h * h, part, ticket, out);
+        return cudaGetLastError();
+    }
     if (sizeof(T) == 4 && nx % 4 == 0 && ((uintptr_t)u) % 16 == 0) {
         const Diag4Geom g = diag4_geom(nx, ny, nz);
         k_diag4<<<g.blocks, dim3(kDX, kDY), 0, s>>>((const float*)u, nx, ny, nz, g.zc, g.tiles_x, g.tiles_y,

@@ -41,7 +41,7 @@ EXPORTED = ("pfc_create", "pfc_destroy", "pfc_energy", "pfc_energy_and_grad", "p
             "pfc_curvature_histogram", "pfc_batch_step_host", "pfc_batch_host_wait", "pfc_hflow_batch_create",
             "pfc_hflow_batch_destroy", "pfc_hflow_batch_field", "pfc_hflow_batch_run", "pfc_batch_step_lazy",
             "pfc_batch_lazy_finish", "pfc_slab_create", "pfc_slab_destroy", "pfc_slab_sweep", "pfc_slab_finish",
-            "pfc_slab_apply_offset", "pfc_measure_fp32_peak")
+            "pfc_slab_apply_offset", "pfc_measure_fp32_peak", "pfc_diagnostics_dev")
 SLAB_ENERGY, SLAB_GRAD, SLAB_STEP = 0, 1, 2
 SLAB_NSUMS = 8
 
@@ -178,6 +178,7 @@ def load_library():
             "pfc_b_to_a": ([dp, dp], ctypes.c_int),
             "pfc_set_coefficient_field": ([vp, vp, vp], ctypes.c_int),
             "pfc_diagnostics": ([vp, vp, dp, vp], ctypes.c_int),
+            "pfc_diagnostics_dev": ([vp, vp, vp, vp], ctypes.c_int),
             "pfc_hflow_set_coefficient_field": ([vp, vp, vp], ctypes.c_int),
             "pfc_hflow_set_mass_field": ([vp, vp, vp], ctypes.c_int),
             "pfc_surface_cells": ([vp, vp, ctypes.c_double, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), vp],
@@ -342,6 +343,16 @@ class Context:
                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)))
         return {"discrepancy": float(out[0]), "cahn_hilliard": float(out[1]), "ratio": float(out[2]),
                 "max": float(out[3]), "min": float(out[4])}
+
+    def diagnostics_dev(self, u: torch.Tensor, out: torch.Tensor, stream=None) -> torch.Tensor:
+        """The five diagnostics values written into out (a CUDA float64 tensor
+        of 5 elements) without synchronising: discrepancy, Cahn-Hilliard
+        energy, ratio, max u, min u."""
+        if out.dtype != torch.float64 or not out.is_cuda or out.numel() < 5 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous CUDA float64 tensor of 5 elements")
+        _check(self._lib.pfc_diagnostics_dev(self._h, _field(u, self.prob, "u"), ctypes.c_void_p(out.data_ptr()),
+                                             _stream(stream)))
+        return out
 
     def surface_cells(self, u: torch.Tensor, level: float | None = None, stream=None) -> torch.Tensor:
         """Cells (area, kappa1, kappa2) of the curvature diagram of {u = level}

@@ -6,6 +6,7 @@ FP64 on the same state 1e-4 relative energy and 1e-3 relative gradient
 2-norm, as for the plain eq. Feps.  Diagnostics: FP64 1e-12 relative, FP32
 1e-5 relative (sums of positive terms) and exact extremes.
 """
+import ctypes
 import math
 
 import numpy as np
@@ -216,7 +217,8 @@ def test_flow_with_mass_field_fp32(sigma):
 
 # ------------------------------------------------------------ diagnostics
 
-@pytest.mark.parametrize("shape", [(7, 9, 11), (40, 33, 64), (1, 4, 8), (20, 17, 45), (6, 5, 33), (37, 8, 32)])
+@pytest.mark.parametrize("shape", [(7, 9, 11), (40, 33, 64), (1, 4, 8), (20, 17, 45), (6, 5, 33), (37, 8, 32),
+                                   (3, 17, 132), (5, 3, 4), (9, 1, 260)])
 def test_diagnostics_vs_oracle(shape):
     for well in (0, 1):
         u = I.noise(shape, 0.3 if well == 0 else -0.1, 0.2, 15)
@@ -233,6 +235,25 @@ def test_diagnostics_vs_oracle(shape):
         for k in ("discrepancy", "cahn_hilliard", "ratio"):
             assert got[k] == pytest.approx(want[k], rel=1e-5), k
         assert got["max"] == want["max"] and got["min"] == want["min"]
+
+
+def test_diagnostics_dev_matches_host_call():
+    u = I.noise((20, 33, 64), 0.3, 0.2, 5)
+    for prec in ("fp32", "fp64"):
+        ctx = pfc.Context(P(u.shape, (1, 0, 1, 0, 0, 0), eps=1.7, h=0.8, prec=prec))
+        d = dev(u, prec)
+        want = ctx.diagnostics(d)
+        out = torch.full((5,), float("nan"), dtype=torch.float64, device="cuda")
+        got = ctx.diagnostics_dev(d, out).cpu().numpy()
+        assert list(got) == [want[k] for k in ("discrepancy", "cahn_hilliard", "ratio", "max", "min")]
+        with pytest.raises(ValueError):
+            ctx.diagnostics_dev(d, torch.empty(5, dtype=torch.float64))
+        # the library itself rejects a host pointer for out_dev
+        host = np.zeros(5)
+        rc = ctx._lib.pfc_diagnostics_dev(ctx._h, ctypes.c_void_p(d.data_ptr()),
+                                          host.ctypes.data_as(ctypes.c_void_p), None)
+        assert rc != 0 and not host.any()
+        ctx.close()
 
 
 def test_diagnostics_tanh_slab_and_constant():
