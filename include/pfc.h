@@ -70,8 +70,8 @@ typedef struct {
     double eps;             /* interface width > 0 (eq. Meps)                            */
     double xi;              /* regularisation > 0 (Sec. 4.1; 1e-6 in the paper)          */
     double a[6];            /* a20 a11 a02 a10 a01 a00 of eq. F, kappa1 >= kappa2         */
-    int32_t tile_y;         /* 0 = automatic (FP64: 8; FP32: 16 or 13 by padded rows times the measured
-                               cost of a row; a batch: over all instances); else 8, 13 or 16 */
+    int32_t tile_y;         /* 0 = automatic (FP64: 8; FP32: 16 or 13, whichever pads ny less; a batch:
+                               by padded rows of all instances times the measured cost of a row); else 8, 13 or 16 */
     int32_t tile_z;         /* 0 = automatic; else planes per CTA z-chunk (>= 1)         */
     /* Orientation term of Sec. 5.2: eps mu (theta . grad u)^2 joins the
      * integrand (grad u the central-difference gradient).  mu = 0 (with any

@@ -113,15 +113,15 @@ static pfc_status check_problem(const pfc_problem* p)
     return PFC_OK;
 }
 
-// Automatic tile height of problems sharing one launch shape (one problem,
-// or all instances of a batch): FP64 8 rows; FP32 the one of 16 and 13 rows
-// with the smaller cost, the rows padded to whole tiles (summed over the
-// problems' x-z planes) times the measured cost of a row.  In the symmetric
-// sweep a 13-row tile's row costs 3.5 % more (four 128^3 problems: 104.3 us
-// at 16 rows, 109.5 us at 13, padded to 130 rows); the general 16-row sweep
-// (20 warps at 96 registers) spills, and there the 16-row tile's row costs
-// 4 % more (a 256^3 problem: 274.2 us at 16 rows, 267.3 us at 13, padded to
-// 260 rows).
+// Automatic tile height of a batch (its launches run the batched
+// instantiations, MAXI = 64): the one of 16 and 13 rows with the smaller
+// cost, the rows padded to whole tiles (summed over the problems' x-z planes)
+// times the measured cost of a row.  In the symmetric sweep a 13-row tile's
+// row costs 3.5 % more (four 128^3 problems: 104.3 us at 16 rows, 109.5 us at
+// 13, padded to 130 rows); the general batched 16-row sweep (20 warps at 96
+// registers) spills, and there the 16-row tile's row costs 4 % more (a 256^3
+// problem: 274.2 us at 16 rows, 267.3 us at 13, padded to 260 rows).  Single
+// problems (MAXI = 1: no spills at 16 rows) take default_tile_y.
 static int auto_tile_y(const pfc_problem* p, int n)
 {
     if (p[0].prec == PFC_FP64) return 8;
@@ -140,7 +140,7 @@ static int auto_tile_y(const pfc_problem* p, int n)
 // so that the grid fills the GPU about twice unless the user fixed tile_z.
 static void geometry(const pfc_problem* p, int sms, int* tile_y, int* zc, int* tx, int* ty, int* cz)
 {
-    int tyv = p->tile_y ? p->tile_y : auto_tile_y(p, 1);
+    int tyv = p->tile_y ? p->tile_y : default_tile_y(p->ny, p->prec == PFC_FP64);
     *tile_y = tyv;
     *tx = (p->nx + 31) / 32;
     *ty = (p->ny + tyv - 1) / tyv;
