@@ -340,7 +340,11 @@ def membrane_block(pfc, I, flush, steps, peak, peak_kind, with_cpu):
     acc1 = accuracy(pfc, [inst], cur)
     del A, B, cur
     peaks, hk = load_peaks()
-    roof = alu_roofline(workload_flops([inst]), msw, peak, peak_kind, "k_fused<float,16,STEP,64> (general sweep)")
+    # a batch's automatic tile height (pfc_batch_create): 16 or 13 rows by padded rows times the
+    # measured cost of a row (the general 16-row batched sweep's rows cost 4 % more)
+    ny = inst.shape[1]
+    ty = 13 if ((ny + 12) // 13 * 13) < ((ny + 15) // 16 * 16) * 1.04 else 16
+    roof = alu_roofline(workload_flops([inst]), msw, peak, peak_kind, f"k_fused<float,{ty},STEP,64> (general sweep)")
     hbm = 8.0 * vox / (msw * 1e-3) / 1e9
     roof["traffic"] = None
     roof["traffic_note"] = "no ncu capture of this launch (512^3 is above the capture size rule)"
