@@ -35,7 +35,11 @@
 namespace pfc {
 
 constexpr int TX = 32;      // output columns per tile in x
-constexpr int UXP = 40;     // u tile row in shared memory: x0-4 .. x0+35
+constexpr int ULX = 40;     // u tile row loaded into shared memory: x0-4 .. x0+35
+// the row's pitch in shared memory: 44 words, so that a halo-column warp,
+// whose lanes read down a column (a stride of one pitch), meets 8 banks
+// (12 i mod 32) instead of 4 (8 i mod 32 at a pitch of 40)
+constexpr int UXP = 44;
 constexpr int NBUF = 8;     // ring of u planes
 constexpr int PD = 3;       // planes in flight ahead of the plane being consumed
 
@@ -103,7 +107,7 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
     using TL = Tile<TY>;
     constexpr int EX = TL::EX, NEXT = TL::NEXT, NT = TL::NT, UY = TL::UY, PLANE = TL::PLANE;
     constexpr int VEC = 16 / (int)sizeof(T);
-    constexpr int NCH = UXP / VEC;
+    constexpr int NCH = ULX / VEC;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* us = reinterpret_cast<T*>(smem_raw);            // [NBUF][UY][UXP]
     T* fs = us + NBUF * PLANE;                          // [2][5][NEXT]
@@ -210,9 +214,9 @@ k_fused(const __grid_constant__ Launch<T, MAXI> L)
                 if (in.vec) {
                     if (ld_off >= 0) cp_async16(dst + ld_dst, src + ld_off);
                 } else {
-                    for (int i = tid; i < PLANE; i += NT) {
-                        const int r = i / UXP, c = i - (i / UXP) * UXP;
-                        cp_async_elem(dst + i, src + wrapi(y0 - 2 + r, ny) * nx + wrapi(x0 - 4 + c, nx));
+                    for (int i = tid; i < UY * ULX; i += NT) {
+                        const int r = i / ULX, c = i - (i / ULX) * ULX;
+                        cp_async_elem(dst + r * UXP + c, src + wrapi(y0 - 2 + r, ny) * nx + wrapi(x0 - 4 + c, nx));
                     }
                 }
             }
