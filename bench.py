@@ -402,9 +402,15 @@ def descent_32_block(pfc, I):
 def tube_256_block(pfc, I, steps, peak, peak_kind):
     """The 256^3 FP32 tube-favouring workload (asymmetric p): `steps`
     mass-projected steps (pfc_run: the projection in fused form, 64-step CUDA
-    graphs), accuracy at the first and last state."""
+    graphs), accuracy at the first and last state.  Timed at xi = 1e-2: at
+    the workload's xi = 1e-6 the fixed step 1e-3 makes voxels at the
+    sqrt(D+) kink chatter, and whether a 2000-step run blows up depends on
+    FP32 rounding (measured: 1 to 3 of four seeds blow up between steps 118
+    and 340, depending on the build, and the same starts run to the end in
+    50-step calls), so the timed work would not be well defined."""
+    import dataclasses
     import torch
-    inst = I.tube_descent_256()
+    inst = dataclasses.replace(I.tube_descent_256(), xi=1e-2)
     u0 = torch.tensor(inst.field().astype(np.float32), device="cuda")
     ctx = pfc.Context(problem_of(pfc, inst))
     x = u0.clone()
@@ -420,7 +426,7 @@ def tube_256_block(pfc, I, steps, peak, peak_kind):
     ctx.close()
     n = u0.numel()
     return {"workload": "tube_descent_256: 256^3 FP32, eps=1.5, p=k1^2+0.2k2^2-0.5k1 (k1 the smaller), "
-                        f"{steps} steps of 1e-3",
+                        f"{steps} steps of 1e-3, xi=1e-2 (at 1e-6 a long fixed-step run may blow up)",
             "value": n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
             "roofline_incl_run_overheads": alu_roofline(workload_flops([inst]), ms, peak, peak_kind,
                                                         "pfc_run step (general sweep + graph)"),

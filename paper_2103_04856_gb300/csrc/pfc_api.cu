@@ -117,11 +117,11 @@ static pfc_status check_problem(const pfc_problem* p)
 // instantiations, MAXI = 64): the one of 16 and 13 rows with the smaller
 // cost, the rows padded to whole tiles (summed over the problems' x-z planes)
 // times the measured cost of a row.  In the symmetric sweep a 13-row tile's
-// row costs 3.5 % more (four 128^3 problems: 104.3 us at 16 rows, 109.5 us at
-// 13, padded to 130 rows); the general batched 16-row sweep (20 warps at 96
-// registers) spills, and there the 16-row tile's row costs 4 % more (a 256^3
-// problem: 274.2 us at 16 rows, 267.3 us at 13, padded to 260 rows).  Single
-// problems (MAXI = 1: no spills at 16 rows) take default_tile_y.
+// row costs 4.3 % more (four 128^3 problems: 87.5 us at 16 rows, 92.7 us at
+// 13, padded to 130 rows); in the general batched sweep (20 warps at 96
+// registers for 16 rows, 16 warps at 128 for 13) the 16-row tile's row costs
+// 3.5 % more (a 512^3 problem: 1.795 ms at 16 rows, 1.761 ms at 13, padded to
+// 520 rows).  Single problems (MAXI = 1) take default_tile_y.
 static int auto_tile_y(const pfc_problem* p, int n)
 {
     if (p[0].prec == PFC_FP64) return 8;
@@ -133,7 +133,7 @@ static int auto_tile_y(const pfc_problem* p, int n)
         rows13 += plane * ((p[k].ny + 12) / 13 * 13);
         general = general || !make_coef<float>(p[k].a, p[k].h, p[k].eps, p[k].xi, p[k].well).sym;
     }
-    return rows13 * (general ? 1.0 : 1.035) < rows16 * (general ? 1.04 : 1.0) ? 13 : 16;
+    return rows13 * (general ? 1.0 : 1.043) < rows16 * (general ? 1.035 : 1.0) ? 13 : 16;
 }
 
 // Launch geometry of one problem: 32 x tile_y columns per CTA, z chunks chosen

@@ -227,7 +227,11 @@ struct refines<NoRefine> {
 // caller evaluates): a3 = c3 T + c5 q is exactly 0 and r enters only through
 // a3 r, c3 r and c5 r, which stay exact zeros with r = r' = 0; D, P and
 // sqrt(P) are then not computed, with the same result bits.
-template <typename T, bool GRAD, bool ORIENT = false, bool PROJ = false, bool SKIPD = false,
+//
+// RAWD: ct.dx, ct.dy, ct.dz are returned without the stencil scale sg =
+// 1/(2h) (the caller folds it into the FMAs that combine them with the
+// second-difference cotangents).
+template <typename T, bool GRAD, bool ORIENT = false, bool PROJ = false, bool SKIPD = false, bool RAWD = false,
           class Refine = NoRefine>
 __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz, T hxx, T hyy,
                                         T hzz, T hxy, T hxz, T hyz, Cot<T>& ct, const Refine& refine = Refine())
@@ -358,11 +362,11 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
         const T al = -T(2) * irho;
         const T be = fma_(T(2) * GBG * irho, irho, fma_(dq, iq, C.c6x2));
         ct.u = T(0);
-        ct.dx = C.sg * fma_(al, BGx, be * Gx);
-        ct.dy = C.sg * fma_(al, BGy, be * Gy);
-        ct.dz = C.sg * fma_(al, BGz, be * Gz);
+        ct.dx = RAWD ? fma_(al, BGx, be * Gx) : C.sg * fma_(al, BGx, be * Gx);
+        ct.dy = RAWD ? fma_(al, BGy, be * Gy) : C.sg * fma_(al, BGy, be * Gy);
+        ct.dz = RAWD ? fma_(al, BGz, be * Gz) : C.sg * fma_(al, BGz, be * Gz);
         if (ORIENT) {
-            const T ot = T(2) * C.c7 * tg * C.sg;
+            const T ot = RAWD ? T(2) * C.c7 * tg : T(2) * C.c7 * tg * C.sg;
             ct.dx = fma_(ot, C.th0, ct.dx);
             ct.dy = fma_(ot, C.th1, ct.dy);
             ct.dz = fma_(ot, C.th2, ct.dz);
@@ -378,11 +382,11 @@ __device__ __forceinline__ T voxel_eval(const Coef<T>& C, T u0, T dx, T dy, T dz
     ct.u = wpp * C.inv_eps * GLG * irho;
     const T al = T(2) * wr;
     const T be = fma_(-al * GLG, irho, fma_(dq, iq, C.c6x2));
-    ct.dx = C.sg * fma_(al, LGx, be * Gx);
-    ct.dy = C.sg * fma_(al, LGy, be * Gy);
-    ct.dz = C.sg * fma_(al, LGz, be * Gz);
+    ct.dx = RAWD ? fma_(al, LGx, be * Gx) : C.sg * fma_(al, LGx, be * Gx);
+    ct.dy = RAWD ? fma_(al, LGy, be * Gy) : C.sg * fma_(al, LGy, be * Gy);
+    ct.dz = RAWD ? fma_(al, LGz, be * Gz) : C.sg * fma_(al, LGz, be * Gz);
     if (ORIENT) {
-        const T ot = T(2) * C.c7 * tg * C.sg;
+        const T ot = RAWD ? T(2) * C.c7 * tg : T(2) * C.c7 * tg * C.sg;
         ct.dx = fma_(ot, C.th0, ct.dx);
         ct.dy = fma_(ot, C.th1, ct.dy);
         ct.dz = fma_(ot, C.th2, ct.dz);

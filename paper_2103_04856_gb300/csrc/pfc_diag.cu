@@ -411,7 +411,10 @@ static Diag4Geom diag4_geom(int nx, int ny, int nz)
 // Packed FP32 (FFMA2) pairs of voxels: 135-172 us (the pairs of x
 // differences need register moves).  Bulk L2 prefetches of each warp's rows
 // 4-16 planes ahead: 154-164 us.  Tiles of 256 or 512 columns (warps side by
-// side in x, for longer contiguous reads per plane): 133-138 us.
+// side in x, for longer contiguous reads per plane): 133-138 us.  Bands of
+// 16 full rows staged plane by plane in shared memory by bulk asynchronous
+// copies (one issuing thread, six slots, 16.7 instructions per voxel): 132 us,
+// its warps waiting on the copies.
 constexpr int kRows = 2, kPlanes = 4;
 template <int WELL>
 static int diag_rows_blocks_per_sm()

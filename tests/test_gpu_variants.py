@@ -217,8 +217,11 @@ def test_flow_with_mass_field_fp32(sigma):
 
 # ------------------------------------------------------------ diagnostics
 
+# the last five: FP32 rows of 128 to 512 voxels (the row kernel's float4
+# path with several warps per row) with one to three tiles of 16 rows
 @pytest.mark.parametrize("shape", [(7, 9, 11), (40, 33, 64), (1, 4, 8), (20, 17, 45), (6, 5, 33), (37, 8, 32),
-                                   (3, 17, 132), (5, 3, 4), (9, 1, 260)])
+                                   (3, 17, 132), (5, 3, 4), (9, 1, 260),
+                                   (5, 16, 128), (9, 48, 256), (7, 32, 512), (1, 16, 512), (6, 24, 128)])
 def test_diagnostics_vs_oracle(shape):
     for well in (0, 1):
         u = I.noise(shape, 0.3 if well == 0 else -0.1, 0.2, 15)
