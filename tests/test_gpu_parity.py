@@ -188,6 +188,55 @@ def test_fp32_vs_fp64_noise():
         assert np.linalg.norm(g32 - g64) / np.linalg.norm(g64) < 1e-3
 
 
+@pytest.mark.parametrize("a", [(1.0, 0.3, 1.0, 0.2, 0.2, 0.1), (0.7, -0.3, 0.2, 0.5, -0.4, 0.3)],
+                         ids=["symmetric", "general"])
+def test_fp32_run_lengths_tiles_and_modes(a):
+    """The FP32 sweep carries its column's stencil values up the z-march and
+    takes two planes per loop trip (a single-plane trip for an odd rest),
+    with the row and halo warps in separate instantiations: every run length
+    of 1 to 5 planes and the uncapped one (one CTA's run up to the whole
+    column), every tile height (ragged in x and y), energy, energy and
+    gradient, and one step, on the symmetric instantiation (p symmetric in
+    kappa1, kappa2) and the general one, against the FP64 oracle on the same
+    FP32-representable field (energy 1e-4; gradient 1e-3 in 2-norm and 2e-3
+    of max|g| per voxel; the step per voxel within one FP32 rounding of u'
+    plus tau times the gradient's bar) and against each other (run lengths
+    and tile heights change only rounding, where a wrong plane or row would
+    change g by O(max|g|): 1e-4 of max|g| per voxel).  xi = 1e-2 keeps the
+    general polynomial's sqrt(D+) kink wide, so that rounding is not
+    amplified there."""
+    shape = (13, 20, 44)
+    u = I.noise(shape, 0.3, 0.1, 21).astype(np.float32).astype(np.float64)
+    ref = P(shape, a, xi=1e-2)
+    Eo, go = oracle.energy_and_grad(u, oprob(ref))
+    tau = 1e-3
+    uo, _ = oracle.step(u, oprob(ref), tau)
+    gbar = 2e-3 * np.abs(go).max()
+    ud = dev(u, "fp32")
+    first = None
+    for tile_y in (16, 13, 8):
+        for tile_z in (1, 2, 3, 4, 5, 0):
+            p = P(shape, a, prec="fp32", xi=1e-2, tile_y=tile_y, tile_z=tile_z)
+            ctx = pfc.Context(p)
+            case = (tile_y, tile_z)
+            assert ctx.energy(ud) == pytest.approx(Eo, rel=1e-4), case
+            E, g = ctx.energy_and_grad(ud)
+            assert E == pytest.approx(Eo, rel=1e-4), case
+            g = g.double().cpu().numpy()
+            assert rel_max(g, go) < 1e-3, case
+            assert np.abs(g - go).max() <= gbar, case
+            if first is None:
+                first = g
+            else:
+                assert np.abs(g - first).max() <= 1e-4 * np.abs(go).max(), case
+            out = torch.empty_like(ud)
+            ctx.step(ud, out, tau)
+            torch.cuda.synchronize()
+            d = np.abs(out.double().cpu().numpy() - uo)
+            assert d.max() <= 2.0 ** -23 * np.abs(uo).max() + tau * gbar, case
+            ctx.close()
+
+
 def test_validation_128_fp32_energy_and_sampled_gradient():
     """The four 128^3 validation problems (tanh sphere R=32 / cylinder r=20,
     eps=2; p = k1^2+k2^2 and k1 k2), FP32 fused, in the configuration the
