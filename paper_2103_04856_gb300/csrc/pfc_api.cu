@@ -118,22 +118,30 @@ static pfc_status check_problem(const pfc_problem* p)
 // cost, the rows padded to whole tiles (summed over the problems' x-z planes)
 // times the measured cost of a row.  In the symmetric sweep a 13-row tile's
 // row costs 4.3 % more (four 128^3 problems: 87.5 us at 16 rows, 92.7 us at
-// 13, padded to 130 rows); in the general batched sweep (20 warps at 96
-// registers for 16 rows, 16 warps at 128 for 13) the 16-row tile's row costs
-// 3.5 % more (a 512^3 problem: 1.795 ms at 16 rows, 1.761 ms at 13, padded to
-// 520 rows).  Single problems (MAXI = 1) take default_tile_y.
+// 13, padded to 130 rows).  In the general sweep the 16-row instantiation (20
+// warps at 96 registers) keeps more values in local memory than the 13-row
+// one (16 warps at 128 registers), the more so when the problems' coefficients
+// differ (they are then loaded per use from the descriptor table): its row
+// costs 3.5 % more with one coefficient set (a 512^3 problem: 1.795 ms at 16
+// rows, 1.761 ms at 13, padded to 520 rows) and 10 % more with many (the
+// 64-instance mixed batch of 64^3, 96^3 and 128^3 problems: 1.03 against 0.97
+// ms per step, 4.1 % more rows at 13).  Single problems (MAXI = 1) take
+// default_tile_y.
 static int auto_tile_y(const pfc_problem* p, int n)
 {
     if (p[0].prec == PFC_FP64) return 8;
-    bool general = false;
+    bool general = false, one_set = true;
     double rows16 = 0.0, rows13 = 0.0;
     for (int k = 0; k < n; ++k) {
         const double plane = (double)p[k].nx * p[k].nz;
         rows16 += plane * ((p[k].ny + 15) / 16 * 16);
         rows13 += plane * ((p[k].ny + 12) / 13 * 13);
         general = general || !make_coef<float>(p[k].a, p[k].h, p[k].eps, p[k].xi, p[k].well).sym;
+        one_set = one_set && memcmp(p[k].a, p[0].a, sizeof(p[0].a)) == 0 && p[k].h == p[0].h &&
+                  p[k].eps == p[0].eps && p[k].xi == p[0].xi && p[k].well == p[0].well;
     }
-    return rows13 * (general ? 1.0 : 1.043) < rows16 * (general ? 1.035 : 1.0) ? 13 : 16;
+    const double c16 = general ? (one_set ? 1.035 : 1.10) : 1.0, c13 = general ? 1.0 : 1.043;
+    return rows13 * c13 < rows16 * c16 ? 13 : 16;
 }
 
 // Launch geometry of one problem: 32 x tile_y columns per CTA, z chunks chosen
