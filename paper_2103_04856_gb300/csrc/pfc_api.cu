@@ -148,7 +148,8 @@ static int auto_tile_y(const pfc_problem* p, int n)
 // so that the grid fills the GPU about twice unless the user fixed tile_z.
 static void geometry(const pfc_problem* p, int sms, int* tile_y, int* zc, int* tx, int* ty, int* cz)
 {
-    int tyv = p->tile_y ? p->tile_y : default_tile_y(p->ny, p->prec == PFC_FP64);
+    const bool general = !make_coef<float>(p->a, p->h, p->eps, p->xi, p->well).sym;
+    int tyv = p->tile_y ? p->tile_y : default_tile_y(p->ny, p->prec == PFC_FP64, general);
     *tile_y = tyv;
     *tx = (p->nx + 31) / 32;
     *ty = (p->ny + tyv - 1) / tyv;

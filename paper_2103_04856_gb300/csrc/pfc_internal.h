@@ -116,11 +116,17 @@ Coef<T> make_coef(const double a[6], double h, double eps, double xi, int well, 
                   const double* theta = nullptr, int proj = 0, int refine = 1);
 
 // Automatic tile height: FP64 8 rows; FP32 the one of 16 and 13 rows that
-// pads the grid's rows least (16 on a tie: its tiles hold more rows).
-inline int default_tile_y(int ny, bool fp64)
+// pads the grid's rows least (16 on a tie: its tiles hold more rows), except
+// for general polynomials (not symmetric in kappa1, kappa2), whose 16-row
+// instantiation keeps more values in local memory than the 13-row one: a row
+// of it costs 4 % more (a 256^3 problem, pfc_run: 0.2354 ms per step at 16
+// rows, 0.2295 ms at 13 with 260 rows), so they take 13 rows unless 16 pads
+// more than 4 % less.
+inline int default_tile_y(int ny, bool fp64, bool general = false)
 {
     if (fp64) return 8;
     const int pad16 = (ny + 15) / 16 * 16, pad13 = (ny + 12) / 13 * 13;
+    if (general) return pad13 < 1.04 * pad16 ? 13 : 16;
     return pad13 < pad16 ? 13 : 16;
 }
 
