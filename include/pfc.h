@@ -52,7 +52,7 @@ typedef enum {
     PFC_ECUDA = -3,         /* a CUDA call failed                                        */
     PFC_ENONFINITE = -4,    /* energy, mass or multiplier became NaN or infinite         */
     PFC_ETIMEOUT = -5,      /* a bounded device wait gave up                             */
-    PFC_EUNSUPPORTED = -6   /* valid request this build does not implement              */
+    PFC_EUNSUPPORTED = -6   /* valid request the library does not implement            */
 } pfc_status;
 
 enum { PFC_WELL_01 = 0,     /* W(u) = u^2 (1-u)^2, wells 0 and 1                         */
